@@ -1,0 +1,110 @@
+"""Seeded synthetic contact scenes.
+
+A scene bundles everything both sides of a parity check consume: the
+permuted system matrix A, its supernodal LDL^T factor (the input of
+``set_system``), the contact mapping (4 node ids and barycentric weights per
+contact, the input of ``set_mapping``), friction coefficients, the obstacle
+that turns proximity positions into direction blocks and gaps, and the
+solver schedule.  All arrays are in the factor's (nested-dissection) node
+order: DOF = 3 * node + axis.
+
+Named workloads:
+  beam_c0   tetrahedral beam on a 4x4x20 node grid (long axis along x), 0.01 m,
+            40 contacts on its bottom face (z = 0) against a plane, seed 0
+  liver_c1  ellipsoid of 0.15 x 0.1 x 0.08 m overall extent (semi-axes 0.075,
+            0.05, 0.04) with ~3,000 nodes, its lowest 20 % of nodes held by
+            1e4 N/m grounding springs, and 300 contacts against a 0.02 m sphere
+            tool pressed 6 mm into its top and sliding at 0.05 m/s, seed 1
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import contacts as ct
+from .factor import Factor, multifrontal_ldlt
+from .fem import assemble
+from .mesh import beam, boundary_faces, ellipsoid
+from .ordering import nested_dissection, node_graph, symbolic
+
+
+@dataclass
+class Scene:
+    name: str
+    X: np.ndarray            # (N, 3) node positions, permuted order
+    T: np.ndarray            # (nt, 4) tets over permuted node ids
+    A: sp.csr_matrix         # (n, n) SPD system matrix, permuted
+    factor: Factor
+    nodes: np.ndarray        # (m, 4) int64 permuted node ids
+    bary: np.ndarray         # (m, 4) barycentric weights
+    mu: np.ndarray           # (m,) friction coefficients
+    p0: np.ndarray           # (m, 3) proximity positions after the free motion
+    obstacle: object         # PlaneObstacle | SphereObstacle
+    n_newton: int
+    n_sweeps: int
+    h: float
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+    @property
+    def m(self) -> int:
+        return self.nodes.shape[0]
+
+    def linearize(self, p: np.ndarray, k: int):
+        """(C_k (m,3,3), delta_k (3m,)) at proximity positions p (m,3)."""
+        return self.obstacle.linearize(np.asarray(p, dtype=np.float64).reshape(-1, 3), k)
+
+
+def _permute(X, T, leaf_nodes):
+    G = node_graph(T, X.shape[0])
+    order, blocks = nested_dissection(X, G, leaf_nodes=leaf_nodes)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size)
+    return X[order], inv[T], blocks
+
+
+def _system(X, T, blocks, **fe):
+    A, _, _ = assemble(X, T, **fe)
+    sym = symbolic(A, blocks)
+    return A, multifrontal_ldlt(A, sym)
+
+
+def beam_scene(nodes_xyz=(20, 4, 4), spacing=0.01, m=40, seed=0, n_newton=3, n_sweeps=50,
+               mu=0.3, leaf_nodes=24, h=0.01, name=None) -> Scene:
+    rng = np.random.default_rng(seed)
+    X, T = beam(nodes_xyz, spacing)
+    X, T, blocks = _permute(X, T, leaf_nodes)
+    A, F = _system(X, T, blocks, h=h)
+    nodes, bary, p0, obst = ct.plane_contacts(rng, X, T, m, n_newton)
+    return Scene(name or f"beam{nodes_xyz}", X, T, A, F, nodes, bary, np.full(m, float(mu)), p0, obst,
+                 n_newton, n_sweeps, h)
+
+
+def ellipsoid_scene(semi=(0.075, 0.05, 0.04), target_nodes=3000, m=300, seed=1, n_newton=5,
+                    n_sweeps=50, mu=0.3, leaf_nodes=24, h=0.01, indent=6e-3, anchor_frac=0.2,
+                    anchor_k=1e4, name=None) -> Scene:
+    rng = np.random.default_rng(seed)
+    X, T, _ = ellipsoid(semi, target_nodes)
+    X, T, blocks = _permute(X, T, leaf_nodes)
+    z = X[:, 2]
+    anchored = np.nonzero(z <= z.min() + anchor_frac * (z.max() - z.min()))[0]
+    A, F = _system(X, T, blocks, h=h, anchor_nodes=anchored, anchor_k=anchor_k)
+    faces, ftet, _ = boundary_faces(T)
+    nodes, bary, p0, obst = ct.sphere_contacts(rng, X, T, faces, ftet, m, indent=indent, h=h)
+    return Scene(name or f"ellipsoid{target_nodes}", X, T, A, F, nodes, bary, np.full(m, float(mu)), p0,
+                 obst, n_newton, n_sweeps, h)
+
+
+def beam_c0() -> Scene:
+    return beam_scene(name="beam_c0")
+
+
+def liver_c1() -> Scene:
+    return ellipsoid_scene(name="liver_c1")
+
+
+NAMED = {"beam_c0": beam_c0, "liver_c1": liver_c1}

@@ -1,0 +1,321 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Every check here compares the oracle with something other than itself: a
+dense inverse, closed forms, brute-force enumeration, the exactness of the
+reformulation, invariants (symmetry, PSD, complementarity) and the paper's
+own printed table.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import delassus as dl
+from oracle import newton as nw
+from oracle import pgs as pg
+from oracle import reach as rc
+import scenegen
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    # 4x3x3-node beam, 8 contacts: small enough for dense inverses everywhere
+    return scenegen.beam_scene(nodes_xyz=(4, 3, 3), m=8, seed=3, n_newton=3, n_sweeps=40, leaf_nodes=6)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------- fixture pins
+def test_factor_reconstructs_A(beam_c0):
+    F = beam_c0.factor
+    L = F.to_sparse_L()
+    R = (L @ sp.diags(F.D) @ L.T - beam_c0.A)
+    assert abs(R).max() <= 1e-13 * abs(beam_c0.A).max()
+    assert np.all(F.D > 0)
+
+
+def test_factor_reconstructs_A_liver(liver_c1):
+    F = liver_c1.factor
+    L = F.to_sparse_L()
+    R = (L @ sp.diags(F.D) @ L.T - liver_c1.A)
+    assert abs(R).max() <= 1e-13 * abs(liver_c1.A).max()
+
+
+def test_supernodes_hold_whole_nodes(beam_c0, liver_c1):
+    for s in (beam_c0, liver_c1):
+        assert np.all(s.factor.sym.super_ptr % 3 == 0)
+        par = s.factor.sym.parent
+        assert np.all((par == -1) | (par > np.arange(par.size)))
+
+
+def test_material_matrix_special_values():
+    # C0 reading: A = (1 + h a_M) M + (h a_K + h^2) K = 1.001 M + 0.0011 K
+    from scenegen.fem import assemble
+    from scenegen.mesh import beam
+    X, T = beam((2, 2, 2), 0.01)
+    A, mdiag, K = assemble(X, T)
+    ref = 1.001 * sp.diags(mdiag) + 0.0011 * K
+    assert abs(A - ref).max() <= 1e-12 * abs(A).max()
+    # rigid translations are in the null space of K; total mass = rho * volume
+    t = np.tile([1.0, 0.0, 0.0], X.shape[0])
+    assert np.abs(K @ t).max() <= 1e-9 * abs(K).max()
+    assert np.isclose(mdiag[0::3].sum(), 1000.0 * 0.01 ** 3)
+
+
+# ---------------------------------------------------------------- H, C, J, W
+def test_mapping_matrix_reproduces_barycentric_points(beam_c0):
+    s = beam_c0
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    q = s.X.reshape(-1)                       # positions as the DOF vector 3*node + axis
+    assert np.allclose(H @ q, s.p0.reshape(-1), atol=1e-15)
+    assert H.shape == (3 * s.m, s.n)
+
+
+def test_W_matches_dense_inverse(tiny):
+    s = tiny
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    C, _ = s.linearize(s.p0, 0)
+    J = dl.jacobian(C, H)
+    W = dl.delassus_standard(dl.SystemSolver(s.A), J)
+    Ainv = np.linalg.inv(s.A.toarray())
+    Jd = np.zeros((3 * s.m, s.n))
+    for a in range(s.m):                      # J written out entry by entry
+        for r in range(3):
+            for i in range(4):
+                for d in range(3):
+                    Jd[3 * a + r, 3 * s.nodes[a, i] + d] += C[a, r, d] * s.bary[a, i]
+    assert _rel(W, Jd @ Ainv @ Jd.T) < 1e-12
+
+
+def test_reformulation_is_exact(beam_c0):
+    s = beam_c0
+    solver = dl.SystemSolver(s.A)
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    C, _ = s.linearize(s.p0, 1)
+    W_std = dl.delassus_standard(solver, dl.jacobian(C, H))
+    W_fast = dl.delassus_fast(C, dl.compliance_mapping(solver, H))
+    assert _rel(W_fast, W_std) < 1e-12
+    assert np.linalg.norm(W_std - W_std.T) <= 1e-13 * np.linalg.norm(W_std)
+    # PD: 3m <= n and the contact points are distinct
+    np.linalg.cholesky(W_std + 1e-14 * np.trace(W_std) * np.eye(W_std.shape[0]))
+
+
+def test_WH_identity_system_closed_form():
+    # A = I gives W_H = H H^T; one contact gives sum_i w_i^2 on the 3x3 diagonal
+    nodes = np.array([[0, 1, 2, 3], [2, 3, 4, 5]])
+    bary = np.array([[0.1, 0.2, 0.3, 0.4], [0.25, 0.25, 0.25, 0.25]])
+    n = 18
+    H = dl.mapping_matrix(nodes, bary, n)
+    WH = dl.compliance_mapping(dl.SystemSolver(sp.identity(n, format="csc")), H)
+    assert np.allclose(WH[:3, :3], 0.30 * np.eye(3), atol=1e-15)
+    assert np.allclose(WH[3:, 3:], 0.25 * np.eye(3), atol=1e-15)
+    # shared nodes 2 and 3: w_2 w'_0 + w_3 w'_1 = 0.3*0.25 + 0.4*0.25
+    assert np.allclose(WH[:3, 3:], 0.175 * np.eye(3), atol=1e-15)
+
+
+def test_WH_lumped_mass_closed_form():
+    # single tet, K = 0, diagonal lumped mass m_i per node: W_H = sum_i w_i^2 / m_i
+    w = np.array([0.4, 0.3, 0.2, 0.1])
+    mass = np.array([1.0, 2.0, 4.0, 8.0])
+    A = sp.diags(np.repeat(mass, 3)).tocsc()
+    H = dl.mapping_matrix(np.array([[0, 1, 2, 3]]), w[None, :], 12)
+    WH = dl.compliance_mapping(dl.SystemSolver(A), H)
+    assert np.allclose(WH, np.sum(w ** 2 / mass) * np.eye(3), rtol=1e-14)
+
+
+def test_direction_matrix_is_block_transpose_sensitive():
+    # C has rows n, t1, t2: J = C H maps q to (n.p, t1.p, t2.p)
+    from scenegen.contacts import tangent_frame
+    n = np.array([[0.0, 0.6, 0.8]])
+    C = tangent_frame(n)
+    H = dl.mapping_matrix(np.array([[0, 1, 2, 3]]), np.array([[1.0, 0, 0, 0]]), 12)
+    q = np.zeros(12)
+    q[:3] = [1.0, 2.0, 3.0]
+    assert np.allclose(dl.jacobian(C, H) @ q, C[0] @ q[:3])
+    assert np.isclose((dl.jacobian(C, H) @ q)[0], 0.6 * 2 + 0.8 * 3)
+
+
+def test_tangent_frame_reading():
+    from scenegen.contacts import tangent_frame
+    C = tangent_frame(np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.6, 0.0, 0.8]]))
+    # n = +z: smallest |n_a| ties between x and y -> x; t1 = z x x = +y, t2 = z x y = -x
+    assert np.allclose(C[0], [[0, 0, 1], [0, 1, 0], [-1, 0, 0]])
+    for blk in C:
+        assert np.allclose(blk @ blk.T, np.eye(3), atol=1e-15)
+        assert np.isclose(np.linalg.det(blk), 1.0)
+
+
+# ---------------------------------------------------------------- PGS
+def test_pgs_single_contact_closed_form():
+    W = np.diag([2.0, 3.0, 3.0])
+    mu = np.array([0.5])
+    # frictionless-looking: small tangential gap stays inside the cone
+    lam, _, _ = pg.pgs(W, np.array([-1.0, 0.1, -0.2]), mu, sweeps=3)
+    assert np.allclose(lam, [0.5, -0.1 / 3, 0.2 / 3])
+    # large slip: tangential force saturates on the cone, opposite to the slip
+    lam, _, _ = pg.pgs(W, np.array([-1.0, 3.0, 4.0]), mu, sweeps=3)
+    assert np.allclose(lam, [0.5, -0.15, -0.2])
+    # separated: positive normal gap gives no force at all
+    lam, _, _ = pg.pgs(W, np.array([0.3, 3.0, 4.0]), mu, sweeps=3)
+    assert np.allclose(lam, 0.0)
+
+
+def _lcp_bruteforce(Wn, dn):
+    m = dn.size
+    for k in range(m + 1):
+        for S in itertools.combinations(range(m), k):
+            S = list(S)
+            lam = np.zeros(m)
+            if S:
+                lam[S] = np.linalg.solve(Wn[np.ix_(S, S)], -dn[S])
+            w = dn + Wn @ lam
+            if np.all(lam >= -1e-12) and np.all(w >= -1e-12):
+                return lam
+    raise AssertionError("no LCP solution")
+
+
+def test_pgs_frictionless_matches_enumerated_lcp(tiny):
+    s = tiny
+    solver = dl.SystemSolver(s.A)
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_standard(solver, dl.jacobian(C, H))
+    mu = np.zeros(s.m)
+    lam, _, _ = pg.pgs(W, delta, mu, sweeps=4000)
+    ref = _lcp_bruteforce(W[0::3, 0::3], delta[0::3])
+    assert 0 < np.count_nonzero(ref) < s.m
+    assert np.allclose(lam[0::3], ref, rtol=1e-7, atol=1e-12 * np.abs(ref).max())
+    assert np.allclose(lam[1::3], 0) and np.allclose(lam[2::3], 0)
+
+
+def test_pgs_full_stick_is_linear_solve():
+    # gaps built as delta = -W lambda* with lambda* strictly inside every cone:
+    # with mu -> infinity every contact sticks and PGS must return lambda*
+    m = 12
+    rng = np.random.default_rng(11)
+    G = rng.normal(size=(3 * m, 3 * m))
+    W = G @ G.T / (3 * m) + np.eye(3 * m)
+    ref = np.zeros(3 * m)
+    ref[0::3] = rng.uniform(0.5, 1.5, m)
+    ref[1::3] = rng.uniform(-0.2, 0.2, m)
+    ref[2::3] = rng.uniform(-0.2, 0.2, m)
+    lam, _, _ = pg.pgs(W, -W @ ref, np.full(m, 1e6), sweeps=4000)
+    assert _rel(lam, ref) < 1e-10
+    assert np.array_equal(pg.classify(lam, np.full(m, 1e6)), np.full(m, pg.STICK))
+
+
+def test_pgs_friction_residuals_vanish(beam_c0):
+    s = beam_c0
+    solver = dl.SystemSolver(s.A)
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_standard(solver, dl.jacobian(C, H))
+    lam, _, eps = pg.pgs(W, delta, s.mu, sweeps=3000)
+    res = pg.residuals(W, delta, lam, s.mu)
+    scale = np.abs(delta).max()
+    assert res["normal"] < 1e-8 * scale and res["stick"] < 1e-8 * scale and res["slip"] < 1e-8 * scale
+    assert res["cone"] < 1e-12 * np.abs(lam).max()
+    cls = pg.classify(lam, s.mu)
+    assert {0, 1, 2} <= set(cls.tolist())     # the C0 mix has all three states
+
+
+def test_pgs_tol_stops_early(beam_c0):
+    s = beam_c0
+    solver = dl.SystemSolver(s.A)
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_standard(solver, dl.jacobian(C, H))
+    lam, done, eps = pg.pgs(W, delta, s.mu, sweeps=5000, tol=1e-6)
+    assert done < 5000 and eps <= 1e-6
+    lam2, _, _ = pg.pgs(W, delta, s.mu, sweeps=done)
+    assert np.array_equal(lam, lam2)
+
+
+# ---------------------------------------------------------------- Newton loops
+def test_standard_and_fast_schemes_agree(beam_c0):
+    s = beam_c0
+    kw = dict(A=s.A, nodes=s.nodes, bary=s.bary, mu=s.mu, p0=s.p0, linearize=s.linearize,
+              n_newton=s.n_newton, sweeps=s.n_sweeps)
+    std = nw.standard_scheme(**kw)
+    fast = nw.fast_scheme(**kw)
+    for a, b in zip(std["iters"], fast["iters"]):
+        assert _rel(b["W"], a["W"]) < 1e-11
+        assert _rel(b["lam"], a["lam"]) < 1e-10
+        assert _rel(b["p"], a["p"]) < 1e-12
+    assert _rel(fast["dq"], std["dq"]) < 1e-10
+
+
+def test_corrective_motion_residual(beam_c0):
+    s = beam_c0
+    fast = nw.fast_scheme(s.A, s.nodes, s.bary, s.mu, s.p0, s.linearize, s.n_newton, s.n_sweeps)
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    rhs = H.T @ fast["u"]
+    assert np.linalg.norm(s.A @ fast["dq"] - rhs) <= 1e-12 * np.linalg.norm(rhs)
+    assert np.linalg.norm(fast["u"]) > 0
+
+
+def test_newton_fixed_directions_accumulate(tiny):
+    # with C_k fixed and every contact resolved in iteration 1, iteration 2 has
+    # nothing left to correct: the total dq equals the one-iteration dq
+    s = tiny
+    C0, d0 = s.linearize(s.p0, 0)
+    anchors = s.p0 + 1e-4 * C0[:, 0, :]       # every normal gap -0.1 mm, no slip
+
+    def lin(p, k):
+        return C0, np.einsum("mij,mj->mi", C0, p - anchors).reshape(-1)
+
+    one = nw.fast_scheme(s.A, s.nodes, s.bary, np.zeros(s.m), s.p0, lin, 1, 6000)
+    two = nw.fast_scheme(s.A, s.nodes, s.bary, np.zeros(s.m), s.p0, lin, 2, 6000)
+    assert np.abs(two["iters"][1]["lam"]).max() <= 1e-9 * np.abs(one["iters"][0]["lam"]).max()
+    assert _rel(two["dq"], one["dq"]) < 1e-8
+
+
+# ---------------------------------------------------------------- reach
+def test_reach_matches_bruteforce_structure():
+    s = scenegen.beam_scene(nodes_xyz=(6, 3, 3), m=10, seed=5, leaf_nodes=4)
+    F = s.factor
+    sym = F.sym
+    L = F.to_sparse_L().toarray()
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n).toarray()
+    X = np.linalg.solve(L, H.T)
+    reach = rc.contact_reach(sym.parent, sym.super_ptr, s.nodes)
+    sod = rc.supernode_of_dof(sym.super_ptr)
+    for a in range(s.m):
+        for d in range(3):
+            rows = np.nonzero(np.abs(X[:, 3 * a + d]) > 0)[0]
+            hit = set(sod[rows].tolist())
+            pred = {sn for sn in range(sym.nsuper) if a in reach[sn]}
+            assert hit <= pred
+            # the supernodes owning the contact's nodes and the root are reached
+            own = {int(sod[3 * nd]) for nd in s.nodes[a] if s.bary[a, list(s.nodes[a]).index(nd)] > 0}
+            assert own <= hit
+    roots = np.nonzero(sym.parent < 0)[0]
+    for r in roots:
+        assert len(reach[r]) == s.m
+
+
+# ---------------------------------------------------------------- paper table
+def test_paper_table_arithmetic():
+    t = json.load(open(os.path.join(GOLD, "table_fast_vs_standard.json")))
+    k = t["newton_iterations"]
+    rn, rt = [], []
+    for row in t["rows"]:
+        st, fa = row["standard"], row["fast"]
+        assert abs(st["rebuild_W"] + st["pgs"] + st["corr"] - st["newton"]) < 0.015
+        assert abs(fa["rebuild_W"] + fa["pgs"] + fa["corr"] - fa["newton"]) < 0.015
+        assert abs(fa["build_WH"] + k * fa["newton"] - fa["total"]) < 0.05
+        assert abs(k * st["newton"] - st["total"]) < 0.05
+        # "Update" is the share of rebuilding W plus the correction in one Newton iteration
+        for v in (st, fa):
+            assert abs(100 * (v["rebuild_W"] + v["corr"]) / v["newton"] - v["update_pct"]) < 0.1
+        rn.append(st["newton"] / fa["newton"])
+        rt.append(st["total"] / fa["total"])
+    assert abs(np.mean(rn) - t["speedup_newton"]) < 0.01
+    assert abs(np.mean(rt) - t["speedup_total"]) < 0.02
