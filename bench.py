@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Constraint steps/s of the fast implicit constraint-resolution scheme.
+
+One step = one time step of Alg. 3 on the liver workload (ellipsoid of
+0.15 x 0.1 x 0.08 m with 3,000 nodes / 9,000 DOF, 300 contacts against a
+sphere tool, 5 Newton iterations x 50 PGS sweeps, FP32):
+build W_H (reach, supernodal forward solve, FP64 pivot scaling,
+contraction), then 5 x (device linearisation of the directions, W = C W_H C^T,
+PGS, proximity update), then the corrective motion dq = A^-1 H^T u.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl icr|reference]
+
+--impl icr (default) times libicr on the GPU; under torchrun every rank runs
+its own replica of the workload on its own GPU (no collective on the data
+path) and rank 0 prints one JSON line.  --impl reference times the FP64 CPU
+oracle on the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "constraint steps/sec (W_H build+W update+PGS) at stated err vs FP64; p50/p99 lat"
+UNIT = "steps/s"
+WORKLOAD = "liver_c1"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def workload_config(scene) -> dict:
+    return {
+        "workload": f"{WORKLOAD}: ellipsoid 0.15x0.1x0.08 m, {scene.X.shape[0]} nodes / {scene.n} DOF, "
+                    f"{scene.m} contacts vs 0.02 m sphere tool, {scene.n_newton} Newton x {scene.n_sweeps} PGS "
+                    f"sweeps, seed 1",
+        "n_dof": scene.n,
+        "contacts": scene.m,
+        "newton_iterations": scene.n_newton,
+        "pgs_sweeps": scene.n_sweeps,
+        "supernodes": int(scene.factor.sym.nsuper),
+        "l2": "flushed (512 MiB write) before every timed step",
+    }
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["icr", "reference"], default="icr")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- clocks
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+def oracle_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_step(scene, solver, newton_iters=None):
+    """One FP64 oracle time step (fast scheme, Alg. 3); ``newton_iters`` limits
+    the Newton iterations for a bounded sample."""
+    from oracle import newton as nw
+    k = scene.n_newton if newton_iters is None else newton_iters
+    return nw.fast_scheme(scene.A, scene.nodes, scene.bary, scene.mu, scene.p0, scene.linearize, k,
+                          scene.n_sweeps, solver=solver)
+
+
+def time_oracle(scene, steps: int, warmup: int, budget_s: float):
+    """Time the oracle; when the full steps would not fit ``budget_s`` each
+    timed step runs the W_H build plus one Newton iteration and the step time
+    is extrapolated to all iterations (the iterations do identical work: a
+    fixed sweep count).  Returns (per-step seconds list, sample description)."""
+    from oracle import delassus as dl
+    from oracle import newton as nw
+    solver = dl.SystemSolver(scene.A)
+    t0 = time.perf_counter()
+    oracle_step(scene, solver)
+    t_full = time.perf_counter() - t0
+    full = (steps + max(0, warmup - 1)) * t_full <= budget_s
+    for _ in range(max(0, warmup - 1)):
+        if full:
+            oracle_step(scene, solver)
+    times = []
+    for _ in range(steps):
+        if full:
+            t0 = time.perf_counter()
+            oracle_step(scene, solver)
+            times.append(time.perf_counter() - t0)
+        else:
+            t0 = time.perf_counter()
+            H = nw.dl.mapping_matrix(scene.nodes, scene.bary, scene.n)
+            WH = nw.dl.compliance_mapping(solver, H)
+            t_wh = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            oracle_step_iter(scene, WH)
+            t_it = time.perf_counter() - t0
+            times.append(t_wh + scene.n_newton * t_it)
+    if full:
+        sample = "full time steps of the FP64 oracle (fast scheme: W_H = H A^-1 H^T by sparse LU, " \
+                 "W = C W_H C^T, PGS, proximity update, dq) on the same scene"
+    else:
+        sample = "per step: the oracle's W_H build plus one Newton iteration (W update, 50 PGS sweeps, " \
+                 "proximity update), step time = W_H + n_newton x iteration (identical iterations)"
+    return times, sample
+
+
+def oracle_step_iter(scene, WH):
+    from oracle import delassus as dl
+    from oracle import pgs as pg
+    C, delta = scene.linearize(scene.p0, 0)
+    W = dl.delassus_fast(C, WH)
+    lam, _, _ = pg.pgs(W, delta, scene.mu, None, scene.n_sweeps)
+    uk = (C.transpose(0, 2, 1) @ lam.reshape(-1, 3, 1)).reshape(-1)
+    return WH @ uk
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import scenegen
+    scene = scenegen.NAMED[WORKLOAD]()
+    times, sample = time_oracle(scene, args.steps, args.warmup, budget_s=150.0)
+    total = sum(times)
+    value = len(times) / total
+    ms = [1e3 * t for t in times]
+    cores = oracle_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(scene),
+        "latency_ms": {"p50": float(statistics.median(ms)), "p99": float(sorted(ms)[int(0.99 * (len(ms) - 1))])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_icr(args):
+    import numpy as np
+    import torch
+
+    import scenegen
+    from paper_2306_06946_gb300 import build, driver, icr
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    scene = scenegen.NAMED[WORKLOAD]()
+    stream = torch.cuda.current_stream(local)
+    ctx = icr.Context(local, stream.cuda_stream)
+    sc = icr.Scene(ctx, precision=icr.FP32, n_sweeps=scene.n_sweeps)
+    driver.load_system(sc, scene.factor)
+    driver.load_contacts(sc, scene.nodes, scene.bary, scene.p0)
+    driver.load_obstacle(sc, scene.obstacle)
+    sc.set_field("MU", scene.mu)
+
+    def step():
+        sc.reset_proximity()
+        sc.build_WH()
+        for k in range(scene.n_newton):
+            sc.linearize(k)
+            sc.update_W()
+            sc.solve_friction(warm_start=(k == 0))
+            sc.update_proximity()
+        sc.correct_motion(want_dq=False, reset=True)
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = sc.launches()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = sc.launches() - l0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- per-phase device times (the paper's table columns), same stream
+    phases = {"build_WH": [], "linearize": [], "update_W": [], "pgs": [], "update_proximity": [], "correct": []}
+    for _ in range(3):
+        flush.fill_(1)
+        sc.reset_proximity()
+        for name, fn in [("build_WH", sc.build_WH)]:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream); fn(); b.record(stream)
+            phases[name].append((a, b))
+        for k in range(scene.n_newton):
+            for name, fn in [("linearize", lambda: sc.linearize(k)), ("update_W", sc.update_W),
+                             ("pgs", lambda: sc.solve_friction(warm_start=(k == 0))),
+                             ("update_proximity", sc.update_proximity)]:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream); fn(); b.record(stream)
+                phases[name].append((a, b))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream); sc.correct_motion(want_dq=False, reset=True); b.record(stream)
+        phases["correct"].append((a, b))
+    torch.cuda.synchronize()
+    phase_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in phases.items()}
+
+    # ---- roofline of the dominant kernel (PGS: one k_pgs launch per Newton iteration)
+    peaks = measured_peaks()
+    m3 = 3 * scene.m
+    pgs_bytes = scene.n_sweeps * m3 * m3 * 4 + m3 * 4 * 3     # W streamed once per sweep + delta, mu, lambda
+    pgs_s = phase_ms["pgs"] / 1e3
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    achieved = pgs_bytes / pgs_s / 1e9
+    roofline = {"kernel": "k_pgs", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
+
+    # ---- end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory().numpy()
+        h_nodes = pin(scene.nodes, np.int32)
+        h_bary = pin(scene.bary, np.float64)
+        h_p0 = pin(scene.p0.reshape(-1), np.float64)
+        h_anch = pin(scene.obstacle.anchors, np.float64)
+        h_mu = pin(scene.mu, np.float64)
+        h_dq = pin(np.zeros(scene.n), np.float64)
+        center = np.asarray(scene.obstacle.center, dtype=np.float64)
+        h2d = h_nodes.nbytes + h_bary.nbytes + h_p0.nbytes + h_anch.nbytes + h_mu.nbytes + center.nbytes
+        d2h = h_dq.nbytes
+
+        def e2e_step():
+            sc.set_mapping(h_nodes, h_bary)
+            sc.set_proximity(h_p0)
+            sc.set_obstacle_sphere(center, scene.obstacle.radius, h_anch)
+            sc.set_field("MU", h_mu)
+            sc.build_WH()
+            for k in range(scene.n_newton):
+                sc.linearize(k)
+                sc.update_W()
+                sc.solve_friction(warm_start=(k == 0))
+                sc.update_proximity()
+            sc.correct_motion(want_dq=True, reset=True, out=h_dq)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        times = []
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        e2e = {"value": world * len(times) / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # ---- parity of the timed configuration (FP32) against the FP64 oracle
+    parity = None
+    cpu = None
+    if rank == 0:
+        from oracle import delassus as dl
+        solver = dl.SystemSolver(scene.A)
+        ref = oracle_step(scene, solver)
+        lam_ref = ref["iters"][-1]["lam"]
+        lam_scale = max(np.linalg.norm(it["lam"]) for it in ref["iters"])
+        sc.reset_proximity()
+        dq, _ = driver.newton_step(sc, scene.n_newton)
+        WH_gpu = sc.get("WH")
+        parity = {"W_H_rel_fro": float(np.linalg.norm(WH_gpu - ref["WH"]) / np.linalg.norm(ref["WH"])),
+                  "dq_rel": float(np.linalg.norm(dq - ref["dq"]) / np.linalg.norm(ref["dq"])),
+                  "lambda_abs_over_scale": float(np.linalg.norm(sc.get("LAMBDA") - lam_ref) / lam_scale)}
+        if world == 1 and not args.no_cpu_baseline:
+            t0 = time.perf_counter()
+            oracle_step(scene, solver)
+            t = time.perf_counter() - t0
+            cpu = {"value": 1.0 / t, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                   "sample": "one full time step of the FP64 oracle (fast scheme, sparse-LU W_H, Python PGS) "
+                             "on the same liver_c1 scene"}
+
+    if rank == 0:
+        ms_sorted = sorted(ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {**workload_config(scene), "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": float(statistics.median(ms)),
+                           "p99": float(ms_sorted[int(round(0.99 * (len(ms) - 1)))])},
+            "phase_ms": phase_ms,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "parity_vs_fp64_oracle": parity,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_icr(args)
+
+
+if __name__ == "__main__":
+    main()

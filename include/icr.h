@@ -1,0 +1,213 @@
+/*
+ * icr.h - C ABI of libicr, the GB300 (sm_103a) implementation of the fast
+ * constraint-matrix update for implicit contact resolution
+ * ("An efficient implicit constraint resolution scheme for interactive FE
+ * simulations", arXiv 2306.06946).
+ *
+ * Problem statement (Sec. 3 and Sec. 5 of the paper).  A deformable body with
+ * n DOFs has the SPD system matrix A = M + h B + h^2 K (Sec. 3.1, Eq.
+ * "dynamic equation soft").  m contacts each carry a proximity point
+ * p_a = G(q) given by barycentric weights on 4 nodes, so H = dG/dq is 3m x n
+ * (Eq. "geometrical mapping"), and a 3x3 direction block C_a whose rows are
+ * the normal n and the tangents t1, t2 (Eq. "jacobian directions").  With
+ * J = C H (Eq. "isolate directions") the Delassus operator is
+ * W = J A^-1 J^T = C W_H C^T, W_H = H A^-1 H^T (Eq. "schur complemnt
+ * reformulated").  W_H is built once per time step; every Newton iteration of
+ * Alg. 3 re-forms W from new directions, solves the frictional contact problem
+ * by projected Gauss-Seidel (Eq. "PGS") and moves the proximity points by
+ * W_H C^T lambda (Eq. "recursive motion correction 7").  The corrective motion
+ * dq = A^-1 H^T sum_k C_k^T lambda_k (Eq. "recursive motion correction 3") is
+ * applied once at the end of the step.
+ *
+ * Units: the library works with lambda~ = h^2 lambda, so delta = delta_free +
+ * W lambda~, dq = A^-1 J^T lambda~ is a position increment and the physical
+ * contact force is lambda~ / h^2.
+ *
+ * Ordering: the system is given through its supernodal factor A = L D L^T in
+ * the factor's DOF order, DOF = 3 * node + axis; supernodes hold whole nodes
+ * (their column ranges start and end on multiples of 3).  Node ids passed to
+ * icr_set_mapping are in that same order.
+ *
+ * Ownership: every set/update call copies what it is given; the caller keeps
+ * its buffers.  The scene owns all device state; nothing returned aliases it.
+ *
+ * Streams: all work of a scene is enqueued on the context's stream.  Calls
+ * that write to host memory (icr_get, non-NULL *_out host pointers, stats)
+ * synchronise that stream before returning; the others return once the work
+ * is enqueued.
+ *
+ * Errors: every call returns ICR_OK or one of the codes below and leaves a
+ * message for icr_last_error() (thread-local).
+ */
+#ifndef ICR_H_
+#define ICR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum icr_status {
+  ICR_OK = 0,
+  ICR_EINVAL = 1,    /* bad argument: shape, range, NaN, non-orthonormal C, bad weights */
+  ICR_ENOTSPD = 2,   /* a pivot D_i is <= 0 or not finite */
+  ICR_ESTATE = 3,    /* calls out of order (e.g. icr_update_W before icr_build_WH) */
+  ICR_ENOMEM = 4,    /* device allocation failed or the context's HBM budget is exceeded */
+  ICR_ENOCONV = 5,   /* non-fatal: PGS used all sweeps with eps above a positive tol */
+  ICR_ETIMEOUT = 6,  /* a bounded device-side wait gave up */
+  ICR_ECUDA = 7      /* a CUDA runtime call failed */
+};
+
+enum icr_precision {
+  ICR_FP32 = 0,      /* L, X, W_H, W and the PGS sweeps in FP32; D^-1/2 applied in FP64 */
+  ICR_FP64 = 1       /* everything in FP64 */
+};
+
+typedef struct icr_ctx icr_ctx;       /* one device + one CUDA stream + an HBM budget */
+typedef struct icr_scene icr_scene;   /* one deformable body with its contacts */
+
+typedef struct icr_params {
+  int32_t precision;   /* enum icr_precision */
+  int32_t n_sweeps;    /* PGS sweep cap (>= 0) */
+  double tol;          /* PGS stop when eps <= tol; tol <= 0 runs every sweep */
+} icr_params;
+
+typedef struct icr_pgs_stats {
+  int32_t sweeps;       /* sweeps run */
+  int32_t n_separated;  /* contacts with lambda_n = 0 */
+  int32_t n_stick;      /* contacts strictly inside the friction cone */
+  int32_t n_slip;       /* contacts on the cone */
+  double eps;           /* ||lambda^i - lambda^(i-1)|| / ||lambda^i|| of the last sweep (Alg. 1) */
+  double res_normal;    /* FP64 max |min(delta_n, lambda_n)| at the end */
+  double res_cone;      /* FP64 max(0, ||lambda_t|| - mu lambda_n) */
+  double res_stick;     /* FP64 max ||delta_t|| over sticking contacts */
+  double res_slip;      /* FP64 max misalignment of delta_t against -lambda_t over slipping contacts */
+} icr_pgs_stats;
+
+enum icr_field {
+  ICR_FIELD_WH = 0,        /* (3m x 3m) double, row-major, symmetric */
+  ICR_FIELD_W = 1,         /* (3m x 3m) double */
+  ICR_FIELD_LAMBDA = 2,    /* (3m) double, lambda~ of the last solve */
+  ICR_FIELD_P = 3,         /* (m x 3) double, proximity positions */
+  ICR_FIELD_DELTA = 4,     /* (3m) double, gaps the next solve starts from */
+  ICR_FIELD_C = 5,         /* (m x 3 x 3) double, direction blocks, rows n, t1, t2 */
+  ICR_FIELD_MU = 6,        /* (m) double, friction coefficients */
+  ICR_FIELD_U = 7,         /* (3m) double, accumulated sum_k C_k^T lambda~_k */
+  ICR_FIELD_REACH_PTR = 8, /* (nsuper + 1) int32, CSR offsets of the reached contacts */
+  ICR_FIELD_REACH_IDX = 9  /* (reach_ptr[nsuper]) int32, ascending contact ids per supernode */
+};
+
+/* Thread-local text of the last error (never NULL). */
+const char* icr_last_error(void);
+
+/* Context on CUDA device `device`.  `cuda_stream` is a cudaStream_t owned by
+ * the caller (NULL = the legacy default stream).  `hbm_budget_bytes` caps the
+ * device memory all scenes of the context may hold (0 = no cap); an
+ * allocation past it fails with ICR_ENOMEM. */
+int icr_ctx_create(icr_ctx** out, int device, void* cuda_stream, uint64_t hbm_budget_bytes);
+int icr_ctx_destroy(icr_ctx* ctx);
+/* Device bytes currently held by the context's scenes. */
+int icr_ctx_bytes_in_use(const icr_ctx* ctx, uint64_t* out);
+
+int icr_scene_create(icr_ctx* ctx, icr_scene** out, const icr_params* params);
+int icr_scene_destroy(icr_scene* scene);
+int icr_set_params(icr_scene* scene, const icr_params* params);
+
+/* The system, through its supernodal factor A = L D L^T (Sec. 3.1, Eq.
+ * "dynamic equation soft"; the factor plays the role of the preconditioner
+ * the paper's results use, Sec. 6).  Host arrays:
+ *   super_ptr    (nsuper+1) int32: supernode s owns DOF columns [super_ptr[s], super_ptr[s+1]),
+ *                 increasing, multiples of 3, super_ptr[nsuper] = n;
+ *   rowpat_ptr   (nsuper+1) int64 offsets into rowpat;
+ *   rowpat       int32 below-diagonal rows R_s of each supernode, ascending, each >= super_ptr[s+1], < n;
+ *   val_ptr      (nsuper+1) int64 offsets into Lpanels; panel s has (w+r) * w entries;
+ *   Lpanels      double, panel s column-major (w + r) x w: rows 0..w-1 the unit lower diagonal
+ *                 block (diagonal and upper part ignored), rows w..w+r-1 L[R_s, cols(s)];
+ *   D            (n) double pivots, each finite and > 0 (else ICR_ENOTSPD);
+ *   etree_parent (nsuper) int32 parent supernode (> s) or -1: the supernode owning min(R_s);
+ *                 R_s minus the columns of the parent must lie in the parent's R.
+ * Replaces any previous system and invalidates the mapping and W_H. */
+int icr_set_system(icr_scene* scene, int32_t n, int32_t nsuper, const int32_t* super_ptr,
+                   const int64_t* rowpat_ptr, const int32_t* rowpat, const int64_t* val_ptr,
+                   const double* Lpanels, const double* D, const int32_t* etree_parent);
+
+/* The geometric mapping H = dG/dq for barycentric proximity points
+ * (Eq. "geometrical mapping"; Eq. "isolate directions" keeps it apart from
+ * the directions).  nodes (m x 4) int32 node ids in factor order, bary
+ * (m x 4) double weights, each >= 0 and summing to 1 within 1e-12.
+ * m = 0 is allowed.  Resets lambda~, u and the proximity positions to 0. */
+int icr_set_mapping(icr_scene* scene, int32_t m, const int32_t* nodes, const double* bary);
+
+/* Proximity positions p (m x 3 double) after the free motion: the start of the
+ * recursion p_0 (Alg. 3 step 4 updates it).  The scene keeps a device copy of
+ * p_0 for icr_reset_proximity. */
+int icr_set_proximity(icr_scene* scene, const double* p);
+/* Start a time step again from the stored p_0: p <- p_0 and u <- 0, on the
+ * device (no host transfer). */
+int icr_reset_proximity(icr_scene* scene);
+
+/* Directions and gaps for the next Newton iteration (Alg. 3 step 1).
+ * C (m x 3 x 3 double, row-major blocks with rows n, t1, t2, each orthonormal
+ * within 1e-6), delta (3m double) the gaps at the current proximity positions,
+ * mu (m double, >= 0) or NULL to keep the previous coefficients. */
+int icr_update_directions(icr_scene* scene, const double* C, const double* delta, const double* mu);
+
+/* Device-side linearisation (Alg. 3 step 1 for two obstacle kinds): computes C
+ * and delta from the current proximity positions without a host round trip.
+ * Tangent frame: e_a = the axis with the smallest |n_a| (lowest index on ties),
+ * t1 = normalize(n x e_a), t2 = n x t1.
+ *   plane:  normals (n_iters x m x 3 double) unit normals for iteration k,
+ *           anchors (m x 3): delta = C (p - anchor);
+ *   sphere: centre (3), radius, anchors (m x 3): n = (p - c)/|p - c|,
+ *           delta = (|p - c| - radius, t1.(p - anchor), t2.(p - anchor)). */
+int icr_set_obstacle_plane(icr_scene* scene, int32_t n_iters, const double* normals, const double* anchors);
+int icr_set_obstacle_sphere(icr_scene* scene, const double* center, double radius, const double* anchors);
+int icr_linearize(icr_scene* scene, int32_t k);
+
+/* W_H = H A^-1 H^T = X^T D^-1 X with X = L^-1 H^T (Eq. "schur complemnt
+ * reformulated"): the symbolic reach of H^T in the elimination tree, the
+ * multi-RHS supernodal forward solve, the FP64 pivot scaling and the
+ * contraction.  Needs icr_set_system and icr_set_mapping. */
+int icr_build_WH(icr_scene* scene);
+
+/* W = C W_H C^T (Alg. 3 step 2).  Needs icr_build_WH and directions. */
+int icr_update_W(icr_scene* scene);
+
+/* Projected Gauss-Seidel on delta = delta_free + W lambda~ (Eq. "PGS", Alg. 3
+ * step 3): contacts in ascending order; local rule: lambda_n <- max(0,
+ * lambda_n - r_n / W_nn); the tangential residual is updated with the change
+ * of lambda_n; lambda_t <- lambda_t - r_t / w_t with w_t = (W_t1t1 + W_t2t2)/2;
+ * lambda_t is projected on the disc ||lambda_t|| <= mu lambda_n.
+ * warm_start = 0 starts from lambda~ = 0, 1 from the last solve's lambda~.
+ * stats (may be NULL) receives the sweep count, eps and FP64 residuals (this
+ * synchronises).  Returns ICR_ENOCONV (non-fatal) when tol > 0 and eps > tol
+ * after n_sweeps; the stats then say why. */
+int icr_solve_friction(icr_scene* scene, int warm_start, icr_pgs_stats* stats);
+
+/* p += W_H C^T lambda~ (Alg. 3 step 4, Eq. "recursive motion correction 7")
+ * and u += C^T lambda~.  dp_out (3m double, host) receives the increment when
+ * not NULL. */
+int icr_update_proximity(icr_scene* scene, double* dp_out);
+
+/* dq = A^-1 H^T u = L^-T D^-1 X u (Eq. "recursive motion correction 3"),
+ * u = sum_k C_k^T lambda~_k.  dq_out (n double, host) may be NULL.  reset = 1
+ * clears u afterwards (start of the next time step). */
+int icr_correct_motion(icr_scene* scene, double* dq_out, int reset);
+
+/* Copy a field to host memory as double (float fields) or int32 (index fields).
+ * `bytes` must equal the field's size; ICR_EINVAL otherwise. */
+int icr_get(icr_scene* scene, int32_t field, void* dst, size_t bytes);
+/* Size in bytes of a field as icr_get returns it. */
+int icr_field_bytes(icr_scene* scene, int32_t field, size_t* out);
+/* Number of kernels the scene has launched since it was created. */
+int icr_scene_launches(icr_scene* scene, uint64_t* out);
+/* Load a float field (W, LAMBDA, DELTA, C, MU, P) from host doubles, to drive
+ * a single step of the path on given operands. */
+int icr_set_field(icr_scene* scene, int32_t field, const double* src, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICR_H_ */

@@ -1,0 +1,862 @@
+// libicr host side: the C ABI declared in include/icr.h.
+//
+// This file validates inputs, derives the symbolic schedule of the
+// supernodal factor once per system (children, etree levels, the row maps of
+// every supernode into its parent's front) and manages the scene's device
+// buffers.  All per-step arithmetic runs in the kernels of icr_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "icr_internal.h"
+
+struct icr_ctx : icr::Ctx {};
+struct icr_scene : icr::Scene {};
+
+namespace icr {
+
+static thread_local std::string g_err = "no error";
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  set_error("%s: CUDA error %d (%s)", where, (int)e, cudaGetErrorString(e));
+  return ICR_ECUDA;
+}
+
+int dalloc(Scene* s, DBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.p && b.bytes >= bytes) return ICR_OK;
+  dfree(s, b);
+  Ctx* c = s->ctx;
+  if (c->budget && c->in_use + bytes > c->budget) {
+    set_error("allocation of %zu bytes exceeds the context HBM budget (%llu of %llu in use)", bytes,
+              (unsigned long long)c->in_use, (unsigned long long)c->budget);
+    return ICR_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    return ICR_ENOMEM;
+  }
+  b.bytes = bytes;
+  c->in_use += bytes;
+  return ICR_OK;
+}
+
+void dfree(Scene* s, DBuf& b) {
+  if (b.p) {
+    cudaFree(b.p);
+    s->ctx->in_use -= b.bytes;
+  }
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+}  // namespace icr
+
+using namespace icr;
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+#define RET(call)                   \
+  do {                              \
+    int r_ = (call);                \
+    if (r_ != ICR_OK) return r_;    \
+  } while (0)
+
+static int check_scene(icr_scene* s) {
+  if (!s) {
+    set_error("scene is NULL");
+    return ICR_EINVAL;
+  }
+  return ICR_OK;
+}
+
+static int set_device(Scene* s) {
+  CK(cudaSetDevice(s->ctx->device));
+  return ICR_OK;
+}
+
+// Copy `count` host doubles into a device buffer of the scene's precision.
+static int upload_T(Scene* s, DBuf& dst, const double* src, size_t count) {
+  if (count == 0) return ICR_OK;
+  if (s->prec == ICR_FP64) {
+    CK(cudaMemcpyAsync(dst.p, src, count * sizeof(double), cudaMemcpyHostToDevice, s->ctx->stream));
+  } else {
+    std::vector<float> tmp(count);
+    for (size_t i = 0; i < count; ++i) tmp[i] = (float)src[i];
+    // pageable source: the call returns once tmp has been staged, so tmp may go
+    CK(cudaMemcpyAsync(dst.p, tmp.data(), count * sizeof(float), cudaMemcpyHostToDevice, s->ctx->stream));
+  }
+  return ICR_OK;
+}
+
+template <class V>
+static int upload(Scene* s, DBuf& dst, const V* src, size_t count) {
+  if (count == 0) return ICR_OK;
+  CK(cudaMemcpyAsync(dst.p, src, count * sizeof(V), cudaMemcpyHostToDevice, s->ctx->stream));
+  return ICR_OK;
+}
+
+// Device buffer of the scene's precision -> host doubles (synchronises).
+static int download_T(Scene* s, const DBuf& src, double* dst, size_t count) {
+  if (count == 0) return ICR_OK;
+  if (s->prec == ICR_FP64) {
+    CK(cudaMemcpyAsync(dst, src.p, count * sizeof(double), cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(cudaStreamSynchronize(s->ctx->stream));
+  } else {
+    std::vector<float> tmp(count);
+    CK(cudaMemcpyAsync(tmp.data(), src.p, count * sizeof(float), cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(cudaStreamSynchronize(s->ctx->stream));
+    for (size_t i = 0; i < count; ++i) dst[i] = tmp[i];
+  }
+  return ICR_OK;
+}
+
+extern "C" {
+
+const char* icr_last_error(void) { return g_err.c_str(); }
+
+int icr_ctx_create(icr_ctx** out, int device, void* cuda_stream, uint64_t hbm_budget_bytes) {
+  if (!out) {
+    set_error("out is NULL");
+    return ICR_EINVAL;
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) {
+    set_error("device %d out of range (%d devices)", device, ndev);
+    return ICR_EINVAL;
+  }
+  CK(cudaSetDevice(device));
+  icr_ctx* c = new (std::nothrow) icr_ctx();
+  if (!c) {
+    set_error("out of host memory");
+    return ICR_ENOMEM;
+  }
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->budget = hbm_budget_bytes;
+  *out = c;
+  return ICR_OK;
+}
+
+int icr_ctx_destroy(icr_ctx* ctx) {
+  delete ctx;
+  return ICR_OK;
+}
+
+int icr_ctx_bytes_in_use(const icr_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) {
+    set_error("NULL argument");
+    return ICR_EINVAL;
+  }
+  *out = ctx->in_use;
+  return ICR_OK;
+}
+
+static int check_params(const icr_params* p) {
+  if (!p) {
+    set_error("params is NULL");
+    return ICR_EINVAL;
+  }
+  if (p->precision != ICR_FP32 && p->precision != ICR_FP64) {
+    set_error("unknown precision %d", p->precision);
+    return ICR_EINVAL;
+  }
+  if (p->n_sweeps < 0 || !std::isfinite(p->tol)) {
+    set_error("n_sweeps must be >= 0 and tol finite");
+    return ICR_EINVAL;
+  }
+  return ICR_OK;
+}
+
+int icr_scene_create(icr_ctx* ctx, icr_scene** out, const icr_params* params) {
+  if (!ctx || !out) {
+    set_error("NULL argument");
+    return ICR_EINVAL;
+  }
+  RET(check_params(params));
+  icr_scene* s = new (std::nothrow) icr_scene();
+  if (!s) {
+    set_error("out of host memory");
+    return ICR_ENOMEM;
+  }
+  s->ctx = ctx;
+  s->params = *params;
+  s->prec = params->precision;
+  s->tsize = s->prec == ICR_FP64 ? 8 : 4;
+  *out = s;
+  return ICR_OK;
+}
+
+int icr_scene_destroy(icr_scene* s) {
+  if (!s) return ICR_OK;
+  cudaSetDevice(s->ctx->device);
+  cudaStreamSynchronize(s->ctx->stream);
+  DBuf* all[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->L, &s->dinv, &s->dinvsqrt,
+                 &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
+                 &s->dof_super, &s->fr_ptr, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
+                 &s->qidx, &s->qpos, &s->X, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->obst_normals, &s->obst_anchors};
+  for (DBuf* b : all) dfree(s, *b);
+  delete s;
+  return ICR_OK;
+}
+
+int icr_set_params(icr_scene* s, const icr_params* params) {
+  RET(check_scene(s));
+  RET(check_params(params));
+  if (params->precision != s->prec) {
+    set_error("precision is fixed when the scene is created");
+    return ICR_EINVAL;
+  }
+  s->params = *params;
+  return ICR_OK;
+}
+
+int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr, const int64_t* rowpat_ptr,
+                   const int32_t* rowpat, const int64_t* val_ptr, const double* Lp, const double* D,
+                   const int32_t* parent) {
+  RET(check_scene(s));
+  if (n <= 0 || n % 3 != 0 || ns <= 0 || ns > n / 3 || !super_ptr || !rowpat_ptr || !val_ptr || !Lp || !D ||
+      !parent || (rowpat_ptr[ns] > 0 && !rowpat)) {
+    set_error("set_system: bad sizes or NULL arrays (n=%d nsuper=%d)", n, ns);
+    return ICR_EINVAL;
+  }
+  if (super_ptr[0] != 0 || super_ptr[ns] != n || rowpat_ptr[0] != 0 || val_ptr[0] != 0) {
+    set_error("set_system: super_ptr must run from 0 to n and offsets start at 0");
+    return ICR_EINVAL;
+  }
+  std::vector<int32_t> sp(super_ptr, super_ptr + ns + 1), par(parent, parent + ns);
+  std::vector<int64_t> rp(rowpat_ptr, rowpat_ptr + ns + 1), vp(val_ptr, val_ptr + ns + 1);
+  int wmax = 0, rmax = 0;
+  for (int k = 0; k < ns; ++k) {
+    int w = sp[k + 1] - sp[k];
+    if (w <= 0 || sp[k] % 3 != 0 || sp[k + 1] % 3 != 0) {
+      set_error("set_system: supernode %d has columns [%d,%d): must be non-empty and hold whole nodes", k, sp[k],
+                sp[k + 1]);
+      return ICR_EINVAL;
+    }
+    int64_t r = rp[k + 1] - rp[k];
+    if (r < 0 || r > n) {
+      set_error("set_system: rowpat_ptr not non-decreasing at %d", k);
+      return ICR_EINVAL;
+    }
+    if (vp[k + 1] - vp[k] != (int64_t)w * (w + r)) {
+      set_error("set_system: panel %d has %lld values, expected (w+r)*w = %lld", k,
+                (long long)(vp[k + 1] - vp[k]), (long long)w * (w + r));
+      return ICR_EINVAL;
+    }
+    for (int64_t i = rp[k]; i < rp[k + 1]; ++i) {
+      int row = rowpat[i];
+      if (row < sp[k + 1] || row >= n || (i > rp[k] && row <= rowpat[i - 1])) {
+        set_error("set_system: below-diagonal rows of supernode %d must be ascending in [%d,%d)", k, sp[k + 1], n);
+        return ICR_EINVAL;
+      }
+    }
+    if (r == 0) {
+      if (par[k] != -1) {
+        set_error("set_system: supernode %d has no below-diagonal rows but parent %d", k, par[k]);
+        return ICR_EINVAL;
+      }
+    } else {
+      int first = rowpat[rp[k]];
+      int p = par[k];
+      if (p <= k || p >= ns || first < sp[p] || first >= sp[p + 1]) {
+        set_error("set_system: parent of supernode %d must own its first below-diagonal row %d", k, first);
+        return ICR_EINVAL;
+      }
+    }
+    wmax = std::max(wmax, w);
+    rmax = std::max(rmax, (int)r);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!(std::isfinite(D[i]) && D[i] > 0)) {
+      set_error("set_system: pivot D[%d] = %g is not finite and positive", i, D[i]);
+      return ICR_ENOTSPD;
+    }
+  }
+  for (int64_t i = 0; i < vp[ns]; ++i) {
+    if (!std::isfinite(Lp[i])) {
+      set_error("set_system: Lpanels[%lld] is not finite", (long long)i);
+      return ICR_EINVAL;
+    }
+  }
+  // children, etree levels (height above the leaves), row maps into parent fronts
+  std::vector<int32_t> nchild(ns, 0), level(ns, 0);
+  for (int k = 0; k < ns; ++k)
+    if (par[k] >= 0) nchild[par[k]]++;
+  std::vector<int32_t> cptr(ns + 1, 0);
+  for (int k = 0; k < ns; ++k) cptr[k + 1] = cptr[k] + nchild[k];
+  std::vector<int32_t> clist(std::max(1, cptr[ns])), fill(cptr.begin(), cptr.end() - 1);
+  for (int k = 0; k < ns; ++k)
+    if (par[k] >= 0) clist[fill[par[k]]++] = k;
+  for (int k = 0; k < ns; ++k)
+    if (par[k] >= 0) level[par[k]] = std::max(level[par[k]], level[k] + 1);
+  std::vector<int32_t> relidx(std::max<int64_t>(1, rp[ns]), 0);
+  for (int k = 0; k < ns; ++k) {
+    int p = par[k];
+    if (p < 0) continue;
+    int wp = sp[p + 1] - sp[p];
+    const int32_t* Rp = rowpat + rp[p];
+    int64_t rpn = rp[p + 1] - rp[p];
+    for (int64_t i = rp[k]; i < rp[k + 1]; ++i) {
+      int row = rowpat[i];
+      if (row < sp[p + 1]) {
+        relidx[i] = row - sp[p];
+      } else {
+        const int32_t* it = std::lower_bound(Rp, Rp + rpn, row);
+        if (it == Rp + rpn || *it != row) {
+          set_error("set_system: row %d of supernode %d is neither a column nor a below-diagonal row of its parent %d",
+                    row, k, p);
+          return ICR_EINVAL;
+        }
+        relidx[i] = wp + (int)(it - Rp);
+      }
+    }
+  }
+  int nlev = 0;
+  for (int k = 0; k < ns; ++k) nlev = std::max(nlev, level[k] + 1);
+  std::vector<Level> levs(nlev);
+  for (int k = 0; k < ns; ++k) levs[level[k]].count++;
+  std::vector<int32_t> llist(ns);
+  {
+    int off = 0;
+    for (auto& L : levs) {
+      L.first = off;
+      off += L.count;
+      L.count = 0;
+    }
+    for (int k = 0; k < ns; ++k) {
+      Level& L = levs[level[k]];
+      llist[L.first + L.count++] = k;
+      L.wmax = std::max(L.wmax, sp[k + 1] - sp[k]);
+      L.rmax = std::max<int>(L.rmax, (int)(rp[k + 1] - rp[k]));
+    }
+  }
+  std::vector<int64_t> frp(ns + 1, 0);
+  for (int k = 0; k < ns; ++k) frp[k + 1] = frp[k] + (sp[k + 1] - sp[k]) + (rp[k + 1] - rp[k]);
+  std::vector<int32_t> dsup(n), nsup(n / 3);
+  for (int k = 0; k < ns; ++k)
+    for (int j = sp[k]; j < sp[k + 1]; ++j) dsup[j] = k;
+  for (int j = 0; j < n / 3; ++j) nsup[j] = dsup[3 * j];
+  std::vector<double> dinv(n), dis(n);
+  for (int i = 0; i < n; ++i) {
+    dinv[i] = 1.0 / D[i];
+    dis[i] = 1.0 / std::sqrt(D[i]);
+  }
+
+  RET(set_device(s));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  RET(dalloc(s, s->super_ptr, (ns + 1) * sizeof(int32_t)));
+  RET(dalloc(s, s->rowpat_ptr, (ns + 1) * sizeof(int64_t)));
+  RET(dalloc(s, s->rowpat, std::max<int64_t>(1, rp[ns]) * sizeof(int32_t)));
+  RET(dalloc(s, s->val_ptr, (ns + 1) * sizeof(int64_t)));
+  RET(dalloc(s, s->L, vp[ns] * s->tsize));
+  RET(dalloc(s, s->dinv, n * sizeof(double)));
+  RET(dalloc(s, s->dinvsqrt, n * sizeof(double)));
+  RET(dalloc(s, s->parent, ns * sizeof(int32_t)));
+  RET(dalloc(s, s->child_ptr, (ns + 1) * sizeof(int32_t)));
+  RET(dalloc(s, s->child_list, clist.size() * sizeof(int32_t)));
+  RET(dalloc(s, s->relidx, relidx.size() * sizeof(int32_t)));
+  RET(dalloc(s, s->level_list, ns * sizeof(int32_t)));
+  RET(dalloc(s, s->node_super, (n / 3) * sizeof(int32_t)));
+  RET(dalloc(s, s->dof_super, n * sizeof(int32_t)));
+  RET(dalloc(s, s->fr_ptr, (ns + 1) * sizeof(int64_t)));
+  RET(upload(s, s->super_ptr, sp.data(), ns + 1));
+  RET(upload(s, s->rowpat_ptr, rp.data(), ns + 1));
+  if (rp[ns]) RET(upload(s, s->rowpat, rowpat, rp[ns]));
+  RET(upload(s, s->val_ptr, vp.data(), ns + 1));
+  RET(upload_T(s, s->L, Lp, vp[ns]));
+  RET(upload(s, s->dinv, dinv.data(), n));
+  RET(upload(s, s->dinvsqrt, dis.data(), n));
+  RET(upload(s, s->parent, par.data(), ns));
+  RET(upload(s, s->child_ptr, cptr.data(), ns + 1));
+  RET(upload(s, s->child_list, clist.data(), clist.size()));
+  RET(upload(s, s->relidx, relidx.data(), relidx.size()));
+  RET(upload(s, s->level_list, llist.data(), ns));
+  RET(upload(s, s->node_super, nsup.data(), n / 3));
+  RET(upload(s, s->dof_super, dsup.data(), n));
+  RET(upload(s, s->fr_ptr, frp.data(), ns + 1));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+
+  s->n = n;
+  s->ns = ns;
+  s->n_nodes = n / 3;
+  s->h_super_ptr = sp;
+  s->h_parent = par;
+  s->h_rowpat_ptr = rp;
+  s->h_val_ptr = vp;
+  s->h_fr_ptr = frp;
+  s->levels = levs;
+  s->total_front_rows = frp[ns];
+  s->wmax = wmax;
+  s->rmax = rmax;
+  s->has_system = true;
+  s->has_mapping = s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
+  return ICR_OK;
+}
+
+int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double* bary) {
+  RET(check_scene(s));
+  if (!s->has_system) {
+    set_error("set_mapping: call icr_set_system first");
+    return ICR_ESTATE;
+  }
+  if (m < 0 || m > 32768 || (m > 0 && (!nodes || !bary))) {
+    set_error("set_mapping: m = %d must be in [0, 32768] with non-NULL arrays", m);
+    return ICR_EINVAL;
+  }
+  for (int a = 0; a < m; ++a) {
+    double sum = 0;
+    for (int i = 0; i < 4; ++i) {
+      int nd = nodes[4 * a + i];
+      double b = bary[4 * a + i];
+      if (nd < 0 || nd >= s->n_nodes) {
+        set_error("set_mapping: node id %d of contact %d out of range [0,%d)", nd, a, s->n_nodes);
+        return ICR_EINVAL;
+      }
+      if (!(std::isfinite(b) && b >= 0)) {
+        set_error("set_mapping: weight %g of contact %d is negative or not finite", b, a);
+        return ICR_EINVAL;
+      }
+      sum += b;
+    }
+    if (std::fabs(sum - 1.0) > 1e-12) {
+      set_error("set_mapping: weights of contact %d sum to %.17g, not 1", a, sum);
+      return ICR_EINVAL;
+    }
+  }
+  RET(set_device(s));
+  const int ns = s->ns;
+  const int words = std::max(1, (m + 31) / 32);
+  const int64_t ldx = std::max<int64_t>(32, ((3 * (int64_t)m + 31) / 32) * 32);
+  const size_t T = s->tsize;
+  const size_t mm = std::max(1, m);
+  RET(dalloc(s, s->nodes, 4 * mm * sizeof(int32_t)));
+  RET(dalloc(s, s->bary, 4 * mm * T));
+  RET(dalloc(s, s->bitmap, (size_t)ns * words * sizeof(uint32_t)));
+  RET(dalloc(s, s->wprefix, (size_t)ns * words * sizeof(int32_t)));
+  RET(dalloc(s, s->qcount, ns * sizeof(int32_t)));
+  RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
+  RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
+  RET(dalloc(s, s->X, (size_t)s->total_front_rows * ldx * T));
+  RET(dalloc(s, s->WH, 9 * mm * mm * T));
+  RET(dalloc(s, s->W, 9 * mm * mm * T));
+  RET(dalloc(s, s->C, 9 * mm * T));
+  RET(dalloc(s, s->delta, 3 * mm * T));
+  RET(dalloc(s, s->mu, mm * T));
+  RET(dalloc(s, s->lam, 3 * mm * T));
+  RET(dalloc(s, s->p, 3 * mm * sizeof(double)));
+  RET(dalloc(s, s->p0, 3 * mm * sizeof(double)));
+  RET(dalloc(s, s->u, 6 * mm * sizeof(double)));   // u (3m) then the last increment dp (3m)
+  RET(dalloc(s, s->uk, 3 * mm * T));
+  RET(dalloc(s, s->ut, 3 * mm * T));
+  RET(dalloc(s, s->y, s->n * T));
+  RET(dalloc(s, s->dq, s->n * T));
+  RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
+  if (m) {
+    RET(upload(s, s->nodes, nodes, 4 * (size_t)m));
+    RET(upload_T(s, s->bary, bary, 4 * (size_t)m));
+  }
+  cudaStream_t st = s->ctx->stream;
+  CK(cudaMemsetAsync(s->lam.p, 0, 3 * mm * T, st));
+  CK(cudaMemsetAsync(s->mu.p, 0, mm * T, st));
+  CK(cudaMemsetAsync(s->delta.p, 0, 3 * mm * T, st));
+  CK(cudaMemsetAsync(s->C.p, 0, 9 * mm * T, st));
+  CK(cudaMemsetAsync(s->p.p, 0, 3 * mm * sizeof(double), st));
+  CK(cudaMemsetAsync(s->p0.p, 0, 3 * mm * sizeof(double), st));
+  CK(cudaMemsetAsync(s->u.p, 0, 6 * mm * sizeof(double), st));
+  CK(cudaMemsetAsync(s->stats.p, 0, sizeof(PgsDevStats), st));
+  s->m = m;
+  s->words = words;
+  s->ldx = ldx;
+  s->has_mapping = true;
+  s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
+  s->obst_kind = 0;
+  return ICR_OK;
+}
+
+static int need_mapping(Scene* s, const char* who) {
+  if (!s->has_mapping) {
+    set_error("%s: call icr_set_mapping first", who);
+    return ICR_ESTATE;
+  }
+  return ICR_OK;
+}
+
+int icr_set_proximity(icr_scene* s, const double* p) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "set_proximity"));
+  if (s->m && !p) {
+    set_error("set_proximity: p is NULL");
+    return ICR_EINVAL;
+  }
+  for (int i = 0; i < 3 * s->m; ++i)
+    if (!std::isfinite(p[i])) {
+      set_error("set_proximity: p[%d] is not finite", i);
+      return ICR_EINVAL;
+    }
+  RET(set_device(s));
+  RET(upload(s, s->p, p, 3 * (size_t)s->m));
+  if (s->m)
+    CK(cudaMemcpyAsync(s->p0.p, s->p.p, 3 * (size_t)s->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                       s->ctx->stream));
+  return ICR_OK;
+}
+
+int icr_reset_proximity(icr_scene* s) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "reset_proximity"));
+  RET(set_device(s));
+  if (s->m) {
+    CK(cudaMemcpyAsync(s->p.p, s->p0.p, 3 * (size_t)s->m * sizeof(double), cudaMemcpyDeviceToDevice,
+                       s->ctx->stream));
+    CK(cudaMemsetAsync(s->u.p, 0, 6 * (size_t)s->m * sizeof(double), s->ctx->stream));
+  }
+  return ICR_OK;
+}
+
+int icr_scene_launches(icr_scene* s, uint64_t* out) {
+  RET(check_scene(s));
+  if (!out) {
+    set_error("out is NULL");
+    return ICR_EINVAL;
+  }
+  *out = s->launches;
+  return ICR_OK;
+}
+
+static int check_directions(const double* C, int m) {
+  for (int a = 0; a < m; ++a) {
+    const double* B = C + 9 * a;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double d = B[3 * i] * B[3 * j] + B[3 * i + 1] * B[3 * j + 1] + B[3 * i + 2] * B[3 * j + 2];
+        if (!(std::fabs(d - (i == j ? 1.0 : 0.0)) <= 1e-6)) {
+          set_error("update_directions: block %d is not orthonormal (row %d . row %d = %g)", a, i, j, d);
+          return ICR_EINVAL;
+        }
+      }
+  }
+  return ICR_OK;
+}
+
+int icr_update_directions(icr_scene* s, const double* C, const double* delta, const double* mu) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "update_directions"));
+  const int m = s->m;
+  if (m && (!C || !delta)) {
+    set_error("update_directions: C and delta must not be NULL");
+    return ICR_EINVAL;
+  }
+  RET(check_directions(C, m));
+  for (int i = 0; i < 3 * m; ++i)
+    if (!std::isfinite(delta[i])) {
+      set_error("update_directions: delta[%d] is not finite", i);
+      return ICR_EINVAL;
+    }
+  if (mu)
+    for (int a = 0; a < m; ++a)
+      if (!(std::isfinite(mu[a]) && mu[a] >= 0)) {
+        set_error("update_directions: mu[%d] = %g must be finite and >= 0", a, mu[a]);
+        return ICR_EINVAL;
+      }
+  RET(set_device(s));
+  RET(upload_T(s, s->C, C, 9 * (size_t)m));
+  RET(upload_T(s, s->delta, delta, 3 * (size_t)m));
+  if (mu) RET(upload_T(s, s->mu, mu, (size_t)m));
+  s->has_dirs = true;
+  s->has_W = false;
+  return ICR_OK;
+}
+
+int icr_set_obstacle_plane(icr_scene* s, int32_t n_iters, const double* normals, const double* anchors) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "set_obstacle_plane"));
+  const int m = s->m;
+  if (n_iters <= 0 || (m && (!normals || !anchors))) {
+    set_error("set_obstacle_plane: n_iters must be > 0 and arrays non-NULL");
+    return ICR_EINVAL;
+  }
+  for (size_t i = 0; i < (size_t)n_iters * m; ++i) {
+    const double* v = normals + 3 * i;
+    double nn = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    if (!(std::fabs(nn - 1.0) <= 1e-6)) {
+      set_error("set_obstacle_plane: normal %zu is not a unit vector", i);
+      return ICR_EINVAL;
+    }
+  }
+  RET(set_device(s));
+  RET(dalloc(s, s->obst_normals, std::max<size_t>(1, (size_t)n_iters * m * 3) * sizeof(double)));
+  RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)m * 3) * sizeof(double)));
+  RET(upload(s, s->obst_normals, normals, (size_t)n_iters * m * 3));
+  RET(upload(s, s->obst_anchors, anchors, (size_t)m * 3));
+  s->obst_kind = 1;
+  s->obst_iters = n_iters;
+  return ICR_OK;
+}
+
+int icr_set_obstacle_sphere(icr_scene* s, const double* center, double radius, const double* anchors) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "set_obstacle_sphere"));
+  if (!center || !(radius > 0) || (s->m && !anchors)) {
+    set_error("set_obstacle_sphere: need a centre, a positive radius and anchors");
+    return ICR_EINVAL;
+  }
+  RET(set_device(s));
+  RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)s->m * 3) * sizeof(double)));
+  RET(upload(s, s->obst_anchors, anchors, (size_t)s->m * 3));
+  for (int i = 0; i < 3; ++i) s->center[i] = center[i];
+  s->radius = radius;
+  s->obst_kind = 2;
+  s->obst_iters = 0;
+  return ICR_OK;
+}
+
+int icr_linearize(icr_scene* s, int32_t k) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "linearize"));
+  if (s->obst_kind == 0) {
+    set_error("linearize: no obstacle set");
+    return ICR_ESTATE;
+  }
+  if (s->obst_kind == 1 && (k < 0 || k >= s->obst_iters)) {
+    set_error("linearize: iteration %d outside the %d plane normal sets", k, s->obst_iters);
+    return ICR_EINVAL;
+  }
+  RET(set_device(s));
+  RET(launch_linearize(s, k));
+  s->has_dirs = true;
+  s->has_W = false;
+  return ICR_OK;
+}
+
+int icr_build_WH(icr_scene* s) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "build_WH"));
+  RET(set_device(s));
+  RET(launch_build_WH(s));
+  s->has_WH = true;
+  s->has_W = false;
+  return ICR_OK;
+}
+
+int icr_update_W(icr_scene* s) {
+  RET(check_scene(s));
+  if (!s->has_WH || !s->has_dirs) {
+    set_error("update_W: needs icr_build_WH and directions first");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  RET(launch_update_W(s));
+  s->has_W = true;
+  return ICR_OK;
+}
+
+int icr_solve_friction(icr_scene* s, int warm_start, icr_pgs_stats* stats) {
+  RET(check_scene(s));
+  if (!s->has_W) {
+    set_error("solve_friction: needs W (icr_update_W or icr_set_field)");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  RET(launch_pgs(s, warm_start ? 1 : 0, stats ? 1 : 0));
+  s->has_lam = true;
+  if (!stats) return ICR_OK;
+  PgsDevStats d;
+  CK(cudaMemcpyAsync(&d, s->stats.p, sizeof(d), cudaMemcpyDeviceToHost, s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  stats->sweeps = d.sweeps;
+  stats->n_separated = d.n_sep;
+  stats->n_stick = d.n_stick;
+  stats->n_slip = d.n_slip;
+  stats->eps = d.eps;
+  double r[4];
+  for (int i = 0; i < 4; ++i) std::memcpy(&r[i], &d.res_bits[i], sizeof(double));
+  stats->res_normal = r[0];
+  stats->res_cone = r[1];
+  stats->res_stick = r[2];
+  stats->res_slip = r[3];
+  if (s->params.tol > 0 && d.eps > s->params.tol && s->m > 0) {
+    set_error("solve_friction: eps %g above tol %g after %d sweeps", d.eps, s->params.tol, d.sweeps);
+    return ICR_ENOCONV;
+  }
+  return ICR_OK;
+}
+
+int icr_update_proximity(icr_scene* s, double* dp_out) {
+  RET(check_scene(s));
+  if (!s->has_lam || !s->has_dirs || !s->has_WH) {
+    set_error("update_proximity: needs W_H, directions and a solve first");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  RET(launch_update_proximity(s));
+  if (dp_out && s->m) {
+    CK(cudaMemcpyAsync(dp_out, (double*)s->u.p + 3 * (size_t)s->m, 3 * (size_t)s->m * sizeof(double),
+                       cudaMemcpyDeviceToHost, s->ctx->stream));
+    CK(cudaStreamSynchronize(s->ctx->stream));
+  }
+  return ICR_OK;
+}
+
+int icr_correct_motion(icr_scene* s, double* dq_out, int reset) {
+  RET(check_scene(s));
+  if (!s->has_WH) {
+    set_error("correct_motion: needs icr_build_WH first");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  RET(launch_correct_motion(s));
+  if (dq_out) RET(download_T(s, s->dq, dq_out, s->n));
+  if (reset && s->m) CK(cudaMemsetAsync(s->u.p, 0, 3 * (size_t)s->m * sizeof(double), s->ctx->stream));
+  return ICR_OK;
+}
+
+static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
+  const size_t m = s->m;
+  *elem = sizeof(double);
+  switch (f) {
+    case ICR_FIELD_WH:
+    case ICR_FIELD_W: *count = 9 * m * m; break;
+    case ICR_FIELD_LAMBDA:
+    case ICR_FIELD_DELTA:
+    case ICR_FIELD_P:
+    case ICR_FIELD_U: *count = 3 * m; break;
+    case ICR_FIELD_C: *count = 9 * m; break;
+    case ICR_FIELD_MU: *count = m; break;
+    case ICR_FIELD_REACH_PTR:
+      *count = s->ns + 1;
+      *elem = sizeof(int32_t);
+      break;
+    case ICR_FIELD_REACH_IDX: {
+      *elem = sizeof(int32_t);
+      std::vector<int32_t> qc(s->ns);
+      cudaMemcpyAsync(qc.data(), s->qcount.p, s->ns * sizeof(int32_t), cudaMemcpyDeviceToHost, s->ctx->stream);
+      cudaError_t e = cudaStreamSynchronize(s->ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "field_size");
+      size_t tot = 0;
+      for (int v : qc) tot += v;
+      *count = tot;
+      break;
+    }
+    default: set_error("unknown field %d", f); return ICR_EINVAL;
+  }
+  return ICR_OK;
+}
+
+int icr_field_bytes(icr_scene* s, int32_t field, size_t* out) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "field_bytes"));
+  if (!out) {
+    set_error("out is NULL");
+    return ICR_EINVAL;
+  }
+  size_t c, e;
+  RET(field_size(s, field, &c, &e));
+  *out = c * e;
+  return ICR_OK;
+}
+
+int icr_get(icr_scene* s, int32_t field, void* dst, size_t bytes) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "get"));
+  RET(set_device(s));
+  size_t c, e;
+  RET(field_size(s, field, &c, &e));
+  if (bytes != c * e || (c && !dst)) {
+    set_error("get: field %d needs %zu bytes, got %zu", field, c * e, bytes);
+    return ICR_EINVAL;
+  }
+  if (c == 0) return ICR_OK;
+  cudaStream_t st = s->ctx->stream;
+  switch (field) {
+    case ICR_FIELD_WH: return download_T(s, s->WH, (double*)dst, c);
+    case ICR_FIELD_W: return download_T(s, s->W, (double*)dst, c);
+    case ICR_FIELD_LAMBDA: return download_T(s, s->lam, (double*)dst, c);
+    case ICR_FIELD_DELTA: return download_T(s, s->delta, (double*)dst, c);
+    case ICR_FIELD_C: return download_T(s, s->C, (double*)dst, c);
+    case ICR_FIELD_MU: return download_T(s, s->mu, (double*)dst, c);
+    case ICR_FIELD_P:
+      CK(cudaMemcpyAsync(dst, s->p.p, bytes, cudaMemcpyDeviceToHost, st));
+      break;
+    case ICR_FIELD_U:
+      CK(cudaMemcpyAsync(dst, s->u.p, bytes, cudaMemcpyDeviceToHost, st));
+      break;
+    case ICR_FIELD_REACH_PTR:
+    case ICR_FIELD_REACH_IDX: {
+      std::vector<int32_t> qc(s->ns), qi((size_t)s->ns * std::max(1, s->m));
+      CK(cudaMemcpyAsync(qc.data(), s->qcount.p, s->ns * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(qi.data(), s->qidx.p, qi.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      int32_t* out = (int32_t*)dst;
+      if (field == ICR_FIELD_REACH_PTR) {
+        out[0] = 0;
+        for (int k = 0; k < s->ns; ++k) out[k + 1] = out[k] + qc[k];
+      } else {
+        size_t o = 0;
+        for (int k = 0; k < s->ns; ++k)
+          for (int j = 0; j < qc[k]; ++j) out[o++] = qi[(size_t)k * s->m + j];
+      }
+      return ICR_OK;
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return ICR_OK;
+}
+
+int icr_set_field(icr_scene* s, int32_t field, const double* src, size_t bytes) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "set_field"));
+  RET(set_device(s));
+  size_t c, e;
+  RET(field_size(s, field, &c, &e));
+  if (bytes != c * e || (c && !src) || e != sizeof(double)) {
+    set_error("set_field: field %d needs %zu bytes of doubles, got %zu", field, c * e, bytes);
+    return ICR_EINVAL;
+  }
+  for (size_t i = 0; i < c; ++i)
+    if (!std::isfinite(src[i])) {
+      set_error("set_field: value %zu is not finite", i);
+      return ICR_EINVAL;
+    }
+  switch (field) {
+    case ICR_FIELD_W: RET(upload_T(s, s->W, src, c)); s->has_W = true; break;
+    case ICR_FIELD_WH: RET(upload_T(s, s->WH, src, c)); s->has_WH = true; break;
+    case ICR_FIELD_LAMBDA: RET(upload_T(s, s->lam, src, c)); s->has_lam = true; break;
+    case ICR_FIELD_DELTA: RET(upload_T(s, s->delta, src, c)); break;
+    case ICR_FIELD_C:
+      RET(check_directions(src, s->m));
+      RET(upload_T(s, s->C, src, c));
+      s->has_dirs = true;
+      break;
+    case ICR_FIELD_MU: RET(upload_T(s, s->mu, src, c)); break;
+    case ICR_FIELD_P: RET(upload(s, s->p, src, c)); break;
+    case ICR_FIELD_U: RET(upload(s, s->u, src, c)); break;
+    default: set_error("set_field: field %d cannot be set", field); return ICR_EINVAL;
+  }
+  return ICR_OK;
+}
+
+}  // extern "C"

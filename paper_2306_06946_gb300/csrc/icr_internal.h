@@ -1,0 +1,91 @@
+// Internal declarations of libicr: scene state and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "icr.h"
+
+namespace icr {
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* where);
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+};
+
+// Device buffer owned by a scene, accounted against the context budget.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Per-level launch geometry of the supernodal elimination tree.
+struct Level {
+  int first = 0;   // offset into level_list
+  int count = 0;   // supernodes in the level
+  int wmax = 0;    // widest supernode
+  int rmax = 0;    // most below-diagonal rows
+};
+
+struct Scene {
+  Ctx* ctx = nullptr;
+  icr_params params{};
+  int prec = ICR_FP32;
+  size_t tsize = 4;
+
+  // ---- system (set_system)
+  bool has_system = false;
+  int n = 0, ns = 0, n_nodes = 0;
+  std::vector<int32_t> h_super_ptr, h_parent, h_qcount;
+  std::vector<int64_t> h_rowpat_ptr, h_val_ptr, h_fr_ptr;
+  std::vector<Level> levels;
+  int64_t total_front_rows = 0;
+  int wmax = 0, rmax = 0;
+  DBuf super_ptr, rowpat_ptr, rowpat, val_ptr, L, dinv, dinvsqrt, parent;
+  DBuf child_ptr, child_list, relidx, level_list, node_super, dof_super, fr_ptr;
+
+  // ---- mapping (set_mapping)
+  bool has_mapping = false;
+  int m = 0, words = 0;
+  int64_t ldx = 0;     // leading dimension (columns) of every front
+  DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, X;
+  DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
+  uint64_t launches = 0;   // kernels launched by this scene
+  bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
+
+  // ---- obstacle (device linearisation)
+  int obst_kind = 0;   // 0 none, 1 plane, 2 sphere
+  int obst_iters = 0;
+  DBuf obst_normals, obst_anchors;
+  double center[3] = {0, 0, 0};
+  double radius = 0;
+};
+
+int dalloc(Scene* s, DBuf& b, size_t bytes);
+void dfree(Scene* s, DBuf& b);
+
+// Device statistics written by the PGS kernels (FP64 residual check).
+struct PgsDevStats {
+  int32_t sweeps;
+  int32_t n_sep, n_stick, n_slip;
+  double eps;
+  unsigned long long res_bits[4];   // normal, cone, stick, slip as non-negative double bits
+};
+
+// ---- launchers (icr_kernels.cu); every one enqueues on s->ctx->stream
+int launch_build_WH(Scene* s);
+int launch_update_W(Scene* s);
+int launch_pgs(Scene* s, int warm_start, int want_residuals);
+int launch_update_proximity(Scene* s);
+int launch_correct_motion(Scene* s);
+int launch_linearize(Scene* s, int k);
+
+}  // namespace icr

@@ -1,0 +1,889 @@
+// libicr device side: the kernels of the constraint-resolution hot path and
+// their launchers.  Every kernel is templated on the storage / arithmetic type
+// T (float or double); D^-1 and D^-1/2 are always applied in FP64.
+//
+// Build of W_H = H A^-1 H^T = X^T D^-1 X, X = L^-1 H^T
+// (Eq. "schur complemnt reformulated" with A = L D L^T):
+//   a1  k_reach_*      which contacts' columns of H^T reach each supernode
+//                      (etree ancestors of the supernodes owning their nodes)
+//   a2  k_trsm         per supernode and 32-contact column tile: assemble the
+//                      front (H^T entries + children's update blocks), then the
+//                      unit lower triangular solve of its diagonal block
+//       k_update       U_s = F_R - L[R_s, s] X_s, the update passed to the parent
+//   a3+a4 k_contract   W_H += Y_s^T Y_s with Y_s = D_s^-1/2 X_s (FP64 scaling)
+// Newton iteration (Alg. 3):
+//   a6  k_update_W     W = C W_H C^T, one 3x3 block pair per thread
+//   a7  k_pgs          projected Gauss-Seidel (Eq. "PGS"), one CTA
+//       k_pgs_residual FP64 complementarity / cone residuals
+//   a8  k_prox_*       p += W_H C^T lambda~, u += C^T lambda~
+// End of step:
+//   a9  k_xu, k_bsolve dq = L^-T D^-1 X u
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "icr_internal.h"
+
+namespace icr {
+
+// checks a launch and counts it in the scene (every launcher has `s` in scope)
+#define LAUNCH_OK(where)                                  \
+  do {                                                    \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where);   \
+    ++s->launches;                                        \
+  } while (0)
+
+static constexpr unsigned FULL = 0xffffffffu;
+static constexpr int TCC = 32;            // contacts per column tile of the forward solve
+static constexpr int TCOLS = 3 * TCC;     // columns per tile
+static constexpr int KB = 32;             // diagonal block of the triangular solves
+static constexpr int SOLVE_THREADS = 192; // 2 x 96 columns
+static constexpr int UR = 64;             // rows per update tile
+static constexpr int CT = 64;             // contraction output tile
+static constexpr int CK_ = 16;            // contraction k-chunk
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int lower_bound_dev(const int* a, int n, int v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------------------------ a1 reach
+// One thread per (contact, node): mark the contact in every supernode on the
+// etree path from the node's supernode to the root.  A thread stops at the
+// first supernode already marked for its contact: whoever marked it walks on.
+__global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
+                             const int* __restrict__ parent, int ns, uint32_t* bitmap, int words) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * m) return;
+  int a = t >> 2;
+  int s = node_super[nodes[t]];
+  uint32_t bit = 1u << (a & 31);
+  int w = a >> 5;
+  for (int guard = 0; s >= 0 && guard < ns; ++guard) {
+    uint32_t old = atomicOr(&bitmap[(size_t)s * words + w], bit);
+    if (old & bit) break;
+    s = parent[s];
+  }
+}
+
+// One block per supernode: count its contacts, prefix the per-word counts and
+// list the contacts in ascending order.
+__global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
+                             int* qidx) {
+  extern __shared__ int sh[];
+  int s = blockIdx.x;
+  int w = threadIdx.x;
+  uint32_t bits = (w < words) ? bitmap[(size_t)s * words + w] : 0u;
+  int c = __popc(bits);
+  sh[w] = c;
+  __syncthreads();
+  for (int off = 1; off < blockDim.x; off <<= 1) {
+    int v = (w >= off) ? sh[w - off] : 0;
+    __syncthreads();
+    sh[w] += v;
+    __syncthreads();
+  }
+  int excl = sh[w] - c;
+  if (w < words) wprefix[(size_t)s * words + w] = excl;
+  if (w == blockDim.x - 1) qcount[s] = sh[w];
+  int* out = qidx + (size_t)s * m + excl;
+  while (bits) {
+    int b = __ffs(bits) - 1;
+    *out++ = 32 * w + b;
+    bits &= bits - 1;
+  }
+}
+
+// Position of each of a supernode's contacts in its parent's contact list.
+__global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
+                                  int m, const int* __restrict__ parent, const int* __restrict__ qcount,
+                                  const int* __restrict__ qidx, int* qpos) {
+  int s = blockIdx.y;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= qcount[s]) return;
+  int p = parent[s];
+  int a = qidx[(size_t)s * m + j];
+  int pos = -1;
+  if (p >= 0) {
+    int w = a >> 5;
+    pos = wprefix[(size_t)p * words + w] + __popc(bitmap[(size_t)p * words + w] & ((1u << (a & 31)) - 1u));
+  }
+  qpos[(size_t)s * m + j] = pos;
+}
+
+// ------------------------------------------------------------------ a2 forward solve
+// Block (supernode s of the level, 32-contact tile t).  The front of s holds
+// w + r rows (its columns, then R_s) and 3 |Q_s| columns (contacts of Q_s in
+// ascending order, 3 axes each), row-major with leading dimension ldx.
+template <class T>
+__global__ void __launch_bounds__(SOLVE_THREADS)
+    k_trsm(const int* __restrict__ level_list, int lvl_first, int ntiles, const int* __restrict__ super_ptr,
+           const int64_t* __restrict__ rowpat_ptr, const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp,
+           const int* __restrict__ child_ptr, const int* __restrict__ child_list, const int* __restrict__ relidx,
+           const int64_t* __restrict__ fr_ptr, const int* __restrict__ node_super, const int* __restrict__ nodes,
+           const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
+           const int* __restrict__ qpos, int m, T* X, int64_t ldx) {
+  __shared__ T sL[KB][KB + 1];
+  __shared__ T sX[KB][TCOLS + 1];
+  const int li = blockIdx.x / ntiles, t = blockIdx.x % ntiles;
+  const int s = level_list[lvl_first + li];
+  const int nq = qcount[s];
+  const int k0 = t * TCC;
+  if (k0 >= nq) return;
+  const int kc = min(TCC, nq - k0);
+  const int ncols = 3 * kc;
+  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+  const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  const int nrows = w + r;
+  const int64_t ldL = nrows;
+  const T* L = Lp + val_ptr[s];
+  T* F = X + fr_ptr[s] * ldx + 3 * k0;
+  const int tid = threadIdx.x;
+
+  // front tile = 0
+  for (int64_t e = tid; e < (int64_t)nrows * ncols; e += blockDim.x) {
+    int i = (int)(e / ncols), j = (int)(e % ncols);
+    F[i * ldx + j] = T(0);
+  }
+  __syncthreads();
+  // + H^T: column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
+  for (int e = tid; e < 4 * kc; e += blockDim.x) {
+    int k = e >> 2, i = e & 3;
+    int a = qidx[(size_t)s * m + k0 + k];
+    int node = nodes[4 * a + i];
+    if (node_super[node] == s) {
+      T b = bary[4 * a + i];
+      int row = 3 * node - c0;
+      for (int d = 0; d < 3; ++d) atomicAdd(&F[(int64_t)(row + d) * ldx + 3 * k + d], b);
+    }
+  }
+  __syncthreads();
+  // + extend-add of every child's update block (rows mapped by relidx,
+  // contacts by their position in this supernode's list)
+  for (int ci = child_ptr[s]; ci < child_ptr[s + 1]; ++ci) {
+    const int c = child_list[ci];
+    const int nqc = qcount[c];
+    const int* pc = qpos + (size_t)c * m;
+    const int j0 = lower_bound_dev(pc, nqc, k0), j1 = lower_bound_dev(pc, nqc, k0 + kc);
+    if (j1 > j0) {
+      const int wc = super_ptr[c + 1] - super_ptr[c];
+      const int rc = (int)(rowpat_ptr[c + 1] - rowpat_ptr[c]);
+      const int* ri = relidx + rowpat_ptr[c];
+      const T* U = X + (fr_ptr[c] + wc) * ldx + 3 * j0;
+      const int cc = 3 * (j1 - j0);
+      for (int64_t e = tid; e < (int64_t)rc * cc; e += blockDim.x) {
+        int i = (int)(e / cc), jj = (int)(e % cc);
+        int col = 3 * (pc[j0 + jj / 3] - k0) + jj % 3;
+        F[(int64_t)ri[i] * ldx + col] += U[(int64_t)i * ldx + jj];
+      }
+    }
+    __syncthreads();
+  }
+  // unit lower triangular solve on the first w rows, 32-row blocks
+  for (int kb = 0; kb < w; kb += KB) {
+    const int nb = min(KB, w - kb);
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+      int k = e / nb, i = e % nb;
+      sL[i][k] = L[(int64_t)(kb + k) * ldL + kb + i];
+    }
+    for (int e = tid; e < nb * ncols; e += blockDim.x) {
+      int i = e / ncols, j = e % ncols;
+      sX[i][j] = F[(int64_t)(kb + i) * ldx + j];
+    }
+    __syncthreads();
+    if (tid < ncols) {
+      for (int k = 0; k < nb; ++k) {
+        T xk = sX[k][tid];
+        for (int i = k + 1; i < nb; ++i) sX[i][tid] -= sL[i][k] * xk;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < nb * ncols; e += blockDim.x) {
+      int i = e / ncols, j = e % ncols;
+      F[(int64_t)(kb + i) * ldx + j] = sX[i][j];
+    }
+    for (int rb = kb + nb; rb < w; rb += KB) {
+      const int nr = min(KB, w - rb);
+      __syncthreads();
+      for (int e = tid; e < nr * nb; e += blockDim.x) {
+        int k = e / nr, i = e % nr;
+        sL[i][k] = L[(int64_t)(kb + k) * ldL + rb + i];
+      }
+      __syncthreads();
+      for (int e = tid; e < nr * ncols; e += blockDim.x) {
+        int i = e / ncols, j = e % ncols;
+        T acc = T(0);
+        for (int k = 0; k < nb; ++k) acc += sL[i][k] * sX[k][j];
+        F[(int64_t)(rb + i) * ldx + j] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Block (supernode, 64-row tile of R_s, 32-contact tile): U -= L[R_s, s] X_s.
+template <class T>
+__global__ void __launch_bounds__(SOLVE_THREADS)
+    k_update(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
+             const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+             const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp, const int64_t* __restrict__ fr_ptr,
+             const int* __restrict__ qcount, T* X, int64_t ldx) {
+  __shared__ T sL[UR][KB + 1];
+  __shared__ T sX[KB][TCOLS + 1];
+  int b = blockIdx.x;
+  const int t = b % ntiles;
+  b /= ntiles;
+  const int rt = b % nrt;
+  const int li = b / nrt;
+  const int s = level_list[lvl_first + li];
+  const int nq = qcount[s];
+  const int k0 = t * TCC;
+  if (k0 >= nq) return;
+  const int ncols = 3 * min(TCC, nq - k0);
+  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+  const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  const int i0 = rt * UR;
+  if (i0 >= r) return;
+  const int nr = min(UR, r - i0);
+  const int64_t ldL = w + r;
+  const T* L = Lp + val_ptr[s];
+  const T* Xs = X + fr_ptr[s] * ldx + 3 * k0;
+  T* U = X + (fr_ptr[s] + w) * ldx + 3 * k0;
+  const int tid = threadIdx.x;
+  const int j = tid % TCOLS, g = tid / TCOLS;
+  T acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = T(0);
+  for (int kb = 0; kb < w; kb += KB) {
+    const int nb = min(KB, w - kb);
+    __syncthreads();
+    for (int e = tid; e < UR * nb; e += blockDim.x) {
+      int k = e / UR, i = e % UR;
+      sL[i][k] = (i < nr) ? L[(int64_t)(kb + k) * ldL + w + i0 + i] : T(0);
+    }
+    for (int e = tid; e < nb * ncols; e += blockDim.x) {
+      int i = e / ncols, jj = e % ncols;
+      sX[i][jj] = Xs[(int64_t)(kb + i) * ldx + jj];
+    }
+    __syncthreads();
+    if (j < ncols) {
+      for (int k = 0; k < nb; ++k) {
+        T xv = sX[k][j];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] += sL[g * 32 + q][k] * xv;
+      }
+    }
+  }
+  if (j < ncols) {
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      int i = g * 32 + q;
+      if (i < nr) U[(int64_t)(i0 + i) * ldx + j] -= acc[q];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ a3 + a4 contraction
+// Block (tile pair I <= J of supernode s's local columns, s):
+// W_H[g(i), g(j)] += sum_k Y[k,i] Y[k,j],  Y = D^-1/2 X (scaling in FP64).
+// Only the upper triangle (g(i) <= g(j)) is accumulated; k_symmetrize mirrors it.
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_contract(int ntc, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+               const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
+               const double* __restrict__ dinvsqrt, const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
+  __shared__ T sA[CK_][CT + 1];
+  __shared__ T sB[CK_][CT + 1];
+  const int s = blockIdx.y;
+  int rem = blockIdx.x, I = 0;
+  while (rem >= ntc - I) {
+    rem -= ntc - I;
+    ++I;
+  }
+  const int J = I + rem;
+  const int ncol = 3 * qcount[s];
+  const int nt = (ncol + CT - 1) / CT;
+  if (J >= nt) return;
+  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+  const T* Xs = X + fr_ptr[s] * ldx;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kb = 0; kb < w; kb += CK_) {
+    const int nb = min(CK_, w - kb);
+    for (int e = tid; e < CK_ * CT; e += blockDim.x) {
+      int k = e / CT, c = e % CT;
+      int ca = I * CT + c, cb = J * CT + c;
+      double ds = (k < nb) ? dinvsqrt[c0 + kb + k] : 0.0;
+      sA[k][c] = (k < nb && ca < ncol) ? T(ds * (double)Xs[(int64_t)(kb + k) * ldx + ca]) : T(0);
+      sB[k][c] = (k < nb && cb < ncol) ? T(ds * (double)Xs[(int64_t)(kb + k) * ldx + cb]) : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CK_; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = sA[k][ty * 4 + a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = sB[k][tx * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+    }
+    __syncthreads();
+  }
+  const int* q = qidx + (size_t)s * m;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    int li = I * CT + ty * 4 + a;
+    if (li >= ncol) continue;
+    int64_t gi = 3 * (int64_t)q[li / 3] + li % 3;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      int lj = J * CT + tx * 4 + b;
+      if (lj >= ncol || li > lj) continue;
+      int64_t gj = 3 * (int64_t)q[lj / 3] + lj % 3;
+      atomicAdd(&WH[gi * ldw + gj], acc[a][b]);
+    }
+  }
+}
+
+template <class T>
+__global__ void k_symmetrize(int nr, T* A) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  if (j < i) A[(int64_t)i * nr + j] = A[(int64_t)j * nr + i];
+}
+
+// ------------------------------------------------------------------ a6 W = C W_H C^T
+template <class T>
+__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W) {
+  const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
+  if (a >= m || b >= m || a > b) return;
+  const int64_t ld = 3 * (int64_t)m;
+  T M[3][3], Ca[3][3], Cb[3][3], t[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
+      Ca[i][j] = C[9 * a + 3 * i + j];
+      Cb[i][j] = C[9 * b + 3 * i + j];
+    }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t[i][j] = M[i][0] * Cb[j][0] + M[i][1] * Cb[j][1] + M[i][2] * Cb[j][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T v = Ca[i][0] * t[0][j] + Ca[i][1] * t[1][j] + Ca[i][2] * t[2][j];
+      W[(3 * a + i) * ld + 3 * b + j] = v;
+      W[(3 * b + j) * ld + 3 * a + i] = v;
+    }
+}
+
+// ------------------------------------------------------------------ a7 PGS
+// One CTA.  Contacts are taken in blocks of 32: all warps first form the
+// block's residuals r = delta + W lambda~ with the newest lambda~ and stage the
+// block's diagonal part of W; warp 0 then runs the block's contacts in order,
+// lane = contact, broadcasting every change of lambda~ so that later lanes fold
+// it into their residual.
+template <class T>
+__global__ void __launch_bounds__(1024)
+    k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, const T* __restrict__ delta,
+          const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* lam = (T*)smraw;          // 3m
+  T* rblk = lam + 3 * m;       // 96
+  T* Wbb = rblk + 96;          // 96 x 97
+  __shared__ double red[32];
+  __shared__ int stop;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int64_t ld = 3 * (int64_t)m;
+  for (int i = tid; i < 3 * m; i += blockDim.x) lam[i] = warm ? lam_g[i] : T(0);
+  if (tid == 0) stop = 0;
+  __syncthreads();
+  const int nblk = (m + 31) / 32;
+  double eps = 0.0;
+  int done = 0;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    double dsum = 0.0;
+    for (int bi = 0; bi < nblk; ++bi) {
+      const int a0 = 32 * bi, nb = min(32, m - a0), R0 = 3 * a0, nr = 3 * nb;
+      for (int i = wid; i < nr; i += nw) {
+        const T* Wr = W + (int64_t)(R0 + i) * ld;
+        T acc = T(0);
+        for (int j = lane; j < 3 * m; j += 32) acc += Wr[j] * lam[j];
+        acc = warp_sum(acc);
+        if (lane == 0) rblk[i] = delta[R0 + i] + acc;
+      }
+      for (int e = tid; e < nr * nr; e += blockDim.x) {
+        int i = e / nr, j = e % nr;
+        Wbb[i * 97 + j] = W[(int64_t)(R0 + i) * ld + R0 + j];
+      }
+      __syncthreads();
+      if (wid == 0) {
+        const bool valid = lane < nb;
+        T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0;
+        if (valid) {
+          r0 = rblk[3 * lane];
+          r1 = rblk[3 * lane + 1];
+          r2 = rblk[3 * lane + 2];
+          l0 = lam[R0 + 3 * lane];
+          l1 = lam[R0 + 3 * lane + 1];
+          l2 = lam[R0 + 3 * lane + 2];
+          mua = mu[a0 + lane];
+        }
+        for (int i = 0; i < nb; ++i) {
+          T d0 = 0, d1 = 0, d2 = 0;
+          if (lane == i) {
+            const T* Wd = Wbb + (3 * i) * 97 + 3 * i;
+            const T Wnn = Wd[0], Wt1n = Wd[97], Wt2n = Wd[194];
+            const T wt = T(0.5) * (Wd[98] + Wd[196]);
+            T ln = l0 - r0 / Wnn;
+            ln = ln > T(0) ? ln : T(0);
+            const T dn = ln - l0;
+            const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
+            T lt1 = l1 - rt1 / wt, lt2 = l2 - rt2 / wt;
+            const T lim = mua * ln;
+            const T nt = hypot(lt1, lt2);
+            if (ln <= T(0)) {
+              lt1 = T(0);
+              lt2 = T(0);
+            } else if (nt > lim) {
+              const T sc = lim / nt;
+              lt1 *= sc;
+              lt2 *= sc;
+            }
+            d0 = ln - l0;
+            d1 = lt1 - l1;
+            d2 = lt2 - l2;
+            l0 = ln;
+            l1 = lt1;
+            l2 = lt2;
+            dsum += (double)d0 * (double)d0 + (double)d1 * (double)d1 + (double)d2 * (double)d2;
+          }
+          d0 = __shfl_sync(FULL, d0, i);
+          d1 = __shfl_sync(FULL, d1, i);
+          d2 = __shfl_sync(FULL, d2, i);
+          if (valid && lane > i) {
+            const T* Wl = Wbb + (3 * lane) * 97 + 3 * i;
+            r0 += Wl[0] * d0 + Wl[1] * d1 + Wl[2] * d2;
+            r1 += Wl[97] * d0 + Wl[98] * d1 + Wl[99] * d2;
+            r2 += Wl[194] * d0 + Wl[195] * d1 + Wl[196] * d2;
+          }
+        }
+        if (valid) {
+          lam[R0 + 3 * lane] = l0;
+          lam[R0 + 3 * lane + 1] = l1;
+          lam[R0 + 3 * lane + 2] = l2;
+        }
+      }
+      __syncthreads();
+    }
+    // eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
+    double nrm = 0.0;
+    for (int i = tid; i < 3 * m; i += blockDim.x) nrm += (double)lam[i] * (double)lam[i];
+    nrm = warp_sum(nrm);
+    if (wid == 0) dsum = warp_sum(dsum);
+    if (lane == 0) red[wid] = nrm;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int k = 0; k < nw; ++k) tot += red[k];
+      eps = tot > 0.0 ? sqrt(dsum / tot) : 0.0;
+      red[0] = eps;
+      stop = (tol > 0.0 && eps <= tol) ? 1 : 0;
+    }
+    __syncthreads();
+    eps = red[0];
+    done = sw + 1;
+    const int brk = stop;
+    __syncthreads();
+    if (brk) break;
+  }
+  for (int i = tid; i < 3 * m; i += blockDim.x) lam_g[i] = lam[i];
+  if (tid == 0) {
+    st->sweeps = done;
+    st->eps = eps;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// FP64 residuals of the final iterate: one warp per contact.
+template <class T>
+__global__ void k_pgs_residual(int m, const T* __restrict__ W, const T* __restrict__ delta,
+                               const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
+  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= m) return;
+  const int64_t ld = 3 * (int64_t)m;
+  double d[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const T* Wr = W + (3 * (int64_t)a + k) * ld;
+    double acc = 0.0;
+    for (int j = lane; j < 3 * m; j += 32) acc += (double)Wr[j] * (double)lam[j];
+    acc = warp_sum(acc);
+    d[k] = (double)delta[3 * a + k] + acc;
+  }
+  if (lane != 0) return;
+  const double L0 = lam[3 * a], L1 = lam[3 * a + 1], L2 = lam[3 * a + 2];
+  const double lim = (double)mu[a] * L0;
+  const double nt = hypot(L1, L2);
+  atomic_max_nonneg(&st->res_bits[0], fabs(fmin(d[0], L0)));
+  atomic_max_nonneg(&st->res_bits[1], fmax(0.0, nt - lim));
+  const bool on_cone = L0 > 0 && nt >= lim * (1.0 - rel) && nt > 0;
+  const bool stick = L0 > 0 && !on_cone;
+  if (L0 <= 0) {
+    atomicAdd(&st->n_sep, 1);
+  } else if (on_cone) {
+    atomicAdd(&st->n_slip, 1);
+    const double tx = L1 / nt, ty = L2 / nt;
+    const double along = d[1] * tx + d[2] * ty;
+    const double px = d[1] - along * tx, py = d[2] - along * ty;
+    atomic_max_nonneg(&st->res_bits[3], hypot(px, py) + fmax(0.0, along));
+  } else if (stick) {
+    atomicAdd(&st->n_stick, 1);
+    atomic_max_nonneg(&st->res_bits[2], hypot(d[1], d[2]));
+  }
+}
+
+// ------------------------------------------------------------------ a8 proximity update
+template <class T>
+__global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= m) return;
+  const T l0 = lam[3 * a], l1 = lam[3 * a + 1], l2 = lam[3 * a + 2];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    T v = C[9 * a + j] * l0 + C[9 * a + 3 + j] * l1 + C[9 * a + 6 + j] * l2;
+    uk[3 * a + j] = v;
+    u[3 * a + j] += (double)v;
+  }
+}
+
+template <class T>
+__global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= 3 * m) return;
+  const T* Wr = WH + (int64_t)i * 3 * m;
+  T acc = T(0);
+  for (int j = lane; j < 3 * m; j += 32) acc += Wr[j] * uk[j];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    p[i] += (double)acc;
+    dp[i] = (double)acc;
+  }
+}
+
+// ------------------------------------------------------------------ a9 corrective motion
+template <class T>
+__global__ void k_cast_u(int n, const double* __restrict__ u, T* ut) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ut[i] = (T)u[i];
+}
+
+// y = D^-1 X u, one warp per DOF row (X restricted to the contacts reaching it)
+template <class T>
+__global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                     const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
+                     const T* __restrict__ ut, const double* __restrict__ dinv, T* y) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int s = dof_super[row];
+  const int ncol = 3 * qcount[s];
+  const T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
+  const int* q = qidx + (size_t)s * m;
+  T acc = T(0);
+  for (int c = lane; c < ncol; c += 32) acc += F[c] * ut[3 * q[c / 3] + c % 3];
+  acc = warp_sum(acc);
+  if (lane == 0) y[row] = (T)(dinv[row] * (double)acc);
+}
+
+// Backward solve L^T dq = y for the supernodes of one level (top-down).
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_bsolve(const int* __restrict__ level_list, int lvl_first, const int* __restrict__ super_ptr,
+             const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
+             const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp, const T* __restrict__ y, T* dq) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* z = (T*)smraw;
+  const int s = level_list[lvl_first + blockIdx.x];
+  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+  const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  const int64_t ldL = w + r;
+  const T* L = Lp + val_ptr[s];
+  const int* R = rowpat + rowpat_ptr[s];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  for (int k = wid; k < w; k += nw) {
+    const T* Lc = L + (int64_t)k * ldL + w;
+    T acc = T(0);
+    for (int i = lane; i < r; i += 32) acc += Lc[i] * dq[R[i]];
+    acc = warp_sum(acc);
+    if (lane == 0) z[k] = y[c0 + k] - acc;
+  }
+  __syncthreads();
+  for (int kb = ((w - 1) / 32) * 32; kb >= 0; kb -= 32) {
+    const int nb = min(32, w - kb);
+    if (wid == 0) {
+      T zl = (lane < nb) ? z[kb + lane] : T(0);
+      for (int k = nb - 1; k >= 0; --k) {
+        const T xk = __shfl_sync(FULL, zl, k);
+        if (lane < k) zl -= L[(int64_t)(kb + lane) * ldL + kb + k] * xk;
+      }
+      if (lane < nb) z[kb + lane] = zl;
+    }
+    __syncthreads();
+    for (int kp = tid; kp < kb; kp += blockDim.x) {
+      const T* Lc = L + (int64_t)kp * ldL + kb;
+      T acc = T(0);
+      for (int i = 0; i < nb; ++i) acc += Lc[i] * z[kb + i];
+      z[kp] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int k = tid; k < w; k += blockDim.x) dq[c0 + k] = z[k];
+}
+
+// ------------------------------------------------------------------ linearisation
+// C rows n, t1, t2 and the gaps from the current proximity positions (FP64).
+template <class T>
+__global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
+                            const double* __restrict__ anchors, double cx, double cy, double cz, double radius,
+                            const double* __restrict__ p, T* C, T* delta) {
+  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= m) return;
+  const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
+  double n0, n1, n2, dist = 0.0;
+  if (kind == 1) {
+    n0 = normals_k[3 * a];
+    n1 = normals_k[3 * a + 1];
+    n2 = normals_k[3 * a + 2];
+  } else {
+    const double dx = px - cx, dy = py - cy, dz = pz - cz;
+    dist = sqrt(dx * dx + dy * dy + dz * dz);
+    n0 = dx / dist;
+    n1 = dy / dist;
+    n2 = dz / dist;
+  }
+  int ax = 0;
+  double best = fabs(n0);
+  if (fabs(n1) < best) {
+    ax = 1;
+    best = fabs(n1);
+  }
+  if (fabs(n2) < best) ax = 2;
+  const double e0 = ax == 0, e1 = ax == 1, e2 = ax == 2;
+  double t10 = n1 * e2 - n2 * e1, t11 = n2 * e0 - n0 * e2, t12 = n0 * e1 - n1 * e0;
+  const double nt = sqrt(t10 * t10 + t11 * t11 + t12 * t12);
+  t10 /= nt;
+  t11 /= nt;
+  t12 /= nt;
+  const double t20 = n1 * t12 - n2 * t11, t21 = n2 * t10 - n0 * t12, t22 = n0 * t11 - n1 * t10;
+  const double rx = px - anchors[3 * a], ry = py - anchors[3 * a + 1], rz = pz - anchors[3 * a + 2];
+  const double dn = kind == 1 ? n0 * rx + n1 * ry + n2 * rz : dist - radius;
+  T* Ca = C + 9 * a;
+  Ca[0] = (T)n0;
+  Ca[1] = (T)n1;
+  Ca[2] = (T)n2;
+  Ca[3] = (T)t10;
+  Ca[4] = (T)t11;
+  Ca[5] = (T)t12;
+  Ca[6] = (T)t20;
+  Ca[7] = (T)t21;
+  Ca[8] = (T)t22;
+  delta[3 * a] = (T)dn;
+  delta[3 * a + 1] = (T)(t10 * rx + t11 * ry + t12 * rz);
+  delta[3 * a + 2] = (T)(t20 * rx + t21 * ry + t22 * rz);
+}
+
+// ------------------------------------------------------------------ launchers
+template <class T>
+static int build_WH_T(Scene* s) {
+  cudaStream_t st = s->ctx->stream;
+  const int m = s->m, ns = s->ns, words = s->words;
+  const int64_t ldx = s->ldx;
+  T* X = (T*)s->X.p;
+  if (m == 0) return ICR_OK;
+  cudaError_t e = cudaMemsetAsync(s->bitmap.p, 0, (size_t)ns * words * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset bitmap");
+  k_reach_mark<<<(4 * m + 255) / 256, 256, 0, st>>>((const int*)s->nodes.p, m, (const int*)s->node_super.p,
+                                                     (const int*)s->parent.p, ns, (uint32_t*)s->bitmap.p, words);
+  LAUNCH_OK("k_reach_mark");
+  const int bt = ((words + 31) / 32) * 32;
+  k_reach_rows<<<ns, bt, bt * sizeof(int), st>>>((const uint32_t*)s->bitmap.p, words, m, (int*)s->wprefix.p,
+                                                  (int*)s->qcount.p, (int*)s->qidx.p);
+  LAUNCH_OK("k_reach_rows");
+  k_reach_parentpos<<<dim3((m + 255) / 256, ns), 256, 0, st>>>(
+      (const uint32_t*)s->bitmap.p, (const int*)s->wprefix.p, words, m, (const int*)s->parent.p,
+      (const int*)s->qcount.p, (const int*)s->qidx.p, (int*)s->qpos.p);
+  LAUNCH_OK("k_reach_parentpos");
+  const int ntiles = (m + TCC - 1) / TCC;
+  for (const Level& lv : s->levels) {
+    k_trsm<T><<<lv.count * ntiles, SOLVE_THREADS, 0, st>>>(
+        (const int*)s->level_list.p, lv.first, ntiles, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
+        (const int64_t*)s->val_ptr.p, (const T*)s->L.p, (const int*)s->child_ptr.p, (const int*)s->child_list.p,
+        (const int*)s->relidx.p, (const int64_t*)s->fr_ptr.p, (const int*)s->node_super.p, (const int*)s->nodes.p,
+        (const T*)s->bary.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qpos.p, m, X, ldx);
+    LAUNCH_OK("k_trsm");
+    if (lv.rmax > 0) {
+      const int nrt = (lv.rmax + UR - 1) / UR;
+      k_update<T><<<lv.count * nrt * ntiles, SOLVE_THREADS, 0, st>>>(
+          (const int*)s->level_list.p, lv.first, nrt, ntiles, (const int*)s->super_ptr.p,
+          (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->L.p,
+          (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, ldx);
+      LAUNCH_OK("k_update");
+    }
+  }
+  const int64_t nr = 3 * (int64_t)m;
+  e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset WH");
+  const int ntc = (int)((nr + CT - 1) / CT);
+  const int npairs = ntc * (ntc + 1) / 2;
+  k_contract<T><<<dim3(npairs, ns), 256, 0, st>>>(ntc, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p,
+                                                  (const int*)s->qcount.p, (const int*)s->qidx.p, m,
+                                                  (const double*)s->dinvsqrt.p, X, ldx, (T*)s->WH.p, nr);
+  LAUNCH_OK("k_contract");
+  k_symmetrize<T><<<dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st>>>((int)nr, (T*)s->WH.p);
+  LAUNCH_OK("k_symmetrize");
+  return ICR_OK;
+}
+
+int launch_build_WH(Scene* s) { return s->prec == ICR_FP64 ? build_WH_T<double>(s) : build_WH_T<float>(s); }
+
+template <class T>
+static int update_W_T(Scene* s) {
+  const int m = s->m;
+  if (m == 0) return ICR_OK;
+  dim3 grid((m + 15) / 16, (m + 15) / 16);
+  k_update_W<T><<<grid, dim3(16, 16), 0, s->ctx->stream>>>(m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p);
+  LAUNCH_OK("k_update_W");
+  return ICR_OK;
+}
+
+int launch_update_W(Scene* s) { return s->prec == ICR_FP64 ? update_W_T<double>(s) : update_W_T<float>(s); }
+
+template <class T>
+static int pgs_T(Scene* s, int warm, int want_res) {
+  cudaStream_t st = s->ctx->stream;
+  const int m = s->m;
+  PgsDevStats* ds = (PgsDevStats*)s->stats.p;
+  cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(PgsDevStats), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset stats");
+  if (m == 0) return ICR_OK;
+  const size_t smem = (3 * (size_t)m + 96 + 96 * 97) * sizeof(T);
+  if (smem > 227 * 1024) {
+    set_error("solve_friction: %d contacts exceed the single-CTA PGS shared-memory capacity", m);
+    return ICR_EINVAL;
+  }
+  e = cudaFuncSetAttribute(k_pgs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
+  k_pgs<T><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, (const T*)s->delta.p,
+                                  (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
+  LAUNCH_OK("k_pgs");
+  if (want_res) {
+    const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
+    k_pgs_residual<T><<<(m + 7) / 8, 256, 0, st>>>(m, (const T*)s->W.p, (const T*)s->delta.p, (const T*)s->mu.p,
+                                                   (const T*)s->lam.p, rel, ds);
+    LAUNCH_OK("k_pgs_residual");
+  }
+  return ICR_OK;
+}
+
+int launch_pgs(Scene* s, int warm, int want_res) {
+  return s->prec == ICR_FP64 ? pgs_T<double>(s, warm, want_res) : pgs_T<float>(s, warm, want_res);
+}
+
+template <class T>
+static int prox_T(Scene* s) {
+  cudaStream_t st = s->ctx->stream;
+  const int m = s->m;
+  if (m == 0) return ICR_OK;
+  double* u = (double*)s->u.p;
+  k_prox_u<T><<<(m + 127) / 128, 128, 0, st>>>(m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u);
+  LAUNCH_OK("k_prox_u");
+  k_prox_p<T><<<(3 * m + 7) / 8, 256, 0, st>>>(m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p,
+                                               u + 3 * (size_t)m);
+  LAUNCH_OK("k_prox_p");
+  return ICR_OK;
+}
+
+int launch_update_proximity(Scene* s) { return s->prec == ICR_FP64 ? prox_T<double>(s) : prox_T<float>(s); }
+
+template <class T>
+static int correct_T(Scene* s) {
+  cudaStream_t st = s->ctx->stream;
+  const int m = s->m, n = s->n;
+  if (m == 0) {
+    cudaError_t e = cudaMemsetAsync(s->dq.p, 0, (size_t)n * sizeof(T), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset dq");
+    return ICR_OK;
+  }
+  k_cast_u<T><<<(3 * m + 255) / 256, 256, 0, st>>>(3 * m, (const double*)s->u.p, (T*)s->ut.p);
+  LAUNCH_OK("k_cast_u");
+  k_xu<T><<<(n + 7) / 8, 256, 0, st>>>(n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
+                                       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
+                                       m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinv.p,
+                                       (T*)s->y.p);
+  LAUNCH_OK("k_xu");
+  const size_t smem = (size_t)s->wmax * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_bsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bsolve)");
+  }
+  for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
+    const Level& lv = s->levels[l];
+    k_bsolve<T><<<lv.count, 256, smem, st>>>((const int*)s->level_list.p, lv.first, (const int*)s->super_ptr.p,
+                                             (const int64_t*)s->rowpat_ptr.p, (const int*)s->rowpat.p,
+                                             (const int64_t*)s->val_ptr.p, (const T*)s->L.p, (const T*)s->y.p,
+                                             (T*)s->dq.p);
+    LAUNCH_OK("k_bsolve");
+  }
+  return ICR_OK;
+}
+
+int launch_correct_motion(Scene* s) { return s->prec == ICR_FP64 ? correct_T<double>(s) : correct_T<float>(s); }
+
+template <class T>
+static int linearize_T(Scene* s, int k) {
+  const int m = s->m;
+  if (m == 0) return ICR_OK;
+  const double* nk = s->obst_kind == 1 ? (const double*)s->obst_normals.p + (size_t)k * m * 3 : nullptr;
+  k_linearize<T><<<(m + 127) / 128, 128, 0, s->ctx->stream>>>(
+      m, s->obst_kind, nk, (const double*)s->obst_anchors.p, s->center[0], s->center[1], s->center[2], s->radius,
+      (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p);
+  LAUNCH_OK("k_linearize");
+  return ICR_OK;
+}
+
+int launch_linearize(Scene* s, int k) { return s->prec == ICR_FP64 ? linearize_T<double>(s, k) : linearize_T<float>(s, k); }
+
+}  // namespace icr

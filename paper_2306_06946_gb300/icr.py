@@ -1,0 +1,271 @@
+"""Python binding of libicr (ctypes): argument marshalling only.
+
+Every function here forwards to the C ABI of the same name declared in
+include/icr.h; all arithmetic of the constraint-resolution path runs in the
+library's CUDA kernels.  The library must have been built
+(``paper_2306_06946_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libicr.so")
+
+OK, EINVAL, ENOTSPD, ESTATE, ENOMEM, ENOCONV, ETIMEOUT, ECUDA = range(8)
+FP32, FP64 = 0, 1
+FIELD = {"WH": 0, "W": 1, "LAMBDA": 2, "P": 3, "DELTA": 4, "C": 5, "MU": 6, "U": 7,
+         "REACH_PTR": 8, "REACH_IDX": 9}
+_INT_FIELDS = {"REACH_PTR", "REACH_IDX"}
+
+# every symbol include/icr.h declares
+EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes_in_use", "icr_scene_create",
+           "icr_scene_destroy", "icr_set_params", "icr_set_system", "icr_set_mapping", "icr_set_proximity",
+           "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere", "icr_linearize",
+           "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
+           "icr_get", "icr_field_bytes", "icr_set_field")
+
+
+class IcrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libicr error {code}: {msg}")
+        self.code = code
+
+
+class Params(ct.Structure):
+    _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double)]
+
+
+class PgsStats(ct.Structure):
+    _fields_ = [("sweeps", ct.c_int32), ("n_separated", ct.c_int32), ("n_stick", ct.c_int32),
+                ("n_slip", ct.c_int32), ("eps", ct.c_double), ("res_normal", ct.c_double),
+                ("res_cone", ct.c_double), ("res_stick", ct.c_double), ("res_slip", ct.c_double)]
+
+
+_lib = None
+P = ct.c_void_p
+
+
+def lib() -> ct.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2306_06946_gb300.build.build()")
+        L = ct.CDLL(LIB_PATH)
+        L.icr_last_error.restype = ct.c_char_p
+        L.icr_last_error.argtypes = []
+        sigs = {
+            "icr_ctx_create": [ct.POINTER(P), ct.c_int, P, ct.c_uint64],
+            "icr_ctx_destroy": [P],
+            "icr_ctx_bytes_in_use": [P, ct.POINTER(ct.c_uint64)],
+            "icr_scene_create": [P, ct.POINTER(P), ct.POINTER(Params)],
+            "icr_scene_destroy": [P],
+            "icr_set_params": [P, ct.POINTER(Params)],
+            "icr_set_system": [P, ct.c_int32, ct.c_int32, P, P, P, P, P, P, P],
+            "icr_set_mapping": [P, ct.c_int32, P, P],
+            "icr_set_proximity": [P, P],
+            "icr_reset_proximity": [P],
+            "icr_scene_launches": [P, ct.POINTER(ct.c_uint64)],
+            "icr_update_directions": [P, P, P, P],
+            "icr_set_obstacle_plane": [P, ct.c_int32, P, P],
+            "icr_set_obstacle_sphere": [P, P, ct.c_double, P],
+            "icr_linearize": [P, ct.c_int32],
+            "icr_build_WH": [P],
+            "icr_update_W": [P],
+            "icr_solve_friction": [P, ct.c_int, ct.POINTER(PgsStats)],
+            "icr_update_proximity": [P, P],
+            "icr_correct_motion": [P, P, ct.c_int],
+            "icr_get": [P, ct.c_int32, P, ct.c_size_t],
+            "icr_field_bytes": [P, ct.c_int32, ct.POINTER(ct.c_size_t)],
+            "icr_set_field": [P, ct.c_int32, P, ct.c_size_t],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise IcrError(code, lib().icr_last_error().decode())
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(P)
+
+
+def _arr(x, dtype, shape=None):
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+class Context:
+    """icr_ctx: one device, one CUDA stream (a raw cudaStream_t handle, 0 for
+    the legacy default stream) and an HBM budget in bytes (0 = none)."""
+
+    def __init__(self, device: int = 0, stream: int = 0, hbm_budget: int = 0):
+        h = P()
+        _check(lib().icr_ctx_create(ct.byref(h), device, P(stream or None), hbm_budget))
+        self.h = h
+
+    @classmethod
+    def on_torch_stream(cls, device: int = 0, hbm_budget: int = 0):
+        import torch
+        return cls(device, torch.cuda.current_stream(device).cuda_stream, hbm_budget)
+
+    def bytes_in_use(self) -> int:
+        v = ct.c_uint64()
+        _check(lib().icr_ctx_bytes_in_use(self.h, ct.byref(v)))
+        return int(v.value)
+
+    def close(self):
+        if self.h:
+            lib().icr_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """icr_scene: one deformable body and its contacts."""
+
+    def __init__(self, ctx: Context, precision: int = FP32, n_sweeps: int = 50, tol: float = 0.0):
+        self.ctx = ctx
+        self.params = Params(precision, n_sweeps, tol)
+        h = P()
+        _check(lib().icr_scene_create(ctx.h, ct.byref(h), ct.byref(self.params)))
+        self.h = h
+        self.n = 0
+        self.m = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().icr_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, n_sweeps: int | None = None, tol: float | None = None):
+        if n_sweeps is not None:
+            self.params.n_sweeps = n_sweeps
+        if tol is not None:
+            self.params.tol = tol
+        _check(lib().icr_set_params(self.h, ct.byref(self.params)))
+
+    def set_system(self, n, super_ptr, rowpat_ptr, rowpat, val_ptr, Lpanels, D, parent):
+        sp = _arr(super_ptr, np.int32)
+        rp = _arr(rowpat_ptr, np.int64)
+        rw = _arr(rowpat, np.int32)
+        vp = _arr(val_ptr, np.int64)
+        Lv = _arr(Lpanels, np.float64)
+        Dv = _arr(D, np.float64)
+        pa = _arr(parent, np.int32)
+        _check(lib().icr_set_system(self.h, int(n), int(sp.size - 1), _ptr(sp), _ptr(rp), _ptr(rw), _ptr(vp),
+                                    _ptr(Lv), _ptr(Dv), _ptr(pa)))
+        self.n = int(n)
+
+    def set_mapping(self, nodes, bary):
+        nd = _arr(nodes, np.int32).reshape(-1, 4)
+        bw = _arr(bary, np.float64).reshape(-1, 4)
+        _check(lib().icr_set_mapping(self.h, int(nd.shape[0]), _ptr(nd), _ptr(bw)))
+        self.m = int(nd.shape[0])
+
+    def set_proximity(self, p):
+        _check(lib().icr_set_proximity(self.h, _ptr(_arr(p, np.float64))))
+
+    def reset_proximity(self):
+        _check(lib().icr_reset_proximity(self.h))
+
+    def launches(self) -> int:
+        v = ct.c_uint64()
+        _check(lib().icr_scene_launches(self.h, ct.byref(v)))
+        return int(v.value)
+
+    def update_directions(self, C, delta, mu=None):
+        mu_a = None if mu is None else _arr(mu, np.float64)
+        _check(lib().icr_update_directions(self.h, _ptr(_arr(C, np.float64)), _ptr(_arr(delta, np.float64)),
+                                           _ptr(mu_a)))
+
+    def set_obstacle_plane(self, normals, anchors):
+        nr = _arr(normals, np.float64)
+        _check(lib().icr_set_obstacle_plane(self.h, int(nr.size // max(1, 3 * self.m)) if self.m else 1,
+                                            _ptr(nr), _ptr(_arr(anchors, np.float64))))
+
+    def set_obstacle_sphere(self, center, radius, anchors):
+        _check(lib().icr_set_obstacle_sphere(self.h, _ptr(_arr(center, np.float64)), float(radius),
+                                             _ptr(_arr(anchors, np.float64))))
+
+    def linearize(self, k: int):
+        _check(lib().icr_linearize(self.h, int(k)))
+
+    def build_WH(self):
+        _check(lib().icr_build_WH(self.h))
+
+    def update_W(self):
+        _check(lib().icr_update_W(self.h))
+
+    def solve_friction(self, warm_start: bool = False, stats: bool = False):
+        """Returns None, or a dict of the FP64 stats when ``stats``; a run that
+        stops above a positive tol reports converged=False instead of raising."""
+        if not stats:
+            _check(lib().icr_solve_friction(self.h, int(bool(warm_start)), None))
+            return None
+        st = PgsStats()
+        code = lib().icr_solve_friction(self.h, int(bool(warm_start)), ct.byref(st))
+        if code not in (OK, ENOCONV):
+            _check(code)
+        out = {f: getattr(st, f) for f, _ in PgsStats._fields_}
+        out["converged"] = code == OK
+        return out
+
+    def update_proximity(self, want_dp: bool = False):
+        if not want_dp:
+            _check(lib().icr_update_proximity(self.h, None))
+            return None
+        dp = np.empty(3 * self.m)
+        _check(lib().icr_update_proximity(self.h, _ptr(dp)))
+        return dp
+
+    def correct_motion(self, want_dq: bool = True, reset: bool = True, out: np.ndarray | None = None):
+        dq = None
+        if want_dq:
+            dq = out if out is not None else np.empty(self.n)
+        _check(lib().icr_correct_motion(self.h, _ptr(dq), int(bool(reset))))
+        return dq
+
+    def field_bytes(self, field: str) -> int:
+        v = ct.c_size_t()
+        _check(lib().icr_field_bytes(self.h, FIELD[field], ct.byref(v)))
+        return int(v.value)
+
+    def get(self, field: str) -> np.ndarray:
+        nb = self.field_bytes(field)
+        dt = np.int32 if field in _INT_FIELDS else np.float64
+        a = np.empty(nb // np.dtype(dt).itemsize, dtype=dt)
+        _check(lib().icr_get(self.h, FIELD[field], _ptr(a), nb))
+        if field in ("WH", "W"):
+            a = a.reshape(3 * self.m, 3 * self.m)
+        elif field == "C":
+            a = a.reshape(self.m, 3, 3)
+        elif field == "P":
+            a = a.reshape(self.m, 3)
+        return a
+
+    def set_field(self, field: str, values):
+        v = _arr(values, np.float64)
+        _check(lib().icr_set_field(self.h, FIELD[field], _ptr(v), v.nbytes))

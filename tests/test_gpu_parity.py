@@ -1,0 +1,306 @@
+"""GPU path (through the C ABI) against the FP64 oracle.
+
+Tolerances: FP32 path, W_H and W within 1e-5 relative Frobenius error and
+lambda~ within 1e-4; FP64 path, W_H within 1e-12, lambda~ within 1e-9 and the
+contact classification identical.  Integer work (the etree reach) is bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import delassus as dl
+from oracle import pgs as pg
+
+from gpu_helpers import (classify, make_scene, margin_mask, oracle_fast, oracle_reach, oracle_WH, rel,
+                         scene)
+
+pytestmark = pytest.mark.gpu
+
+SCENES = ["beam_c0", "beam_mid", "liver_c1", "beam_one"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2306_06946_gb300 import build, icr
+    build.build()
+    return icr.Context(0)
+
+
+# ---------------------------------------------------------------- a1 reach (bit-exact)
+@pytest.mark.parametrize("name", SCENES)
+def test_reach_is_bitexact(ctx, name):
+    from paper_2306_06946_gb300 import icr
+    sc = make_scene(ctx, name, icr.FP32)
+    sc.build_WH()
+    ptr = sc.get("REACH_PTR")
+    idx = sc.get("REACH_IDX")
+    ref = oracle_reach(name)
+    assert ptr.size == len(ref) + 1
+    for s, lst in enumerate(ref):
+        assert idx[ptr[s]:ptr[s + 1]].tolist() == lst
+
+
+# ---------------------------------------------------------------- a2-a4 W_H
+@pytest.mark.parametrize("name", SCENES)
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
+def test_WH_matches_oracle(ctx, name, prec, tol):
+    sc = make_scene(ctx, name, prec)
+    sc.build_WH()
+    WH = sc.get("WH")
+    ref = oracle_WH(name)
+    assert rel(WH, ref) < tol
+    assert np.array_equal(WH, WH.T)
+
+
+def test_WH_rebuild_is_repeatable(ctx):
+    from paper_2306_06946_gb300 import icr
+    sc = make_scene(ctx, "beam_mid", icr.FP64)
+    sc.build_WH()
+    a = sc.get("WH")
+    sc.build_WH()
+    b = sc.get("WH")
+    assert rel(a, b) < 1e-14
+
+
+# ---------------------------------------------------------------- a5 device linearisation
+@pytest.mark.parametrize("name", ["beam_c0", "liver_c1"])
+def test_device_linearize_matches_scene_rule(ctx, name):
+    from paper_2306_06946_gb300 import icr
+    s = scene(name)
+    sc = make_scene(ctx, name, icr.FP64)
+    for k in range(min(2, s.n_newton)):
+        sc.linearize(k)
+        C, delta = s.linearize(s.p0, k)
+        assert np.abs(sc.get("C") - C).max() < 1e-14
+        assert np.abs(sc.get("DELTA") - delta).max() < 1e-15
+
+
+# ---------------------------------------------------------------- a6 W = C W_H C^T
+@pytest.mark.parametrize("name", SCENES)
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
+def test_W_matches_oracle(ctx, name, prec, tol):
+    s = scene(name)
+    sc = make_scene(ctx, name, prec)
+    sc.build_WH()
+    C, delta = s.linearize(s.p0, 0)
+    sc.update_directions(C, delta, s.mu)
+    sc.update_W()
+    W = sc.get("W")
+    ref = dl.delassus_fast(C, oracle_WH(name))
+    assert rel(W, ref) < tol
+    assert np.array_equal(W, W.T)
+
+
+# ---------------------------------------------------------------- a7 PGS on a given W
+@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1"])
+def test_pgs_fp64_matches_oracle_exactly_in_classification(ctx, name):
+    from paper_2306_06946_gb300 import icr
+    s = scene(name)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_fast(C, oracle_WH(name))
+    lam_ref, sweeps, eps_ref = pg.pgs(W, delta, s.mu, sweeps=s.n_sweeps)
+    sc = make_scene(ctx, name, icr.FP64)
+    sc.set_field("W", W)
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    st = sc.solve_friction(stats=True)
+    lam = sc.get("LAMBDA")
+    assert st["sweeps"] == s.n_sweeps
+    assert rel(lam, lam_ref) < 1e-9
+    assert np.array_equal(classify(lam, s.mu), classify(lam_ref, s.mu))
+    assert abs(st["eps"] - eps_ref) <= 1e-6 * max(eps_ref, 1e-12) + 1e-12
+    cls = classify(lam_ref, s.mu)
+    assert st["n_separated"] == int((cls == 0).sum())
+    assert st["n_slip"] + st["n_stick"] == int((cls > 0).sum())
+
+
+@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1"])
+def test_pgs_fp32_matches_oracle(ctx, name):
+    from paper_2306_06946_gb300 import icr
+    s = scene(name)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_fast(C, oracle_WH(name))
+    lam_ref, _, _ = pg.pgs(W, delta, s.mu, sweeps=s.n_sweeps)
+    sc = make_scene(ctx, name, icr.FP32)
+    sc.set_field("W", W)
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    sc.solve_friction()
+    lam = sc.get("LAMBDA")
+    assert rel(lam, lam_ref) < 1e-4
+    ok = margin_mask(lam_ref, s.mu)
+    assert np.array_equal(classify(lam, s.mu, 1e-5)[ok], classify(lam_ref, s.mu)[ok])
+
+
+def test_pgs_tol_stops_at_the_oracle_sweep(ctx):
+    from paper_2306_06946_gb300 import icr
+    s = scene("beam_c0")
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_fast(C, oracle_WH("beam_c0"))
+    lam_ref, sweeps, eps = pg.pgs(W, delta, s.mu, sweeps=2000, tol=1e-8)
+    assert sweeps < 2000
+    sc = make_scene(ctx, "beam_c0", icr.FP64, n_sweeps=2000, tol=1e-8)
+    sc.set_field("W", W)
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    st = sc.solve_friction(stats=True)
+    assert st["converged"] and st["sweeps"] == sweeps
+    assert rel(sc.get("LAMBDA"), lam_ref) < 1e-9
+
+
+def test_pgs_reports_noconv(ctx):
+    from paper_2306_06946_gb300 import icr
+    s = scene("beam_c0")
+    C, delta = s.linearize(s.p0, 0)
+    sc = make_scene(ctx, "beam_c0", icr.FP64, n_sweeps=2, tol=1e-14)
+    sc.set_field("W", dl.delassus_fast(C, oracle_WH("beam_c0")))
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    st = sc.solve_friction(stats=True)
+    assert not st["converged"] and st["sweeps"] == 2
+
+
+def test_pgs_warm_start_continues(ctx):
+    # 20 sweeps, then 30 more warm-started, equal 50 sweeps from zero
+    from paper_2306_06946_gb300 import icr
+    s = scene("beam_mid")
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_fast(C, oracle_WH("beam_mid"))
+    lam_ref, _, _ = pg.pgs(W, delta, s.mu, sweeps=50)
+    sc = make_scene(ctx, "beam_mid", icr.FP64, n_sweeps=20)
+    sc.set_field("W", W)
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    sc.solve_friction()
+    sc.set_params(n_sweeps=30)
+    sc.solve_friction(warm_start=True)
+    assert rel(sc.get("LAMBDA"), lam_ref) < 1e-10
+
+
+# ---------------------------------------------------------------- a8 + a9
+@pytest.mark.parametrize("name", ["beam_c0", "liver_c1"])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 2e-5)])
+def test_proximity_and_correction_match_oracle(ctx, name, prec, tol):
+    s = scene(name)
+    sc = make_scene(ctx, name, prec)
+    sc.build_WH()
+    rng = np.random.default_rng(5)
+    lam = np.abs(rng.normal(size=3 * s.m))
+    C, delta = s.linearize(s.p0, 0)
+    sc.update_directions(C, delta, s.mu)
+    sc.set_field("LAMBDA", lam)
+    dp = sc.update_proximity(want_dp=True)
+    uk = np.einsum("aji,aj->ai", C, lam.reshape(-1, 3)).reshape(-1)
+    WH = oracle_WH(name)
+    assert rel(dp, WH @ uk) < tol
+    assert rel(sc.get("P").reshape(-1) - s.p0.reshape(-1), WH @ uk) < tol
+    assert rel(sc.get("U"), uk) < (1e-15 if prec == 1 else 1e-7)
+    dq = sc.correct_motion()
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    ref = dl.correct_motion(dl.SystemSolver(s.A), H, uk)
+    assert rel(dq, ref) < (1e-12 if prec == 1 else 1e-4)
+    assert np.abs(sc.get("U")).max() == 0.0        # reset
+
+
+# ---------------------------------------------------------------- full step (Alg. 3)
+@pytest.mark.parametrize("name,prec", [("beam_c0", 1), ("beam_c0", 0), ("beam_mid", 0), ("liver_c1", 1),
+                                       ("liver_c1", 0)])
+def test_newton_step_matches_oracle(ctx, name, prec):
+    from paper_2306_06946_gb300 import driver
+    s = scene(name)
+    ref = oracle_fast(name)
+    sc = make_scene(ctx, name, prec)
+    sc.build_WH()
+    lam_scale = max(np.linalg.norm(it["lam"]) for it in ref["iters"])
+    disp_ref = ref["p"].reshape(-1) - s.p0.reshape(-1)
+    lam_tol = 1e-9 if prec == 1 else 1e-4
+    for k, it in enumerate(ref["iters"]):
+        sc.linearize(k)
+        if k == 0:
+            sc.set_field("MU", s.mu)
+        sc.update_W()
+        sc.solve_friction()
+        lam = sc.get("LAMBDA")
+        assert np.linalg.norm(lam - it["lam"]) <= lam_tol * lam_scale, f"iteration {k}"
+        if prec == 1:
+            assert np.array_equal(classify(lam, s.mu), classify(it["lam"], s.mu))
+        sc.update_proximity()
+    disp = sc.get("P").reshape(-1) - s.p0.reshape(-1)
+    assert rel(disp, disp_ref) < lam_tol
+    dq = sc.correct_motion()
+    assert rel(dq, ref["dq"]) < (1e-9 if prec == 1 else 1e-4)
+    # the driver's call sequence gives the same step
+    sc2 = make_scene(ctx, name, prec)
+    dq2, _ = driver.newton_step(sc2, s.n_newton, mu=s.mu)
+    assert rel(dq2, dq) < (1e-12 if prec == 1 else 1e-5)
+
+
+def test_host_directions_match_device_directions(ctx):
+    from paper_2306_06946_gb300 import driver, icr
+    s = scene("liver_c1")
+    a = make_scene(ctx, "liver_c1", icr.FP64)
+    dq_dev, _ = driver.newton_step(a, s.n_newton, mu=s.mu)
+    b = make_scene(ctx, "liver_c1", icr.FP64)
+    dq_host, _ = driver.newton_step(b, s.n_newton, mu=s.mu, linearize=s.linearize)
+    assert rel(dq_host, dq_dev) < 1e-12
+
+
+# ---------------------------------------------------------------- edge cases and errors
+def test_no_contacts(ctx):
+    from paper_2306_06946_gb300 import icr
+    s = scene("beam_c0")
+    sc = icr.Scene(ctx, precision=icr.FP32)
+    from paper_2306_06946_gb300 import driver
+    driver.load_system(sc, s.factor)
+    sc.set_mapping(np.zeros((0, 4), np.int32), np.zeros((0, 4)))
+    sc.build_WH()
+    sc.update_directions(np.zeros((0, 3, 3)), np.zeros(0))
+    sc.update_W()
+    st = sc.solve_friction(stats=True)
+    assert st["sweeps"] == 0 or st["n_separated"] == 0
+    sc.update_proximity()
+    assert np.all(sc.correct_motion() == 0)
+
+
+def test_call_order_and_argument_errors(ctx):
+    from paper_2306_06946_gb300 import driver, icr
+    s = scene("beam_c0")
+    sc = icr.Scene(ctx, precision=icr.FP32)
+    with pytest.raises(icr.IcrError) as e:
+        sc.build_WH()
+    assert e.value.code == icr.ESTATE
+    driver.load_system(sc, s.factor)
+    bad = s.bary.copy()
+    bad[0, 0] += 1e-6
+    with pytest.raises(icr.IcrError) as e:
+        sc.set_mapping(s.nodes, bad)
+    assert e.value.code == icr.EINVAL
+    with pytest.raises(icr.IcrError) as e:
+        sc.set_mapping(s.nodes + 10 ** 6, s.bary)
+    assert e.value.code == icr.EINVAL
+    sc.set_mapping(s.nodes, s.bary)
+    with pytest.raises(icr.IcrError) as e:
+        sc.update_W()
+    assert e.value.code == icr.ESTATE
+    C, delta = s.linearize(s.p0, 0)
+    C2 = C.copy()
+    C2[0, 0] *= 1.01
+    with pytest.raises(icr.IcrError) as e:
+        sc.update_directions(C2, delta)
+    assert e.value.code == icr.EINVAL
+    D = s.factor.D.copy()
+    D[5] = -1.0
+    sym = s.factor.sym
+    with pytest.raises(icr.IcrError) as e:
+        sc.set_system(sym.n, sym.super_ptr, sym.rowpat_ptr, sym.rowpat, s.factor.val_ptr, s.factor.Lpanels, D,
+                      sym.parent)
+    assert e.value.code == icr.ENOTSPD
+
+
+def test_hbm_budget_is_enforced():
+    from paper_2306_06946_gb300 import driver, icr
+    s = scene("liver_c1")
+    small = icr.Context(0, hbm_budget=1 << 20)
+    sc = icr.Scene(small, precision=icr.FP32)
+    with pytest.raises(icr.IcrError) as e:
+        driver.load_system(sc, s.factor)
+    assert e.value.code == icr.ENOMEM
