@@ -161,6 +161,11 @@ int icr_ctx_create(icr_ctx** out, int device, void* cuda_stream, uint64_t hbm_bu
 }
 
 int icr_ctx_destroy(icr_ctx* ctx) {
+  if (!ctx) return ICR_OK;
+  if (ctx->scenes > 0) {
+    ctx->destroyed = true;   // freed by the last icr_scene_destroy
+    return ICR_OK;
+  }
   delete ctx;
   return ICR_OK;
 }
@@ -202,6 +207,7 @@ int icr_scene_create(icr_ctx* ctx, icr_scene** out, const icr_params* params) {
     return ICR_ENOMEM;
   }
   s->ctx = ctx;
+  ctx->scenes++;
   s->params = *params;
   s->prec = params->precision;
   s->tsize = s->prec == ICR_FP64 ? 8 : 4;
@@ -219,7 +225,9 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->qidx, &s->qpos, &s->X, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
                  &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
+  icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
+  if (--c->scenes == 0 && c->destroyed) delete c;
   return ICR_OK;
 }
 

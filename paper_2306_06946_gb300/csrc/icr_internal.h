@@ -19,6 +19,8 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   uint64_t budget = 0;
   uint64_t in_use = 0;
+  int scenes = 0;          // live scenes; the context is freed after the last one
+  bool destroyed = false;  // icr_ctx_destroy was called while scenes were alive
 };
 
 // Device buffer owned by a scene, accounted against the context budget.

@@ -298,15 +298,32 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
   }
 }
 
-// ------------------------------------------------------------------ a3 + a4 contraction
+// ------------------------------------------------------------------ a3 pivot scaling
+// Y = D^-1/2 X in place on the first w rows of every front (one warp per DOF
+// row), the product taken in FP64 and rounded once to T.
+template <class T>
+__global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+                        const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                        const double* __restrict__ dinvsqrt, T* X, int64_t ldx) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const int s = dof_super[row];
+  const int ncol = 3 * qcount[s];
+  const double ds = dinvsqrt[row];
+  T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
+  for (int c = lane; c < ncol; c += 32) F[c] = (T)(ds * (double)F[c]);
+}
+
+// ------------------------------------------------------------------ a4 contraction
 // Block (tile pair I <= J of supernode s's local columns, s):
-// W_H[g(i), g(j)] += sum_k Y[k,i] Y[k,j],  Y = D^-1/2 X (scaling in FP64).
+// W_H[g(i), g(j)] += sum_k Y[k,i] Y[k,j] over the scaled fronts Y = D^-1/2 X.
 // Only the upper triangle (g(i) <= g(j)) is accumulated; k_symmetrize mirrors it.
 template <class T>
 __global__ void __launch_bounds__(256)
     k_contract(int ntc, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
                const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
-               const double* __restrict__ dinvsqrt, const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
+               const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
   const int s = blockIdx.y;
@@ -332,9 +349,8 @@ __global__ void __launch_bounds__(256)
     for (int e = tid; e < CK_ * CT; e += blockDim.x) {
       int k = e / CT, c = e % CT;
       int ca = I * CT + c, cb = J * CT + c;
-      double ds = (k < nb) ? dinvsqrt[c0 + kb + k] : 0.0;
-      sA[k][c] = (k < nb && ca < ncol) ? T(ds * (double)Xs[(int64_t)(kb + k) * ldx + ca]) : T(0);
-      sB[k][c] = (k < nb && cb < ncol) ? T(ds * (double)Xs[(int64_t)(kb + k) * ldx + cb]) : T(0);
+      sA[k][c] = (k < nb && ca < ncol) ? Xs[(int64_t)(kb + k) * ldx + ca] : T(0);
+      sB[k][c] = (k < nb && cb < ncol) ? Xs[(int64_t)(kb + k) * ldx + cb] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -404,130 +420,202 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 }
 
 // ------------------------------------------------------------------ a7 PGS
-// One CTA.  Contacts are taken in blocks of 32: all warps first form the
-// block's residuals r = delta + W lambda~ with the newest lambda~ and stage the
-// block's diagonal part of W; warp 0 then runs the block's contacts in order,
-// lane = contact, broadcasting every change of lambda~ so that later lanes fold
-// it into their residual.
-template <class T>
+// One CTA of 1024 threads.  The residual r = delta + W lambda~ of every row is
+// kept in shared memory.  Contacts are taken in blocks of BC; for each block:
+//   [A] all warps fold the previous block's lambda~ changes into this block's
+//       residuals (a BR x BR product with the prefetched cross block of W);
+//   [B] warp 0 runs the block's contacts in order (lane = contact), each lane
+//       folding the earlier lanes' changes into its residual, while warps
+//       1..31 fold the previous block's changes into all other residuals
+//       (streaming the previous block's rows of W) and prefetch the next
+//       block's diagonal block and cross block of W.
+// Visiting order, residual definition and local rule are those of Eq. "PGS"
+// with contacts in ascending order; only the summation order differs.
+template <class T, int BC>
 __global__ void __launch_bounds__(1024)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, const T* __restrict__ delta,
           const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
+  constexpr int BR = 3 * BC;
+  constexpr int LD = BR + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* lam = (T*)smraw;          // 3m
-  T* rblk = lam + 3 * m;       // 96
-  T* Wbb = rblk + 96;          // 96 x 97
+  T* r = lam + 3 * m;          // 3m
+  T* dl = r + 3 * m;           // 2 x BR: lambda~ changes of the last two blocks
+  T* WD = dl + 2 * BR;         // 2 x BR x LD: diagonal blocks (current, next)
+  T* WX = WD + 2 * BR * LD;    // BR x LD: W[next block rows, current block cols]
   __shared__ double red[32];
-  __shared__ int stop;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const int64_t ld = 3 * (int64_t)m;
-  for (int i = tid; i < 3 * m; i += blockDim.x) lam[i] = warm ? lam_g[i] : T(0);
-  if (tid == 0) stop = 0;
+  __shared__ int flag;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
+  const int n3 = 3 * m;
+  const int64_t ld = n3;
+  const int nblk = (m + BC - 1) / BC;
+  for (int i = tid; i < n3; i += nthr) lam[i] = warm ? lam_g[i] : T(0);
+  for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
   __syncthreads();
-  const int nblk = (m + 31) / 32;
-  double eps = 0.0;
-  int done = 0;
-  for (int sw = 0; sw < sweeps; ++sw) {
-    double dsum = 0.0;
-    for (int bi = 0; bi < nblk; ++bi) {
-      const int a0 = 32 * bi, nb = min(32, m - a0), R0 = 3 * a0, nr = 3 * nb;
-      for (int i = wid; i < nr; i += nw) {
-        const T* Wr = W + (int64_t)(R0 + i) * ld;
-        T acc = T(0);
-        for (int j = lane; j < 3 * m; j += 32) acc += Wr[j] * lam[j];
-        acc = warp_sum(acc);
-        if (lane == 0) rblk[i] = delta[R0 + i] + acc;
-      }
-      for (int e = tid; e < nr * nr; e += blockDim.x) {
-        int i = e / nr, j = e % nr;
-        Wbb[i * 97 + j] = W[(int64_t)(R0 + i) * ld + R0 + j];
-      }
-      __syncthreads();
-      if (wid == 0) {
-        const bool valid = lane < nb;
-        T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0;
-        if (valid) {
-          r0 = rblk[3 * lane];
-          r1 = rblk[3 * lane + 1];
-          r2 = rblk[3 * lane + 2];
-          l0 = lam[R0 + 3 * lane];
-          l1 = lam[R0 + 3 * lane + 1];
-          l2 = lam[R0 + 3 * lane + 2];
-          mua = mu[a0 + lane];
-        }
-        for (int i = 0; i < nb; ++i) {
-          T d0 = 0, d1 = 0, d2 = 0;
-          if (lane == i) {
-            const T* Wd = Wbb + (3 * i) * 97 + 3 * i;
-            const T Wnn = Wd[0], Wt1n = Wd[97], Wt2n = Wd[194];
-            const T wt = T(0.5) * (Wd[98] + Wd[196]);
-            T ln = l0 - r0 / Wnn;
-            ln = ln > T(0) ? ln : T(0);
-            const T dn = ln - l0;
-            const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
-            T lt1 = l1 - rt1 / wt, lt2 = l2 - rt2 / wt;
-            const T lim = mua * ln;
-            const T nt = hypot(lt1, lt2);
-            if (ln <= T(0)) {
-              lt1 = T(0);
-              lt2 = T(0);
-            } else if (nt > lim) {
-              const T sc = lim / nt;
-              lt1 *= sc;
-              lt2 *= sc;
-            }
-            d0 = ln - l0;
-            d1 = lt1 - l1;
-            d2 = lt2 - l2;
-            l0 = ln;
-            l1 = lt1;
-            l2 = lt2;
-            dsum += (double)d0 * (double)d0 + (double)d1 * (double)d1 + (double)d2 * (double)d2;
-          }
-          d0 = __shfl_sync(FULL, d0, i);
-          d1 = __shfl_sync(FULL, d1, i);
-          d2 = __shfl_sync(FULL, d2, i);
-          if (valid && lane > i) {
-            const T* Wl = Wbb + (3 * lane) * 97 + 3 * i;
-            r0 += Wl[0] * d0 + Wl[1] * d1 + Wl[2] * d2;
-            r1 += Wl[97] * d0 + Wl[98] * d1 + Wl[99] * d2;
-            r2 += Wl[194] * d0 + Wl[195] * d1 + Wl[196] * d2;
-          }
-        }
-        if (valid) {
-          lam[R0 + 3 * lane] = l0;
-          lam[R0 + 3 * lane + 1] = l1;
-          lam[R0 + 3 * lane + 2] = l2;
-        }
-      }
-      __syncthreads();
-    }
-    // eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
-    double nrm = 0.0;
-    for (int i = tid; i < 3 * m; i += blockDim.x) nrm += (double)lam[i] * (double)lam[i];
-    nrm = warp_sum(nrm);
-    if (wid == 0) dsum = warp_sum(dsum);
-    if (lane == 0) red[wid] = nrm;
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int k = 0; k < nw; ++k) tot += red[k];
-      eps = tot > 0.0 ? sqrt(dsum / tot) : 0.0;
-      red[0] = eps;
-      stop = (tol > 0.0 && eps <= tol) ? 1 : 0;
-    }
-    __syncthreads();
-    eps = red[0];
-    done = sw + 1;
-    const int brk = stop;
-    __syncthreads();
-    if (brk) break;
+  for (int row = wid; row < n3; row += 32) {
+    const T* Wr = W + (int64_t)row * ld;
+    T acc = T(0);
+    for (int j = lane; j < n3; j += 32) acc += Wr[j] * lam[j];
+    acc = warp_sum(acc);
+    if (lane == 0) r[row] = delta[row] + acc;
   }
-  for (int i = tid; i < 3 * m; i += blockDim.x) lam_g[i] = lam[i];
+  {
+    const int nr0 = 3 * min(BC, m);
+    for (int e = tid; e < nr0 * nr0; e += nthr) {
+      int i = e / nr0, j = e % nr0;
+      WD[i * LD + j] = W[(int64_t)i * ld + j];
+    }
+  }
+  __syncthreads();
+  int cur = 0, pb = -1, done = 0;
+  double eps = 0.0, dsum = 0.0;
+  const long total = (long)sweeps * nblk;
+  for (long t = 0; t < total; ++t) {
+    const int b = (int)(t % nblk);
+    const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0, nr = 3 * nb;
+    const int dc = (int)(t & 1);
+    T* dlc = dl + dc * BR;
+    const T* dlp = dl + (1 - dc) * BR;
+    const int pnr = pb >= 0 ? 3 * min(BC, m - pb * BC) : 0;
+    const int pR0 = pb >= 0 ? 3 * pb * BC : 0;
+    // [A] critical: this block's residuals take the previous block's changes
+    if (pb >= 0) {
+      for (int i = wid; i < nr; i += 32) {
+        T acc = T(0);
+        for (int j = lane; j < pnr; j += 32) acc += WX[i * LD + j] * dlp[j];
+        acc = warp_sum(acc);
+        if (lane == 0) r[R0 + i] += acc;
+      }
+    }
+    __syncthreads();
+    // [B]
+    if (wid == 0) {
+      const T* WDc = WD + cur * BR * LD;
+      const bool valid = lane < nb;
+      T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0;
+      if (valid) {
+        r0 = r[R0 + 3 * lane];
+        r1 = r[R0 + 3 * lane + 1];
+        r2 = r[R0 + 3 * lane + 2];
+        l0 = lam[R0 + 3 * lane];
+        l1 = lam[R0 + 3 * lane + 1];
+        l2 = lam[R0 + 3 * lane + 2];
+        mua = mu[a0 + lane];
+      }
+      T e0 = 0, e1 = 0, e2 = 0;
+      for (int i = 0; i < nb; ++i) {
+        T d0 = 0, d1 = 0, d2 = 0;
+        if (lane == i) {
+          const T* Wd = WDc + (3 * i) * LD + 3 * i;
+          const T Wnn = Wd[0], Wt1n = Wd[LD], Wt2n = Wd[2 * LD];
+          const T wt = T(0.5) * (Wd[LD + 1] + Wd[2 * LD + 2]);
+          T ln = l0 - r0 / Wnn;
+          ln = ln > T(0) ? ln : T(0);
+          const T dn = ln - l0;
+          const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
+          T lt1 = l1 - rt1 / wt, lt2 = l2 - rt2 / wt;
+          const T lim = mua * ln;
+          const T nt = hypot(lt1, lt2);
+          if (ln <= T(0)) {
+            lt1 = T(0);
+            lt2 = T(0);
+          } else if (nt > lim) {
+            const T sc = lim / nt;
+            lt1 *= sc;
+            lt2 *= sc;
+          }
+          d0 = ln - l0;
+          d1 = lt1 - l1;
+          d2 = lt2 - l2;
+          e0 = d0;
+          e1 = d1;
+          e2 = d2;
+          l0 = ln;
+          l1 = lt1;
+          l2 = lt2;
+          dsum += (double)d0 * (double)d0 + (double)d1 * (double)d1 + (double)d2 * (double)d2;
+        }
+        d0 = __shfl_sync(FULL, d0, i);
+        d1 = __shfl_sync(FULL, d1, i);
+        d2 = __shfl_sync(FULL, d2, i);
+        if (valid && lane > i) {
+          const T* Wl = WDc + (3 * lane) * LD + 3 * i;
+          r0 += Wl[0] * d0 + Wl[1] * d1 + Wl[2] * d2;
+          r1 += Wl[LD] * d0 + Wl[LD + 1] * d1 + Wl[LD + 2] * d2;
+          r2 += Wl[2 * LD] * d0 + Wl[2 * LD + 1] * d1 + Wl[2 * LD + 2] * d2;
+        }
+      }
+      if (valid) {
+        lam[R0 + 3 * lane] = l0;
+        lam[R0 + 3 * lane + 1] = l1;
+        lam[R0 + 3 * lane + 2] = l2;
+        dlc[3 * lane] = e0;
+        dlc[3 * lane + 1] = e1;
+        dlc[3 * lane + 2] = e2;
+      }
+    } else {
+      const int t2 = tid - 32, n2 = nthr - 32;
+      if (pb >= 0) {
+        for (int j = t2; j < n3; j += n2) {
+          if (j >= R0 && j < R0 + nr) continue;
+          T acc = T(0);
+#pragma unroll 8
+          for (int i = 0; i < pnr; ++i) acc += W[(int64_t)(pR0 + i) * ld + j] * dlp[i];
+          r[j] += acc;
+        }
+      }
+      if (t + 1 < total) {
+        const int bn = (b + 1) % nblk;
+        const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC);
+        T* WDn = WD + (1 - cur) * BR * LD;
+        for (int e = t2; e < nnr * nnr; e += n2) {
+          int i = e / nnr, j = e % nnr;
+          WDn[i * LD + j] = W[(int64_t)(n0 + i) * ld + n0 + j];
+        }
+        for (int e = t2; e < nnr * nr; e += n2) {
+          int i = e / nr, j = e % nr;
+          WX[i * LD + j] = W[(int64_t)(n0 + i) * ld + R0 + j];
+        }
+      }
+    }
+    __syncthreads();
+    if (b == nblk - 1) {
+      // eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
+      double nrm = 0.0;
+      for (int i = tid; i < n3; i += nthr) nrm += (double)lam[i] * (double)lam[i];
+      nrm = warp_sum(nrm);
+      if (lane == 0) red[wid] = nrm;
+      double ds = wid == 0 ? warp_sum(dsum) : 0.0;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < 32; ++k) tot += red[k];
+        const double e = tot > 0.0 ? sqrt(ds / tot) : 0.0;
+        red[0] = e;
+        flag = (tol > 0.0 && e <= tol) ? 1 : 0;
+      }
+      __syncthreads();
+      eps = red[0];
+      dsum = 0.0;
+      done = (int)(t / nblk) + 1;
+      const int brk = flag;
+      __syncthreads();
+      if (brk) break;
+    }
+    pb = b;
+    cur = 1 - cur;
+  }
+  for (int i = tid; i < n3; i += nthr) lam_g[i] = lam[i];
   if (tid == 0) {
     st->sweeps = done;
     st->eps = eps;
   }
+}
+
+template <class T, int BC>
+static size_t pgs_smem_bytes(int m) {
+  const size_t BR = 3 * BC, LD = BR + 1;
+  return (6 * (size_t)m + 2 * BR + 3 * BR * LD) * sizeof(T);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
@@ -609,12 +697,13 @@ __global__ void k_cast_u(int n, const double* __restrict__ u, T* ut) {
   if (i < n) ut[i] = (T)u[i];
 }
 
-// y = D^-1 X u, one warp per DOF row (X restricted to the contacts reaching it)
+// y = D^-1 X u = D^-1/2 (Y u), one warp per DOF row (Y holds the scaled front
+// rows, restricted to the contacts reaching them)
 template <class T>
 __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                      const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                      const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
-                     const T* __restrict__ ut, const double* __restrict__ dinv, T* y) {
+                     const T* __restrict__ ut, const double* __restrict__ dinvsqrt, T* y) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -625,7 +714,7 @@ __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __rest
   T acc = T(0);
   for (int c = lane; c < ncol; c += 32) acc += F[c] * ut[3 * q[c / 3] + c % 3];
   acc = warp_sum(acc);
-  if (lane == 0) y[row] = (T)(dinv[row] * (double)acc);
+  if (lane == 0) y[row] = (T)(dinvsqrt[row] * (double)acc);
 }
 
 // Backward solve L^T dq = y for the supernodes of one level (top-down).
@@ -763,14 +852,18 @@ static int build_WH_T(Scene* s) {
       LAUNCH_OK("k_update");
     }
   }
+  k_scale<T><<<(s->n + 7) / 8, 256, 0, st>>>(s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
+                                             (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
+                                             (const double*)s->dinvsqrt.p, X, ldx);
+  LAUNCH_OK("k_scale");
   const int64_t nr = 3 * (int64_t)m;
   e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset WH");
   const int ntc = (int)((nr + CT - 1) / CT);
   const int npairs = ntc * (ntc + 1) / 2;
   k_contract<T><<<dim3(npairs, ns), 256, 0, st>>>(ntc, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p,
-                                                  (const int*)s->qcount.p, (const int*)s->qidx.p, m,
-                                                  (const double*)s->dinvsqrt.p, X, ldx, (T*)s->WH.p, nr);
+                                                  (const int*)s->qcount.p, (const int*)s->qidx.p, m, X, ldx,
+                                                  (T*)s->WH.p, nr);
   LAUNCH_OK("k_contract");
   k_symmetrize<T><<<dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st>>>((int)nr, (T*)s->WH.p);
   LAUNCH_OK("k_symmetrize");
@@ -791,7 +884,7 @@ static int update_W_T(Scene* s) {
 
 int launch_update_W(Scene* s) { return s->prec == ICR_FP64 ? update_W_T<double>(s) : update_W_T<float>(s); }
 
-template <class T>
+template <class T, int BC>
 static int pgs_T(Scene* s, int warm, int want_res) {
   cudaStream_t st = s->ctx->stream;
   const int m = s->m;
@@ -799,15 +892,19 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(PgsDevStats), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset stats");
   if (m == 0) return ICR_OK;
-  const size_t smem = (3 * (size_t)m + 96 + 96 * 97) * sizeof(T);
+  const size_t smem = pgs_smem_bytes<T, BC>(m);
   if (smem > 227 * 1024) {
     set_error("solve_friction: %d contacts exceed the single-CTA PGS shared-memory capacity", m);
     return ICR_EINVAL;
   }
-  e = cudaFuncSetAttribute(k_pgs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
-  k_pgs<T><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, (const T*)s->delta.p,
-                                  (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(k_pgs<T, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
+    attr_set = true;
+  }
+  k_pgs<T, BC><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p,
+                                      (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
   LAUNCH_OK("k_pgs");
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
@@ -819,7 +916,7 @@ static int pgs_T(Scene* s, int warm, int want_res) {
 }
 
 int launch_pgs(Scene* s, int warm, int want_res) {
-  return s->prec == ICR_FP64 ? pgs_T<double>(s, warm, want_res) : pgs_T<float>(s, warm, want_res);
+  return s->prec == ICR_FP64 ? pgs_T<double, 16>(s, warm, want_res) : pgs_T<float, 32>(s, warm, want_res);
 }
 
 template <class T>
@@ -851,7 +948,7 @@ static int correct_T(Scene* s) {
   LAUNCH_OK("k_cast_u");
   k_xu<T><<<(n + 7) / 8, 256, 0, st>>>(n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
-                                       m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinv.p,
+                                       m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinvsqrt.p,
                                        (T*)s->y.p);
   LAUNCH_OK("k_xu");
   const size_t smem = (size_t)s->wmax * sizeof(T);
