@@ -893,15 +893,16 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (e != cudaSuccess) return cuda_fail(e, "memset stats");
   if (m == 0) return ICR_OK;
   const size_t smem = pgs_smem_bytes<T, BC>(m);
-  if (smem > 227 * 1024) {
+  // the opt-in limit (227 KiB) covers static plus dynamic shared memory
+  if (smem > 226 * 1024) {
     set_error("solve_friction: %d contacts exceed the single-CTA PGS shared-memory capacity", m);
     return ICR_EINVAL;
   }
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(k_pgs<T, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  static size_t attr_bytes = 48 * 1024;
+  if (smem > attr_bytes) {
+    e = cudaFuncSetAttribute(k_pgs<T, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
-    attr_set = true;
+    attr_bytes = smem;
   }
   k_pgs<T, BC><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p,
                                       (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
