@@ -9,8 +9,10 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "icr_internal.h"
@@ -131,6 +133,54 @@ static int download_T(Scene* s, const DBuf& src, double* dst, size_t count) {
   return ICR_OK;
 }
 
+// Solve operator of every supernode, from its factor panel (FP64):
+//   G_s = [ L_ss^-1 ; L[R_s, s] L_ss^-1 ],  (w + r) x w, column-major,
+// so that the forward solve of a front is X_s = L_ss^-1 F_top and
+// U_s = F_R - (L_Rs L_ss^-1) F_top, and the backward solve is
+// dq_s = G_s^T [y_s ; -dq_R].  Supernodes are spread over host threads.
+static void compute_G(int ns, const std::vector<int32_t>& sp, const std::vector<int64_t>& rp,
+                      const std::vector<int64_t>& vp, const double* Lp, std::vector<double>& G) {
+  G.assign(vp[ns], 0.0);
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    std::vector<double> z;
+    for (int k = next++; k < ns; k = next++) {
+      const int w = sp[k + 1] - sp[k];
+      const int64_t r = rp[k + 1] - rp[k];
+      const int64_t ld = w + r;
+      const double* L = Lp + vp[k];
+      double* Gk = G.data() + vp[k];
+      // L_ss^-1, one column at a time: z = L^-1 e_j by column-oriented substitution
+      z.assign(w, 0.0);
+      for (int j = 0; j < w; ++j) {
+        std::fill(z.begin(), z.end(), 0.0);
+        z[j] = 1.0;
+        for (int c = j; c < w; ++c) {
+          const double zc = z[c];
+          if (zc == 0.0) continue;
+          const double* Lc = L + (int64_t)c * ld;
+          for (int i = c + 1; i < w; ++i) z[i] -= Lc[i] * zc;
+        }
+        double* Gj = Gk + (int64_t)j * ld;
+        for (int i = j; i < w; ++i) Gj[i] = z[i];
+        // P[:, j] = sum_{c >= j} L[R, c] Z[c, j]
+        double* Pj = Gj + w;
+        for (int c = j; c < w; ++c) {
+          const double zc = z[c];
+          if (zc == 0.0) continue;
+          const double* Lc = L + (int64_t)c * ld + w;
+          for (int64_t i = 0; i < r; ++i) Pj[i] += Lc[i] * zc;
+        }
+      }
+    }
+  };
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < nt; ++t) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+}
+
 extern "C" {
 
 const char* icr_last_error(void) { return g_err.c_str(); }
@@ -219,10 +269,10 @@ int icr_scene_destroy(icr_scene* s) {
   if (!s) return ICR_OK;
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->ctx->stream);
-  DBuf* all[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->L, &s->dinv, &s->dinvsqrt,
+  DBuf* all[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->G, &s->dinv, &s->dinvsqrt,
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
-                 &s->qidx, &s->qpos, &s->X, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
+                 &s->qidx, &s->qpos, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
                  &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -374,13 +424,16 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
     dis[i] = 1.0 / std::sqrt(D[i]);
   }
 
+  std::vector<double> Gpanels;
+  compute_G(ns, sp, rp, vp, Lp, Gpanels);
+
   RET(set_device(s));
   CK(cudaStreamSynchronize(s->ctx->stream));
   RET(dalloc(s, s->super_ptr, (ns + 1) * sizeof(int32_t)));
   RET(dalloc(s, s->rowpat_ptr, (ns + 1) * sizeof(int64_t)));
   RET(dalloc(s, s->rowpat, std::max<int64_t>(1, rp[ns]) * sizeof(int32_t)));
   RET(dalloc(s, s->val_ptr, (ns + 1) * sizeof(int64_t)));
-  RET(dalloc(s, s->L, vp[ns] * s->tsize));
+  RET(dalloc(s, s->G, vp[ns] * s->tsize));
   RET(dalloc(s, s->dinv, n * sizeof(double)));
   RET(dalloc(s, s->dinvsqrt, n * sizeof(double)));
   RET(dalloc(s, s->parent, ns * sizeof(int32_t)));
@@ -395,7 +448,7 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   RET(upload(s, s->rowpat_ptr, rp.data(), ns + 1));
   if (rp[ns]) RET(upload(s, s->rowpat, rowpat, rp[ns]));
   RET(upload(s, s->val_ptr, vp.data(), ns + 1));
-  RET(upload_T(s, s->L, Lp, vp[ns]));
+  RET(upload_T(s, s->G, Gpanels.data(), vp[ns]));
   RET(upload(s, s->dinv, dinv.data(), n));
   RET(upload(s, s->dinvsqrt, dis.data(), n));
   RET(upload(s, s->parent, par.data(), ns));
@@ -469,6 +522,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->X, (size_t)s->total_front_rows * ldx * T));
+  RET(dalloc(s, s->Ftop, (size_t)s->n * ldx * T));
   RET(dalloc(s, s->WH, 9 * mm * mm * T));
   RET(dalloc(s, s->W, 9 * mm * mm * T));
   RET(dalloc(s, s->C, 9 * mm * T));

@@ -6,10 +6,11 @@
 // (Eq. "schur complemnt reformulated" with A = L D L^T):
 //   a1  k_reach_*      which contacts' columns of H^T reach each supernode
 //                      (etree ancestors of the supernodes owning their nodes)
-//   a2  k_trsm         per supernode and 32-contact column tile: assemble the
-//                      front (H^T entries + children's update blocks), then the
-//                      unit lower triangular solve of its diagonal block
-//       k_update       U_s = F_R - L[R_s, s] X_s, the update passed to the parent
+//   a2  k_assemble     per supernode and 32-contact column tile: the front's
+//                      H^T entries plus the children's update blocks
+//       k_front_gemm   X_s = L_ss^-1 F_top and U_s = F_R - L_Rs L_ss^-1 F_top,
+//                      one register-tiled product with the precomputed
+//                      G_s = [L_ss^-1; L_Rs L_ss^-1] (per level, all tiles)
 //   a3+a4 k_contract   W_H += Y_s^T Y_s with Y_s = D_s^-1/2 X_s (FP64 scaling)
 // Newton iteration (Alg. 3):
 //   a6  k_update_W     W = C W_H C^T, one 3x3 block pair per thread
@@ -17,7 +18,8 @@
 //       k_pgs_residual FP64 complementarity / cone residuals
 //   a8  k_prox_*       p += W_H C^T lambda~, u += C^T lambda~
 // End of step:
-//   a9  k_xu, k_bsolve dq = L^-T D^-1 X u
+//   a9  k_xu, k_bsolve dq = L^-T D^-1 X u, the backward solve as
+//                      dq_s = G_s^T [y_s; -dq_R] per level, top-down
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -39,7 +41,6 @@ static constexpr int TCC = 32;            // contacts per column tile of the for
 static constexpr int TCOLS = 3 * TCC;     // columns per tile
 static constexpr int KB = 32;             // diagonal block of the triangular solves
 static constexpr int SOLVE_THREADS = 192; // 2 x 96 columns
-static constexpr int UR = 64;             // rows per update tile
 static constexpr int CT = 64;             // contraction output tile
 static constexpr int CK_ = 16;            // contraction k-chunk
 
@@ -127,19 +128,23 @@ __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int
 }
 
 // ------------------------------------------------------------------ a2 forward solve
-// Block (supernode s of the level, 32-contact tile t).  The front of s holds
-// w + r rows (its columns, then R_s) and 3 |Q_s| columns (contacts of Q_s in
-// ascending order, 3 axes each), row-major with leading dimension ldx.
+// The front of supernode s has w + r rows (its DOF columns, then R_s) and
+// 3 |Q_s| columns (the contacts of Q_s in ascending order, 3 axes each).
+// Its first w rows are assembled in Ftop (indexed by DOF row), the last r rows
+// in the front itself; after the solve the front holds X_s then U_s:
+//   X_s = L_ss^-1 F_top,  U_s = F_R - (L_Rs L_ss^-1) F_top,
+// one dense product with the precomputed operator G_s = [L_ss^-1; L_Rs L_ss^-1].
+
+// Block (supernode s of the level, 32-contact tile): assemble the tile,
+// H^T entries plus the children's update blocks (extend-add).
 template <class T>
 __global__ void __launch_bounds__(SOLVE_THREADS)
-    k_trsm(const int* __restrict__ level_list, int lvl_first, int ntiles, const int* __restrict__ super_ptr,
-           const int64_t* __restrict__ rowpat_ptr, const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp,
-           const int* __restrict__ child_ptr, const int* __restrict__ child_list, const int* __restrict__ relidx,
-           const int64_t* __restrict__ fr_ptr, const int* __restrict__ node_super, const int* __restrict__ nodes,
-           const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
-           const int* __restrict__ qpos, int m, T* X, int64_t ldx) {
-  __shared__ T sL[KB][KB + 1];
-  __shared__ T sX[KB][TCOLS + 1];
+    k_assemble(const int* __restrict__ level_list, int lvl_first, int ntiles, const int* __restrict__ super_ptr,
+               const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ child_ptr,
+               const int* __restrict__ child_list, const int* __restrict__ relidx,
+               const int64_t* __restrict__ fr_ptr, const int* __restrict__ node_super,
+               const int* __restrict__ nodes, const T* __restrict__ bary, const int* __restrict__ qcount,
+               const int* __restrict__ qidx, const int* __restrict__ qpos, int m, T* X, T* Ftop, int64_t ldx) {
   const int li = blockIdx.x / ntiles, t = blockIdx.x % ntiles;
   const int s = level_list[lvl_first + li];
   const int nq = qcount[s];
@@ -149,19 +154,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
   const int ncols = 3 * kc;
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
   const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-  const int nrows = w + r;
-  const int64_t ldL = nrows;
-  const T* L = Lp + val_ptr[s];
-  T* F = X + fr_ptr[s] * ldx + 3 * k0;
+  T* Ft = Ftop + (int64_t)c0 * ldx + 3 * k0;
+  T* Uf = X + (fr_ptr[s] + w) * ldx + 3 * k0;
   const int tid = threadIdx.x;
-
-  // front tile = 0
-  for (int64_t e = tid; e < (int64_t)nrows * ncols; e += blockDim.x) {
-    int i = (int)(e / ncols), j = (int)(e % ncols);
-    F[i * ldx + j] = T(0);
+  const int j = tid % TCOLS, i0 = tid / TCOLS, di = SOLVE_THREADS / TCOLS;
+  if (j < ncols) {
+    for (int i = i0; i < w; i += di) Ft[(int64_t)i * ldx + j] = T(0);
+    for (int i = i0; i < r; i += di) Uf[(int64_t)i * ldx + j] = T(0);
   }
   __syncthreads();
-  // + H^T: column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
+  // H^T: column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
   for (int e = tid; e < 4 * kc; e += blockDim.x) {
     int k = e >> 2, i = e & 3;
     int a = qidx[(size_t)s * m + k0 + k];
@@ -169,82 +171,46 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
     if (node_super[node] == s) {
       T b = bary[4 * a + i];
       int row = 3 * node - c0;
-      for (int d = 0; d < 3; ++d) atomicAdd(&F[(int64_t)(row + d) * ldx + 3 * k + d], b);
+      for (int d = 0; d < 3; ++d) atomicAdd(&Ft[(int64_t)(row + d) * ldx + 3 * k + d], b);
     }
   }
   __syncthreads();
-  // + extend-add of every child's update block (rows mapped by relidx,
-  // contacts by their position in this supernode's list)
   for (int ci = child_ptr[s]; ci < child_ptr[s + 1]; ++ci) {
     const int c = child_list[ci];
     const int nqc = qcount[c];
     const int* pc = qpos + (size_t)c * m;
     const int j0 = lower_bound_dev(pc, nqc, k0), j1 = lower_bound_dev(pc, nqc, k0 + kc);
-    if (j1 > j0) {
+    const int cc = 3 * (j1 - j0);
+    if (j < cc) {
       const int wc = super_ptr[c + 1] - super_ptr[c];
       const int rc = (int)(rowpat_ptr[c + 1] - rowpat_ptr[c]);
       const int* ri = relidx + rowpat_ptr[c];
-      const T* U = X + (fr_ptr[c] + wc) * ldx + 3 * j0;
-      const int cc = 3 * (j1 - j0);
-      for (int64_t e = tid; e < (int64_t)rc * cc; e += blockDim.x) {
-        int i = (int)(e / cc), jj = (int)(e % cc);
-        int col = 3 * (pc[j0 + jj / 3] - k0) + jj % 3;
-        F[(int64_t)ri[i] * ldx + col] += U[(int64_t)i * ldx + jj];
-      }
-    }
-    __syncthreads();
-  }
-  // unit lower triangular solve on the first w rows, 32-row blocks
-  for (int kb = 0; kb < w; kb += KB) {
-    const int nb = min(KB, w - kb);
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-      int k = e / nb, i = e % nb;
-      sL[i][k] = L[(int64_t)(kb + k) * ldL + kb + i];
-    }
-    for (int e = tid; e < nb * ncols; e += blockDim.x) {
-      int i = e / ncols, j = e % ncols;
-      sX[i][j] = F[(int64_t)(kb + i) * ldx + j];
-    }
-    __syncthreads();
-    if (tid < ncols) {
-      for (int k = 0; k < nb; ++k) {
-        T xk = sX[k][tid];
-        for (int i = k + 1; i < nb; ++i) sX[i][tid] -= sL[i][k] * xk;
-      }
-    }
-    __syncthreads();
-    for (int e = tid; e < nb * ncols; e += blockDim.x) {
-      int i = e / ncols, j = e % ncols;
-      F[(int64_t)(kb + i) * ldx + j] = sX[i][j];
-    }
-    for (int rb = kb + nb; rb < w; rb += KB) {
-      const int nr = min(KB, w - rb);
-      __syncthreads();
-      for (int e = tid; e < nr * nb; e += blockDim.x) {
-        int k = e / nr, i = e % nr;
-        sL[i][k] = L[(int64_t)(kb + k) * ldL + rb + i];
-      }
-      __syncthreads();
-      for (int e = tid; e < nr * ncols; e += blockDim.x) {
-        int i = e / ncols, j = e % ncols;
-        T acc = T(0);
-        for (int k = 0; k < nb; ++k) acc += sL[i][k] * sX[k][j];
-        F[(int64_t)(rb + i) * ldx + j] -= acc;
+      const T* U = X + (fr_ptr[c] + wc) * ldx + 3 * j0 + j;
+      const int col = 3 * (pc[j0 + j / 3] - k0) + j % 3;
+      for (int i = i0; i < rc; i += di) {
+        const int tr = ri[i];
+        const T v = U[(int64_t)i * ldx];
+        if (tr < w)
+          Ft[(int64_t)tr * ldx + col] += v;
+        else
+          Uf[(int64_t)(tr - w) * ldx + col] += v;
       }
     }
     __syncthreads();
   }
 }
 
-// Block (supernode, 64-row tile of R_s, 32-contact tile): U -= L[R_s, s] X_s.
+// Block (supernode, 64-row tile of the w + r front rows, 32-contact tile):
+// out = G_s[rows, :] F_top; top rows store X_s = out, bottom rows U_s -= out.
+static constexpr int GR = 64;   // rows per tile
 template <class T>
-__global__ void __launch_bounds__(SOLVE_THREADS)
-    k_update(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
-             const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
-             const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp, const int64_t* __restrict__ fr_ptr,
-             const int* __restrict__ qcount, T* X, int64_t ldx) {
-  __shared__ T sL[UR][KB + 1];
-  __shared__ T sX[KB][TCOLS + 1];
+__global__ void __launch_bounds__(256)
+    k_front_gemm(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
+                 const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
+                 const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
+  __shared__ __align__(16) T sG[KB][GR + 4];
+  __shared__ __align__(16) T sF[KB][TCOLS + 4];
   int b = blockIdx.x;
   const int t = b % ntiles;
   b /= ntiles;
@@ -256,44 +222,56 @@ __global__ void __launch_bounds__(SOLVE_THREADS)
   if (k0 >= nq) return;
   const int ncols = 3 * min(TCC, nq - k0);
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
-  const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-  const int i0 = rt * UR;
-  if (i0 >= r) return;
-  const int nr = min(UR, r - i0);
-  const int64_t ldL = w + r;
-  const T* L = Lp + val_ptr[s];
-  const T* Xs = X + fr_ptr[s] * ldx + 3 * k0;
-  T* U = X + (fr_ptr[s] + w) * ldx + 3 * k0;
-  const int tid = threadIdx.x;
-  const int j = tid % TCOLS, g = tid / TCOLS;
-  T acc[32];
+  const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  const int row0 = rt * GR;
+  if (row0 >= nrows) return;
+  const int64_t ldG = nrows;
+  const T* Gs = G + val_ptr[s];
+  const T* Ft = Ftop + (int64_t)c0 * ldx + 3 * k0;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][6];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) acc[q] = T(0);
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[q][c] = T(0);
   for (int kb = 0; kb < w; kb += KB) {
     const int nb = min(KB, w - kb);
-    __syncthreads();
-    for (int e = tid; e < UR * nb; e += blockDim.x) {
-      int k = e / UR, i = e % UR;
-      sL[i][k] = (i < nr) ? L[(int64_t)(kb + k) * ldL + w + i0 + i] : T(0);
+    for (int e = tid; e < KB * GR; e += 256) {
+      const int k = e / GR, i = e % GR;
+      sG[k][i] = (k < nb && row0 + i < nrows) ? Gs[(int64_t)(kb + k) * ldG + row0 + i] : T(0);
     }
-    for (int e = tid; e < nb * ncols; e += blockDim.x) {
-      int i = e / ncols, jj = e % ncols;
-      sX[i][jj] = Xs[(int64_t)(kb + i) * ldx + jj];
+    for (int e = tid; e < KB * TCOLS; e += 256) {
+      const int k = e / TCOLS, jj = e % TCOLS;
+      sF[k][jj] = (k < nb && jj < ncols) ? Ft[(int64_t)(kb + k) * ldx + jj] : T(0);
     }
     __syncthreads();
-    if (j < ncols) {
-      for (int k = 0; k < nb; ++k) {
-        T xv = sX[k][j];
+#pragma unroll 8
+    for (int k = 0; k < KB; ++k) {
+      T a[4], bv[6];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) acc[q] += sL[g * 32 + q][k] * xv;
-      }
+      for (int q = 0; q < 4; ++q) a[q] = sG[k][4 * ty + q];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) bv[c] = sF[k][6 * tx + c];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[q][c] += a[q] * bv[c];
     }
+    __syncthreads();
   }
-  if (j < ncols) {
+  T* F = X + fr_ptr[s] * ldx + 3 * k0;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      int i = g * 32 + q;
-      if (i < nr) U[(int64_t)(i0 + i) * ldx + j] -= acc[q];
+  for (int q = 0; q < 4; ++q) {
+    const int row = row0 + 4 * ty + q;
+    if (row >= nrows) continue;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const int col = 6 * tx + c;
+      if (col >= ncols) continue;
+      if (row < w)
+        F[(int64_t)row * ldx + col] = acc[q][c];
+      else
+        F[(int64_t)row * ldx + col] -= acc[q][c];
     }
   }
 }
@@ -468,7 +446,8 @@ __global__ void __launch_bounds__(1024)
   }
   __syncthreads();
   int cur = 0, pb = -1, done = 0;
-  double eps = 0.0, dsum = 0.0;
+  double eps = 0.0;
+  T dsum = T(0);   // warp 0: sum of squared changes this sweep (FP64 stays off the serial chain)
   const long total = (long)sweeps * nblk;
   for (long t = 0; t < total; ++t) {
     const int b = (int)(t % nblk);
@@ -515,7 +494,7 @@ __global__ void __launch_bounds__(1024)
           const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
           T lt1 = l1 - rt1 / wt, lt2 = l2 - rt2 / wt;
           const T lim = mua * ln;
-          const T nt = hypot(lt1, lt2);
+          const T nt = sqrt(lt1 * lt1 + lt2 * lt2);
           if (ln <= T(0)) {
             lt1 = T(0);
             lt2 = T(0);
@@ -533,7 +512,7 @@ __global__ void __launch_bounds__(1024)
           l0 = ln;
           l1 = lt1;
           l2 = lt2;
-          dsum += (double)d0 * (double)d0 + (double)d1 * (double)d1 + (double)d2 * (double)d2;
+          dsum += d0 * d0 + d1 * d1 + d2 * d2;
         }
         d0 = __shfl_sync(FULL, d0, i);
         d1 = __shfl_sync(FULL, d1, i);
@@ -585,7 +564,7 @@ __global__ void __launch_bounds__(1024)
       for (int i = tid; i < n3; i += nthr) nrm += (double)lam[i] * (double)lam[i];
       nrm = warp_sum(nrm);
       if (lane == 0) red[wid] = nrm;
-      double ds = wid == 0 ? warp_sum(dsum) : 0.0;
+      double ds = wid == 0 ? warp_sum((double)dsum) : 0.0;
       __syncthreads();
       if (tid == 0) {
         double tot = 0.0;
@@ -596,7 +575,7 @@ __global__ void __launch_bounds__(1024)
       }
       __syncthreads();
       eps = red[0];
-      dsum = 0.0;
+      dsum = T(0);
       done = (int)(t / nblk) + 1;
       const int brk = flag;
       __syncthreads();
@@ -717,49 +696,26 @@ __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __rest
   if (lane == 0) y[row] = (T)(dinvsqrt[row] * (double)acc);
 }
 
-// Backward solve L^T dq = y for the supernodes of one level (top-down).
+// Backward solve L^T dq = y for the supernodes of one level (top-down):
+// dq_s = G_s^T [y_s ; -dq_R], one warp per DOF column of the supernode.
 template <class T>
 __global__ void __launch_bounds__(256)
-    k_bsolve(const int* __restrict__ level_list, int lvl_first, const int* __restrict__ super_ptr,
+    k_bsolve(const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
              const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
-             const int64_t* __restrict__ val_ptr, const T* __restrict__ Lp, const T* __restrict__ y, T* dq) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* z = (T*)smraw;
-  const int s = level_list[lvl_first + blockIdx.x];
+             const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const T* __restrict__ y, T* dq) {
+  const int s = level_list[lvl_first + blockIdx.x / nchunk];
+  const int k = (blockIdx.x % nchunk) * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+  if (k >= w) return;
   const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-  const int64_t ldL = w + r;
-  const T* L = Lp + val_ptr[s];
+  const T* Gk = G + val_ptr[s] + (int64_t)k * (w + r);
   const int* R = rowpat + rowpat_ptr[s];
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (int k = wid; k < w; k += nw) {
-    const T* Lc = L + (int64_t)k * ldL + w;
-    T acc = T(0);
-    for (int i = lane; i < r; i += 32) acc += Lc[i] * dq[R[i]];
-    acc = warp_sum(acc);
-    if (lane == 0) z[k] = y[c0 + k] - acc;
-  }
-  __syncthreads();
-  for (int kb = ((w - 1) / 32) * 32; kb >= 0; kb -= 32) {
-    const int nb = min(32, w - kb);
-    if (wid == 0) {
-      T zl = (lane < nb) ? z[kb + lane] : T(0);
-      for (int k = nb - 1; k >= 0; --k) {
-        const T xk = __shfl_sync(FULL, zl, k);
-        if (lane < k) zl -= L[(int64_t)(kb + lane) * ldL + kb + k] * xk;
-      }
-      if (lane < nb) z[kb + lane] = zl;
-    }
-    __syncthreads();
-    for (int kp = tid; kp < kb; kp += blockDim.x) {
-      const T* Lc = L + (int64_t)kp * ldL + kb;
-      T acc = T(0);
-      for (int i = 0; i < nb; ++i) acc += Lc[i] * z[kb + i];
-      z[kp] -= acc;
-    }
-    __syncthreads();
-  }
-  for (int k = tid; k < w; k += blockDim.x) dq[c0 + k] = z[k];
+  T acc = T(0);
+  for (int i = (k & ~31) + lane; i < w; i += 32) acc += Gk[i] * y[c0 + i];
+  for (int i = lane; i < r; i += 32) acc -= Gk[w + i] * dq[R[i]];
+  acc = warp_sum(acc);
+  if (lane == 0) dq[c0 + k] = acc;
 }
 
 // ------------------------------------------------------------------ linearisation
@@ -837,20 +793,18 @@ static int build_WH_T(Scene* s) {
   LAUNCH_OK("k_reach_parentpos");
   const int ntiles = (m + TCC - 1) / TCC;
   for (const Level& lv : s->levels) {
-    k_trsm<T><<<lv.count * ntiles, SOLVE_THREADS, 0, st>>>(
+    k_assemble<T><<<lv.count * ntiles, SOLVE_THREADS, 0, st>>>(
         (const int*)s->level_list.p, lv.first, ntiles, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
-        (const int64_t*)s->val_ptr.p, (const T*)s->L.p, (const int*)s->child_ptr.p, (const int*)s->child_list.p,
-        (const int*)s->relidx.p, (const int64_t*)s->fr_ptr.p, (const int*)s->node_super.p, (const int*)s->nodes.p,
-        (const T*)s->bary.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qpos.p, m, X, ldx);
-    LAUNCH_OK("k_trsm");
-    if (lv.rmax > 0) {
-      const int nrt = (lv.rmax + UR - 1) / UR;
-      k_update<T><<<lv.count * nrt * ntiles, SOLVE_THREADS, 0, st>>>(
-          (const int*)s->level_list.p, lv.first, nrt, ntiles, (const int*)s->super_ptr.p,
-          (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->L.p,
-          (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, ldx);
-      LAUNCH_OK("k_update");
-    }
+        (const int*)s->child_ptr.p, (const int*)s->child_list.p, (const int*)s->relidx.p,
+        (const int64_t*)s->fr_ptr.p, (const int*)s->node_super.p, (const int*)s->nodes.p, (const T*)s->bary.p,
+        (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qpos.p, m, X, (T*)s->Ftop.p, ldx);
+    LAUNCH_OK("k_assemble");
+    const int nrt = (lv.wmax + lv.rmax + GR - 1) / GR;
+    k_front_gemm<T><<<lv.count * nrt * ntiles, 256, 0, st>>>(
+        (const int*)s->level_list.p, lv.first, nrt, ntiles, (const int*)s->super_ptr.p,
+        (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
+        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
+    LAUNCH_OK("k_front_gemm");
   }
   k_scale<T><<<(s->n + 7) / 8, 256, 0, st>>>(s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                              (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
@@ -952,17 +906,13 @@ static int correct_T(Scene* s) {
                                        m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinvsqrt.p,
                                        (T*)s->y.p);
   LAUNCH_OK("k_xu");
-  const size_t smem = (size_t)s->wmax * sizeof(T);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_bsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_bsolve)");
-  }
   for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
     const Level& lv = s->levels[l];
-    k_bsolve<T><<<lv.count, 256, smem, st>>>((const int*)s->level_list.p, lv.first, (const int*)s->super_ptr.p,
-                                             (const int64_t*)s->rowpat_ptr.p, (const int*)s->rowpat.p,
-                                             (const int64_t*)s->val_ptr.p, (const T*)s->L.p, (const T*)s->y.p,
-                                             (T*)s->dq.p);
+    const int nchunk = (lv.wmax + 7) / 8;
+    k_bsolve<T><<<lv.count * nchunk, 256, 0, st>>>((const int*)s->level_list.p, lv.first, nchunk,
+                                                   (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
+                                                   (const int*)s->rowpat.p, (const int64_t*)s->val_ptr.p,
+                                                   (const T*)s->G.p, (const T*)s->y.p, (T*)s->dq.p);
     LAUNCH_OK("k_bsolve");
   }
   return ICR_OK;
