@@ -404,11 +404,34 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 //       residuals (a BR x BR product with the prefetched cross block of W);
 //   [B] warp 0 runs the block's contacts in order (lane = contact), each lane
 //       folding the earlier lanes' changes into its residual, while warps
-//       1..31 fold the previous block's changes into all other residuals
-//       (streaming the previous block's rows of W) and prefetch the next
-//       block's diagonal block and cross block of W.
+//       1..31 fold the previous block's non-zero changes into all other
+//       residuals (streaming those rows of W) and prefetch, with cp.async,
+//       the next block's diagonal block and cross block of W.
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
-// with contacts in ascending order; only the summation order differs.
+// with contacts in ascending order; the local rule uses reciprocals and an
+// rsqrt scale, so results differ from the plain formulas by rounding only.
+template <class T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) {
+  return rsqrtf(x);
+}
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) {
+  return 1.0 / sqrt(x);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <class T, int BC>
 __global__ void __launch_bounds__(1024)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, const T* __restrict__ delta,
@@ -472,7 +495,9 @@ __global__ void __launch_bounds__(1024)
       const T* WDc = WD + cur * BR * LD;
       const bool valid = lane < nb;
       T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0;
+      T iWnn = 0, Wt1n = 0, Wt2n = 0, iwt = 0;
       if (valid) {
+        const T* Wo = WDc + (3 * lane) * LD + 3 * lane;
         r0 = r[R0 + 3 * lane];
         r1 = r[R0 + 3 * lane + 1];
         r2 = r[R0 + 3 * lane + 2];
@@ -480,26 +505,35 @@ __global__ void __launch_bounds__(1024)
         l1 = lam[R0 + 3 * lane + 1];
         l2 = lam[R0 + 3 * lane + 2];
         mua = mu[a0 + lane];
+        iWnn = T(1) / Wo[0];
+        Wt1n = Wo[LD];
+        Wt2n = Wo[2 * LD];
+        iwt = T(1) / (T(0.5) * (Wo[LD + 1] + Wo[2 * LD + 2]));
       }
       T e0 = 0, e1 = 0, e2 = 0;
       for (int i = 0; i < nb; ++i) {
+        // coupling of my residual to contact i (independent of the chain)
+        T w[9];
+        const bool upd = valid && lane > i;
+        const T* Wl = WDc + (3 * lane) * LD + 3 * i;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) w[3 * q + c] = upd ? Wl[q * LD + c] : T(0);
         T d0 = 0, d1 = 0, d2 = 0;
         if (lane == i) {
-          const T* Wd = WDc + (3 * i) * LD + 3 * i;
-          const T Wnn = Wd[0], Wt1n = Wd[LD], Wt2n = Wd[2 * LD];
-          const T wt = T(0.5) * (Wd[LD + 1] + Wd[2 * LD + 2]);
-          T ln = l0 - r0 / Wnn;
+          T ln = l0 - r0 * iWnn;
           ln = ln > T(0) ? ln : T(0);
           const T dn = ln - l0;
           const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
-          T lt1 = l1 - rt1 / wt, lt2 = l2 - rt2 / wt;
+          T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
           const T lim = mua * ln;
-          const T nt = sqrt(lt1 * lt1 + lt2 * lt2);
+          const T s2 = lt1 * lt1 + lt2 * lt2;
           if (ln <= T(0)) {
             lt1 = T(0);
             lt2 = T(0);
-          } else if (nt > lim) {
-            const T sc = lim / nt;
+          } else if (s2 > lim * lim) {
+            const T sc = lim * rsqrt_t(s2);
             lt1 *= sc;
             lt2 *= sc;
           }
@@ -517,11 +551,10 @@ __global__ void __launch_bounds__(1024)
         d0 = __shfl_sync(FULL, d0, i);
         d1 = __shfl_sync(FULL, d1, i);
         d2 = __shfl_sync(FULL, d2, i);
-        if (valid && lane > i) {
-          const T* Wl = WDc + (3 * lane) * LD + 3 * i;
-          r0 += Wl[0] * d0 + Wl[1] * d1 + Wl[2] * d2;
-          r1 += Wl[LD] * d0 + Wl[LD + 1] * d1 + Wl[LD + 2] * d2;
-          r2 += Wl[2 * LD] * d0 + Wl[2 * LD + 1] * d1 + Wl[2 * LD + 2] * d2;
+        if (d0 != T(0) || d1 != T(0) || d2 != T(0)) {
+          r0 += w[0] * d0 + w[1] * d1 + w[2] * d2;
+          r1 += w[3] * d0 + w[4] * d1 + w[5] * d2;
+          r2 += w[6] * d0 + w[7] * d1 + w[8] * d2;
         }
       }
       if (valid) {
@@ -534,28 +567,32 @@ __global__ void __launch_bounds__(1024)
       }
     } else {
       const int t2 = tid - 32, n2 = nthr - 32;
+      // prefetch first, so the copies run while this warp streams
+      if (t + 1 < total && t2 < 10 * BR) {
+        const int bn = (b + 1) % nblk;
+        const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC);
+        T* WDn = WD + (1 - cur) * BR * LD;
+        const int j = t2 % BR;
+        for (int i = t2 / BR; i < nnr; i += 10) {
+          if (j < nnr) cp_async<sizeof(T)>(&WDn[i * LD + j], &W[(int64_t)(n0 + i) * ld + n0 + j]);
+          if (j < nr) cp_async<sizeof(T)>(&WX[i * LD + j], &W[(int64_t)(n0 + i) * ld + R0 + j]);
+        }
+        cp_async_commit();
+      }
       if (pb >= 0) {
         for (int j = t2; j < n3; j += n2) {
           if (j >= R0 && j < R0 + nr) continue;
           T acc = T(0);
+          const T* Wc = W + (int64_t)pR0 * ld + j;
 #pragma unroll 8
-          for (int i = 0; i < pnr; ++i) acc += W[(int64_t)(pR0 + i) * ld + j] * dlp[i];
+          for (int i = 0; i < pnr; ++i) {
+            const T di = dlp[i];
+            if (di != T(0)) acc += Wc[(int64_t)i * ld] * di;
+          }
           r[j] += acc;
         }
       }
-      if (t + 1 < total) {
-        const int bn = (b + 1) % nblk;
-        const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC);
-        T* WDn = WD + (1 - cur) * BR * LD;
-        for (int e = t2; e < nnr * nnr; e += n2) {
-          int i = e / nnr, j = e % nnr;
-          WDn[i * LD + j] = W[(int64_t)(n0 + i) * ld + n0 + j];
-        }
-        for (int e = t2; e < nnr * nr; e += n2) {
-          int i = e / nr, j = e % nr;
-          WX[i * LD + j] = W[(int64_t)(n0 + i) * ld + R0 + j];
-        }
-      }
+      cp_async_wait_all();
     }
     __syncthreads();
     if (b == nblk - 1) {
