@@ -118,6 +118,36 @@ static int upload(Scene* s, DBuf& dst, const V* src, size_t count) {
   return ICR_OK;
 }
 
+// Host doubles (rows x cols, dense) into a device matrix with leading dimension ld.
+static int upload_T_2d(Scene* s, DBuf& dst, int64_t ld, const double* src, size_t rows, size_t cols) {
+  if (rows == 0 || cols == 0) return ICR_OK;
+  const size_t es = s->tsize;
+  std::vector<unsigned char> tmp(rows * cols * es);
+  if (s->prec == ICR_FP64)
+    std::memcpy(tmp.data(), src, tmp.size());
+  else
+    for (size_t i = 0; i < rows * cols; ++i) ((float*)tmp.data())[i] = (float)src[i];
+  CK(cudaMemcpy2DAsync(dst.p, ld * es, tmp.data(), cols * es, cols * es, rows, cudaMemcpyHostToDevice,
+                       s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  return ICR_OK;
+}
+
+// Device matrix with leading dimension ld -> host doubles (synchronises).
+static int download_T_2d(Scene* s, const DBuf& src, int64_t ld, double* dst, size_t rows, size_t cols) {
+  if (rows == 0 || cols == 0) return ICR_OK;
+  const size_t es = s->tsize;
+  std::vector<unsigned char> tmp(rows * cols * es);
+  CK(cudaMemcpy2DAsync(tmp.data(), cols * es, src.p, ld * es, cols * es, rows, cudaMemcpyDeviceToHost,
+                       s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  if (s->prec == ICR_FP64)
+    std::memcpy(dst, tmp.data(), tmp.size());
+  else
+    for (size_t i = 0; i < rows * cols; ++i) dst[i] = ((float*)tmp.data())[i];
+  return ICR_OK;
+}
+
 // Device buffer of the scene's precision -> host doubles (synchronises).
 static int download_T(Scene* s, const DBuf& src, double* dst, size_t count) {
   if (count == 0) return ICR_OK;
@@ -512,6 +542,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   const int ns = s->ns;
   const int words = std::max(1, (m + 31) / 32);
   const int64_t ldx = std::max<int64_t>(32, ((3 * (int64_t)m + 31) / 32) * 32);
+  const int64_t ldw = std::max<int64_t>(96, ((3 * (int64_t)m + 95) / 96) * 96);
   const size_t T = s->tsize;
   const size_t mm = std::max(1, m);
   RET(dalloc(s, s->nodes, 4 * mm * sizeof(int32_t)));
@@ -524,7 +555,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->X, (size_t)s->total_front_rows * ldx * T));
   RET(dalloc(s, s->Ftop, (size_t)s->n * ldx * T));
   RET(dalloc(s, s->WH, 9 * mm * mm * T));
-  RET(dalloc(s, s->W, 9 * mm * mm * T));
+  RET(dalloc(s, s->W, 3 * mm * (size_t)ldw * T));
   RET(dalloc(s, s->C, 9 * mm * T));
   RET(dalloc(s, s->delta, 3 * mm * T));
   RET(dalloc(s, s->mu, mm * T));
@@ -542,6 +573,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
     RET(upload_T(s, s->bary, bary, 4 * (size_t)m));
   }
   cudaStream_t st = s->ctx->stream;
+  CK(cudaMemsetAsync(s->W.p, 0, 3 * mm * (size_t)ldw * T, st));   // padding columns stay 0
   CK(cudaMemsetAsync(s->lam.p, 0, 3 * mm * T, st));
   CK(cudaMemsetAsync(s->mu.p, 0, mm * T, st));
   CK(cudaMemsetAsync(s->delta.p, 0, 3 * mm * T, st));
@@ -553,6 +585,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   s->m = m;
   s->words = words;
   s->ldx = ldx;
+  s->ldw = ldw;
   s->has_mapping = true;
   s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
   s->obst_kind = 0;
@@ -855,7 +888,7 @@ int icr_get(icr_scene* s, int32_t field, void* dst, size_t bytes) {
   cudaStream_t st = s->ctx->stream;
   switch (field) {
     case ICR_FIELD_WH: return download_T(s, s->WH, (double*)dst, c);
-    case ICR_FIELD_W: return download_T(s, s->W, (double*)dst, c);
+    case ICR_FIELD_W: return download_T_2d(s, s->W, s->ldw, (double*)dst, 3 * (size_t)s->m, 3 * (size_t)s->m);
     case ICR_FIELD_LAMBDA: return download_T(s, s->lam, (double*)dst, c);
     case ICR_FIELD_DELTA: return download_T(s, s->delta, (double*)dst, c);
     case ICR_FIELD_C: return download_T(s, s->C, (double*)dst, c);
@@ -904,7 +937,10 @@ int icr_set_field(icr_scene* s, int32_t field, const double* src, size_t bytes) 
       return ICR_EINVAL;
     }
   switch (field) {
-    case ICR_FIELD_W: RET(upload_T(s, s->W, src, c)); s->has_W = true; break;
+    case ICR_FIELD_W:
+      RET(upload_T_2d(s, s->W, s->ldw, src, 3 * (size_t)s->m, 3 * (size_t)s->m));
+      s->has_W = true;
+      break;
     case ICR_FIELD_WH: RET(upload_T(s, s->WH, src, c)); s->has_WH = true; break;
     case ICR_FIELD_LAMBDA: RET(upload_T(s, s->lam, src, c)); s->has_lam = true; break;
     case ICR_FIELD_DELTA: RET(upload_T(s, s->delta, src, c)); break;

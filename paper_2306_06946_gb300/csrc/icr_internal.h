@@ -58,6 +58,7 @@ struct Scene {
   bool has_mapping = false;
   int m = 0, words = 0;
   int64_t ldx = 0;     // leading dimension (columns) of every front
+  int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
   uint64_t launches = 0;   // kernels launched by this scene

@@ -370,7 +370,7 @@ __global__ void k_symmetrize(int nr, T* A) {
 
 // ------------------------------------------------------------------ a6 W = C W_H C^T
 template <class T>
-__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W) {
+__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw) {
   const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
   if (a >= m || b >= m || a > b) return;
   const int64_t ld = 3 * (int64_t)m;
@@ -392,8 +392,8 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       T v = Ca[i][0] * t[0][j] + Ca[i][1] * t[1][j] + Ca[i][2] * t[2][j];
-      W[(3 * a + i) * ld + 3 * b + j] = v;
-      W[(3 * b + j) * ld + 3 * a + i] = v;
+      W[(3 * a + i) * ldw + 3 * b + j] = v;
+      W[(3 * b + j) * ldw + 3 * a + i] = v;
     }
 }
 
@@ -434,118 +434,122 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 template <class T, int BC>
 __global__ void __launch_bounds__(1024)
-    k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, const T* __restrict__ delta,
+    k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
           const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
   constexpr int BR = 3 * BC;
-  constexpr int LD = BR + 1;
+  constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
+  constexpr int RCH = BR / CH;                 // 16-byte copies per block row
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* lam = (T*)smraw;          // 3m
-  T* r = lam + 3 * m;          // 3m
-  T* dl = r + 3 * m;           // 2 x BR: lambda~ changes of the last two blocks
-  T* WD = dl + 2 * BR;         // 2 x BR x LD: diagonal blocks (current, next)
-  T* WX = WD + 2 * BR * LD;    // BR x LD: W[next block rows, current block cols]
+  // stage k holds, for the block it was loaded for, WD = W[block rows, block
+  // cols] and WR = W[block rows, next block's cols] (row-major, ld BR); warp 0
+  // reads them through the symmetry of W as W[cols, rows], bank-conflict free.
+  T* WD = (T*)smraw;               // 2 x BR x BR
+  T* WR = WD + 2 * BR * BR;        // 2 x BR x BR
+  T* lam = WR + 2 * BR * BR;       // 3m
+  T* r = lam + 3 * m;              // 3m
+  T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
   __shared__ double red[32];
   __shared__ int flag;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
-  const int64_t ld = n3;
   const int nblk = (m + BC - 1) / BC;
+  // W[rows of block bn, cols of blocks bn and bn+1] -> stage k
+  auto prefetch = [&](int bn, int k, int t0, int nt) {
+    const int bn1 = (bn + 1) % nblk;
+    const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC), c1 = 3 * bn1 * BC;
+    T* D = WD + k * BR * BR;
+    T* Rr = WR + k * BR * BR;
+    for (int e = t0; e < nnr * RCH; e += nt) {
+      const int i = e / RCH, c = (e % RCH) * CH;
+      const T* src = W + (int64_t)(n0 + i) * ldw;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(&D[i * BR + c])),
+                   "l"(src + n0 + c));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(&Rr[i * BR + c])),
+                   "l"(src + c1 + c));
+    }
+    cp_async_commit();
+  };
   for (int i = tid; i < n3; i += nthr) lam[i] = warm ? lam_g[i] : T(0);
   for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
+  prefetch(0, 0, tid, nthr);
   __syncthreads();
   for (int row = wid; row < n3; row += 32) {
-    const T* Wr = W + (int64_t)row * ld;
+    const T* Wr = W + (int64_t)row * ldw;
     T acc = T(0);
     for (int j = lane; j < n3; j += 32) acc += Wr[j] * lam[j];
     acc = warp_sum(acc);
     if (lane == 0) r[row] = delta[row] + acc;
   }
-  {
-    const int nr0 = 3 * min(BC, m);
-    for (int e = tid; e < nr0 * nr0; e += nthr) {
-      int i = e / nr0, j = e % nr0;
-      WD[i * LD + j] = W[(int64_t)i * ld + j];
-    }
-  }
+  cp_async_wait_all();
   __syncthreads();
-  int cur = 0, pb = -1, done = 0;
+
+  // warp 0 state: lane l holds contact l of the current block and the pending
+  // changes (p) of contact l of the next block
+  T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0, iWnn = 0, Wt1n = 0, Wt2n = 0, iwt = 0;
+  T p0 = 0, p1 = 0, p2 = 0, dsum = T(0);
+  int done = 0, b = 0;
   double eps = 0.0;
-  T dsum = T(0);   // warp 0: sum of squared changes this sweep (FP64 stays off the serial chain)
   const long total = (long)sweeps * nblk;
   for (long t = 0; t < total; ++t) {
-    const int b = (int)(t % nblk);
-    const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0, nr = 3 * nb;
-    const int dc = (int)(t & 1);
-    T* dlc = dl + dc * BR;
-    const T* dlp = dl + (1 - dc) * BR;
-    const int pnr = pb >= 0 ? 3 * min(BC, m - pb * BC) : 0;
-    const int pR0 = pb >= 0 ? 3 * pb * BC : 0;
-    // [A] critical: this block's residuals take the previous block's changes
-    if (pb >= 0) {
-      for (int i = wid; i < nr; i += 32) {
-        T acc = T(0);
-        for (int j = lane; j < pnr; j += 32) acc += WX[i * LD + j] * dlp[j];
-        acc = warp_sum(acc);
-        if (lane == 0) r[R0 + i] += acc;
-      }
-    }
-    __syncthreads();
-    // [B]
+    const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0;
+    const int bn = b + 1 == nblk ? 0 : b + 1;
+    const int stg = (int)(t & 1);
+    const int dc = stg;
+    const int pb = t > 0 ? (b == 0 ? nblk - 1 : b - 1) : -1;
     if (wid == 0) {
-      const T* WDc = WD + cur * BR * LD;
+      const T* WDc = WD + stg * BR * BR;
+      const T* WRc = WR + stg * BR * BR;
       const bool valid = lane < nb;
-      T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0;
-      T iWnn = 0, Wt1n = 0, Wt2n = 0, iwt = 0;
       if (valid) {
-        const T* Wo = WDc + (3 * lane) * LD + 3 * lane;
-        r0 = r[R0 + 3 * lane];
-        r1 = r[R0 + 3 * lane + 1];
-        r2 = r[R0 + 3 * lane + 2];
+        const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
+        r0 = r[R0 + 3 * lane] + p0;
+        r1 = r[R0 + 3 * lane + 1] + p1;
+        r2 = r[R0 + 3 * lane + 2] + p2;
         l0 = lam[R0 + 3 * lane];
         l1 = lam[R0 + 3 * lane + 1];
         l2 = lam[R0 + 3 * lane + 2];
         mua = mu[a0 + lane];
         iWnn = T(1) / Wo[0];
-        Wt1n = Wo[LD];
-        Wt2n = Wo[2 * LD];
-        iwt = T(1) / (T(0.5) * (Wo[LD + 1] + Wo[2 * LD + 2]));
+        Wt1n = Wo[BR];
+        Wt2n = Wo[2 * BR];
+        iwt = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
+      } else {
+        r0 = r1 = r2 = l0 = l1 = l2 = mua = iWnn = Wt1n = Wt2n = iwt = T(0);
       }
+      p0 = p1 = p2 = T(0);
       T e0 = 0, e1 = 0, e2 = 0;
+      const int ll = lane < BC ? lane : BC - 1;   // lanes past the block read a valid column
+#pragma unroll 2
       for (int i = 0; i < nb; ++i) {
-        // coupling of my residual to contact i (independent of the chain)
-        T w[9];
-        const bool upd = valid && lane > i;
-        const T* Wl = WDc + (3 * lane) * LD + 3 * i;
+        // couplings W[3i+c, 3l+q] (this block) and W[3i+c, next 3l+q], read by rows of contact i
+        T w[9], x[9];
 #pragma unroll
-        for (int q = 0; q < 3; ++q)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) w[3 * q + c] = upd ? Wl[q * LD + c] : T(0);
-        T d0 = 0, d1 = 0, d2 = 0;
-        if (lane == i) {
-          T ln = l0 - r0 * iWnn;
-          ln = ln > T(0) ? ln : T(0);
-          const T dn = ln - l0;
-          const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
-          T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
-          const T lim = mua * ln;
-          const T s2 = lt1 * lt1 + lt2 * lt2;
-          if (ln <= T(0)) {
-            lt1 = T(0);
-            lt2 = T(0);
-          } else if (s2 > lim * lim) {
-            const T sc = lim * rsqrt_t(s2);
-            lt1 *= sc;
-            lt2 *= sc;
+          for (int q = 0; q < 3; ++q) {
+            w[3 * q + c] = WDc[(3 * i + c) * BR + 3 * ll + q];
+            x[3 * q + c] = WRc[(3 * i + c) * BR + 3 * ll + q];
           }
-          d0 = ln - l0;
-          d1 = lt1 - l1;
-          d2 = lt2 - l2;
-          e0 = d0;
-          e1 = d1;
-          e2 = d2;
+        // every lane solves its own contact; lane i commits
+        T ln = l0 - r0 * iWnn;
+        ln = ln > T(0) ? ln : T(0);
+        const T dn = ln - l0;
+        const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
+        T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
+        const T lim = mua * ln;
+        const T s2 = lt1 * lt1 + lt2 * lt2;
+        T sc = s2 > lim * lim ? lim * rsqrt_t(s2) : T(1);
+        sc = ln > T(0) ? sc : T(0);
+        lt1 *= sc;
+        lt2 *= sc;
+        T d0 = ln - l0, d1 = lt1 - l1, d2 = lt2 - l2;
+        if (lane == i) {
           l0 = ln;
           l1 = lt1;
           l2 = lt2;
+          e0 = d0;
+          e1 = d1;
+          e2 = d2;
           dsum += d0 * d0 + d1 * d1 + d2 * d2;
         }
         d0 = __shfl_sync(FULL, d0, i);
@@ -555,39 +559,40 @@ __global__ void __launch_bounds__(1024)
           r0 += w[0] * d0 + w[1] * d1 + w[2] * d2;
           r1 += w[3] * d0 + w[4] * d1 + w[5] * d2;
           r2 += w[6] * d0 + w[7] * d1 + w[8] * d2;
+          p0 += x[0] * d0 + x[1] * d1 + x[2] * d2;
+          p1 += x[3] * d0 + x[4] * d1 + x[5] * d2;
+          p2 += x[6] * d0 + x[7] * d1 + x[8] * d2;
         }
       }
       if (valid) {
         lam[R0 + 3 * lane] = l0;
         lam[R0 + 3 * lane + 1] = l1;
         lam[R0 + 3 * lane + 2] = l2;
-        dlc[3 * lane] = e0;
-        dlc[3 * lane + 1] = e1;
-        dlc[3 * lane + 2] = e2;
+        r[R0 + 3 * lane] = r0;       // complete residual of this block's rows
+        r[R0 + 3 * lane + 1] = r1;
+        r[R0 + 3 * lane + 2] = r2;
       }
+      if (lane < BC) {                // lanes in [nb, BC) write zeros
+        dl[dc * BR + 3 * lane] = e0;
+        dl[dc * BR + 3 * lane + 1] = e1;
+        dl[dc * BR + 3 * lane + 2] = e2;
+      }
+      if (bn == b) p0 = p1 = p2 = T(0);   // single block: the residual already has them
     } else {
       const int t2 = tid - 32, n2 = nthr - 32;
-      // prefetch first, so the copies run while this warp streams
-      if (t + 1 < total && t2 < 10 * BR) {
-        const int bn = (b + 1) % nblk;
-        const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC);
-        T* WDn = WD + (1 - cur) * BR * LD;
-        const int j = t2 % BR;
-        for (int i = t2 / BR; i < nnr; i += 10) {
-          if (j < nnr) cp_async<sizeof(T)>(&WDn[i * LD + j], &W[(int64_t)(n0 + i) * ld + n0 + j]);
-          if (j < nr) cp_async<sizeof(T)>(&WX[i * LD + j], &W[(int64_t)(n0 + i) * ld + R0 + j]);
-        }
-        cp_async_commit();
-      }
+      if (t + 1 < total) prefetch(bn, 1 - stg, t2, n2);
       if (pb >= 0) {
+        // fold the previous block's changes into every row but this block's and its own
+        const T* dlp = dl + (1 - dc) * BR;
+        const int pR0 = 3 * pb * BC, pnr = 3 * min(BC, m - pb * BC);
         for (int j = t2; j < n3; j += n2) {
-          if (j >= R0 && j < R0 + nr) continue;
+          if ((j >= R0 && j < R0 + 3 * nb) || (j >= pR0 && j < pR0 + pnr)) continue;
           T acc = T(0);
-          const T* Wc = W + (int64_t)pR0 * ld + j;
+          const T* Wc = W + (int64_t)pR0 * ldw + j;
 #pragma unroll 8
           for (int i = 0; i < pnr; ++i) {
             const T di = dlp[i];
-            if (di != T(0)) acc += Wc[(int64_t)i * ld] * di;
+            if (di != T(0)) acc += Wc[(int64_t)i * ldw] * di;
           }
           r[j] += acc;
         }
@@ -595,13 +600,13 @@ __global__ void __launch_bounds__(1024)
       cp_async_wait_all();
     }
     __syncthreads();
-    if (b == nblk - 1) {
-      // eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
+    if (bn == 0) {
+      // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
       double nrm = 0.0;
       for (int i = tid; i < n3; i += nthr) nrm += (double)lam[i] * (double)lam[i];
       nrm = warp_sum(nrm);
       if (lane == 0) red[wid] = nrm;
-      double ds = wid == 0 ? warp_sum((double)dsum) : 0.0;
+      const double ds = wid == 0 ? warp_sum((double)dsum) : 0.0;
       __syncthreads();
       if (tid == 0) {
         double tot = 0.0;
@@ -613,13 +618,12 @@ __global__ void __launch_bounds__(1024)
       __syncthreads();
       eps = red[0];
       dsum = T(0);
-      done = (int)(t / nblk) + 1;
+      ++done;
       const int brk = flag;
       __syncthreads();
       if (brk) break;
     }
-    pb = b;
-    cur = 1 - cur;
+    b = bn;
   }
   for (int i = tid; i < n3; i += nthr) lam_g[i] = lam[i];
   if (tid == 0) {
@@ -630,8 +634,8 @@ __global__ void __launch_bounds__(1024)
 
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
-  const size_t BR = 3 * BC, LD = BR + 1;
-  return (6 * (size_t)m + 2 * BR + 3 * BR * LD) * sizeof(T);
+  const size_t BR = 3 * BC;
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
@@ -640,16 +644,15 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 
 // FP64 residuals of the final iterate: one warp per contact.
 template <class T>
-__global__ void k_pgs_residual(int m, const T* __restrict__ W, const T* __restrict__ delta,
+__global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
                                const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
   const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= m) return;
-  const int64_t ld = 3 * (int64_t)m;
   double d[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const T* Wr = W + (3 * (int64_t)a + k) * ld;
+    const T* Wr = W + (3 * (int64_t)a + k) * ldw;
     double acc = 0.0;
     for (int j = lane; j < 3 * m; j += 32) acc += (double)Wr[j] * (double)lam[j];
     acc = warp_sum(acc);
@@ -868,7 +871,7 @@ static int update_W_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   dim3 grid((m + 15) / 16, (m + 15) / 16);
-  k_update_W<T><<<grid, dim3(16, 16), 0, s->ctx->stream>>>(m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p);
+  k_update_W<T><<<grid, dim3(16, 16), 0, s->ctx->stream>>>(m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw);
   LAUNCH_OK("k_update_W");
   return ICR_OK;
 }
@@ -895,12 +898,12 @@ static int pgs_T(Scene* s, int warm, int want_res) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
     attr_bytes = smem;
   }
-  k_pgs<T, BC><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p,
+  k_pgs<T, BC><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
                                       (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
   LAUNCH_OK("k_pgs");
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
-    k_pgs_residual<T><<<(m + 7) / 8, 256, 0, st>>>(m, (const T*)s->W.p, (const T*)s->delta.p, (const T*)s->mu.p,
+    k_pgs_residual<T><<<(m + 7) / 8, 256, 0, st>>>(m, (const T*)s->W.p, s->ldw, (const T*)s->delta.p, (const T*)s->mu.p,
                                                    (const T*)s->lam.p, rel, ds);
     LAUNCH_OK("k_pgs_residual");
   }
