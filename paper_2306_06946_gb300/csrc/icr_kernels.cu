@@ -399,14 +399,14 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 
 // ------------------------------------------------------------------ a7 PGS
 // One CTA of 1024 threads.  The residual r = delta + W lambda~ of every row is
-// kept in shared memory.  Contacts are taken in blocks of BC; for each block:
-//   [A] all warps fold the previous block's lambda~ changes into this block's
-//       residuals (a BR x BR product with the prefetched cross block of W);
-//   [B] warp 0 runs the block's contacts in order (lane = contact), each lane
-//       folding the earlier lanes' changes into its residual, while warps
+// kept in shared memory.  Contacts are taken in blocks of BC; for each block,
+// with one barrier per block:
+//       warp 0 runs the block's contacts in order: every lane solves contact
+//       i from its complete residual, lane l folds the change into its own
+//       residual (contact l) and into the next block's contact l, while warps
 //       1..31 fold the previous block's non-zero changes into all other
 //       residuals (streaming those rows of W) and prefetch, with cp.async,
-//       the next block's diagonal block and cross block of W.
+//       the next block's rows of W (its diagonal block and the block to its right).
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
 // with contacts in ascending order; the local rule uses reciprocals and an
 // rsqrt scale, so results differ from the plain formulas by rounding only.
@@ -433,7 +433,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <class T, int BC>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(1024, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
           const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
   constexpr int BR = 3 * BC;
@@ -448,6 +448,7 @@ __global__ void __launch_bounds__(1024)
   T* lam = WR + 2 * BR * BR;       // 3m
   T* r = lam + 3 * m;              // 3m
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
+  T* sdg = dl + 2 * BR;            // 5 x BC: 1/W_nn, W_t1n, W_t2n, 1/w_t, mu of the block's contacts
   __shared__ double red[32];
   __shared__ int flag;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
@@ -483,9 +484,8 @@ __global__ void __launch_bounds__(1024)
   cp_async_wait_all();
   __syncthreads();
 
-  // warp 0 state: lane l holds contact l of the current block and the pending
-  // changes (p) of contact l of the next block
-  T r0 = 0, r1 = 0, r2 = 0, l0 = 0, l1 = 0, l2 = 0, mua = 0, iWnn = 0, Wt1n = 0, Wt2n = 0, iwt = 0;
+  // warp 0: lane l holds the residual (q) of contact l of the current block and
+  // the pending changes (p) of contact l of the next block
   T p0 = 0, p1 = 0, p2 = 0, dsum = T(0);
   int done = 0, b = 0;
   double eps = 0.0;
@@ -500,41 +500,37 @@ __global__ void __launch_bounds__(1024)
       const T* WDc = WD + stg * BR * BR;
       const T* WRc = WR + stg * BR * BR;
       const bool valid = lane < nb;
+      const int ll = lane < BC ? lane : BC - 1;   // lanes past the block read a valid column
+      // own residual (complete once the pending changes of the previous block are in)
+      T q0 = T(0), q1 = T(0), q2 = T(0);
       if (valid) {
         const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
-        r0 = r[R0 + 3 * lane] + p0;
-        r1 = r[R0 + 3 * lane + 1] + p1;
-        r2 = r[R0 + 3 * lane + 2] + p2;
-        l0 = lam[R0 + 3 * lane];
-        l1 = lam[R0 + 3 * lane + 1];
-        l2 = lam[R0 + 3 * lane + 2];
-        mua = mu[a0 + lane];
-        iWnn = T(1) / Wo[0];
-        Wt1n = Wo[BR];
-        Wt2n = Wo[2 * BR];
-        iwt = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
-      } else {
-        r0 = r1 = r2 = l0 = l1 = l2 = mua = iWnn = Wt1n = Wt2n = iwt = T(0);
+        q0 = r[R0 + 3 * lane] + p0;
+        q1 = r[R0 + 3 * lane + 1] + p1;
+        q2 = r[R0 + 3 * lane + 2] + p2;
+        sdg[lane] = T(1) / Wo[0];
+        sdg[BC + lane] = Wo[BR];
+        sdg[2 * BC + lane] = Wo[2 * BR];
+        sdg[3 * BC + lane] = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
+        sdg[4 * BC + lane] = mu[a0 + lane];
       }
       p0 = p1 = p2 = T(0);
+      __syncwarp();
       T e0 = 0, e1 = 0, e2 = 0;
-      const int ll = lane < BC ? lane : BC - 1;   // lanes past the block read a valid column
-#pragma unroll 2
+      // every lane carries the complete residual (c) of the contact being solved
+      T c0 = __shfl_sync(FULL, q0, 0), c1 = __shfl_sync(FULL, q1, 0), c2 = __shfl_sync(FULL, q2, 0);
       for (int i = 0; i < nb; ++i) {
-        // couplings W[3i+c, 3l+q] (this block) and W[3i+c, next 3l+q], read by rows of contact i
-        T w[9], x[9];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            w[3 * q + c] = WDc[(3 * i + c) * BR + 3 * ll + q];
-            x[3 * q + c] = WRc[(3 * i + c) * BR + 3 * ll + q];
-          }
-        // every lane solves its own contact; lane i commits
-        T ln = l0 - r0 * iWnn;
+        // residual of contact i+1 before contact i changes (off the dependency chain)
+        const int inx = i + 1 < nb ? i + 1 : i;
+        const T n0 = __shfl_sync(FULL, q0, inx), n1 = __shfl_sync(FULL, q1, inx), n2 = __shfl_sync(FULL, q2, inx);
+        const T l0 = lam[R0 + 3 * i], l1 = lam[R0 + 3 * i + 1], l2 = lam[R0 + 3 * i + 2];
+        const T iWnn = sdg[i], Wt1n = sdg[BC + i], Wt2n = sdg[2 * BC + i], iwt = sdg[3 * BC + i];
+        const T mua = sdg[4 * BC + i];
+        // local Signorini-Coulomb solve of contact i, done by every lane
+        T ln = l0 - c0 * iWnn;
         ln = ln > T(0) ? ln : T(0);
         const T dn = ln - l0;
-        const T rt1 = r1 + Wt1n * dn, rt2 = r2 + Wt2n * dn;
+        const T rt1 = c1 + Wt1n * dn, rt2 = c2 + Wt2n * dn;
         T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
         const T lim = mua * ln;
         const T s2 = lt1 * lt1 + lt2 * lt2;
@@ -542,35 +538,40 @@ __global__ void __launch_bounds__(1024)
         sc = ln > T(0) ? sc : T(0);
         lt1 *= sc;
         lt2 *= sc;
-        T d0 = ln - l0, d1 = lt1 - l1, d2 = lt2 - l2;
+        const T d0 = ln - l0, d1 = lt1 - l1, d2 = lt2 - l2;
         if (lane == i) {
-          l0 = ln;
-          l1 = lt1;
-          l2 = lt2;
+          lam[R0 + 3 * i] = ln;
+          lam[R0 + 3 * i + 1] = lt1;
+          lam[R0 + 3 * i + 2] = lt2;
           e0 = d0;
           e1 = d1;
           e2 = d2;
           dsum += d0 * d0 + d1 * d1 + d2 * d2;
         }
-        d0 = __shfl_sync(FULL, d0, i);
-        d1 = __shfl_sync(FULL, d1, i);
-        d2 = __shfl_sync(FULL, d2, i);
         if (d0 != T(0) || d1 != T(0) || d2 != T(0)) {
-          r0 += w[0] * d0 + w[1] * d1 + w[2] * d2;
-          r1 += w[3] * d0 + w[4] * d1 + w[5] * d2;
-          r2 += w[6] * d0 + w[7] * d1 + w[8] * d2;
-          p0 += x[0] * d0 + x[1] * d1 + x[2] * d2;
-          p1 += x[3] * d0 + x[4] * d1 + x[5] * d2;
-          p2 += x[6] * d0 + x[7] * d1 + x[8] * d2;
+          // next contact's complete residual, its own row block of W (symmetric reads)
+          const T* Wn = WDc + (3 * i) * BR + 3 * inx;
+          c0 = n0 + Wn[0] * d0 + Wn[BR] * d1 + Wn[2 * BR] * d2;
+          c1 = n1 + Wn[1] * d0 + Wn[BR + 1] * d1 + Wn[2 * BR + 1] * d2;
+          c2 = n2 + Wn[2] * d0 + Wn[BR + 2] * d1 + Wn[2 * BR + 2] * d2;
+          const T* Wl = WDc + (3 * i) * BR + 3 * ll;
+          q0 += Wl[0] * d0 + Wl[BR] * d1 + Wl[2 * BR] * d2;
+          q1 += Wl[1] * d0 + Wl[BR + 1] * d1 + Wl[2 * BR + 1] * d2;
+          q2 += Wl[2] * d0 + Wl[BR + 2] * d1 + Wl[2 * BR + 2] * d2;
+          const T* Xl = WRc + (3 * i) * BR + 3 * ll;
+          p0 += Xl[0] * d0 + Xl[BR] * d1 + Xl[2 * BR] * d2;
+          p1 += Xl[1] * d0 + Xl[BR + 1] * d1 + Xl[2 * BR + 1] * d2;
+          p2 += Xl[2] * d0 + Xl[BR + 2] * d1 + Xl[2 * BR + 2] * d2;
+        } else {
+          c0 = n0;
+          c1 = n1;
+          c2 = n2;
         }
       }
       if (valid) {
-        lam[R0 + 3 * lane] = l0;
-        lam[R0 + 3 * lane + 1] = l1;
-        lam[R0 + 3 * lane + 2] = l2;
-        r[R0 + 3 * lane] = r0;       // complete residual of this block's rows
-        r[R0 + 3 * lane + 1] = r1;
-        r[R0 + 3 * lane + 2] = r2;
+        r[R0 + 3 * lane] = q0;       // complete residual of this block's rows
+        r[R0 + 3 * lane + 1] = q1;
+        r[R0 + 3 * lane + 2] = q2;
       }
       if (lane < BC) {                // lanes in [nb, BC) write zeros
         dl[dc * BR + 3 * lane] = e0;
@@ -635,7 +636,7 @@ __global__ void __launch_bounds__(1024)
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
-  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T);
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR + 5 * BC) * sizeof(T);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
