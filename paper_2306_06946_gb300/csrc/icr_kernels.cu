@@ -401,9 +401,9 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 // One CTA of 1024 threads.  The residual r = delta + W lambda~ of every row is
 // kept in shared memory.  Contacts are taken in blocks of BC; for each block,
 // with one barrier per block:
-//       warp 0 runs the block's contacts in order: every lane solves contact
-//       i from its complete residual, lane l folds the change into its own
-//       residual (contact l) and into the next block's contact l, while warps
+//       warp 0 runs the block's contacts in order (lane = contact); the lane
+//       of contact i solves it and every lane folds the change into its own
+//       residual and into the next block's contact of the same lane, while warps
 //       1..31 fold the previous block's non-zero changes into all other
 //       residuals (streaming those rows of W) and prefetch, with cp.async,
 //       the next block's rows of W (its diagonal block and the block to its right).
@@ -448,7 +448,6 @@ __global__ void __launch_bounds__(1024, 1)
   T* lam = WR + 2 * BR * BR;       // 3m
   T* r = lam + 3 * m;              // 3m
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
-  T* sdg = dl + 2 * BR;            // 5 x BC: 1/W_nn, W_t1n, W_t2n, 1/w_t, mu of the block's contacts
   __shared__ double red[32];
   __shared__ int flag;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
@@ -501,59 +500,68 @@ __global__ void __launch_bounds__(1024, 1)
       const T* WRc = WR + stg * BR * BR;
       const bool valid = lane < nb;
       const int ll = lane < BC ? lane : BC - 1;   // lanes past the block read a valid column
-      // own residual (complete once the pending changes of the previous block are in)
-      T q0 = T(0), q1 = T(0), q2 = T(0);
+      // lane l: contact l of this block (residual q, lambda~ l, its 3x3 diagonal data)
+      T q0 = T(0), q1 = T(0), q2 = T(0), l0 = T(0), l1 = T(0), l2 = T(0);
+      T iWnn = T(0), Wt1n = T(0), Wt2n = T(0), iwt = T(0), mua = T(0);
       if (valid) {
         const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
         q0 = r[R0 + 3 * lane] + p0;
         q1 = r[R0 + 3 * lane + 1] + p1;
         q2 = r[R0 + 3 * lane + 2] + p2;
-        sdg[lane] = T(1) / Wo[0];
-        sdg[BC + lane] = Wo[BR];
-        sdg[2 * BC + lane] = Wo[2 * BR];
-        sdg[3 * BC + lane] = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
-        sdg[4 * BC + lane] = mu[a0 + lane];
+        l0 = lam[R0 + 3 * lane];
+        l1 = lam[R0 + 3 * lane + 1];
+        l2 = lam[R0 + 3 * lane + 2];
+        iWnn = T(1) / Wo[0];
+        Wt1n = Wo[BR];
+        Wt2n = Wo[2 * BR];
+        iwt = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
+        mua = mu[a0 + lane];
       }
       p0 = p1 = p2 = T(0);
-      __syncwarp();
       T e0 = 0, e1 = 0, e2 = 0;
-      // every lane carries the complete residual (c) of the contact being solved
-      T c0 = __shfl_sync(FULL, q0, 0), c1 = __shfl_sync(FULL, q1, 0), c2 = __shfl_sync(FULL, q2, 0);
-      for (int i = 0; i < nb; ++i) {
-        // residual of contact i+1 before contact i changes (off the dependency chain)
-        const int inx = i + 1 < nb ? i + 1 : i;
-        const T n0 = __shfl_sync(FULL, q0, inx), n1 = __shfl_sync(FULL, q1, inx), n2 = __shfl_sync(FULL, q2, inx);
-        const T l0 = lam[R0 + 3 * i], l1 = lam[R0 + 3 * i + 1], l2 = lam[R0 + 3 * i + 2];
-        const T iWnn = sdg[i], Wt1n = sdg[BC + i], Wt2n = sdg[2 * BC + i], iwt = sdg[3 * BC + i];
-        const T mua = sdg[4 * BC + i];
-        // local Signorini-Coulomb solve of contact i, done by every lane
-        T ln = l0 - c0 * iWnn;
-        ln = ln > T(0) ? ln : T(0);
-        const T dn = ln - l0;
-        const T rt1 = c1 + Wt1n * dn, rt2 = c2 + Wt2n * dn;
-        T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
-        const T lim = mua * ln;
-        const T s2 = lt1 * lt1 + lt2 * lt2;
-        T sc = s2 > lim * lim ? lim * rsqrt_t(s2) : T(1);
-        sc = ln > T(0) ? sc : T(0);
-        lt1 *= sc;
-        lt2 *= sc;
-        const T d0 = ln - l0, d1 = lt1 - l1, d2 = lt2 - l2;
+      // A contact with lambda~ = 0 and a non-negative normal residual is left
+      // unchanged by the local rule (lambda_n stays 0, so lambda_t is zeroed):
+      // the sweep visits contacts in order but jumps over such contacts, which
+      // gives exactly the iterate of visiting them.
+      int i = -1;
+      while (true) {
+        const unsigned act =
+            __ballot_sync(FULL, valid && lane > i && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0)));
+        if (act == 0u) break;
+        i = __ffs(act) - 1;
+        T d0 = T(0), d1 = T(0), d2 = T(0);
         if (lane == i) {
-          lam[R0 + 3 * i] = ln;
-          lam[R0 + 3 * i + 1] = lt1;
-          lam[R0 + 3 * i + 2] = lt2;
+          T ln = l0 - q0 * iWnn;
+          ln = ln > T(0) ? ln : T(0);
+          const T dn = ln - l0;
+          const T rt1 = q1 + Wt1n * dn, rt2 = q2 + Wt2n * dn;
+          T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
+          const T lim = mua * ln;
+          const T s2 = lt1 * lt1 + lt2 * lt2;
+          if (ln <= T(0)) {
+            lt1 = T(0);
+            lt2 = T(0);
+          } else if (s2 > lim * lim) {
+            const T sc = lim * rsqrt_t(s2);
+            lt1 *= sc;
+            lt2 *= sc;
+          }
+          d0 = ln - l0;
+          d1 = lt1 - l1;
+          d2 = lt2 - l2;
           e0 = d0;
           e1 = d1;
           e2 = d2;
+          l0 = ln;
+          l1 = lt1;
+          l2 = lt2;
           dsum += d0 * d0 + d1 * d1 + d2 * d2;
         }
+        d0 = __shfl_sync(FULL, d0, i);
+        d1 = __shfl_sync(FULL, d1, i);
+        d2 = __shfl_sync(FULL, d2, i);
         if (d0 != T(0) || d1 != T(0) || d2 != T(0)) {
-          // next contact's complete residual, its own row block of W (symmetric reads)
-          const T* Wn = WDc + (3 * i) * BR + 3 * inx;
-          c0 = n0 + Wn[0] * d0 + Wn[BR] * d1 + Wn[2 * BR] * d2;
-          c1 = n1 + Wn[1] * d0 + Wn[BR + 1] * d1 + Wn[2 * BR + 1] * d2;
-          c2 = n2 + Wn[2] * d0 + Wn[BR + 2] * d1 + Wn[2 * BR + 2] * d2;
+          // couplings W[3i+c, 3l+q] (this block) and W[3i+c, next block's 3l+q]
           const T* Wl = WDc + (3 * i) * BR + 3 * ll;
           q0 += Wl[0] * d0 + Wl[BR] * d1 + Wl[2 * BR] * d2;
           q1 += Wl[1] * d0 + Wl[BR + 1] * d1 + Wl[2 * BR + 1] * d2;
@@ -562,18 +570,17 @@ __global__ void __launch_bounds__(1024, 1)
           p0 += Xl[0] * d0 + Xl[BR] * d1 + Xl[2 * BR] * d2;
           p1 += Xl[1] * d0 + Xl[BR + 1] * d1 + Xl[2 * BR + 1] * d2;
           p2 += Xl[2] * d0 + Xl[BR + 2] * d1 + Xl[2 * BR + 2] * d2;
-        } else {
-          c0 = n0;
-          c1 = n1;
-          c2 = n2;
         }
       }
       if (valid) {
+        lam[R0 + 3 * lane] = l0;
+        lam[R0 + 3 * lane + 1] = l1;
+        lam[R0 + 3 * lane + 2] = l2;
         r[R0 + 3 * lane] = q0;       // complete residual of this block's rows
         r[R0 + 3 * lane + 1] = q1;
         r[R0 + 3 * lane + 2] = q2;
       }
-      if (lane < BC) {                // lanes in [nb, BC) write zeros
+      if (lane < BC) {                // lanes without a change write zeros
         dl[dc * BR + 3 * lane] = e0;
         dl[dc * BR + 3 * lane + 1] = e1;
         dl[dc * BR + 3 * lane + 2] = e2;
@@ -636,7 +643,7 @@ __global__ void __launch_bounds__(1024, 1)
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
-  return (4 * BR * BR + 6 * (size_t)m + 2 * BR + 5 * BC) * sizeof(T);
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
