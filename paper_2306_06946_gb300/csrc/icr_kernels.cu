@@ -448,7 +448,8 @@ __global__ void __launch_bounds__(1024, 1)
   T* lam = WR + 2 * BR * BR;       // 3m
   T* r = lam + 3 * m;              // 3m
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
-  __shared__ double red[32];
+  int* nzl = (int*)(dl + 2 * BR);  // 31 x BR: per streaming warp, rows with a non-zero change
+  __shared__ T red[32];
   __shared__ int flag;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
@@ -473,12 +474,17 @@ __global__ void __launch_bounds__(1024, 1)
   for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
   prefetch(0, 0, tid, nthr);
   __syncthreads();
-  for (int row = wid; row < n3; row += 32) {
-    const T* Wr = W + (int64_t)row * ldw;
-    T acc = T(0);
-    for (int j = lane; j < n3; j += 32) acc += Wr[j] * lam[j];
-    acc = warp_sum(acc);
-    if (lane == 0) r[row] = delta[row] + acc;
+  if (warm) {
+    for (int row = wid; row < n3; row += 32) {
+      const T* Wr = W + (int64_t)row * ldw;
+      T acc = T(0);
+#pragma unroll 4
+      for (int j = lane; j < n3; j += 32) acc += Wr[j] * lam[j];
+      acc = warp_sum(acc);
+      if (lane == 0) r[row] = delta[row] + acc;
+    }
+  } else {
+    for (int i = tid; i < n3; i += nthr) r[i] = delta[i];
   }
   cp_async_wait_all();
   __syncthreads();
@@ -590,19 +596,32 @@ __global__ void __launch_bounds__(1024, 1)
       const int t2 = tid - 32, n2 = nthr - 32;
       if (t + 1 < total) prefetch(bn, 1 - stg, t2, n2);
       if (pb >= 0) {
-        // fold the previous block's changes into every row but this block's and its own
+        // fold the previous block's non-zero changes into every row but this
+        // block's and its own; each warp lists the non-zero rows by ballot
         const T* dlp = dl + (1 - dc) * BR;
         const int pR0 = 3 * pb * BC, pnr = 3 * min(BC, m - pb * BC);
-        for (int j = t2; j < n3; j += n2) {
-          if ((j >= R0 && j < R0 + 3 * nb) || (j >= pR0 && j < pR0 + pnr)) continue;
-          T acc = T(0);
-          const T* Wc = W + (int64_t)pR0 * ldw + j;
+        int* lst = nzl + (wid - 1) * BR;
+        int cnt = 0;
+#pragma unroll
+        for (int w0 = 0; w0 < BR; w0 += 32) {
+          const bool nz = w0 + lane < pnr && dlp[w0 + lane] != T(0);
+          const unsigned msk = __ballot_sync(FULL, nz);
+          if (nz) lst[cnt + __popc(msk & ((1u << lane) - 1u))] = w0 + lane;
+          cnt += __popc(msk);
+        }
+        __syncwarp();
+        if (cnt > 0) {
+          for (int j = t2; j < n3; j += n2) {
+            if ((j >= R0 && j < R0 + 3 * nb) || (j >= pR0 && j < pR0 + pnr)) continue;
+            T acc = T(0);
+            const T* Wc = W + (int64_t)pR0 * ldw + j;
 #pragma unroll 8
-          for (int i = 0; i < pnr; ++i) {
-            const T di = dlp[i];
-            if (di != T(0)) acc += Wc[(int64_t)i * ldw] * di;
+            for (int k = 0; k < cnt; ++k) {
+              const int i = lst[k];
+              acc += Wc[(int64_t)i * ldw] * dlp[i];
+            }
+            r[j] += acc;
           }
-          r[j] += acc;
         }
       }
       cp_async_wait_all();
@@ -610,21 +629,21 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     if (bn == 0) {
       // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
-      double nrm = 0.0;
-      for (int i = tid; i < n3; i += nthr) nrm += (double)lam[i] * (double)lam[i];
+      T nrm = T(0);
+      for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
       nrm = warp_sum(nrm);
       if (lane == 0) red[wid] = nrm;
-      const double ds = wid == 0 ? warp_sum((double)dsum) : 0.0;
+      const T ds = wid == 0 ? warp_sum(dsum) : T(0);
       __syncthreads();
       if (tid == 0) {
-        double tot = 0.0;
+        T tot = T(0);
         for (int k = 0; k < 32; ++k) tot += red[k];
-        const double e = tot > 0.0 ? sqrt(ds / tot) : 0.0;
+        const T e = tot > T(0) ? sqrt(ds / tot) : T(0);
         red[0] = e;
-        flag = (tol > 0.0 && e <= tol) ? 1 : 0;
+        flag = (tol > 0.0 && (double)e <= tol) ? 1 : 0;
       }
       __syncthreads();
-      eps = red[0];
+      eps = (double)red[0];
       dsum = T(0);
       ++done;
       const int brk = flag;
@@ -643,7 +662,7 @@ __global__ void __launch_bounds__(1024, 1)
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
-  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T);
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T) + 31 * BR * sizeof(int);
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
