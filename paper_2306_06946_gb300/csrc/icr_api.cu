@@ -301,8 +301,8 @@ int icr_scene_destroy(icr_scene* s) {
   cudaStreamSynchronize(s->ctx->stream);
   DBuf* all[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->G, &s->dinv, &s->dinvsqrt,
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
-                 &s->dof_super, &s->fr_ptr, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
-                 &s->qidx, &s->qpos, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
+                 &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
+                 &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
                  &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -423,6 +423,27 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
       }
     }
   }
+  // front-row contribution lists: for every row of every front, the
+  // (child, child update row) pairs the extend-add sums into it, children in
+  // ascending order
+  std::vector<int64_t> frp0(ns + 1, 0);
+  for (int k = 0; k < ns; ++k) frp0[k + 1] = frp0[k] + (sp[k + 1] - sp[k]) + (rp[k + 1] - rp[k]);
+  std::vector<int32_t> cptr_rows(frp0[ns] + 1, 0), crow_child(std::max<int64_t>(1, rp[ns])),
+      crow_row(std::max<int64_t>(1, rp[ns]));
+  for (int k = 0; k < ns; ++k)
+    if (par[k] >= 0)
+      for (int64_t i = rp[k]; i < rp[k + 1]; ++i) cptr_rows[frp0[par[k]] + relidx[i] + 1]++;
+  for (int64_t i = 0; i < frp0[ns]; ++i) cptr_rows[i + 1] += cptr_rows[i];
+  {
+    std::vector<int32_t> fillr(cptr_rows.begin(), cptr_rows.end() - 1);
+    for (int k = 0; k < ns; ++k)
+      if (par[k] >= 0)
+        for (int64_t i = rp[k]; i < rp[k + 1]; ++i) {
+          const int64_t slot = fillr[frp0[par[k]] + relidx[i]]++;
+          crow_child[slot] = k;
+          crow_row[slot] = (int32_t)(i - rp[k]);
+        }
+  }
   int nlev = 0;
   for (int k = 0; k < ns; ++k) nlev = std::max(nlev, level[k] + 1);
   std::vector<Level> levs(nlev);
@@ -474,6 +495,9 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   RET(dalloc(s, s->node_super, (n / 3) * sizeof(int32_t)));
   RET(dalloc(s, s->dof_super, n * sizeof(int32_t)));
   RET(dalloc(s, s->fr_ptr, (ns + 1) * sizeof(int64_t)));
+  RET(dalloc(s, s->ctr_ptr, cptr_rows.size() * sizeof(int32_t)));
+  RET(dalloc(s, s->ctr_child, crow_child.size() * sizeof(int32_t)));
+  RET(dalloc(s, s->ctr_row, crow_row.size() * sizeof(int32_t)));
   RET(upload(s, s->super_ptr, sp.data(), ns + 1));
   RET(upload(s, s->rowpat_ptr, rp.data(), ns + 1));
   if (rp[ns]) RET(upload(s, s->rowpat, rowpat, rp[ns]));
@@ -489,6 +513,9 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   RET(upload(s, s->node_super, nsup.data(), n / 3));
   RET(upload(s, s->dof_super, dsup.data(), n));
   RET(upload(s, s->fr_ptr, frp.data(), ns + 1));
+  RET(upload(s, s->ctr_ptr, cptr_rows.data(), cptr_rows.size()));
+  RET(upload(s, s->ctr_child, crow_child.data(), crow_child.size()));
+  RET(upload(s, s->ctr_row, crow_row.data(), crow_row.size()));
   CK(cudaStreamSynchronize(s->ctx->stream));
 
   s->n = n;
@@ -552,6 +579,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->qcount, ns * sizeof(int32_t)));
   RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
+  RET(dalloc(s, s->qinv, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->X, (size_t)s->total_front_rows * ldx * T));
   RET(dalloc(s, s->Ftop, (size_t)s->n * ldx * T));
   RET(dalloc(s, s->WH, 9 * mm * mm * T));

@@ -53,13 +53,14 @@ struct Scene {
   int wmax = 0, rmax = 0;
   DBuf super_ptr, rowpat_ptr, rowpat, val_ptr, G, dinv, dinvsqrt, parent;  // G: per-supernode solve operators
   DBuf child_ptr, child_list, relidx, level_list, node_super, dof_super, fr_ptr;
+  DBuf ctr_ptr, ctr_child, ctr_row;   // per front row: (child, child row) pairs of the extend-add
 
   // ---- mapping (set_mapping)
   bool has_mapping = false;
   int m = 0, words = 0;
   int64_t ldx = 0;     // leading dimension (columns) of every front
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
-  DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, X, Ftop;  // Ftop: assembled top rows (n x ldx)
+  DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
   uint64_t launches = 0;   // kernels launched by this scene
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;

@@ -6,8 +6,8 @@
 // (Eq. "schur complemnt reformulated" with A = L D L^T):
 //   a1  k_reach_*      which contacts' columns of H^T reach each supernode
 //                      (etree ancestors of the supernodes owning their nodes)
-//   a2  k_assemble     per supernode and 32-contact column tile: the front's
-//                      H^T entries plus the children's update blocks
+//   a2  k_assemble     one thread per front element: its H^T entry plus the
+//                      children's update entries (extend-add as a gather)
 //       k_front_gemm   X_s = L_ss^-1 F_top and U_s = F_R - L_Rs L_ss^-1 F_top,
 //                      one register-tiled product with the precomputed
 //                      G_s = [L_ss^-1; L_Rs L_ss^-1] (per level, all tiles)
@@ -62,6 +62,9 @@ __device__ __forceinline__ int lower_bound_dev(const int* a, int n, int v) {
   }
   return lo;
 }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------ a1 reach
 // One thread per (contact, node): mark the contact in every supernode on the
@@ -127,6 +130,20 @@ __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int
   qpos[(size_t)s * m + j] = pos;
 }
 
+// For every supernode c: the local position in c's contact list of each
+// contact of its parent's list (-1 when the contact does not reach c).
+__global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __restrict__ qcount,
+                            const int* __restrict__ qpos, int* qinv) {
+  const int c = blockIdx.x;
+  const int p = parent[c];
+  if (p < 0) return;
+  const int np = qcount[p], nc = qcount[c];
+  int* inv = qinv + (size_t)c * m;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) inv[k] = -1;
+  __syncthreads();
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) inv[qpos[(size_t)c * m + j]] = j;
+}
+
 // ------------------------------------------------------------------ a2 forward solve
 // The front of supernode s has w + r rows (its DOF columns, then R_s) and
 // 3 |Q_s| columns (the contacts of Q_s in ascending order, 3 axes each).
@@ -135,82 +152,82 @@ __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int
 //   X_s = L_ss^-1 F_top,  U_s = F_R - (L_Rs L_ss^-1) F_top,
 // one dense product with the precomputed operator G_s = [L_ss^-1; L_Rs L_ss^-1].
 
-// Block (supernode s of the level, 32-contact tile): assemble the tile,
-// H^T entries plus the children's update blocks (extend-add).
+// Block (supernode s of the level, 4-row tile of its front, 32-contact tile),
+// one thread per front element: the H^T entry plus the children's update
+// entries listed for that row (extend-add as a gather, children in ascending
+// order).  Rows < w go to Ftop, rows >= w to the front's update rows.
+static constexpr int AR = 4;   // front rows per assembly block
 template <class T>
-__global__ void __launch_bounds__(SOLVE_THREADS)
-    k_assemble(const int* __restrict__ level_list, int lvl_first, int ntiles, const int* __restrict__ super_ptr,
-               const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ child_ptr,
-               const int* __restrict__ child_list, const int* __restrict__ relidx,
-               const int64_t* __restrict__ fr_ptr, const int* __restrict__ node_super,
-               const int* __restrict__ nodes, const T* __restrict__ bary, const int* __restrict__ qcount,
-               const int* __restrict__ qidx, const int* __restrict__ qpos, int m, T* X, T* Ftop, int64_t ldx) {
-  const int li = blockIdx.x / ntiles, t = blockIdx.x % ntiles;
-  const int s = level_list[lvl_first + li];
+__global__ void __launch_bounds__(AR * TCOLS)
+    k_assemble(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
+               const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+               const int64_t* __restrict__ fr_ptr, const int* __restrict__ ctr_ptr,
+               const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
+               const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
+               const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
+  int bq = blockIdx.x;
+  const int t = bq % ntiles;
+  bq /= ntiles;
+  const int rt = bq % nrt;
+  const int s = level_list[lvl_first + bq / nrt];
   const int nq = qcount[s];
   const int k0 = t * TCC;
   if (k0 >= nq) return;
-  const int kc = min(TCC, nq - k0);
-  const int ncols = 3 * kc;
+  const int ncols = 3 * min(TCC, nq - k0);
+  const int col = threadIdx.x;
+  const int row = rt * AR + threadIdx.y;
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
-  const int r = (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-  T* Ft = Ftop + (int64_t)c0 * ldx + 3 * k0;
-  T* Uf = X + (fr_ptr[s] + w) * ldx + 3 * k0;
-  const int tid = threadIdx.x;
-  const int j = tid % TCOLS, i0 = tid / TCOLS, di = SOLVE_THREADS / TCOLS;
-  if (j < ncols) {
-    for (int i = i0; i < w; i += di) Ft[(int64_t)i * ldx + j] = T(0);
-    for (int i = i0; i < r; i += di) Uf[(int64_t)i * ldx + j] = T(0);
+  const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  if (row >= nrows || col >= ncols) return;
+  const int kl = k0 + col / 3, d = col % 3;
+  T v = T(0);
+  if (row < w && (c0 + row) % 3 == d) {
+    // column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
+    const int node = (c0 + row) / 3;
+    const int a = qidx[(size_t)s * m + kl];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (nodes[4 * a + i] == node) v += bary[4 * a + i];
   }
-  __syncthreads();
-  // H^T: column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
-  for (int e = tid; e < 4 * kc; e += blockDim.x) {
-    int k = e >> 2, i = e & 3;
-    int a = qidx[(size_t)s * m + k0 + k];
-    int node = nodes[4 * a + i];
-    if (node_super[node] == s) {
-      T b = bary[4 * a + i];
-      int row = 3 * node - c0;
-      for (int d = 0; d < 3; ++d) atomicAdd(&Ft[(int64_t)(row + d) * ldx + 3 * k + d], b);
-    }
-  }
-  __syncthreads();
-  for (int ci = child_ptr[s]; ci < child_ptr[s + 1]; ++ci) {
-    const int c = child_list[ci];
-    const int nqc = qcount[c];
-    const int* pc = qpos + (size_t)c * m;
-    const int j0 = lower_bound_dev(pc, nqc, k0), j1 = lower_bound_dev(pc, nqc, k0 + kc);
-    const int cc = 3 * (j1 - j0);
-    if (j < cc) {
+  const int64_t fr = fr_ptr[s] + row;
+  for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
+    const int c = ctr_child[e];
+    const int jl = qinv[(size_t)c * m + kl];
+    if (jl >= 0) {
       const int wc = super_ptr[c + 1] - super_ptr[c];
-      const int rc = (int)(rowpat_ptr[c + 1] - rowpat_ptr[c]);
-      const int* ri = relidx + rowpat_ptr[c];
-      const T* U = X + (fr_ptr[c] + wc) * ldx + 3 * j0 + j;
-      const int col = 3 * (pc[j0 + j / 3] - k0) + j % 3;
-      for (int i = i0; i < rc; i += di) {
-        const int tr = ri[i];
-        const T v = U[(int64_t)i * ldx];
-        if (tr < w)
-          Ft[(int64_t)tr * ldx + col] += v;
-        else
-          Uf[(int64_t)(tr - w) * ldx + col] += v;
-      }
+      v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
     }
-    __syncthreads();
   }
+  if (row < w)
+    Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
+  else
+    X[fr * ldx + 3 * k0 + col] = v;
 }
 
 // Block (supernode, 64-row tile of the w + r front rows, 32-contact tile):
 // out = G_s[rows, :] F_top; top rows store X_s = out, bottom rows U_s -= out.
+// K is streamed in 32-wide chunks through a double-buffered cp.async pipeline.
 static constexpr int GR = 64;   // rows per tile
+static constexpr int GLD = GR + 4, FLD = TCOLS + 4;
+template <class T>
+__device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool ok) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = ok ? (int)sizeof(T) : 0;   // 0 bytes read: the element is zero-filled
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
+}
+
 template <class T>
 __global__ void __launch_bounds__(256)
     k_front_gemm(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
                  const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                  const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
                  const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
-  __shared__ __align__(16) T sG[KB][GR + 4];
-  __shared__ __align__(16) T sF[KB][TCOLS + 4];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sG = (T*)smraw;                 // 2 x KB x GLD
+  T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
   int b = blockIdx.x;
   const int t = b % ntiles;
   b /= ntiles;
@@ -229,35 +246,53 @@ __global__ void __launch_bounds__(256)
   const T* Gs = G + val_ptr[s];
   const T* Ft = Ftop + (int64_t)c0 * ldx + 3 * k0;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  auto load = [&](int kb, int buf) {
+    const int nb = min(KB, w - kb);
+    T* dG = sG + buf * KB * GLD;
+    T* dF = sF + buf * KB * FLD;
+    for (int e = tid; e < KB * GR; e += 256) {
+      const int k = e / GR, i = e % GR;
+      const bool ok = k < nb && row0 + i < nrows;
+      cp_async_zfill(&dG[k * GLD + i], ok ? &Gs[(int64_t)(kb + k) * ldG + row0 + i] : Gs, ok);
+    }
+    for (int e = tid; e < KB * TCOLS; e += 256) {
+      const int k = e / TCOLS, jj = e % TCOLS;
+      const bool ok = k < nb && jj < ncols;
+      cp_async_zfill(&dF[k * FLD + jj], ok ? &Ft[(int64_t)(kb + k) * ldx + jj] : Ft, ok);
+    }
+    cp_async_commit();
+  };
   T acc[4][6];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[q][c] = T(0);
+  load(0, 0);
+  int buf = 0;
   for (int kb = 0; kb < w; kb += KB) {
-    const int nb = min(KB, w - kb);
-    for (int e = tid; e < KB * GR; e += 256) {
-      const int k = e / GR, i = e % GR;
-      sG[k][i] = (k < nb && row0 + i < nrows) ? Gs[(int64_t)(kb + k) * ldG + row0 + i] : T(0);
-    }
-    for (int e = tid; e < KB * TCOLS; e += 256) {
-      const int k = e / TCOLS, jj = e % TCOLS;
-      sF[k][jj] = (k < nb && jj < ncols) ? Ft[(int64_t)(kb + k) * ldx + jj] : T(0);
+    if (kb + KB < w) {
+      load(kb + KB, buf ^ 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      cp_async_wait_all();
     }
     __syncthreads();
+    const T* cG = sG + buf * KB * GLD;
+    const T* cF = sF + buf * KB * FLD;
 #pragma unroll 8
     for (int k = 0; k < KB; ++k) {
       T a[4], bv[6];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = sG[k][4 * ty + q];
+      for (int q = 0; q < 4; ++q) a[q] = cG[k * GLD + 4 * ty + q];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) bv[c] = sF[k][6 * tx + c];
+      for (int c = 0; c < 6; ++c) bv[c] = cF[k * FLD + 6 * tx + c];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[q][c] += a[q] * bv[c];
     }
     __syncthreads();
+    buf ^= 1;
   }
   T* F = X + fr_ptr[s] * ldx + 3 * k0;
 #pragma unroll
@@ -274,6 +309,11 @@ __global__ void __launch_bounds__(256)
         F[(int64_t)row * ldx + col] -= acc[q][c];
     }
   }
+}
+
+template <class T>
+static size_t gemm_smem_bytes() {
+  return 2 * (size_t)KB * (GLD + FLD) * sizeof(T);
 }
 
 // ------------------------------------------------------------------ a3 pivot scaling
@@ -421,16 +461,7 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) {
   return 1.0 / sqrt(x);
 }
 
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if constexpr (BYTES == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 
 template <class T, int BC>
 __global__ void __launch_bounds__(1024, 1)
@@ -858,16 +889,26 @@ static int build_WH_T(Scene* s) {
       (const uint32_t*)s->bitmap.p, (const int*)s->wprefix.p, words, m, (const int*)s->parent.p,
       (const int*)s->qcount.p, (const int*)s->qidx.p, (int*)s->qpos.p);
   LAUNCH_OK("k_reach_parentpos");
+  k_reach_inv<<<ns, 256, 0, st>>>(m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
+                                  (int*)s->qinv.p);
+  LAUNCH_OK("k_reach_inv");
+  static bool gemm_attr = false;
+  if (!gemm_attr) {
+    e = cudaFuncSetAttribute(k_front_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<T>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
+    gemm_attr = true;
+  }
   const int ntiles = (m + TCC - 1) / TCC;
   for (const Level& lv : s->levels) {
-    k_assemble<T><<<lv.count * ntiles, SOLVE_THREADS, 0, st>>>(
-        (const int*)s->level_list.p, lv.first, ntiles, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
-        (const int*)s->child_ptr.p, (const int*)s->child_list.p, (const int*)s->relidx.p,
-        (const int64_t*)s->fr_ptr.p, (const int*)s->node_super.p, (const int*)s->nodes.p, (const T*)s->bary.p,
-        (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qpos.p, m, X, (T*)s->Ftop.p, ldx);
+    const int nrt_a = (lv.wmax + lv.rmax + AR - 1) / AR;
+    k_assemble<T><<<lv.count * nrt_a * ntiles, dim3(TCOLS, AR), 0, st>>>(
+        (const int*)s->level_list.p, lv.first, nrt_a, ntiles, (const int*)s->super_ptr.p,
+        (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
+        (const int*)s->ctr_child.p, (const int*)s->ctr_row.p, (const int*)s->nodes.p, (const T*)s->bary.p,
+        (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qinv.p, m, X, (T*)s->Ftop.p, ldx);
     LAUNCH_OK("k_assemble");
     const int nrt = (lv.wmax + lv.rmax + GR - 1) / GR;
-    k_front_gemm<T><<<lv.count * nrt * ntiles, 256, 0, st>>>(
+    k_front_gemm<T><<<lv.count * nrt * ntiles, 256, gemm_smem_bytes<T>(), st>>>(
         (const int*)s->level_list.p, lv.first, nrt, ntiles, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
         (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
