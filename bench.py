@@ -132,6 +132,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def profiled_traffic(kernel_marker: str, end_marker: str, profile: str):
+    """DRAM bytes per launch recorded by the ncu capture in ``profiles/``, or
+    None when the kernel's source has changed since that capture."""
+    import hashlib
+    try:
+        src = open(os.path.join(ROOT, "paper_2306_06946_gb300", "csrc", "icr_kernels.cu")).read()
+        a, b = src.index(kernel_marker), src.index(end_marker)
+        h = hashlib.sha256(src[a:b].encode()).hexdigest()
+        rec = {}
+        for line in open(os.path.join(ROOT, "profiles", profile)):
+            if ":" in line and line.split(":")[0] in ("dram_bytes_per_launch", "kernel_source_sha256"):
+                k, v = line.split(":", 1)
+                rec[k.strip()] = v.strip()
+        if rec.get("kernel_source_sha256") == h:
+            return int(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def measured_peaks() -> dict:
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -321,8 +341,11 @@ def run_icr(args):
     pgs_s = phase_ms["pgs"] / 1e3
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     achieved = pgs_bytes / pgs_s / 1e9
+    traffic = profiled_traffic("template <class T, int BC>\n__global__ void __launch_bounds__(1024, 1)\n    k_pgs(",
+                               "template <class T, int BC>\nstatic size_t pgs_smem_bytes", "k_pgs_liver_c1.md")
     roofline = {"kernel": "k_pgs", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "algorithmic_bytes": pgs_bytes,
                 "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
 
     # ---- end to end through the public API with host buffers (pinned)
