@@ -207,6 +207,36 @@ int icr_scene_launches(icr_scene* scene, uint64_t* out);
  * a single step of the path on given operands. */
 int icr_set_field(icr_scene* scene, int32_t field, const double* src, size_t bytes);
 
+/* Allocation-free elimination-tree reach (the paper has no counterpart: this
+ * call exists for callers that cannot allocate device memory, such as a
+ * real-time simulation or haptics loop that forbids allocation after start-up,
+ * or a host framework that owns every device allocation through its own pool).
+ *
+ * Computes the same reach as icr_build_WH does internally: for every
+ * supernode s, the ascending list of contacts whose columns of H^T reach s in
+ * the supernodal elimination tree.  All pointers are DEVICE pointers owned by
+ * the caller:
+ *   nodes      (m x 4) int32 node ids of each contact, each in [0, n_nodes);
+ *   node_super (n_nodes) int32 supernode owning each node;
+ *   parent     (nsuper) int32 etree parent (> s) or -1;
+ *   qcount     (nsuper) int32 output: number of contacts reaching s;
+ *   qidx       (nsuper x m) int32 output: the list of supernode s starts at s*m.
+ * The work is enqueued on `cuda_stream` (NULL = legacy default stream) and the
+ * call returns after that stream has finished it.
+ *
+ * Working memory is a fixed static device array of ICR_NOALLOC_SCRATCH_WORDS
+ * 32-bit words (4 MiB), held by every GPU that loads the library until the
+ * process exits; the call allocates nothing.  nsuper * ceil(m / 32) must not
+ * exceed that size (ICR_EINVAL otherwise).  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Every call shares the array and clears the part
+ * it uses; calls that overlap on the GPU (for instance on two streams) race and
+ * must be serialised by the caller.  An out-of-range node or supernode id gives
+ * ICR_EINVAL with incomplete outputs. */
+#define ICR_NOALLOC_SCRATCH_WORDS (1 << 20)
+int icr_reach_noalloc(int32_t m, int32_t nsuper, int32_t n_nodes, const int32_t* nodes, const int32_t* node_super,
+                      const int32_t* parent, int32_t* qcount, int32_t* qidx, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,7 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_scene_destroy", "icr_set_params", "icr_set_system", "icr_set_mapping", "icr_set_proximity",
            "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
-           "icr_get", "icr_field_bytes", "icr_set_field")
+           "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc")
 
 
 class IcrError(RuntimeError):
@@ -81,6 +81,7 @@ def lib() -> ct.CDLL:
             "icr_get": [P, ct.c_int32, P, ct.c_size_t],
             "icr_field_bytes": [P, ct.c_int32, ct.POINTER(ct.c_size_t)],
             "icr_set_field": [P, ct.c_int32, P, ct.c_size_t],
+            "icr_reach_noalloc": [ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P, P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -104,6 +105,18 @@ def _arr(x, dtype, shape=None):
     if shape is not None:
         a = a.reshape(shape)
     return a
+
+
+NOALLOC_SCRATCH_WORDS = 1 << 20
+
+
+def reach_noalloc(m: int, nsuper: int, n_nodes: int, nodes_ptr: int, node_super_ptr: int, parent_ptr: int,
+                  qcount_ptr: int, qidx_ptr: int, stream: int = 0) -> None:
+    """icr_reach_noalloc: every argument after the sizes is a raw device
+    address owned by the caller; the library allocates nothing."""
+    _check(lib().icr_reach_noalloc(int(m), int(nsuper), int(n_nodes), P(nodes_ptr or None),
+                                   P(node_super_ptr or None), P(parent_ptr or None), P(qcount_ptr or None),
+                                   P(qidx_ptr or None), P(stream or None)))
 
 
 class Context:
