@@ -447,6 +447,8 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 //       1..31 fold the previous block's non-zero changes into all other
 //       residuals (streaming those rows of W) and prefetch, with cp.async,
 //       the next block's rows of W (its diagonal block and the block to its right).
+// A block whose contacts all have lambda~ = 0 and non-negative normal
+// residuals is a no-op and is passed without reading W.
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
 // with contacts in ascending order; the local rule uses reciprocals and an
 // rsqrt scale, so results differ from the plain formulas by rounding only.
@@ -462,6 +464,8 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) {
 }
 
 
+
+static constexpr int PGS_MAX_BLOCKS = 1024;   // contact blocks per scene (m <= 1024 BC)
 
 template <class T, int BC>
 __global__ void __launch_bounds__(1024, 1)
@@ -482,6 +486,8 @@ __global__ void __launch_bounds__(1024, 1)
   int* nzl = (int*)(dl + 2 * BR);  // 31 x BR: per streaming warp, rows with a non-zero change
   __shared__ T red[32];
   __shared__ int flag;
+  __shared__ int pref[2];            // stage k holds the prefetched rows of its block
+  __shared__ unsigned actb[PGS_MAX_BLOCKS / 32];   // block had a changing contact in its last visit
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
   const int nblk = (m + BC - 1) / BC;
@@ -503,6 +509,11 @@ __global__ void __launch_bounds__(1024, 1)
   };
   for (int i = tid; i < n3; i += nthr) lam[i] = warm ? lam_g[i] : T(0);
   for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
+  for (int i = tid; i < PGS_MAX_BLOCKS / 32; i += nthr) actb[i] = ~0u;
+  if (tid == 0) {
+    pref[0] = 1;
+    pref[1] = 0;
+  }
   prefetch(0, 0, tid, nthr);
   __syncthreads();
   if (warm) {
@@ -541,27 +552,55 @@ __global__ void __launch_bounds__(1024, 1)
       T q0 = T(0), q1 = T(0), q2 = T(0), l0 = T(0), l1 = T(0), l2 = T(0);
       T iWnn = T(0), Wt1n = T(0), Wt2n = T(0), iwt = T(0), mua = T(0);
       if (valid) {
-        const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
         q0 = r[R0 + 3 * lane] + p0;
         q1 = r[R0 + 3 * lane + 1] + p1;
         q2 = r[R0 + 3 * lane + 2] + p2;
         l0 = lam[R0 + 3 * lane];
         l1 = lam[R0 + 3 * lane + 1];
         l2 = lam[R0 + 3 * lane + 2];
+      }
+      p0 = p1 = p2 = T(0);
+      T e0 = 0, e1 = 0, e2 = 0;
+      // No contact of the block can change unless one starts active (changes
+      // only come from active contacts): such a block needs no rows of W.
+      const bool any = __ballot_sync(FULL, valid && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0))) != 0u;
+      if (lane == 0) {
+        if (any)
+          actb[b >> 5] |= 1u << (b & 31);
+        else
+          actb[b >> 5] &= ~(1u << (b & 31));
+      }
+      if (any && !pref[stg]) {
+        // rows not prefetched: warp 0 fetches them now
+        T* D = WD + stg * BR * BR;
+        T* Rr = WR + stg * BR * BR;
+        const int c1 = 3 * bn * BC, nr = 3 * nb;
+        for (int e = lane; e < nr * RCH; e += 32) {
+          const int i = e / RCH, c = (e % RCH) * CH;
+          const T* src = W + (int64_t)(R0 + i) * ldw;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(&D[i * BR + c])),
+                       "l"(src + R0 + c));
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(&Rr[i * BR + c])),
+                       "l"(src + c1 + c));
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+      }
+      if (any && valid) {
+        const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
         iWnn = T(1) / Wo[0];
         Wt1n = Wo[BR];
         Wt2n = Wo[2 * BR];
         iwt = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
         mua = mu[a0 + lane];
       }
-      p0 = p1 = p2 = T(0);
-      T e0 = 0, e1 = 0, e2 = 0;
       // A contact with lambda~ = 0 and a non-negative normal residual is left
       // unchanged by the local rule (lambda_n stays 0, so lambda_t is zeroed):
       // the sweep visits contacts in order but jumps over such contacts, which
       // gives exactly the iterate of visiting them.
-      int i = -1;
-      while (true) {
+      int i = any ? -1 : nb;
+      while (i < nb) {
         const unsigned act =
             __ballot_sync(FULL, valid && lane > i && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0)));
         if (act == 0u) break;
@@ -625,7 +664,21 @@ __global__ void __launch_bounds__(1024, 1)
       if (bn == b) p0 = p1 = p2 = T(0);   // single block: the residual already has them
     } else {
       const int t2 = tid - 32, n2 = nthr - 32;
-      if (t + 1 < total) prefetch(bn, 1 - stg, t2, n2);
+      if (t + 1 < total) {
+        // prefetch the next block's rows when it has a non-zero lambda~ or
+        // changed in its last visit (data no streaming warp writes, so every
+        // warp takes the same decision); a block that needs rows it did not
+        // get has them fetched by warp 0
+        const int nbn = min(BC, m - bn * BC), bn0 = 3 * bn * BC;
+        bool need = nblk <= 2 || ((actb[bn >> 5] >> (bn & 31)) & 1u);
+        if (!need) {
+          const bool nz = lane < nbn && (lam[bn0 + 3 * lane] != T(0) || lam[bn0 + 3 * lane + 1] != T(0) ||
+                                         lam[bn0 + 3 * lane + 2] != T(0));
+          need = __ballot_sync(FULL, nz) != 0u;
+        }
+        if (need) prefetch(bn, 1 - stg, t2, n2);
+        if (t2 == 0) pref[1 - stg] = need ? 1 : 0;
+      }
       if (pb >= 0) {
         // fold the previous block's non-zero changes into every row but this
         // block's and its own; each warp lists the non-zero rows by ballot
@@ -956,7 +1009,7 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (m == 0) return ICR_OK;
   const size_t smem = pgs_smem_bytes<T, BC>(m);
   // the opt-in limit (227 KiB) covers static plus dynamic shared memory
-  if (smem > 226 * 1024) {
+  if (smem > 226 * 1024 || (m + BC - 1) / BC > PGS_MAX_BLOCKS) {
     set_error("solve_friction: %d contacts exceed the single-CTA PGS shared-memory capacity", m);
     return ICR_EINVAL;
   }
