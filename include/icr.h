@@ -68,10 +68,23 @@ enum icr_precision {
 typedef struct icr_ctx icr_ctx;       /* one device + one CUDA stream + an HBM budget */
 typedef struct icr_scene icr_scene;   /* one deformable body with its contacts */
 
+/* How the contraction W_H = Y^T Y (Y = D^-1/2 L^-1 H^T) is computed in an FP32
+ * scene.  FP64 scenes always use FP64 SIMT arithmetic. */
+enum icr_contraction {
+  ICR_CONTRACT_AUTO = 0,    /* FP32 scenes: ICR_CONTRACT_TF32X3 */
+  ICR_CONTRACT_SIMT = 1,    /* FP32 CUDA cores */
+  ICR_CONTRACT_TF32X3 = 2,  /* tensor cores, each operand split into two TF32 parts, three products
+                               (FP32-level error) */
+  ICR_CONTRACT_TF32 = 3,    /* tensor cores, TF32 operands, FP32 accumulation */
+  ICR_CONTRACT_BF16 = 4     /* tensor cores, BF16 operands, FP32 accumulation */
+};
+
 typedef struct icr_params {
-  int32_t precision;   /* enum icr_precision */
-  int32_t n_sweeps;    /* PGS sweep cap (>= 0) */
-  double tol;          /* PGS stop when eps <= tol; tol <= 0 runs every sweep */
+  int32_t precision;     /* enum icr_precision */
+  int32_t n_sweeps;      /* PGS sweep cap (>= 0) */
+  double tol;            /* PGS stop when eps <= tol; tol <= 0 runs every sweep */
+  int32_t contraction;   /* enum icr_contraction */
+  int32_t reserved;      /* 0 */
 } icr_params;
 
 typedef struct icr_pgs_stats {

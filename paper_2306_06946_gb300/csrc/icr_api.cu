@@ -211,6 +211,21 @@ static void compute_G(int ns, const std::vector<int32_t>& sp, const std::vector<
   for (auto& t : pool) t.join();
 }
 
+namespace icr {
+int check_device_error(Scene* s) {
+  if (!s->dev_err.p) return ICR_OK;
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, s->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  if (h) {
+    CK(cudaMemsetAsync(s->dev_err.p, 0, sizeof(int), s->ctx->stream));
+    set_error("a bounded device-side wait ran out (tensor-core contraction); W_H is incomplete");
+    return ICR_ETIMEOUT;
+  }
+  return ICR_OK;
+}
+}  // namespace icr
+
 extern "C" {
 
 const char* icr_last_error(void) { return g_err.c_str(); }
@@ -272,6 +287,10 @@ static int check_params(const icr_params* p) {
     set_error("n_sweeps must be >= 0 and tol finite");
     return ICR_EINVAL;
   }
+  if (p->contraction < ICR_CONTRACT_AUTO || p->contraction > ICR_CONTRACT_BF16) {
+    set_error("unknown contraction mode %d", p->contraction);
+    return ICR_EINVAL;
+  }
   return ICR_OK;
 }
 
@@ -303,7 +322,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->obst_normals, &s->obst_anchors};
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
@@ -596,6 +615,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->y, s->n * T));
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
+  RET(dalloc(s, s->dev_err, sizeof(int)));
   if (m) {
     RET(upload(s, s->nodes, nodes, 4 * (size_t)m));
     RET(upload_T(s, s->bary, bary, 4 * (size_t)m));
@@ -610,6 +630,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   CK(cudaMemsetAsync(s->p0.p, 0, 3 * mm * sizeof(double), st));
   CK(cudaMemsetAsync(s->u.p, 0, 6 * mm * sizeof(double), st));
   CK(cudaMemsetAsync(s->stats.p, 0, sizeof(PgsDevStats), st));
+  CK(cudaMemsetAsync(s->dev_err.p, 0, sizeof(int), st));
   s->m = m;
   s->words = words;
   s->ldx = ldx;
@@ -807,6 +828,7 @@ int icr_solve_friction(icr_scene* s, int warm_start, icr_pgs_stats* stats) {
   RET(launch_pgs(s, warm_start ? 1 : 0, stats ? 1 : 0));
   s->has_lam = true;
   if (!stats) return ICR_OK;
+  RET(check_device_error(s));
   PgsDevStats d;
   CK(cudaMemcpyAsync(&d, s->stats.p, sizeof(d), cudaMemcpyDeviceToHost, s->ctx->stream));
   CK(cudaStreamSynchronize(s->ctx->stream));
@@ -906,6 +928,7 @@ int icr_get(icr_scene* s, int32_t field, void* dst, size_t bytes) {
   RET(check_scene(s));
   RET(need_mapping(s, "get"));
   RET(set_device(s));
+  RET(check_device_error(s));
   size_t c, e;
   RET(field_size(s, field, &c, &e));
   if (bytes != c * e || (c && !dst)) {

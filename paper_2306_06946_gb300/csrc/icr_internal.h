@@ -62,6 +62,7 @@ struct Scene {
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
+  DBuf dev_err;            // int set by a kernel whose bounded wait ran out
   uint64_t launches = 0;   // kernels launched by this scene
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
 
@@ -91,5 +92,9 @@ int launch_pgs(Scene* s, int warm_start, int want_residuals);
 int launch_update_proximity(Scene* s);
 int launch_correct_motion(Scene* s);
 int launch_linearize(Scene* s, int k);
+// tcgen05 contraction for supernodes with at least min_cols front columns (icr_tc.cu)
+int launch_contract_tc(Scene* s, int mode, int min_cols);
+// ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
+int check_device_error(Scene* s);
 
 }  // namespace icr

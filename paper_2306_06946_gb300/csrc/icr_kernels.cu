@@ -43,6 +43,7 @@ static constexpr int KB = 32;             // diagonal block of the triangular so
 static constexpr int SOLVE_THREADS = 192; // 2 x 96 columns
 static constexpr int CT = 64;             // contraction output tile
 static constexpr int CK_ = 16;            // contraction k-chunk
+static constexpr int TC_MIN_COLS = 64;    // fronts this wide use the tensor-core contraction
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -339,7 +340,7 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
 // Only the upper triangle (g(i) <= g(j)) is accumulated; k_symmetrize mirrors it.
 template <class T>
 __global__ void __launch_bounds__(256)
-    k_contract(int ntc, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+    k_contract(int ntc, int max_cols, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
                const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
                const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
   __shared__ T sA[CK_][CT + 1];
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(256)
   const int J = I + rem;
   const int ncol = 3 * qcount[s];
   const int nt = (ncol + CT - 1) / CT;
-  if (J >= nt) return;
+  if (J >= nt || ncol >= max_cols) return;   // wider fronts go to the tensor-core kernel
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
   const T* Xs = X + fr_ptr[s] * ldx;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -974,12 +975,22 @@ static int build_WH_T(Scene* s) {
   const int64_t nr = 3 * (int64_t)m;
   e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset WH");
+  // contraction: FP32 scenes put fronts of TC_MIN_COLS or more columns on the
+  // tensor cores (unless SIMT is asked for), the rest on CUDA cores
+  int mode = s->params.contraction;
+  if (sizeof(T) == 8) mode = ICR_CONTRACT_SIMT;
+  if (mode == ICR_CONTRACT_AUTO) mode = ICR_CONTRACT_TF32X3;
+  const int simt_max = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
   const int ntc = (int)((nr + CT - 1) / CT);
   const int npairs = ntc * (ntc + 1) / 2;
-  k_contract<T><<<dim3(npairs, ns), 256, 0, st>>>(ntc, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p,
+  k_contract<T><<<dim3(npairs, ns), 256, 0, st>>>(ntc, simt_max, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p,
                                                   (const int*)s->qcount.p, (const int*)s->qidx.p, m, X, ldx,
                                                   (T*)s->WH.p, nr);
   LAUNCH_OK("k_contract");
+  if (mode != ICR_CONTRACT_SIMT) {
+    const int rc = launch_contract_tc(s, mode, TC_MIN_COLS);
+    if (rc != ICR_OK) return rc;
+  }
   k_symmetrize<T><<<dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st>>>((int)nr, (T*)s->WH.p);
   LAUNCH_OK("k_symmetrize");
   return ICR_OK;

@@ -35,8 +35,12 @@ class IcrError(RuntimeError):
         self.code = code
 
 
+CONTRACT = {"auto": 0, "simt": 1, "tf32x3": 2, "tf32": 3, "bf16": 4}
+
+
 class Params(ct.Structure):
-    _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double)]
+    _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double),
+                ("contraction", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class PgsStats(ct.Structure):
@@ -153,9 +157,10 @@ class Context:
 class Scene:
     """icr_scene: one deformable body and its contacts."""
 
-    def __init__(self, ctx: Context, precision: int = FP32, n_sweeps: int = 50, tol: float = 0.0):
+    def __init__(self, ctx: Context, precision: int = FP32, n_sweeps: int = 50, tol: float = 0.0,
+                 contraction: str = "auto"):
         self.ctx = ctx
-        self.params = Params(precision, n_sweeps, tol)
+        self.params = Params(precision, n_sweeps, tol, CONTRACT[contraction], 0)
         h = P()
         _check(lib().icr_scene_create(ctx.h, ct.byref(h), ct.byref(self.params)))
         self.h = h
@@ -173,11 +178,13 @@ class Scene:
         except Exception:
             pass
 
-    def set_params(self, n_sweeps: int | None = None, tol: float | None = None):
+    def set_params(self, n_sweeps: int | None = None, tol: float | None = None, contraction: str | None = None):
         if n_sweeps is not None:
             self.params.n_sweeps = n_sweeps
         if tol is not None:
             self.params.tol = tol
+        if contraction is not None:
+            self.params.contraction = CONTRACT[contraction]
         _check(lib().icr_set_params(self.h, ct.byref(self.params)))
 
     def set_system(self, n, super_ptr, rowpat_ptr, rowpat, val_ptr, Lpanels, D, parent):
