@@ -304,3 +304,20 @@ def test_hbm_budget_is_enforced():
     with pytest.raises(icr.IcrError) as e:
         driver.load_system(sc, s.factor)
     assert e.value.code == icr.ENOMEM
+
+
+# ---------------------------------------------------------------- contraction variants
+@pytest.mark.parametrize("name", ["beam_mid", "liver_c1"])
+@pytest.mark.parametrize("mode,tol", [("simt", 1e-5), ("tf32x3", 1e-5), ("tf32", 2e-3), ("bf16", 2e-2)])
+def test_WH_contraction_modes(ctx, name, mode, tol):
+    from paper_2306_06946_gb300 import driver, icr
+    s = scene(name)
+    sc = icr.Scene(ctx, precision=icr.FP32, contraction=mode)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    sc.build_WH()
+    WH = sc.get("WH")
+    err = rel(WH, oracle_WH(name))
+    print(f"{name} {mode}: relative Frobenius error of W_H vs FP64 oracle {err:.3e}")
+    assert err < tol
+    assert np.array_equal(WH, WH.T)
