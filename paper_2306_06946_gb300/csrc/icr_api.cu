@@ -322,7 +322,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->obst_normals, &s->obst_anchors};
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
@@ -616,6 +616,17 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
   RET(dalloc(s, s->dev_err, sizeof(int)));
+  if (s->prec == ICR_FP32) {
+    // tensor-core operand blocks: per supernode ceil(3m/128) column tiles x
+    // ceil(w/32) row chunks, 32 KiB each (two TF32 planes)
+    const int tmax = std::max(1, (int)((3 * (int64_t)m + 127) / 128));
+    std::vector<int64_t> boff(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) boff[k + 1] = boff[k] + (int64_t)tmax * ((s->h_super_ptr[k + 1] - s->h_super_ptr[k] + 31) / 32);
+    RET(dalloc(s, s->tc_boff, (ns + 1) * sizeof(int64_t)));
+    RET(upload(s, s->tc_boff, boff.data(), ns + 1));
+    RET(dalloc(s, s->Ypk, (size_t)boff[ns] * 32768));
+    s->tc_tmax = tmax;
+  }
   if (m) {
     RET(upload(s, s->nodes, nodes, 4 * (size_t)m));
     RET(upload_T(s, s->bary, bary, 4 * (size_t)m));

@@ -63,6 +63,8 @@ struct Scene {
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
   DBuf dev_err;            // int set by a kernel whose bounded wait ran out
+  DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
+  int tc_tmax = 0;         // 128-column tiles of the widest possible front
   uint64_t launches = 0;   // kernels launched by this scene
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
 

@@ -2,14 +2,14 @@
 // scaled front Y_s = D_s^-1/2 X_s has at least TC_MIN_COLS columns
 // (Eq. "schur complemnt reformulated": W_H = H A^-1 H^T = X^T D^-1 X).
 //
-// Block (128 x 128 output tile pair I <= J, supernode s), 4 warps:
-//   * the K dimension (the w_s rows of Y_s) is streamed in 32-row chunks
-//     through two shared-memory stages; all threads convert their share of
-//     the chunk to the MMA operand type and store it in the K-major
-//     core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle);
-//   * one thread issues tcgen05.mma (M = N = 128) into a 128-column TMEM
-//     accumulator and commits to the stage's mbarrier, which releases the
-//     stage two chunks later;
+// k_pack_tc writes Y_s once per step as operand blocks (128 front columns x
+// 32 front rows, K-major core-matrix layout: 8 rows x 16 bytes per core matrix,
+// no swizzle), converted to the MMA operand type.
+// k_contract_tc, block (128 x 128 output tile pair I <= J, supernode s), 4 warps:
+//   * one thread streams the blocks of tiles I and J through three
+//     shared-memory stages with cp.async.bulk (mbarrier transaction counts)
+//     and issues tcgen05.mma (M = N = 128) into a 128-column TMEM
+//     accumulator, committing to the stage's release barrier;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w..32w+31, i.e. the tile's rows) and adds the upper-triangle
 //     entries into W_H.
@@ -87,30 +87,80 @@ template <int MODE>
 __host__ __device__ constexpr int tile_bytes() {
   return TM * KT * TcTraits<MODE>::EB;
 }
-template <int MODE>
-__host__ __device__ constexpr int stage_bytes() {
-  return 2 * TcTraits<MODE>::PARTS * tile_bytes<MODE>();   // A and B parts
-}
-
 // byte offset of element (r, k) of a K-major TM x KT tile: core matrix (r/8, k/C)
 // with C elements per 16 bytes; core matrices contiguous along K, 8-row groups
 // KT/C core matrices apart
 template <int EB>
-__device__ __forceinline__ int tile_off(int r, int k) {
-  constexpr int C = 16 / EB;
-  constexpr int SBO = (KT / C) * 128;
-  return (r >> 3) * SBO + (k / C) * 128 + (r & 7) * 16 + (k % C) * EB;
+__host__ __device__ constexpr int tile_off(int r, int k) {
+  return (r >> 3) * ((KT / (16 / EB)) * 128) + (k / (16 / EB)) * 128 + (r & 7) * 16 + (k % (16 / EB)) * EB;
+}
+
+constexpr int STAGES = 3;
+
+// Packs the scaled front Y_s into operand blocks: block (s, I, kt) holds rows
+// kt*KT.. of Y_s restricted to columns I*TM.., as PARTS planes of a K-major
+// TM x KT tile (tile row r = front column I*TM + r, tile k = front row kt*KT + k).
+// Staged through shared memory so that global reads and writes are coalesced.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+    k_pack_tc(int tmax, int min_cols, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+              const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ Y,
+              int64_t ldx, unsigned char* pk) {
+  using TR = TcTraits<MODE>;
+  __shared__ float sy[KT][TM + 1];
+  const int s = blockIdx.y;
+  const int ncol = 3 * qcount[s];
+  const int w = super_ptr[s + 1] - super_ptr[s];
+  const int nk = (w + KT - 1) / KT;
+  const int I = blockIdx.x / nk, kt = blockIdx.x % nk;
+  if (ncol < min_cols || I * TM >= ncol || I >= tmax) return;
+  const float* Ys = Y + fr_ptr[s] * ldx;
+  for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
+    const int k = e / TM, r = e % TM;
+    const int row = kt * KT + k, col = I * TM + r;
+    sy[k][r] = (row < w && col < ncol) ? Ys[(int64_t)row * ldx + col] : 0.f;
+  }
+  __syncthreads();
+  unsigned char* blk = pk + (boff[s] + (int64_t)I * nk + kt) * (int64_t)(TR::PARTS * tile_bytes<MODE>());
+  // 16-byte chunk q of the tile: core matrix (g, j), row r8: elements k = j*C .. j*C + C-1
+  constexpr int C = 16 / TR::EB;
+  constexpr int CHUNKS = TM * KT / C;
+  for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
+    const int cm = q >> 3, r8 = q & 7;                 // core matrix index, row inside it
+    const int g = cm / (KT / C), j = cm % (KT / C);
+    const int r = g * 8 + r8;
+    if constexpr (MODE == ICR_CONTRACT_BF16) {
+      unsigned short h[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sy[j * C + c][r]));
+      *(uint4*)(blk + q * 16) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                           h[6] | (h[7] << 16));
+    } else {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float x = sy[j * C + c][r];
+        hi[c] = to_tf32(x);
+        lo[c] = to_tf32(x - __uint_as_float(hi[c]));
+      }
+      *(uint4*)(blk + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      if constexpr (TR::PARTS == 2)
+        *(uint4*)(blk + tile_bytes<MODE>() + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(128, 1)
-    k_contract_tc(int ntc, int min_cols, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
-                  const int* __restrict__ qcount, const int* __restrict__ qidx, int m, const float* __restrict__ Y,
-                  int64_t ldx, float* WH, int64_t ldw, int* dev_err) {
+    k_contract_tc(int ntc, int tmax, int min_cols, const int* __restrict__ super_ptr,
+                  const int* __restrict__ qcount, const int* __restrict__ qidx, const int64_t* __restrict__ boff,
+                  int m, const unsigned char* __restrict__ pk, float* WH, int64_t ldw, int* dev_err) {
   using TR = TcTraits<MODE>;
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[2];
+  constexpr int BLK = TR::PARTS * tile_bytes<MODE>();   // one packed operand block
+  extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block)
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
   __shared__ uint32_t tmem_base;
+  __shared__ int ok_sh;
   const int s = blockIdx.y;
   int rem = blockIdx.x, I = 0;
   while (rem >= ntc - I) {
@@ -119,10 +169,13 @@ __global__ void __launch_bounds__(128, 1)
   }
   const int J = I + rem;
   const int ncol = 3 * qcount[s];
-  if (ncol < min_cols || J * TM >= ncol) return;   // uniform: before any allocation
-  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
-  const float* Ys = Y + fr_ptr[s] * ldx;
+  if (ncol < min_cols || J * TM >= ncol || J >= tmax) return;   // uniform: before any allocation
+  const int w = super_ptr[s + 1] - super_ptr[s];
+  const int nk = (w + KT - 1) / KT;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned char* blkA = pk + (boff[s] + (int64_t)I * nk) * BLK;
+  const unsigned char* blkB = pk + (boff[s] + (int64_t)J * nk) * BLK;
+  const bool same = I == J;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -130,84 +183,90 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bars[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&bars[1])), "r"(1));
+    for (int i = 0; i < STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&empty[i])), "r"(1));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n");
+    ok_sh = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = instr_desc(TR::TYPE);
-  constexpr int SBO = (KT / (16 / TR::EB)) * 128;
-  const int nk = (w + KT - 1) / KT;
-  bool ok = true;
-  for (int kt = 0; kt < nk; ++kt) {
-    const int buf = kt & 1;
-    unsigned char* st = smem + buf * stage_bytes<MODE>();
-    unsigned char* sA = st;                                   // PARTS tiles
-    unsigned char* sB = st + TR::PARTS * tile_bytes<MODE>();  // PARTS tiles
-    if (kt >= 2 && !mbar_wait(smem_u32(&bars[buf]), ((kt - 2) >> 1) & 1)) {
-      ok = false;
-      break;
-    }
-    // stage: element (r, k) of A is Y[k0 + k, I*TM + r], of B is Y[k0 + k, J*TM + r]
-    const int k0 = kt * KT;
-    for (int e = tid; e < TM * KT; e += 128) {
-      const int k = e / TM, r = e % TM;
-      const bool kin = k0 + k < w;
-      const int ca = I * TM + r, cb = J * TM + r;
-      const float a = (kin && ca < ncol) ? Ys[(int64_t)(k0 + k) * ldx + ca] : 0.f;
-      const float b = (kin && cb < ncol) ? Ys[(int64_t)(k0 + k) * ldx + cb] : 0.f;
-      const int o = tile_off<TR::EB>(r, k);
-      if constexpr (MODE == ICR_CONTRACT_BF16) {
-        const unsigned short ah = __bfloat16_as_ushort(__float2bfloat16_rn(a));
-        const unsigned short bh = __bfloat16_as_ushort(__float2bfloat16_rn(b));
-        *(unsigned short*)(sA + o) = ah;
-        *(unsigned short*)(sB + o) = bh;
-      } else {
-        const uint32_t ah = to_tf32(a), bh = to_tf32(b);
-        *(uint32_t*)(sA + o) = ah;
-        *(uint32_t*)(sB + o) = bh;
-        if constexpr (TR::PARTS == 2) {
-          *(uint32_t*)(sA + tile_bytes<MODE>() + o) = to_tf32(a - __uint_as_float(ah));
-          *(uint32_t*)(sB + tile_bytes<MODE>() + o) = to_tf32(b - __uint_as_float(bh));
+  if (tid == 0) {
+    const uint32_t idesc = instr_desc(TR::TYPE);
+    constexpr int SBO = (KT / (16 / TR::EB)) * 128;
+    const uint32_t bytes = same ? BLK : 2 * BLK;
+    bool ok = true;
+    for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
+      if (kt < nk) {   // load chunk kt
+        const int st = kt % STAGES;
+        if (kt >= STAGES && !mbar_wait(smem_u32(&empty[st]), ((kt / STAGES) - 1) & 1)) {
+          ok = false;
+          break;
         }
+        unsigned char* dA = smem + st * 2 * BLK;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&full[st])), "r"(bytes));
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(dA)),
+            "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
+            : "memory");
+        if (!same)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                  smem_u32(dA + BLK)),
+              "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
+              : "memory");
+      }
+      const int kc = kt - (STAGES - 1);
+      if (kc >= 0) {   // multiply chunk kc
+        const int st = kc % STAGES;
+        if (!mbar_wait(smem_u32(&full[st]), (kc / STAGES) & 1)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const unsigned char* sA = smem + st * 2 * BLK;
+        const unsigned char* sB = same ? sA : sA + BLK;
+#pragma unroll
+        for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
+          const uint32_t off = kk * 256;   // two core matrices along K per MMA
+#pragma unroll
+          for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
+            const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
+            const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
+            const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
+            const uint32_t acc = (kc > 0 || kk > 0 || term > 0) ? 1u : 0u;
+            if constexpr (MODE == ICR_CONTRACT_BF16)
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            else
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                      tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&empty[st])));
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-#pragma unroll
-      for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
-        const uint32_t off = kk * 256;   // two core matrices along K per MMA
-#pragma unroll
-        for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
-          const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
-          const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
-          const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
-          const uint32_t acc = (kt > 0 || kk > 0 || term > 0) ? 1u : 0u;
-          if constexpr (MODE == ICR_CONTRACT_BF16)
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          else
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&bars[buf])));
+    // the last commit tracks every MMA issued before it
+    if (ok && !mbar_wait(smem_u32(&empty[(nk - 1) % STAGES]), ((nk - 1) / STAGES) & 1)) ok = false;
+    if (!ok) {
+      ok_sh = 0;
+      atomicExch(dev_err, 1);
+      // let copies already in flight land before the block leaves
+      for (int st = 0; st < STAGES; ++st) mbar_wait(smem_u32(&full[st]), 0);
     }
   }
-  // all MMAs done: the last commit tracks every earlier MMA of this thread
-  if (ok && nk > 0 && !mbar_wait(smem_u32(&bars[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) ok = false;
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
-  if (ok && nk > 0) {
+  if (ok_sh) {
     const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread (TMEM lane)
     const bool row_ok = li < ncol;
     const int64_t gi = row_ok ? 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3 : 0;
@@ -229,8 +288,6 @@ __global__ void __launch_bounds__(128, 1)
         atomicAdd(&WH[gi * ldw + gj], __uint_as_float(v[j]));
       }
     }
-  } else if (!ok && tid == 0) {
-    atomicExch(dev_err, 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
@@ -243,17 +300,24 @@ int contract_tc_T(Scene* s, int min_cols) {
   const int64_t nr = 3 * (int64_t)m;
   const int ntc = (int)((nr + TM - 1) / TM);
   const int npairs = ntc * (ntc + 1) / 2;
-  const size_t smem = 2 * (size_t)stage_bytes<MODE>();
+  const size_t smem = STAGES * 2 * (size_t)(TcTraits<MODE>::PARTS * tile_bytes<MODE>());
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_contract_tc)");
     attr = true;
   }
-  k_contract_tc<MODE><<<dim3(npairs, s->ns), 128, smem, s->ctx->stream>>>(
-      ntc, min_cols, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
-      (const int*)s->qidx.p, m, (const float*)s->X.p, s->ldx, (float*)s->WH.p, nr, (int*)s->dev_err.p);
+  const int nkmax = (s->wmax + KT - 1) / KT;
+  k_pack_tc<MODE><<<dim3(s->tc_tmax * nkmax, s->ns), 256, 0, s->ctx->stream>>>(
+      s->tc_tmax, min_cols, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
+      (const int64_t*)s->tc_boff.p, (const float*)s->X.p, s->ldx, (unsigned char*)s->Ypk.p);
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc");
+  ++s->launches;
+  k_contract_tc<MODE><<<dim3(npairs, s->ns), 128, smem, s->ctx->stream>>>(
+      ntc, s->tc_tmax, min_cols, (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
+      (const int64_t*)s->tc_boff.p, m, (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_contract_tc");
   ++s->launches;
   return ICR_OK;
