@@ -280,7 +280,7 @@ def run_icr(args):
         for k in range(scene.n_newton):
             sc.linearize(k)
             sc.update_W()
-            sc.solve_friction(warm_start=(k == 0))
+            sc.solve_friction(warm_start=False)
             sc.update_proximity()
         sc.correct_motion(want_dq=False, reset=True)
 
@@ -323,7 +323,7 @@ def run_icr(args):
             phases[name].append((a, b))
         for k in range(scene.n_newton):
             for name, fn in [("linearize", lambda: sc.linearize(k)), ("update_W", sc.update_W),
-                             ("pgs", lambda: sc.solve_friction(warm_start=(k == 0))),
+                             ("pgs", lambda: sc.solve_friction(warm_start=False)),
                              ("update_proximity", sc.update_proximity)]:
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream); fn(); b.record(stream)
@@ -371,7 +371,7 @@ def run_icr(args):
             for k in range(scene.n_newton):
                 sc.linearize(k)
                 sc.update_W()
-                sc.solve_friction(warm_start=(k == 0))
+                sc.solve_friction(warm_start=False)
                 sc.update_proximity()
             sc.correct_motion(want_dq=True, reset=True, out=h_dq)
 

@@ -82,7 +82,7 @@ enum icr_contraction {
 typedef struct icr_params {
   int32_t precision;     /* enum icr_precision */
   int32_t n_sweeps;      /* PGS sweep cap (>= 0) */
-  double tol;            /* PGS stop when eps <= tol; tol <= 0 runs every sweep */
+  double tol;            /* PGS stop when eps <= tol (tol > 0); a sweep without change always stops */
   int32_t contraction;   /* enum icr_contraction */
   int32_t reserved;      /* 0 */
 } icr_params;
@@ -193,6 +193,8 @@ int icr_update_W(icr_scene* scene);
  * lambda_n - r_n / W_nn); the tangential residual is updated with the change
  * of lambda_n; lambda_t <- lambda_t - r_t / w_t with w_t = (W_t1t1 + W_t2t2)/2;
  * lambda_t is projected on the disc ||lambda_t|| <= mu lambda_n.
+ * The solve stops after n_sweeps, when eps <= tol (tol > 0), or after a sweep
+ * that changed no lambda~ (a fixed point: every later sweep would repeat it).
  * warm_start = 0 starts from lambda~ = 0, 1 from the last solve's lambda~.
  * stats (may be NULL) receives the sweep count, eps and FP64 residuals (this
  * synchronises).  Returns ICR_ENOCONV (non-fatal) when tol > 0 and eps > tol

@@ -16,7 +16,10 @@ Local rule (the paper only names the two laws):
   3. tangent: lambda_t <- lambda_t - r_t / w_t,  w_t = (W_t1t1 + W_t2t2) / 2
   4. project lambda_t onto the disc of radius mu * lambda_n.
 Stopping (Alg. 1): eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i|| (0 when
-lambda^i = 0); stop when eps <= tol; tol <= 0 runs the full sweep count.
+lambda^i = 0); stop when eps <= tol for a positive tol.  A sweep that changes
+no lambda~ at all is a fixed point of the iteration (every later sweep repeats
+it exactly), so the solve also stops there: this is Alg. 1's test with
+PGS_error = 0.
 """
 from __future__ import annotations
 
@@ -56,7 +59,7 @@ def pgs(W: np.ndarray, delta: np.ndarray, mu: np.ndarray, lam0=None, sweeps: int
         done += 1
         nrm = float(np.linalg.norm(lam))
         eps = float(np.linalg.norm(lam - prev)) / nrm if nrm > 0 else 0.0
-        if tol > 0 and eps <= tol:
+        if np.array_equal(lam, prev) or (tol > 0 and eps <= tol):
             break
     return lam, done, eps
 

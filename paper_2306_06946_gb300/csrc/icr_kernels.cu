@@ -450,6 +450,8 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 //       the next block's rows of W (its diagonal block and the block to its right).
 // A block whose contacts all have lambda~ = 0 and non-negative normal
 // residuals is a no-op and is passed without reading W.
+// The solve stops when eps <= tol (tol > 0) or after a sweep that changed
+// nothing, a fixed point of the iteration (Alg. 1's test with PGS_error = 0).
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
 // with contacts in ascending order; the local rule uses reciprocals and an
 // rsqrt scale, so results differ from the plain formulas by rounding only.
@@ -488,6 +490,7 @@ __global__ void __launch_bounds__(1024, 1)
   __shared__ T red[32];
   __shared__ int flag;
   __shared__ int pref[2];            // stage k holds the prefetched rows of its block
+  __shared__ int changed;            // some lambda~ changed in the current sweep
   __shared__ unsigned actb[PGS_MAX_BLOCKS / 32];   // block had a changing contact in its last visit
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
@@ -514,6 +517,7 @@ __global__ void __launch_bounds__(1024, 1)
   if (tid == 0) {
     pref[0] = 1;
     pref[1] = 0;
+    changed = 0;
   }
   prefetch(0, 0, tid, nthr);
   __syncthreads();
@@ -657,6 +661,7 @@ __global__ void __launch_bounds__(1024, 1)
         r[R0 + 3 * lane + 1] = q1;
         r[R0 + 3 * lane + 2] = q2;
       }
+      if (__any_sync(FULL, e0 != T(0) || e1 != T(0) || e2 != T(0)) && lane == 0) changed = 1;
       if (lane < BC) {                // lanes without a change write zeros
         dl[dc * BR + 3 * lane] = e0;
         dl[dc * BR + 3 * lane + 1] = e1;
@@ -725,7 +730,10 @@ __global__ void __launch_bounds__(1024, 1)
         for (int k = 0; k < 32; ++k) tot += red[k];
         const T e = tot > T(0) ? sqrt(ds / tot) : T(0);
         red[0] = e;
-        flag = (tol > 0.0 && (double)e <= tol) ? 1 : 0;
+        // stop at eps <= tol, or after a sweep that changed nothing (a fixed
+        // point: every later sweep would repeat it exactly)
+        flag = (!changed || (tol > 0.0 && (double)e <= tol)) ? 1 : 0;
+        changed = 0;
       }
       __syncthreads();
       eps = (double)red[0];
