@@ -109,7 +109,8 @@ enum icr_field {
   ICR_FIELD_MU = 6,        /* (m) double, friction coefficients */
   ICR_FIELD_U = 7,         /* (3m) double, accumulated sum_k C_k^T lambda~_k */
   ICR_FIELD_REACH_PTR = 8, /* (nsuper + 1) int32, CSR offsets of the reached contacts */
-  ICR_FIELD_REACH_IDX = 9  /* (reach_ptr[nsuper]) int32, ascending contact ids per supernode */
+  ICR_FIELD_REACH_IDX = 9, /* (reach_ptr[nsuper]) int32, ascending contact ids per supernode */
+  ICR_FIELD_DQ = 10        /* (n) double, the last corrective motion */
 };
 
 /* Thread-local text of the last error (never NULL). */
@@ -210,6 +211,36 @@ int icr_update_proximity(icr_scene* scene, double* dp_out);
  * u = sum_k C_k^T lambda~_k.  dq_out (n double, host) may be NULL.  reset = 1
  * clears u afterwards (start of the next time step). */
 int icr_correct_motion(icr_scene* scene, double* dq_out, int reset);
+
+/* One time step of the fast scheme (Alg. 3) enqueued entirely on the device,
+ * with directions from the scene's obstacle (icr_linearize): p <- p_0, u <- 0,
+ * icr_build_WH, then n_newton x (icr_linearize(k), icr_update_W,
+ * icr_solve_friction from lambda~ = 0, icr_update_proximity), then
+ * icr_correct_motion without a host copy (dq, p, lambda~ stay on the device).
+ * Needs a system, a mapping, p_0 and an obstacle; returns once the work is
+ * enqueued. */
+int icr_step(icr_scene* scene, int32_t n_newton);
+/* Capture icr_step(scene, n_newton) into a CUDA graph owned by the scene (one
+ * plain step runs first so that every kernel is set up).  The context's stream
+ * must not be the legacy default stream (ICR_EINVAL).  A later icr_set_mapping
+ * invalidates the graph. */
+int icr_step_capture(icr_scene* scene, int32_t n_newton);
+/* Launch the captured step on the context's stream (ICR_ESTATE without one). */
+int icr_step_launch(icr_scene* scene);
+/* Wait until the context's stream has finished the scene's work. */
+int icr_sync(icr_scene* scene);
+
+/* Continuous batching of time steps over resident scenes (a request loop).
+ * Every scene must have a captured step (icr_step_capture) and live on one
+ * device.  Request r asks for one step of scene req_scene[r] at time
+ * req_arrival_s[r] (seconds from the call, non-decreasing).  The loop replays
+ * the schedule in real time with n_slots concurrent streams: an arrived
+ * request starts on a free slot as soon as its scene has no step in flight, so
+ * requests that arrive while others run on the GPU overlap with them.
+ * latency_s[r] receives arrival-to-completion seconds, *makespan_s (may be
+ * NULL) the time until the last completion.  ICR_ETIMEOUT after timeout_s. */
+int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene, const double* req_arrival_s,
+              int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s);
 
 /* Copy a field to host memory as double (float fields) or int32 (index fields).
  * `bytes` must equal the field's size; ICR_EINVAL otherwise. */

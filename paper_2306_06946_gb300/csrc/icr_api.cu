@@ -324,6 +324,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
                  &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors};
   for (DBuf* b : all) dfree(s, *b);
+  if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
   if (--c->scenes == 0 && c->destroyed) delete c;
@@ -649,6 +650,10 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   s->has_mapping = true;
   s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
   s->obst_kind = 0;
+  if (s->step_graph) {
+    cudaGraphExecDestroy(s->step_graph);
+    s->step_graph = nullptr;
+  }
   return ICR_OK;
 }
 
@@ -890,6 +895,38 @@ int icr_correct_motion(icr_scene* s, double* dq_out, int reset) {
   return ICR_OK;
 }
 
+static int step_enqueue(Scene* s, int n_newton) {
+  if (!s->has_mapping || !s->has_system) {
+    set_error("step: needs icr_set_system and icr_set_mapping");
+    return ICR_ESTATE;
+  }
+  if (s->obst_kind == 0) {
+    set_error("step: needs an obstacle (icr_set_obstacle_plane / icr_set_obstacle_sphere)");
+    return ICR_ESTATE;
+  }
+  if (n_newton < 0 || (s->obst_kind == 1 && n_newton > s->obst_iters)) {
+    set_error("step: %d Newton iterations not available for this obstacle", n_newton);
+    return ICR_EINVAL;
+  }
+  cudaStream_t st = s->ctx->stream;
+  if (s->m) {
+    CK(cudaMemcpyAsync(s->p.p, s->p0.p, 3 * (size_t)s->m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemsetAsync(s->u.p, 0, 6 * (size_t)s->m * sizeof(double), st));
+  }
+  RET(launch_build_WH(s));
+  s->has_WH = true;
+  for (int k = 0; k < n_newton; ++k) {
+    RET(launch_linearize(s, k));
+    RET(launch_update_W(s));
+    RET(launch_pgs(s, 0, 0));
+    RET(launch_update_proximity(s));
+  }
+  RET(launch_correct_motion(s));
+  if (s->m) CK(cudaMemsetAsync(s->u.p, 0, 3 * (size_t)s->m * sizeof(double), st));
+  s->has_dirs = s->has_W = s->has_lam = true;
+  return ICR_OK;
+}
+
 static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
   const size_t m = s->m;
   *elem = sizeof(double);
@@ -902,6 +939,7 @@ static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
     case ICR_FIELD_U: *count = 3 * m; break;
     case ICR_FIELD_C: *count = 9 * m; break;
     case ICR_FIELD_MU: *count = m; break;
+    case ICR_FIELD_DQ: *count = s->n; break;
     case ICR_FIELD_REACH_PTR:
       *count = s->ns + 1;
       *elem = sizeof(int32_t);
@@ -920,6 +958,66 @@ static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
     default: set_error("unknown field %d", f); return ICR_EINVAL;
   }
   return ICR_OK;
+}
+
+int icr_step(icr_scene* s, int32_t n_newton) {
+  RET(check_scene(s));
+  RET(set_device(s));
+  return step_enqueue(s, n_newton);
+}
+
+int icr_step_capture(icr_scene* s, int32_t n_newton) {
+  RET(check_scene(s));
+  RET(set_device(s));
+  cudaStream_t st = s->ctx->stream;
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) {
+    set_error("step_capture: the context needs its own CUDA stream to capture a graph");
+    return ICR_EINVAL;
+  }
+  RET(step_enqueue(s, n_newton));   // a plain step sets every kernel up before capture
+  CK(cudaStreamSynchronize(st));
+  if (s->step_graph) {
+    cudaGraphExecDestroy(s->step_graph);
+    s->step_graph = nullptr;
+  }
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const uint64_t before = s->launches;
+  const int rc = step_enqueue(s, n_newton);
+  s->graph_kernels = s->launches - before;   // recorded into the graph, not launched
+  s->launches = before;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc != ICR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t e2 = cudaGraphInstantiate(&s->step_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    s->step_graph = nullptr;
+    return cuda_fail(e2, "cudaGraphInstantiate");
+  }
+  return ICR_OK;
+}
+
+int icr_step_launch(icr_scene* s) {
+  RET(check_scene(s));
+  if (!s->step_graph) {
+    set_error("step_launch: no captured step (icr_step_capture)");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  CK(cudaGraphLaunch(s->step_graph, s->ctx->stream));
+  s->launches += s->graph_kernels;
+  return ICR_OK;
+}
+
+int icr_sync(icr_scene* s) {
+  RET(check_scene(s));
+  RET(set_device(s));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  return check_device_error(s);
 }
 
 int icr_field_bytes(icr_scene* s, int32_t field, size_t* out) {
@@ -955,6 +1053,7 @@ int icr_get(icr_scene* s, int32_t field, void* dst, size_t bytes) {
     case ICR_FIELD_DELTA: return download_T(s, s->delta, (double*)dst, c);
     case ICR_FIELD_C: return download_T(s, s->C, (double*)dst, c);
     case ICR_FIELD_MU: return download_T(s, s->mu, (double*)dst, c);
+    case ICR_FIELD_DQ: return download_T(s, s->dq, (double*)dst, c);
     case ICR_FIELD_P:
       CK(cudaMemcpyAsync(dst, s->p.p, bytes, cudaMemcpyDeviceToHost, st));
       break;

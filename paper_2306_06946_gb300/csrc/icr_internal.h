@@ -66,6 +66,8 @@ struct Scene {
   DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
   int tc_tmax = 0;         // 128-column tiles of the widest possible front
   uint64_t launches = 0;   // kernels launched by this scene
+  cudaGraphExec_t step_graph = nullptr;   // captured icr_step
+  uint64_t graph_kernels = 0;             // kernels in the captured step
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
 
   // ---- obstacle (device linearisation)

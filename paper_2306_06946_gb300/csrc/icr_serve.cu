@@ -1,0 +1,142 @@
+// Request loop for many resident scenes: continuous batching of time steps.
+//
+// Every scene keeps its system, mapping, obstacle and captured step graph
+// (icr_step_capture) on the device.  A request asks for one time step of one
+// scene at a given arrival time.  The loop replays the arrival schedule in
+// real time: a request is admitted once it has arrived, waits while its scene
+// already has a step in flight (a scene's steps share its buffers), and is
+// started on the first free slot stream; slots complete independently, so
+// requests that arrive while others run on the GPU overlap with them.  The
+// latency of a request is the time from its arrival to the moment its slot's
+// completion event is seen.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdint>
+#include <deque>
+#include <vector>
+
+#include "icr_internal.h"
+
+struct icr_scene : icr::Scene {};
+
+using namespace icr;
+
+namespace {
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  int request = -1;   // request running on the slot, -1 when free
+};
+
+int serve_fail(std::vector<Slot>& slots, int code) {
+  for (Slot& sl : slots) {
+    if (sl.stream) {
+      cudaStreamSynchronize(sl.stream);
+      cudaStreamDestroy(sl.stream);
+    }
+    if (sl.done) cudaEventDestroy(sl.done);
+  }
+  return code;
+}
+
+}  // namespace
+
+extern "C" int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene,
+                         const double* req_arrival_s, int32_t n_req, int32_t n_slots, double timeout_s,
+                         double* latency_s, double* makespan_s) {
+  if (!scenes || n_scenes <= 0 || n_req < 0 || (n_req > 0 && (!req_scene || !req_arrival_s || !latency_s)) ||
+      n_slots <= 0 || !(timeout_s > 0)) {
+    set_error("serve: need scenes, a request schedule, n_slots > 0 and a positive timeout");
+    return ICR_EINVAL;
+  }
+  int device = -1;
+  for (int i = 0; i < n_scenes; ++i) {
+    if (!scenes[i] || !scenes[i]->step_graph) {
+      set_error("serve: scene %d has no captured step (icr_step_capture)", i);
+      return ICR_ESTATE;
+    }
+    if (device < 0) device = scenes[i]->ctx->device;
+    if (scenes[i]->ctx->device != device) {
+      set_error("serve: all scenes must live on one device");
+      return ICR_EINVAL;
+    }
+  }
+  for (int r = 0; r < n_req; ++r) {
+    if (req_scene[r] < 0 || req_scene[r] >= n_scenes || !(req_arrival_s[r] >= 0)) {
+      set_error("serve: request %d has a bad scene id or arrival time", r);
+      return ICR_EINVAL;
+    }
+    if (r > 0 && req_arrival_s[r] < req_arrival_s[r - 1]) {
+      set_error("serve: arrival times must be non-decreasing");
+      return ICR_EINVAL;
+    }
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "serve: cudaSetDevice");
+  // scenes' own streams must be idle before their graphs move to slot streams
+  for (int i = 0; i < n_scenes; ++i) {
+    e = cudaStreamSynchronize(scenes[i]->ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "serve: scene stream");
+  }
+  std::vector<Slot> slots(n_slots);
+  for (Slot& sl : slots) {
+    e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return serve_fail(slots, cuda_fail(e, "serve: cudaStreamCreate"));
+    e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return serve_fail(slots, cuda_fail(e, "serve: cudaEventCreate"));
+  }
+  using clock = std::chrono::steady_clock;
+  const auto t0 = clock::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(clock::now() - t0).count(); };
+  std::vector<char> busy(n_scenes, 0);
+  std::deque<int> pending;   // arrived, not yet started, in arrival order
+  int next = 0, finished = 0;
+  while (finished < n_req) {
+    const double t = now_s();
+    if (t > timeout_s) {
+      set_error("serve: %d of %d requests unfinished after %g s", n_req - finished, n_req, timeout_s);
+      return serve_fail(slots, ICR_ETIMEOUT);
+    }
+    while (next < n_req && req_arrival_s[next] <= t) pending.push_back(next++);
+    // completions
+    for (Slot& sl : slots) {
+      if (sl.request < 0) continue;
+      e = cudaEventQuery(sl.done);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) return serve_fail(slots, cuda_fail(e, "serve: step"));
+      latency_s[sl.request] = now_s() - req_arrival_s[sl.request];
+      busy[req_scene[sl.request]] = 0;
+      sl.request = -1;
+      ++finished;
+    }
+    // starts: oldest pending request whose scene is idle, on a free slot
+    for (Slot& sl : slots) {
+      if (sl.request >= 0) continue;
+      auto it = std::find_if(pending.begin(), pending.end(), [&](int r) { return !busy[req_scene[r]]; });
+      if (it == pending.end()) break;
+      const int r = *it;
+      pending.erase(it);
+      Scene* s = scenes[req_scene[r]];
+      e = cudaGraphLaunch(s->step_graph, sl.stream);
+      if (e != cudaSuccess) return serve_fail(slots, cuda_fail(e, "serve: cudaGraphLaunch"));
+      e = cudaEventRecord(sl.done, sl.stream);
+      if (e != cudaSuccess) return serve_fail(slots, cuda_fail(e, "serve: cudaEventRecord"));
+      s->launches += s->graph_kernels;
+      busy[req_scene[r]] = 1;
+      sl.request = r;
+    }
+  }
+  if (makespan_s) *makespan_s = now_s();
+  for (Slot& sl : slots) {
+    cudaStreamDestroy(sl.stream);
+    cudaEventDestroy(sl.done);
+  }
+  for (int i = 0; i < n_scenes; ++i) {
+    const int rc = check_device_error(scenes[i]);
+    if (rc != ICR_OK) return rc;
+  }
+  return ICR_OK;
+}

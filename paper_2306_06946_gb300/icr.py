@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libicr.so")
 OK, EINVAL, ENOTSPD, ESTATE, ENOMEM, ENOCONV, ETIMEOUT, ECUDA = range(8)
 FP32, FP64 = 0, 1
 FIELD = {"WH": 0, "W": 1, "LAMBDA": 2, "P": 3, "DELTA": 4, "C": 5, "MU": 6, "U": 7,
-         "REACH_PTR": 8, "REACH_IDX": 9}
+         "REACH_PTR": 8, "REACH_IDX": 9, "DQ": 10}
 _INT_FIELDS = {"REACH_PTR", "REACH_IDX"}
 
 # every symbol include/icr.h declares
@@ -26,7 +26,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_scene_destroy", "icr_set_params", "icr_set_system", "icr_set_mapping", "icr_set_proximity",
            "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
-           "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc")
+           "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
+           "icr_step_launch", "icr_sync", "icr_serve")
 
 
 class IcrError(RuntimeError):
@@ -86,6 +87,11 @@ def lib() -> ct.CDLL:
             "icr_field_bytes": [P, ct.c_int32, ct.POINTER(ct.c_size_t)],
             "icr_set_field": [P, ct.c_int32, P, ct.c_size_t],
             "icr_reach_noalloc": [ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P, P],
+            "icr_step": [P, ct.c_int32],
+            "icr_step_capture": [P, ct.c_int32],
+            "icr_step_launch": [P],
+            "icr_sync": [P],
+            "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -121,6 +127,18 @@ def reach_noalloc(m: int, nsuper: int, n_nodes: int, nodes_ptr: int, node_super_
     _check(lib().icr_reach_noalloc(int(m), int(nsuper), int(n_nodes), P(nodes_ptr or None),
                                    P(node_super_ptr or None), P(parent_ptr or None), P(qcount_ptr or None),
                                    P(qidx_ptr or None), P(stream or None)))
+
+
+def serve(scenes, req_scene, req_arrival_s, n_slots: int, timeout_s: float = 120.0):
+    """icr_serve: returns (latency_s per request, makespan_s)."""
+    arr = (P * len(scenes))(*[sc.h for sc in scenes])
+    rs = _arr(req_scene, np.int32)
+    ra = _arr(req_arrival_s, np.float64)
+    lat = np.zeros(rs.size)
+    mk = ct.c_double()
+    _check(lib().icr_serve(arr, len(scenes), _ptr(rs), _ptr(ra), int(rs.size), int(n_slots), float(timeout_s),
+                           _ptr(lat), ct.byref(mk)))
+    return lat, float(mk.value)
 
 
 class Context:
@@ -267,6 +285,18 @@ class Scene:
             dq = out if out is not None else np.empty(self.n)
         _check(lib().icr_correct_motion(self.h, _ptr(dq), int(bool(reset))))
         return dq
+
+    def step(self, n_newton: int):
+        _check(lib().icr_step(self.h, int(n_newton)))
+
+    def step_capture(self, n_newton: int):
+        _check(lib().icr_step_capture(self.h, int(n_newton)))
+
+    def step_launch(self):
+        _check(lib().icr_step_launch(self.h))
+
+    def sync(self):
+        _check(lib().icr_sync(self.h))
 
     def field_bytes(self, field: str) -> int:
         v = ct.c_size_t()

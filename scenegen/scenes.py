@@ -99,6 +99,44 @@ def ellipsoid_scene(semi=(0.075, 0.05, 0.04), target_nodes=3000, m=300, seed=1, 
                  obst, n_newton, n_sweeps, h)
 
 
+def _batch_member(args):
+    """One scene of the batched workload (kept at module level for process pools)."""
+    i, nodes, m, mu_seed = args
+    rng = np.random.default_rng(mu_seed)
+    if i % 2 == 0:
+        sc = ellipsoid_scene(target_nodes=nodes, m=m, seed=1000 + i, name=f"batch{i}_ellipsoid")
+    else:
+        length = max(4, int(round(nodes / 16)))
+        cand = 2 * 3 * (length - 1)   # tets with a face on the bottom (z = 0)
+        sc = beam_scene(nodes_xyz=(length, 4, 4), m=min(m, cand), seed=1000 + i, n_newton=5,
+                        name=f"batch{i}_beam")
+    sc.mu = rng.uniform(0.1, 0.6, size=sc.m)
+    return sc
+
+
+def batch_specs(n_scenes=64, seed=2, min_nodes=500, max_nodes=8000, min_m=20, max_m=600):
+    """Sizes of the batched workload: node counts log-uniform in [min_nodes,
+    max_nodes], contact counts uniform in [min_m, max_m] (beams are capped at
+    their number of bottom tets), scenes alternate ellipsoid and beam."""
+    rng = np.random.default_rng(seed)
+    nodes = np.exp(rng.uniform(np.log(min_nodes), np.log(max_nodes), size=n_scenes)).round().astype(int)
+    ms = rng.integers(min_m, max_m + 1, size=n_scenes)
+    return [(i, int(nodes[i]), int(min(ms[i], nodes[i] // 3)), seed * 1000 + i) for i in range(n_scenes)]
+
+
+def batch_scenes(n_scenes=64, seed=2, processes=None, **kw) -> list[Scene]:
+    """The batched workload (64 independent scenes by default), generated in a
+    spawn-started process pool."""
+    import multiprocessing as mp
+    import os
+    specs = batch_specs(n_scenes, seed, **kw)
+    procs = processes or min(len(specs), os.cpu_count() or 1)
+    if procs <= 1:
+        return [_batch_member(a) for a in specs]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_batch_member, specs, chunksize=1)
+
+
 def beam_c0() -> Scene:
     return beam_scene(name="beam_c0")
 

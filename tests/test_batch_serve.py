@@ -1,0 +1,112 @@
+"""Device-resident steps, captured step graphs, batching and the request loop.
+
+A scene's step must give the same result when it runs alone and when it runs
+in the mix with other scenes' steps on other streams (batching and serving),
+and the device-resident step must match the host-driven call sequence and the
+FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import newton as nw
+
+from gpu_helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def batch():
+    import scenegen
+    return scenegen.batch_scenes(6, seed=5, min_nodes=200, max_nodes=900, min_m=20, max_m=120)
+
+
+def _load(icr, driver, ctx, s):
+    sc = icr.Scene(ctx, precision=icr.FP32, n_sweeps=s.n_sweeps)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    driver.load_obstacle(sc, s.obstacle)
+    sc.set_field("MU", s.mu)
+    return sc
+
+
+@pytest.fixture(scope="module")
+def loaded(batch, torch_mod):
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    streams = [torch_mod.cuda.Stream() for _ in batch]
+    ctxs = [icr.Context(0, st.cuda_stream) for st in streams]
+    scenes = [_load(icr, driver, c, s) for c, s in zip(ctxs, batch)]
+    alone = []
+    for sc, s in zip(scenes, batch):
+        sc.step(s.n_newton)
+        sc.sync()
+        alone.append(sc.get("DQ"))
+    return streams, ctxs, scenes, alone
+
+
+def test_step_matches_host_sequence_and_oracle(batch, loaded):
+    from paper_2306_06946_gb300 import driver, icr
+    _, ctxs, scenes, alone = loaded
+    for i in (0, 1):
+        s = batch[i]
+        sc2 = _load(icr, driver, ctxs[i], s)
+        dq_host, _ = driver.newton_step(sc2, s.n_newton)
+        assert rel(alone[i], dq_host) < 1e-5
+        ref = nw.fast_scheme(s.A, s.nodes, s.bary, s.mu, s.p0, s.linearize, s.n_newton, s.n_sweeps)
+        assert rel(alone[i], ref["dq"]) < 1e-4
+
+
+def test_batch_in_mix_equals_alone(batch, loaded):
+    from paper_2306_06946_gb300 import icr
+    _, _, scenes, alone = loaded
+    for sc, s in zip(scenes, batch):
+        sc.step_capture(s.n_newton)
+    n = len(scenes)
+    lat, makespan = icr.serve(scenes, np.arange(n), np.zeros(n), n_slots=n)
+    assert np.all(lat > 0) and makespan >= lat.max() * 0.999
+    for sc, a in zip(scenes, alone):
+        assert rel(sc.get("DQ"), a) < 1e-5
+
+
+def test_serve_poisson_arrivals(batch, loaded):
+    from paper_2306_06946_gb300 import icr
+    _, _, scenes, alone = loaded
+    for sc, s in zip(scenes, batch):
+        sc.step_capture(s.n_newton)
+    rng = np.random.default_rng(9)
+    nreq = 40
+    arrivals = np.cumsum(rng.exponential(1.0 / 2000.0, size=nreq))
+    which = rng.integers(0, len(scenes), size=nreq)
+    lat, makespan = icr.serve(scenes, which, arrivals, n_slots=4)
+    assert lat.shape == (nreq,) and np.all(lat > 0)
+    assert makespan >= arrivals[-1]
+    for sc, a in zip(scenes, alone):
+        assert rel(sc.get("DQ"), a) < 1e-5
+
+
+def test_serve_argument_and_state_errors(batch, torch_mod):
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    st = torch_mod.cuda.Stream()
+    ctx = icr.Context(0, st.cuda_stream)
+    sc = _load(icr, driver, ctx, batch[0])
+    with pytest.raises(icr.IcrError) as e:
+        icr.serve([sc], [0], [0.0], n_slots=1)
+    assert e.value.code == icr.ESTATE
+    sc.step_capture(batch[0].n_newton)
+    with pytest.raises(icr.IcrError) as e:
+        icr.serve([sc], [3], [0.0], n_slots=1)
+    assert e.value.code == icr.EINVAL
+    with pytest.raises(icr.IcrError) as e:
+        icr.serve([sc], [0, 0], [0.5, 0.1], n_slots=1)
+    assert e.value.code == icr.EINVAL
+    default = icr.Context(0)
+    sc2 = _load(icr, driver, default, batch[0])
+    with pytest.raises(icr.IcrError) as e:
+        sc2.step_capture(batch[0].n_newton)
+    assert e.value.code == icr.EINVAL
