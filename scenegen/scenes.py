@@ -133,8 +133,19 @@ def batch_scenes(n_scenes=64, seed=2, processes=None, **kw) -> list[Scene]:
     procs = processes or min(len(specs), os.cpu_count() or 1)
     if procs <= 1:
         return [_batch_member(a) for a in specs]
-    with mp.get_context("spawn").Pool(procs) as pool:
-        return pool.map(_batch_member, specs, chunksize=1)
+    # one BLAS thread per worker: the pool already fills the cores
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            return pool.map(_batch_member, specs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 def beam_c0() -> Scene:
