@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -56,12 +58,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["icr", "reference"], default="icr")
-    ap.add_argument("--workload", choices=["liver_c1", "batch_c2", "serve_c4"], default="liver_c1",
+    ap.add_argument("--workload", choices=["liver_c1", "batch_c2", "precision_c3", "serve_c4"], default="liver_c1",
                     help="liver_c1 is the bench line; the others print their own line")
     ap.add_argument("--scenes", type=int, default=64, help="batch_c2: number of scenes")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve_c4: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=3.0, help="serve_c4: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=32, help="serve_c4: concurrent streams")
+    ap.add_argument("--oracle-columns", type=int, default=32, help="precision_c3: W_H columns checked by the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -364,14 +367,16 @@ def run_icr(args):
         h_anch = pin(scene.obstacle.anchors, np.float64)
         h_mu = pin(scene.mu, np.float64)
         h_dq = pin(np.zeros(scene.n), np.float64)
-        center = np.asarray(scene.obstacle.center, dtype=np.float64)
-        h2d = h_nodes.nbytes + h_bary.nbytes + h_p0.nbytes + h_anch.nbytes + h_mu.nbytes + center.nbytes
+        h_spheres = pin(np.concatenate([scene.obstacle.centers, scene.obstacle.radii[:, None]], axis=1), np.float64)
+        h_tool = pin(scene.obstacle.tool, np.int32)
+        h2d = (h_nodes.nbytes + h_bary.nbytes + h_p0.nbytes + h_anch.nbytes + h_mu.nbytes + h_spheres.nbytes
+               + h_tool.nbytes)
         d2h = h_dq.nbytes
 
         def e2e_step():
             sc.set_mapping(h_nodes, h_bary)
             sc.set_proximity(h_p0)
-            sc.set_obstacle_sphere(center, scene.obstacle.radius, h_anch)
+            sc.set_obstacle_spheres(h_spheres, h_tool, h_anch)
             sc.set_field("MU", h_mu)
             sc.build_WH()
             for k in range(scene.n_newton):
@@ -566,6 +571,139 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- precision table
+def _oracle_columns(A, nodes, bary, n, cols):
+    """cpu_baseline leg of the precision table: columns ``cols`` of
+    W_H = H A^-1 H^T through the oracle's sparse LU (run in a spawned process)."""
+    from oracle import delassus as dl
+    t0 = time.perf_counter()
+    solver = dl.SystemSolver(A)
+    t1 = time.perf_counter()
+    H = dl.mapping_matrix(nodes, bary, n)
+    Z = solver.solve(H.T[:, cols].toarray())
+    return np.asarray(H @ Z), t1 - t0, time.perf_counter() - t1
+
+
+def _states(lam, mu):
+    """0 separated, 1 stick, 2 slip (on the cone within 1e-9 relative)."""
+    L = np.asarray(lam, dtype=np.float64).reshape(-1, 3)
+    nt = np.linalg.norm(L[:, 1:], axis=1)
+    out = np.where(nt >= mu * L[:, 0] * (1 - 1e-9), 2, 1)
+    return np.where(L[:, 0] <= 0, 0, out)
+
+
+def run_precision(args):
+    """precision_c3: one time step of the 60k-DOF two-tool scene in FP64 and in
+    FP32 with each contraction dtype; errors of W_H, W, lambda~ and dq against
+    the FP64 path (W and the state classification at Newton iteration 1, the
+    lambda~ increments of every iteration), the FP64 path's dq residual
+    A dq - H^T u, and sampled W_H columns against the oracle."""
+    import multiprocessing as mp
+
+    import torch
+
+    import scenegen
+    from paper_2306_06946_gb300 import build, driver, icr
+    scene = scenegen.NAMED["tissue_c3"]()
+    pool = fut = None
+    cols = np.sort(np.random.default_rng(3).choice(3 * scene.m, size=min(args.oracle_columns, 3 * scene.m),
+                                                   replace=False))
+    if cols.size:
+        pool = mp.get_context("spawn").Pool(1)
+        fut = pool.apply_async(_oracle_columns, (scene.A, scene.nodes, scene.bary, scene.n, cols))
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = icr.Context(0, stream.cuda_stream)
+
+    def hT(u):
+        r = np.zeros(scene.n)
+        U = u.reshape(-1, 3)
+        for i in range(4):
+            for ax in range(3):
+                np.add.at(r, 3 * scene.nodes[:, i] + ax, scene.bary[:, i] * U[:, ax])
+        return r
+
+    def run(prec, mode):
+        sc = icr.Scene(ctx, precision=prec, n_sweeps=scene.n_sweeps, contraction=mode)
+        driver.load_system(sc, scene.factor)
+        driver.load_contacts(sc, scene.nodes, scene.bary, scene.p0)
+        driver.load_obstacle(sc, scene.obstacle)
+        sc.set_field("MU", scene.mu)
+        sc.build_WH()
+        lams = []
+        for k in range(scene.n_newton):
+            sc.linearize(k)
+            sc.update_W()
+            if k == 0:
+                W1 = sc.get("W")
+            sc.solve_friction()
+            lams.append(sc.get("LAMBDA"))
+            sc.update_proximity()
+        out = {"WH": sc.get("WH"), "W": W1, "lams": lams, "u": sc.get("U")}
+        out["dq"] = sc.correct_motion(want_dq=True, reset=True)
+        # timing: whole steps and the W_H build alone, CUDA events on the scene stream
+        for _ in range(args.warmup):
+            sc.step(scene.n_newton)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(args.steps):
+            sc.step(scene.n_newton)
+        e[1].record(stream)
+        e[2].record(stream)
+        for _ in range(args.steps):
+            sc.build_WH()
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        out["ms_step"] = e[0].elapsed_time(e[1]) / args.steps
+        out["ms_build_WH"] = e[2].elapsed_time(e[3]) / args.steps
+        sc.close()
+        return out
+
+    rf = lambda a, b: float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+    with ClockSampler(0) as clk:
+        ref = run(icr.FP64, "simt")
+        rows = {}
+        for mode in ("simt", "tf32x3", "tf32", "bf16"):
+            r = run(icr.FP32, mode)
+            st_ref, st = _states(ref["lams"][0], scene.mu), _states(r["lams"][0], scene.mu)
+            d2 = sum(float(np.linalg.norm(a - b) ** 2) for a, b in zip(r["lams"], ref["lams"]))
+            n2 = sum(float(np.linalg.norm(b) ** 2) for b in ref["lams"])
+            rows[mode] = {"W_H_rel_fro": rf(r["WH"], ref["WH"]), "W_rel_fro": rf(r["W"], ref["W"]),
+                          "lambda_rel_iter1": rf(r["lams"][0], ref["lams"][0]),
+                          "lambda_rel_all_iters": (d2 / max(n2, 1e-300)) ** 0.5, "dq_rel": rf(r["dq"], ref["dq"]),
+                          "state_mismatches_iter1": int(np.sum(st != st_ref)),
+                          "ms_per_step": r["ms_step"], "ms_build_WH": r["ms_build_WH"]}
+    b = hT(ref["u"])
+    res = float(np.linalg.norm(scene.A @ ref["dq"] - b) / max(np.linalg.norm(b), 1e-300))
+    fp64 = {"ms_per_step": ref["ms_step"], "ms_build_WH": ref["ms_build_WH"], "dq_residual_rel": res,
+            "states_iter1": {k: int(v) for k, v in zip(("separated", "stick", "slip"),
+                                                       np.bincount(_states(ref["lams"][0], scene.mu), minlength=3))},
+            "lambda_norm_per_iter": [float(np.linalg.norm(x)) for x in ref["lams"]]}
+    cpu = None
+    if fut is not None:
+        WHc, t_fac, t_sol = fut.get()
+        pool.close()
+        pool.join()
+        fp64["W_H_columns_vs_oracle_rel"] = rf(ref["WH"][:, cols], WHc)
+        fp64["oracle_columns"] = int(cols.size)
+        cpu = {"value": cols.size / (t_fac + t_sol), "unit": "W_H columns/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cols.size} columns of W_H through the oracle's sparse LU (factor {t_fac:.1f} s, "
+                         f"solve {t_sol:.1f} s)"}
+    line = {
+        "metric": METRIC, "value": 1e3 / rows["tf32x3"]["ms_per_step"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rows["tf32x3"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"precision_c3: ellipsoid {scene.n} DOF, {scene.m} contacts split between 2 "
+                               f"sphere tools, {scene.n_newton} Newton x {scene.n_sweeps} PGS sweeps, seed 3; "
+                               "value = FP32 path with 3xTF32 contraction",
+                   "supernodes": int(scene.factor.sym.nsuper)},
+        "errors_vs_fp64": rows, "fp64": fp64, "cpu_baseline": cpu, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -574,6 +712,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve_c4":
         run_serve(args)
+    elif args.workload == "precision_c3":
+        run_precision(args)
     else:
         run_icr(args)
 

@@ -84,7 +84,10 @@ typedef struct icr_params {
   int32_t n_sweeps;      /* PGS sweep cap (>= 0) */
   double tol;            /* PGS stop when eps <= tol (tol > 0); a sweep without change always stops */
   int32_t contraction;   /* enum icr_contraction */
-  int32_t reserved;      /* 0 */
+  int32_t warm_start;    /* 1: the first PGS of a time step (Newton iteration 1) starts from the
+                            previous step's iteration-1 lambda~ (zero before the first step),
+                            Newton iterations 2..k start from 0 (incremental reading of Alg. 3);
+                            0: every PGS starts from 0.  Read by icr_step / icr_step_capture. */
 } icr_params;
 
 typedef struct icr_pgs_stats {
@@ -178,6 +181,12 @@ int icr_update_directions(icr_scene* scene, const double* C, const double* delta
  *           delta = (|p - c| - radius, t1.(p - anchor), t2.(p - anchor)). */
 int icr_set_obstacle_plane(icr_scene* scene, int32_t n_iters, const double* normals, const double* anchors);
 int icr_set_obstacle_sphere(icr_scene* scene, const double* center, double radius, const double* anchors);
+/* Several sphere tools: spheres is n_spheres x 4 (centre x, y, z, radius > 0),
+ * contact_sphere (m int32, each in [0, n_spheres)) names the tool each contact
+ * touches, anchors as for one sphere.  icr_set_obstacle_sphere is the case
+ * n_spheres = 1.  Copies its inputs; ICR_EINVAL on a bad radius or index. */
+int icr_set_obstacle_spheres(icr_scene* scene, int32_t n_spheres, const double* spheres,
+                             const int32_t* contact_sphere, const double* anchors);
 int icr_linearize(icr_scene* scene, int32_t k);
 
 /* W_H = H A^-1 H^T = X^T D^-1 X with X = L^-1 H^T (Eq. "schur complemnt

@@ -291,6 +291,10 @@ static int check_params(const icr_params* p) {
     set_error("unknown contraction mode %d", p->contraction);
     return ICR_EINVAL;
   }
+  if (p->warm_start != 0 && p->warm_start != 1) {
+    set_error("warm_start must be 0 or 1");
+    return ICR_EINVAL;
+  }
   return ICR_OK;
 }
 
@@ -322,7 +326,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors};
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -608,6 +612,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->delta, 3 * mm * T));
   RET(dalloc(s, s->mu, mm * T));
   RET(dalloc(s, s->lam, 3 * mm * T));
+  RET(dalloc(s, s->lam0, 3 * mm * T));
   RET(dalloc(s, s->p, 3 * mm * sizeof(double)));
   RET(dalloc(s, s->p0, 3 * mm * sizeof(double)));
   RET(dalloc(s, s->u, 6 * mm * sizeof(double)));   // u (3m) then the last increment dp (3m)
@@ -635,6 +640,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   cudaStream_t st = s->ctx->stream;
   CK(cudaMemsetAsync(s->W.p, 0, 3 * mm * (size_t)ldw * T, st));   // padding columns stay 0
   CK(cudaMemsetAsync(s->lam.p, 0, 3 * mm * T, st));
+  CK(cudaMemsetAsync(s->lam0.p, 0, 3 * mm * T, st));
   CK(cudaMemsetAsync(s->mu.p, 0, mm * T, st));
   CK(cudaMemsetAsync(s->delta.p, 0, 3 * mm * T, st));
   CK(cudaMemsetAsync(s->C.p, 0, 9 * mm * T, st));
@@ -777,21 +783,48 @@ int icr_set_obstacle_plane(icr_scene* s, int32_t n_iters, const double* normals,
   return ICR_OK;
 }
 
-int icr_set_obstacle_sphere(icr_scene* s, const double* center, double radius, const double* anchors) {
+int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
+                             const double* anchors) {
   RET(check_scene(s));
-  RET(need_mapping(s, "set_obstacle_sphere"));
-  if (!center || !(radius > 0) || (s->m && !anchors)) {
-    set_error("set_obstacle_sphere: need a centre, a positive radius and anchors");
+  RET(need_mapping(s, "set_obstacle_spheres"));
+  const int m = s->m;
+  if (n_spheres <= 0 || !spheres || (m && (!anchors || !contact_sphere))) {
+    set_error("set_obstacle_spheres: need n_spheres > 0, the spheres, each contact's sphere and anchors");
     return ICR_EINVAL;
   }
+  for (int i = 0; i < n_spheres; ++i) {
+    const double* q = spheres + 4 * i;
+    if (!(std::isfinite(q[0]) && std::isfinite(q[1]) && std::isfinite(q[2]) && q[3] > 0 && std::isfinite(q[3]))) {
+      set_error("set_obstacle_spheres: sphere %d needs a finite centre and a positive radius", i);
+      return ICR_EINVAL;
+    }
+  }
+  for (int a = 0; a < m; ++a)
+    if (contact_sphere[a] < 0 || contact_sphere[a] >= n_spheres) {
+      set_error("set_obstacle_spheres: contact %d names sphere %d of %d", a, contact_sphere[a], n_spheres);
+      return ICR_EINVAL;
+    }
   RET(set_device(s));
-  RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)s->m * 3) * sizeof(double)));
-  RET(upload(s, s->obst_anchors, anchors, (size_t)s->m * 3));
-  for (int i = 0; i < 3; ++i) s->center[i] = center[i];
-  s->radius = radius;
+  RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)m * 3) * sizeof(double)));
+  RET(dalloc(s, s->obst_spheres, (size_t)n_spheres * 4 * sizeof(double)));
+  RET(dalloc(s, s->obst_of, std::max<size_t>(1, (size_t)m) * sizeof(int32_t)));
+  RET(upload(s, s->obst_anchors, anchors, (size_t)m * 3));
+  RET(upload(s, s->obst_spheres, spheres, (size_t)n_spheres * 4));
+  if (m) RET(upload(s, s->obst_of, contact_sphere, (size_t)m));
   s->obst_kind = 2;
   s->obst_iters = 0;
   return ICR_OK;
+}
+
+int icr_set_obstacle_sphere(icr_scene* s, const double* center, double radius, const double* anchors) {
+  RET(check_scene(s));
+  if (!center) {
+    set_error("set_obstacle_sphere: need a centre");
+    return ICR_EINVAL;
+  }
+  const double q[4] = {center[0], center[1], center[2], radius};
+  std::vector<int32_t> of(std::max(0, s->m), 0);
+  return icr_set_obstacle_spheres(s, 1, q, of.data(), anchors);
 }
 
 int icr_linearize(icr_scene* s, int32_t k) {
@@ -915,10 +948,18 @@ static int step_enqueue(Scene* s, int n_newton) {
   }
   RET(launch_build_WH(s));
   s->has_WH = true;
+  const size_t lam_bytes = 3 * (size_t)s->m * s->tsize;
   for (int k = 0; k < n_newton; ++k) {
     RET(launch_linearize(s, k));
     RET(launch_update_W(s));
-    RET(launch_pgs(s, 0, 0));
+    if (k == 0 && s->params.warm_start && s->m) {
+      // Newton iteration 1 starts from the previous time step's iteration-1 solution
+      CK(cudaMemcpyAsync(s->lam.p, s->lam0.p, lam_bytes, cudaMemcpyDeviceToDevice, st));
+      RET(launch_pgs(s, 1, 0));
+      CK(cudaMemcpyAsync(s->lam0.p, s->lam.p, lam_bytes, cudaMemcpyDeviceToDevice, st));
+    } else {
+      RET(launch_pgs(s, 0, 0));
+    }
     RET(launch_update_proximity(s));
   }
   RET(launch_correct_motion(s));

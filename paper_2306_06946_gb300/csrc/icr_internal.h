@@ -61,7 +61,7 @@ struct Scene {
   int64_t ldx = 0;     // leading dimension (columns) of every front
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
-  DBuf WH, W, C, delta, mu, lam, p, p0, u, uk, ut, y, dq, stats;
+  DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, ut, y, dq, stats;
   DBuf dev_err;            // int set by a kernel whose bounded wait ran out
   DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
   int tc_tmax = 0;         // 128-column tiles of the widest possible front
@@ -74,8 +74,7 @@ struct Scene {
   int obst_kind = 0;   // 0 none, 1 plane, 2 sphere
   int obst_iters = 0;
   DBuf obst_normals, obst_anchors;
-  double center[3] = {0, 0, 0};
-  double radius = 0;
+  DBuf obst_spheres, obst_of;   // sphere tools (n x 4 doubles) and each contact's tool (m int32)
 };
 
 int dalloc(Scene* s, DBuf& b, size_t bytes);

@@ -882,18 +882,20 @@ __global__ void __launch_bounds__(256)
 // C rows n, t1, t2 and the gaps from the current proximity positions (FP64).
 template <class T>
 __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
-                            const double* __restrict__ anchors, double cx, double cy, double cz, double radius,
-                            const double* __restrict__ p, T* C, T* delta) {
+                            const double* __restrict__ anchors, const double* __restrict__ spheres,
+                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta) {
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
-  double n0, n1, n2, dist = 0.0;
+  double n0, n1, n2, dist = 0.0, radius = 0.0;
   if (kind == 1) {
     n0 = normals_k[3 * a];
     n1 = normals_k[3 * a + 1];
     n2 = normals_k[3 * a + 2];
   } else {
-    const double dx = px - cx, dy = py - cy, dz = pz - cz;
+    const double* sp = spheres + 4 * sphere_of[a];
+    radius = sp[3];
+    const double dx = px - sp[0], dy = py - sp[1], dz = pz - sp[2];
     dist = sqrt(dx * dx + dy * dy + dz * dz);
     n0 = dx / dist;
     n1 = dy / dist;
@@ -1106,8 +1108,8 @@ static int linearize_T(Scene* s, int k) {
   if (m == 0) return ICR_OK;
   const double* nk = s->obst_kind == 1 ? (const double*)s->obst_normals.p + (size_t)k * m * 3 : nullptr;
   k_linearize<T><<<(m + 127) / 128, 128, 0, s->ctx->stream>>>(
-      m, s->obst_kind, nk, (const double*)s->obst_anchors.p, s->center[0], s->center[1], s->center[2], s->radius,
-      (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p);
+      m, s->obst_kind, nk, (const double*)s->obst_anchors.p, (const double*)s->obst_spheres.p,
+      (const int*)s->obst_of.p, (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p);
   LAUNCH_OK("k_linearize");
   return ICR_OK;
 }

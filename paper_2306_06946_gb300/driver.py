@@ -29,11 +29,14 @@ def load_contacts(sc: icr.Scene, nodes, bary, p0) -> None:
 
 def load_obstacle(sc: icr.Scene, obstacle) -> None:
     """Plane obstacles expose ``normals`` (iters x m x 3) and ``anchors``;
-    sphere obstacles ``center``, ``radius`` and ``anchors``."""
+    sphere obstacles ``centers`` (tools x 3), ``radii`` (tools), ``tool``
+    (each contact's tool) and ``anchors``."""
     if obstacle.kind == "plane":
         sc.set_obstacle_plane(obstacle.normals, obstacle.anchors)
     elif obstacle.kind == "sphere":
-        sc.set_obstacle_sphere(obstacle.center, obstacle.radius, obstacle.anchors)
+        spheres = np.concatenate([np.asarray(obstacle.centers, dtype=np.float64).reshape(-1, 3),
+                                  np.asarray(obstacle.radii, dtype=np.float64).reshape(-1, 1)], axis=1)
+        sc.set_obstacle_spheres(spheres, obstacle.tool, obstacle.anchors)
     else:
         raise ValueError(f"unknown obstacle kind {obstacle.kind!r}")
 

@@ -24,7 +24,8 @@ _INT_FIELDS = {"REACH_PTR", "REACH_IDX"}
 # every symbol include/icr.h declares
 EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes_in_use", "icr_scene_create",
            "icr_scene_destroy", "icr_set_params", "icr_set_system", "icr_set_mapping", "icr_set_proximity",
-           "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere", "icr_linearize",
+           "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere",
+           "icr_set_obstacle_spheres", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
            "icr_step_launch", "icr_sync", "icr_serve")
@@ -41,7 +42,7 @@ CONTRACT = {"auto": 0, "simt": 1, "tf32x3": 2, "tf32": 3, "bf16": 4}
 
 class Params(ct.Structure):
     _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double),
-                ("contraction", ct.c_int32), ("reserved", ct.c_int32)]
+                ("contraction", ct.c_int32), ("warm_start", ct.c_int32)]
 
 
 class PgsStats(ct.Structure):
@@ -77,6 +78,7 @@ def lib() -> ct.CDLL:
             "icr_update_directions": [P, P, P, P],
             "icr_set_obstacle_plane": [P, ct.c_int32, P, P],
             "icr_set_obstacle_sphere": [P, P, ct.c_double, P],
+            "icr_set_obstacle_spheres": [P, ct.c_int32, P, P, P],
             "icr_linearize": [P, ct.c_int32],
             "icr_build_WH": [P],
             "icr_update_W": [P],
@@ -176,9 +178,9 @@ class Scene:
     """icr_scene: one deformable body and its contacts."""
 
     def __init__(self, ctx: Context, precision: int = FP32, n_sweeps: int = 50, tol: float = 0.0,
-                 contraction: str = "auto"):
+                 contraction: str = "auto", warm_start: bool = False):
         self.ctx = ctx
-        self.params = Params(precision, n_sweeps, tol, CONTRACT[contraction], 0)
+        self.params = Params(precision, n_sweeps, tol, CONTRACT[contraction], int(bool(warm_start)))
         h = P()
         _check(lib().icr_scene_create(ctx.h, ct.byref(h), ct.byref(self.params)))
         self.h = h
@@ -196,7 +198,10 @@ class Scene:
         except Exception:
             pass
 
-    def set_params(self, n_sweeps: int | None = None, tol: float | None = None, contraction: str | None = None):
+    def set_params(self, n_sweeps: int | None = None, tol: float | None = None, contraction: str | None = None,
+                   warm_start: bool | None = None):
+        if warm_start is not None:
+            self.params.warm_start = int(bool(warm_start))
         if n_sweeps is not None:
             self.params.n_sweeps = n_sweeps
         if tol is not None:
@@ -247,6 +252,11 @@ class Scene:
     def set_obstacle_sphere(self, center, radius, anchors):
         _check(lib().icr_set_obstacle_sphere(self.h, _ptr(_arr(center, np.float64)), float(radius),
                                              _ptr(_arr(anchors, np.float64))))
+
+    def set_obstacle_spheres(self, spheres, contact_sphere, anchors):
+        sp = _arr(spheres, np.float64).reshape(-1, 4)
+        _check(lib().icr_set_obstacle_spheres(self.h, int(sp.shape[0]), _ptr(sp),
+                                              _ptr(_arr(contact_sphere, np.int32)), _ptr(_arr(anchors, np.float64))))
 
     def linearize(self, k: int):
         _check(lib().icr_linearize(self.h, int(k)))

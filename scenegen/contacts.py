@@ -57,21 +57,24 @@ class PlaneObstacle:
 
 @dataclass
 class SphereObstacle:
-    """Rigid sphere tool (centre at the end of the step, radius) translating
-    with ``velocity``; anchors are the tool-surface points each contact
-    started from, already moved with the tool to the end of the step."""
-    center: np.ndarray
-    radius: float
-    anchors: np.ndarray
+    """Rigid sphere tools (centres at the end of the step, radii), each
+    translating with its own velocity; ``tool`` names the tool each contact
+    touches and the anchors are the tool-surface points each contact started
+    from, already moved with its tool to the end of the step."""
+    centers: np.ndarray      # (tools, 3)
+    radii: np.ndarray        # (tools,)
+    tool: np.ndarray         # (m,) int
+    anchors: np.ndarray      # (m, 3)
     kind: str = field(default="sphere", init=False)
 
     def linearize(self, p: np.ndarray, k: int):
-        d = p - self.center[None, :]
+        c = self.centers[self.tool]
+        d = p - c
         dist = np.linalg.norm(d, axis=1)
         n = d / dist[:, None]
         C = tangent_frame(n)
         rel = p - self.anchors
-        delta = np.stack([dist - self.radius,
+        delta = np.stack([dist - self.radii[self.tool],
                           np.einsum("mj,mj->m", C[:, 1], rel),
                           np.einsum("mj,mj->m", C[:, 2], rel)], axis=1).reshape(-1)
         return C, delta
@@ -96,41 +99,68 @@ def plane_contacts(rng, X, T, m, n_newton, tilt_sigma=0.05, gap_mm=0.5, slip_mm=
 
 
 def sphere_contacts(rng, X, T, faces, face_tet, m, radius=0.02, indent=3e-3,
-                    velocity=(0.05, 0.0, 0.0), h=0.01):
-    """Contacts inside the m boundary tets nearest a sphere tool pressed
-    ``indent`` into the top of the body.
+                    velocity=(0.05, 0.0, 0.0), h=0.01, tools=((0.0, 0.0, 1.0),)):
+    """Contacts inside the boundary tets nearest sphere tools pressed
+    ``indent`` into the body.
 
-    The proximity point of each contact is uniform in its tet (barycentric
-    weights on all four nodes); tets are taken nearest first and each must
-    bring a node that no earlier contact uses, so H has full row rank.
+    Tool i presses along -tools[i] at the extreme point of the body in the
+    direction tools[i] (the first tool on the top, +z); the m contacts are split
+    evenly between the tools (the first tools take the remainder).  Tool i moves
+    with ``velocity`` turned from +z onto tools[i] (the same vector for the
+    +z tool).  The proximity point of each contact is uniform in its tet
+    (barycentric weights on all four nodes); tets are taken nearest first and
+    each must bring a node that no earlier contact uses, so H has full row rank.
     """
-    ztop = X[:, 2].max()
-    center = np.array([0.0, 0.0, ztop + radius - indent])
+    nt = len(tools)
+    dirs = [np.asarray(t, dtype=np.float64) / np.linalg.norm(t) for t in tools]
+    v0 = np.asarray(velocity, dtype=np.float64)
+    centers, vels = [], []
+    for d in dirs:
+        centers.append(d * (float((X @ d).max()) + radius - indent))
+        vels.append(_turn_z_onto(d) @ v0)
     cen = X[faces].mean(axis=1)
-    dist = np.linalg.norm(cen - center[None, :], axis=1)
-    order = np.argsort(dist, kind="stable")
-    # nearest first; a tet is kept only if it brings a node no kept tet uses,
-    # which makes the barycentric rows (and H) full row rank
     used = np.zeros(X.shape[0], dtype=bool)
     seen = set()
-    tets = []
-    for f in order:
-        t = int(face_tet[f])
-        if t in seen:
-            continue
-        seen.add(t)
-        if not used[T[t]].all():
-            used[T[t]] = True
-            tets.append(t)
-            if len(tets) == m:
+    tets, tool = [], []
+    counts = [m // nt + (1 if i < m % nt else 0) for i in range(nt)]
+    for i in range(nt):
+        dist = np.linalg.norm(cen - centers[i][None, :], axis=1)
+        order = np.argsort(dist, kind="stable")
+        got = 0
+        # nearest first; a tet is kept only if it brings a node no kept tet
+        # uses, which makes the barycentric rows (and H) full row rank
+        for f in order:
+            if got == counts[i]:
                 break
-    if len(tets) < m:
-        raise ValueError("not enough boundary tets for the requested contact count")
-    nodes = T[np.asarray(tets)].astype(np.int64)
+            t = int(face_tet[f])
+            if t in seen:
+                continue
+            seen.add(t)
+            if not used[T[t]].all():
+                used[T[t]] = True
+                tets.append(t)
+                tool.append(i)
+                got += 1
+        if got < counts[i]:
+            raise ValueError("not enough boundary tets for the requested contact count")
+    nodes = T[np.asarray(tets, dtype=np.int64)].astype(np.int64)
+    tool = np.asarray(tool, dtype=np.int64)
     bary = dirichlet(rng, m, 4)
     p0 = np.einsum("mi,mij->mj", bary, X[nodes])
-    v = np.asarray(velocity, dtype=np.float64)
-    c_start = center - v * h
-    d0 = p0 - c_start[None, :]
-    anchors = c_start[None, :] + radius * d0 / np.linalg.norm(d0, axis=1, keepdims=True) + v[None, :] * h
-    return nodes, bary, p0, SphereObstacle(center=center, radius=radius, anchors=anchors)
+    C = np.asarray(centers)
+    V = np.asarray(vels)
+    c_start = C[tool] - V[tool] * h
+    d0 = p0 - c_start
+    anchors = c_start + radius * d0 / np.linalg.norm(d0, axis=1, keepdims=True) + V[tool] * h
+    return nodes, bary, p0, SphereObstacle(centers=C, radii=np.full(nt, float(radius)), tool=tool, anchors=anchors)
+
+
+def _turn_z_onto(d):
+    """Rotation taking +z onto the unit vector d (identity for d = +z)."""
+    z = np.array([0.0, 0.0, 1.0])
+    v = np.cross(z, d)
+    c = float(z @ d)
+    if np.linalg.norm(v) < 1e-15:
+        return np.eye(3) if c > 0 else np.diag([1.0, -1.0, -1.0])
+    K = np.array([[0, -v[2], v[1]], [v[2], 0, -v[0]], [-v[1], v[0], 0]])
+    return np.eye(3) + K + K @ K / (1.0 + c)

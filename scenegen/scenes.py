@@ -15,6 +15,9 @@ Named workloads:
             0.05, 0.04) with ~3,000 nodes, its lowest 20 % of nodes held by
             1e4 N/m grounding springs, and 300 contacts against a 0.02 m sphere
             tool pressed 6 mm into its top and sliding at 0.05 m/s, seed 1
+  tissue_c3 the same ellipsoid meshed to ~20,000 nodes (~60k DOF) with 1,500
+            contacts split between two 0.02 m sphere tools, one pressed into
+            its top (+z) and one into its +x end, seed 3
 """
 from __future__ import annotations
 
@@ -86,7 +89,7 @@ def beam_scene(nodes_xyz=(20, 4, 4), spacing=0.01, m=40, seed=0, n_newton=3, n_s
 
 def ellipsoid_scene(semi=(0.075, 0.05, 0.04), target_nodes=3000, m=300, seed=1, n_newton=5,
                     n_sweeps=50, mu=0.3, leaf_nodes=24, h=0.01, indent=6e-3, anchor_frac=0.2,
-                    anchor_k=1e4, name=None) -> Scene:
+                    anchor_k=1e4, tools=((0.0, 0.0, 1.0),), name=None) -> Scene:
     rng = np.random.default_rng(seed)
     X, T, _ = ellipsoid(semi, target_nodes)
     X, T, blocks = _permute(X, T, leaf_nodes)
@@ -94,7 +97,7 @@ def ellipsoid_scene(semi=(0.075, 0.05, 0.04), target_nodes=3000, m=300, seed=1, 
     anchored = np.nonzero(z <= z.min() + anchor_frac * (z.max() - z.min()))[0]
     A, F = _system(X, T, blocks, h=h, anchor_nodes=anchored, anchor_k=anchor_k)
     faces, ftet, _ = boundary_faces(T)
-    nodes, bary, p0, obst = ct.sphere_contacts(rng, X, T, faces, ftet, m, indent=indent, h=h)
+    nodes, bary, p0, obst = ct.sphere_contacts(rng, X, T, faces, ftet, m, indent=indent, h=h, tools=tools)
     return Scene(name or f"ellipsoid{target_nodes}", X, T, A, F, nodes, bary, np.full(m, float(mu)), p0,
                  obst, n_newton, n_sweeps, h)
 
@@ -156,4 +159,9 @@ def liver_c1() -> Scene:
     return ellipsoid_scene(name="liver_c1")
 
 
-NAMED = {"beam_c0": beam_c0, "liver_c1": liver_c1}
+def tissue_c3() -> Scene:
+    return ellipsoid_scene(target_nodes=20000, m=1500, seed=3, tools=((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)),
+                           name="tissue_c3")
+
+
+NAMED = {"beam_c0": beam_c0, "liver_c1": liver_c1, "tissue_c3": tissue_c3}

@@ -27,6 +27,9 @@ def scene(name: str):
         return scenegen.NAMED["liver_c1"]()
     if name == "beam_mid":      # several tiles, ragged tail: 77 contacts, 2,160 DOF
         return scenegen.beam_scene(nodes_xyz=(24, 6, 5), m=77, seed=7, n_newton=3, n_sweeps=40, name="beam_mid")
+    if name == "tools2":        # two sphere tools (top and +x end), 90 contacts on a 900-node ellipsoid
+        return scenegen.ellipsoid_scene(target_nodes=900, m=90, seed=11, tools=((0.0, 0.0, 1.0), (1.0, 0.0, 0.0)),
+                                        name="tools2")
     if name == "beam_one":      # a single contact
         return scenegen.beam_scene(nodes_xyz=(6, 3, 3), m=1, seed=2, n_newton=2, n_sweeps=10, name="beam_one")
     raise KeyError(name)

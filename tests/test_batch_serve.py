@@ -110,3 +110,94 @@ def test_serve_argument_and_state_errors(batch, torch_mod):
     with pytest.raises(icr.IcrError) as e:
         sc2.step_capture(batch[0].n_newton)
     assert e.value.code == icr.EINVAL
+
+
+# ---------------------------------------------------------------- warm start (Newton iteration 1)
+@pytest.mark.parametrize("prec,tol", [(1, 1e-9), (0, 1e-4)])
+def test_warm_started_steps_follow_the_oracle_chain(batch, torch_mod, prec, tol):
+    """With warm_start, iteration 1 of each step starts from the previous
+    step's iteration-1 lambda~; the oracle run with lam0 chained the same way
+    gives the same steps.  Five sweeps keep PGS far from converged, so a warm
+    and a cold start differ well above the tolerance."""
+    from oracle import delassus as dl
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    s = batch[0]
+    sweeps = 5
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    sc = icr.Scene(ctx, precision=prec, n_sweeps=sweeps, warm_start=True)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    driver.load_obstacle(sc, s.obstacle)
+    sc.set_field("MU", s.mu)
+    solver = dl.SystemSolver(s.A)
+    cold = nw.fast_scheme(s.A, s.nodes, s.bary, s.mu, s.p0, s.linearize, s.n_newton, sweeps, solver=solver)
+    lam0 = None
+    for j in range(3):
+        sc.step(s.n_newton)
+        ref = nw.fast_scheme(s.A, s.nodes, s.bary, s.mu, s.p0, s.linearize, s.n_newton, sweeps,
+                             lam0=lam0, solver=solver)
+        lam0 = ref["iters"][0]["lam"]
+        assert rel(sc.get("DQ"), ref["dq"]) < tol, f"step {j}"
+        scale = max(np.linalg.norm(ref["iters"][-1]["lam"]), 1e-300)
+        assert np.linalg.norm(sc.get("LAMBDA") - ref["iters"][-1]["lam"]) <= tol * scale
+        if j > 0:
+            assert rel(ref["dq"], cold["dq"]) > 100 * tol
+
+
+def test_warm_started_scenes_alone_equal_the_mix(batch, torch_mod):
+    """Warm-started scenes carry lambda~ from step to step; a scene served in
+    the mix with others ends in the same state as the same number of its
+    steps run alone."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    rng = np.random.default_rng(21)
+    nreq = 30
+    which = rng.integers(0, len(batch), size=nreq)
+    arrivals = np.cumsum(rng.exponential(1.0 / 4000.0, size=nreq))
+
+    def fresh():
+        out = []
+        for s in batch:
+            ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+            sc = icr.Scene(ctx, precision=icr.FP32, n_sweeps=s.n_sweeps, warm_start=True)
+            driver.load_system(sc, s.factor)
+            driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+            driver.load_obstacle(sc, s.obstacle)
+            sc.set_field("MU", s.mu)
+            sc.step_capture(s.n_newton)
+            out.append(sc)
+        return out
+
+    alone = fresh()
+    for i, sc in enumerate(alone):
+        for _ in range(int(np.sum(which == i))):
+            sc.step_launch()
+        sc.sync()
+    mixed = fresh()
+    icr.serve(mixed, which, arrivals, n_slots=3)
+    # the contraction's atomic scatter-add makes W_H reproducible to rounding
+    # only, so the comparison is at the FP32 tolerances (dq 1e-5, lambda~ 1e-4)
+    for a, b in zip(alone, mixed):
+        assert rel(b.get("DQ"), a.get("DQ")) < 1e-5
+        assert rel(b.get("LAMBDA"), a.get("LAMBDA")) < 1e-4
+
+
+def test_two_sphere_obstacle_errors(batch, torch_mod):
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    s = batch[0]
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    sc = icr.Scene(ctx, precision=icr.FP32)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    anchors = np.asarray(s.p0, dtype=np.float64)
+    two = np.array([[0.0, 0.0, 1.0, 0.02], [1.0, 0.0, 0.0, 0.02]])
+    for spheres, tool in [(two, np.full(s.m, 2)), (two, np.full(s.m, -1)),
+                          (np.array([[0.0, 0.0, 1.0, 0.0]]), np.zeros(s.m))]:
+        with pytest.raises(icr.IcrError) as e:
+            sc.set_obstacle_spheres(spheres, tool, anchors)
+        assert e.value.code == icr.EINVAL
+    import ctypes as ct
+    sc.params.warm_start = 2
+    assert icr.lib().icr_set_params(sc.h, ct.byref(sc.params)) == icr.EINVAL

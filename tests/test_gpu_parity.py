@@ -62,7 +62,7 @@ def test_WH_rebuild_is_repeatable(ctx):
 
 
 # ---------------------------------------------------------------- a5 device linearisation
-@pytest.mark.parametrize("name", ["beam_c0", "liver_c1"])
+@pytest.mark.parametrize("name", ["beam_c0", "liver_c1", "tools2"])
 def test_device_linearize_matches_scene_rule(ctx, name):
     from paper_2306_06946_gb300 import icr
     s = scene(name)
@@ -221,7 +221,7 @@ def test_proximity_and_correction_match_oracle(ctx, name, prec, tol):
 
 # ---------------------------------------------------------------- full step (Alg. 3)
 @pytest.mark.parametrize("name,prec", [("beam_c0", 1), ("beam_c0", 0), ("beam_mid", 0), ("liver_c1", 1),
-                                       ("liver_c1", 0)])
+                                       ("liver_c1", 0), ("tools2", 1), ("tools2", 0)])
 def test_newton_step_matches_oracle(ctx, name, prec):
     from paper_2306_06946_gb300 import driver
     s = scene(name)
