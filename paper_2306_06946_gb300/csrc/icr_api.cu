@@ -249,6 +249,11 @@ int icr_ctx_create(icr_ctx** out, int device, void* cuda_stream, uint64_t hbm_bu
     return ICR_ENOMEM;
   }
   c->device = device;
+  e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaDeviceGetAttribute(MultiProcessorCount)");
+  }
   c->stream = (cudaStream_t)cuda_stream;
   c->budget = hbm_budget_bytes;
   *out = c;
@@ -326,7 +331,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0};
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -601,6 +606,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->bitmap, (size_t)ns * words * sizeof(uint32_t)));
   RET(dalloc(s, s->wprefix, (size_t)ns * words * sizeof(int32_t)));
   RET(dalloc(s, s->qcount, ns * sizeof(int32_t)));
+  RET(dalloc(s, s->plan, ((size_t)PLAN_LISTS * (ns + 1) + PLAN_COUNTERS) * sizeof(int32_t)));
   RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qinv, (size_t)ns * mm * sizeof(int32_t)));

@@ -16,6 +16,7 @@ int cuda_fail(cudaError_t e, const char* where);
 
 struct Ctx {
   int device = 0;
+  int sm_count = 1;
   cudaStream_t stream = nullptr;
   uint64_t budget = 0;
   uint64_t in_use = 0;
@@ -28,6 +29,16 @@ struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
 };
+
+// Work lists of one W_H build, written on the device by the planner right
+// after the reach pass: for every position p of level_list (p = 0..ns), the
+// exclusive prefix sum of the work units the supernodes before p contribute to
+// each list.  A kernel over a level range [a, b) of positions covers units
+// plan[a] .. plan[b] - 1; the unit's supernode is found by binary search.
+enum PlanList { PLAN_ASM = 0, PLAN_GEMM = 1, PLAN_SIMT = 2, PLAN_PACK = 3, PLAN_TC = 4, PLAN_LISTS = 5 };
+constexpr int PLAN_COUNTERS = 2;   // dynamic-scheduling counters: SIMT and tensor-core contraction
+constexpr int TC_TILE = 128;       // tensor-core output tile (M = N)
+constexpr int TC_KT = 32;          // front rows per packed operand block
 
 // Per-level launch geometry of the supernodal elimination tree.
 struct Level {
@@ -62,6 +73,7 @@ struct Scene {
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, ut, y, dq, stats;
+  DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then PLAN_COUNTERS counters (int32)
   DBuf dev_err;            // int set by a kernel whose bounded wait ran out
   DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
   int tc_tmax = 0;         // 128-column tiles of the widest possible front
@@ -96,7 +108,7 @@ int launch_update_proximity(Scene* s);
 int launch_correct_motion(Scene* s);
 int launch_linearize(Scene* s, int k);
 // tcgen05 contraction for supernodes with at least min_cols front columns (icr_tc.cu)
-int launch_contract_tc(Scene* s, int mode, int min_cols);
+int launch_contract_tc(Scene* s, int mode);
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);
 

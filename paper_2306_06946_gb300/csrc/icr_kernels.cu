@@ -22,6 +22,7 @@
 //                      dq_s = G_s^T [y_s; -dq_R] per level, top-down
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "icr_internal.h"
@@ -44,6 +45,7 @@ static constexpr int SOLVE_THREADS = 192; // 2 x 96 columns
 static constexpr int CT = 64;             // contraction output tile
 static constexpr int CK_ = 16;            // contraction k-chunk
 static constexpr int TC_MIN_COLS = 64;    // fronts this wide use the tensor-core contraction
+static constexpr int GR = 64;             // front rows per front-GEMM tile
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -158,57 +160,160 @@ __global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __
 // entries listed for that row (extend-add as a gather, children in ascending
 // order).  Rows < w go to Ftop, rows >= w to the front's update rows.
 static constexpr int AR = 4;   // front rows per assembly block
+
+// largest position p in [lo, hi) with P[p] <= u, for a non-decreasing prefix
+// array P with P[lo] <= u < P[hi]: the supernode that owns work unit u
+__device__ __forceinline__ int find_pos(const int* __restrict__ P, int lo, int hi, int u) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P[mid] <= u)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Work units per supernode for the lists of one build (PlanList order):
+// assembly and front-GEMM tiles, SIMT contraction tile pairs of fronts
+// narrower than simt_max columns, packed tensor-core operand blocks and
+// tensor-core tile pairs of fronts at least tc_min columns wide.
+__device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super_ptr,
+                                            const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount,
+                                            int simt_max, int tc_min, int* c) {
+  const int q = qcount[s];
+  const int w = super_ptr[s + 1] - super_ptr[s];
+  const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  const int nt = cdiv(q, TCC);
+  const int ncol = 3 * q;
+  c[PLAN_ASM] = cdiv(nrows, AR) * nt;
+  c[PLAN_GEMM] = cdiv(nrows, GR) * nt;
+  const int ns_ = cdiv(ncol, CT);
+  c[PLAN_SIMT] = (q > 0 && ncol < simt_max) ? ns_ * (ns_ + 1) / 2 : 0;
+  const int nI = cdiv(ncol, TC_TILE);
+  const bool tc = q > 0 && ncol >= tc_min;
+  c[PLAN_PACK] = tc ? nI * cdiv(w, TC_KT) : 0;
+  c[PLAN_TC] = tc ? nI * (nI + 1) / 2 : 0;
+}
+
+// One block: exclusive prefix sums of the per-supernode unit counts over the
+// positions of level_list, and the contraction counters reset to zero.
+__global__ void __launch_bounds__(1024)
+    k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+           const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
+           int* plan) {
+  __shared__ int wsum[PLAN_LISTS][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int per = cdiv(ns, blockDim.x);
+  const int p0 = min(ns, tid * per), p1 = min(ns, p0 + per);
+  int tot[PLAN_LISTS] = {0, 0, 0, 0, 0};
+  for (int p = p0; p < p1; ++p) {
+    int c[PLAN_LISTS];
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, c);
+#pragma unroll
+    for (int l = 0; l < PLAN_LISTS; ++l) tot[l] += c[l];
+  }
+  int off[PLAN_LISTS];
+#pragma unroll
+  for (int l = 0; l < PLAN_LISTS; ++l) {   // inclusive scan inside the warp
+    int v = tot[l];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, v, o);
+      if (lane >= o) v += y;
+    }
+    off[l] = v - tot[l];
+    if (lane == 31) wsum[l][warp] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int l = 0; l < PLAN_LISTS; ++l) {   // exclusive scan of the warp totals
+      const int t = lane < nw ? wsum[l][lane] : 0;
+      int v = t;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane < nw) wsum[l][lane] = v - t;
+      if (lane == 31) plan[l * (ns + 1) + ns] = v;   // list total
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int l = 0; l < PLAN_LISTS; ++l) off[l] += wsum[l][warp];
+  for (int p = p0; p < p1; ++p) {
+    int c[PLAN_LISTS];
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, c);
+#pragma unroll
+    for (int l = 0; l < PLAN_LISTS; ++l) {
+      plan[l * (ns + 1) + p] = off[l];
+      off[l] += c[l];
+    }
+  }
+  if (tid < PLAN_COUNTERS) plan[PLAN_LISTS * (ns + 1) + tid] = 0;
+}
+
+// Assembly of the fronts of one level (positions [pa, pb) of level_list).
+// Work unit (supernode, AR-row tile, TCC-contact tile); one thread per front
+// element: its H^T entry, plus the children's update entries listed for that
+// row (extend-add as a gather, children in ascending order).  Rows < w go to
+// Ftop, rows >= w to the front's update rows.
 template <class T>
 __global__ void __launch_bounds__(AR * TCOLS)
-    k_assemble(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
+    k_assemble(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
                const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                const int64_t* __restrict__ fr_ptr, const int* __restrict__ ctr_ptr,
                const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
                const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
                const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
-  int bq = blockIdx.x;
-  const int t = bq % ntiles;
-  bq /= ntiles;
-  const int rt = bq % nrt;
-  const int s = level_list[lvl_first + bq / nrt];
-  const int nq = qcount[s];
-  const int k0 = t * TCC;
-  if (k0 >= nq) return;
-  const int ncols = 3 * min(TCC, nq - k0);
-  const int col = threadIdx.x;
-  const int row = rt * AR + threadIdx.y;
-  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
-  const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-  if (row >= nrows || col >= ncols) return;
-  const int kl = k0 + col / 3, d = col % 3;
-  T v = T(0);
-  if (row < w && (c0 + row) % 3 == d) {
-    // column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
-    const int node = (c0 + row) / 3;
-    const int a = qidx[(size_t)s * m + kl];
+  const int u1 = plan[pb];
+  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {
+    const int pos = find_pos(plan, pa, pb, u);
+    const int s = level_list[pos];
+    const int nq = qcount[s];
+    const int local = u - plan[pos];
+    const int nt = cdiv(nq, TCC);
+    const int rt = local / nt, t = local % nt;
+    const int k0 = t * TCC;
+    const int ncols = 3 * min(TCC, nq - k0);
+    const int col = threadIdx.x;
+    const int row = rt * AR + threadIdx.y;
+    const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+    const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+    if (row >= nrows || col >= ncols) continue;
+    const int kl = k0 + col / 3, d = col % 3;
+    T v = T(0);
+    if (row < w && (c0 + row) % 3 == d) {
+      // column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
+      const int node = (c0 + row) / 3;
+      const int a = qidx[(size_t)s * m + kl];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (nodes[4 * a + i] == node) v += bary[4 * a + i];
-  }
-  const int64_t fr = fr_ptr[s] + row;
-  for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
-    const int c = ctr_child[e];
-    const int jl = qinv[(size_t)c * m + kl];
-    if (jl >= 0) {
-      const int wc = super_ptr[c + 1] - super_ptr[c];
-      v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
+      for (int i = 0; i < 4; ++i)
+        if (nodes[4 * a + i] == node) v += bary[4 * a + i];
     }
+    const int64_t fr = fr_ptr[s] + row;
+    for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
+      const int c = ctr_child[e];
+      const int jl = qinv[(size_t)c * m + kl];
+      if (jl >= 0) {
+        const int wc = super_ptr[c + 1] - super_ptr[c];
+        v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
+      }
+    }
+    if (row < w)
+      Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
+    else
+      X[fr * ldx + 3 * k0 + col] = v;
   }
-  if (row < w)
-    Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
-  else
-    X[fr * ldx + 3 * k0 + col] = v;
 }
 
 // Block (supernode, 64-row tile of the w + r front rows, 32-contact tile):
 // out = G_s[rows, :] F_top; top rows store X_s = out, bottom rows U_s -= out.
 // K is streamed in 32-wide chunks through a double-buffered cp.async pipeline.
-static constexpr int GR = 64;   // rows per tile
 static constexpr int GLD = GR + 4, FLD = TCOLS + 4;
 template <class T>
 __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool ok) {
@@ -221,28 +326,16 @@ __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool ok) 
 }
 
 template <class T>
-__global__ void __launch_bounds__(256)
-    k_front_gemm(const int* __restrict__ level_list, int lvl_first, int nrt, int ntiles,
-                 const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
-                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
-                 const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sG = (T*)smraw;                 // 2 x KB x GLD
-  T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
-  int b = blockIdx.x;
-  const int t = b % ntiles;
-  b /= ntiles;
-  const int rt = b % nrt;
-  const int li = b / nrt;
-  const int s = level_list[lvl_first + li];
-  const int nq = qcount[s];
+__device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, const int* __restrict__ super_ptr,
+                                                const int64_t* __restrict__ rowpat_ptr,
+                                                const int64_t* __restrict__ val_ptr, const T* __restrict__ G,
+                                                const int64_t* __restrict__ fr_ptr, T* X,
+                                                const T* __restrict__ Ftop, int64_t ldx, T* sG, T* sF) {
   const int k0 = t * TCC;
-  if (k0 >= nq) return;
   const int ncols = 3 * min(TCC, nq - k0);
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
   const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
   const int row0 = rt * GR;
-  if (row0 >= nrows) return;
   const int64_t ldG = nrows;
   const T* Gs = G + val_ptr[s];
   const T* Ft = Ftop + (int64_t)c0 * ldx + 3 * k0;
@@ -313,6 +406,27 @@ __global__ void __launch_bounds__(256)
 }
 
 template <class T>
+__global__ void __launch_bounds__(256)
+    k_front_gemm(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+                 const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
+                 const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sG = (T*)smraw;                 // 2 x KB x GLD
+  T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
+  const int u1 = plan[pb];
+  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {   // block-uniform
+    const int pos = find_pos(plan, pa, pb, u);
+    const int s = level_list[pos];
+    const int nq = qcount[s];
+    const int local = u - plan[pos];
+    const int nt = cdiv(nq, TCC);
+    const int rt = local / nt, t = local % nt;
+    front_gemm_tile<T>(s, rt, t, nq, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, X, Ftop, ldx, sG, sF);
+  }
+}
+
+template <class T>
 static size_t gemm_smem_bytes() {
   return 2 * (size_t)KB * (GLD + FLD) * sizeof(T);
 }
@@ -335,69 +449,83 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
 }
 
 // ------------------------------------------------------------------ a4 contraction
-// Block (tile pair I <= J of supernode s's local columns, s):
+// Work unit (supernode s, tile pair I <= J of its local columns), for the
+// fronts narrower than the tensor-core threshold (all fronts in SIMT mode):
 // W_H[g(i), g(j)] += sum_k Y[k,i] Y[k,j] over the scaled fronts Y = D^-1/2 X.
-// Only the upper triangle (g(i) <= g(j)) is accumulated; k_symmetrize mirrors it.
+// Only the upper triangle (g(i) <= g(j)) is accumulated; k_symmetrize mirrors
+// it.  Blocks take units from a counter, largest supernodes (the end of
+// level_list) first.
 template <class T>
 __global__ void __launch_bounds__(256)
-    k_contract(int ntc, int max_cols, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+    k_contract(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
                const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
                const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
-  const int s = blockIdx.y;
-  int rem = blockIdx.x, I = 0;
-  while (rem >= ntc - I) {
-    rem -= ntc - I;
-    ++I;
-  }
-  const int J = I + rem;
-  const int ncol = 3 * qcount[s];
-  const int nt = (ncol + CT - 1) / CT;
-  if (J >= nt || ncol >= max_cols) return;   // wider fronts go to the tensor-core kernel
-  const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
-  const T* Xs = X + fr_ptr[s] * ldx;
+  __shared__ int unit_sh;
+  const int total = plan[ns];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  T acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  for (int kb = 0; kb < w; kb += CK_) {
-    const int nb = min(CK_, w - kb);
-    for (int e = tid; e < CK_ * CT; e += blockDim.x) {
-      int k = e / CT, c = e % CT;
-      int ca = I * CT + c, cb = J * CT + c;
-      sA[k][c] = (k < nb && ca < ncol) ? Xs[(int64_t)(kb + k) * ldx + ca] : T(0);
-      sB[k][c] = (k < nb && cb < ncol) ? Xs[(int64_t)(kb + k) * ldx + cb] : T(0);
-    }
+  for (;;) {
+    if (tid == 0) unit_sh = atomicAdd(counter, 1);
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < CK_; ++k) {
-      T av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = sA[k][ty * 4 + a];
-#pragma unroll
-      for (int b = 0; b < 4; ++b) bv[b] = sB[k][tx * 4 + b];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-    }
+    const int ur = unit_sh;
     __syncthreads();
-  }
-  const int* q = qidx + (size_t)s * m;
+    if (ur >= total) break;
+    const int u = total - 1 - ur;
+    const int pos = find_pos(plan, 0, ns, u);
+    const int s = level_list[pos];
+    const int ncol = 3 * qcount[s];
+    const int nt = cdiv(ncol, CT);
+    int rem = u - plan[pos], I = 0;
+    while (rem >= nt - I) {
+      rem -= nt - I;
+      ++I;
+    }
+    const int J = I + rem;
+    const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
+    const T* Xs = X + fr_ptr[s] * ldx;
+    T acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    int li = I * CT + ty * 4 + a;
-    if (li >= ncol) continue;
-    int64_t gi = 3 * (int64_t)q[li / 3] + li % 3;
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      int lj = J * CT + tx * 4 + b;
-      if (lj >= ncol || li > lj) continue;
-      int64_t gj = 3 * (int64_t)q[lj / 3] + lj % 3;
-      atomicAdd(&WH[gi * ldw + gj], acc[a][b]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int kb = 0; kb < w; kb += CK_) {
+      const int nb = min(CK_, w - kb);
+      for (int e = tid; e < CK_ * CT; e += blockDim.x) {
+        int k = e / CT, c = e % CT;
+        int ca = I * CT + c, cb = J * CT + c;
+        sA[k][c] = (k < nb && ca < ncol) ? Xs[(int64_t)(kb + k) * ldx + ca] : T(0);
+        sB[k][c] = (k < nb && cb < ncol) ? Xs[(int64_t)(kb + k) * ldx + cb] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < CK_; ++k) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = sA[k][ty * 4 + a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = sB[k][tx * 4 + b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      }
+      __syncthreads();
+    }
+    const int* q = qidx + (size_t)s * m;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      int li = I * CT + ty * 4 + a;
+      if (li >= ncol) continue;
+      int64_t gi = 3 * (int64_t)q[li / 3] + li % 3;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        int lj = J * CT + tx * 4 + b;
+        if (lj >= ncol || li > lj) continue;
+        int64_t gj = 3 * (int64_t)q[lj / 3] + lj % 3;
+        atomicAdd(&WH[gi * ldw + gj], acc[a][b]);
+      }
     }
   }
 }
@@ -957,23 +1085,40 @@ static int build_WH_T(Scene* s) {
                                   (int*)s->qinv.p);
   LAUNCH_OK("k_reach_inv");
   static bool gemm_attr = false;
+  static int gemm_occ = 1;
   if (!gemm_attr) {
     e = cudaFuncSetAttribute(k_front_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<T>());
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gemm_occ, k_front_gemm<T>, 256, gemm_smem_bytes<T>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_front_gemm)");
+    gemm_occ = std::max(1, gemm_occ);
     gemm_attr = true;
   }
+  // contraction: FP32 scenes put fronts of TC_MIN_COLS or more columns on the
+  // tensor cores (unless SIMT is asked for), the rest on CUDA cores
+  int mode = s->params.contraction;
+  if (sizeof(T) == 8) mode = ICR_CONTRACT_SIMT;
+  if (mode == ICR_CONTRACT_AUTO) mode = ICR_CONTRACT_TF32X3;
+  const int simt_max = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
+  const int tc_min = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
+  int* plan = (int*)s->plan.p;
+  k_plan<<<1, 1024, 0, st>>>(ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+                             (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, plan);
+  LAUNCH_OK("k_plan");
+  const int nsm = s->ctx->sm_count;
   const int ntiles = (m + TCC - 1) / TCC;
   for (const Level& lv : s->levels) {
-    const int nrt_a = (lv.wmax + lv.rmax + AR - 1) / AR;
-    k_assemble<T><<<lv.count * nrt_a * ntiles, dim3(TCOLS, AR), 0, st>>>(
-        (const int*)s->level_list.p, lv.first, nrt_a, ntiles, (const int*)s->super_ptr.p,
+    const int pa = lv.first, pb = lv.first + lv.count;
+    const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + AR - 1) / AR) * ntiles;
+    k_assemble<T><<<(unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st>>>(
+        plan + PLAN_ASM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
         (const int*)s->ctr_child.p, (const int*)s->ctr_row.p, (const int*)s->nodes.p, (const T*)s->bary.p,
         (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qinv.p, m, X, (T*)s->Ftop.p, ldx);
     LAUNCH_OK("k_assemble");
-    const int nrt = (lv.wmax + lv.rmax + GR - 1) / GR;
-    k_front_gemm<T><<<lv.count * nrt * ntiles, 256, gemm_smem_bytes<T>(), st>>>(
-        (const int*)s->level_list.p, lv.first, nrt, ntiles, (const int*)s->super_ptr.p,
+    const int64_t ub_g = (int64_t)lv.count * ((lv.wmax + lv.rmax + GR - 1) / GR) * ntiles;
+    k_front_gemm<T><<<(unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st>>>(
+        plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
         (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
     LAUNCH_OK("k_front_gemm");
@@ -985,20 +1130,17 @@ static int build_WH_T(Scene* s) {
   const int64_t nr = 3 * (int64_t)m;
   e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset WH");
-  // contraction: FP32 scenes put fronts of TC_MIN_COLS or more columns on the
-  // tensor cores (unless SIMT is asked for), the rest on CUDA cores
-  int mode = s->params.contraction;
-  if (sizeof(T) == 8) mode = ICR_CONTRACT_SIMT;
-  if (mode == ICR_CONTRACT_AUTO) mode = ICR_CONTRACT_TF32X3;
-  const int simt_max = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
-  const int ntc = (int)((nr + CT - 1) / CT);
-  const int npairs = ntc * (ntc + 1) / 2;
-  k_contract<T><<<dim3(npairs, ns), 256, 0, st>>>(ntc, simt_max, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p,
-                                                  (const int*)s->qcount.p, (const int*)s->qidx.p, m, X, ldx,
-                                                  (T*)s->WH.p, nr);
-  LAUNCH_OK("k_contract");
+  {
+    const int64_t ntc = (nr + CT - 1) / CT;
+    const int64_t ub = (int64_t)ns * (ntc * (ntc + 1) / 2);
+    k_contract<T><<<(unsigned)std::min<int64_t>(ub, 4 * nsm), 256, 0, st>>>(
+        plan + PLAN_SIMT * (ns + 1), plan + PLAN_LISTS * (ns + 1), ns, (const int*)s->level_list.p,
+        (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, m,
+        X, ldx, (T*)s->WH.p, nr);
+    LAUNCH_OK("k_contract");
+  }
   if (mode != ICR_CONTRACT_SIMT) {
-    const int rc = launch_contract_tc(s, mode, TC_MIN_COLS);
+    const int rc = launch_contract_tc(s, mode);
     if (rc != ICR_OK) return rc;
   }
   k_symmetrize<T><<<dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st>>>((int)nr, (T*)s->WH.p);

@@ -5,7 +5,8 @@
 // k_pack_tc writes Y_s once per step as operand blocks (128 front columns x
 // 32 front rows, K-major core-matrix layout: 8 rows x 16 bytes per core matrix,
 // no swizzle), converted to the MMA operand type.
-// k_contract_tc, block (128 x 128 output tile pair I <= J, supernode s), 4 warps:
+// k_contract_tc, persistent blocks of 4 warps taking work units (128 x 128
+// output tile pair I <= J of supernode s) from a counter, largest fronts first:
 //   * one thread streams the blocks of tiles I and J through three
 //     shared-memory stages with cp.async.bulk (mbarrier transaction counts)
 //     and issues tcgen05.mma (M = N = 128) into a 128-column TMEM
@@ -13,6 +14,8 @@
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w..32w+31, i.e. the tile's rows) and adds the upper-triangle
 //     entries into W_H.
+// The pipeline's stage and phase come from running load / MMA counters that
+// carry over from one unit to the next.
 // Modes: TF32X3 splits every operand into a TF32 part and a TF32 remainder and
 // accumulates hi*hi + hi*lo + lo*hi (FP32-level error); TF32 and BF16 use one
 // rounded part.  Every mbarrier wait is bounded; a wait that runs out sets the
@@ -20,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "icr_internal.h"
@@ -27,11 +31,24 @@
 namespace icr {
 namespace {
 
-constexpr int TM = 128;   // output tile (M = N)
-constexpr int KT = 32;    // K rows per stage
+constexpr int TM = TC_TILE;   // output tile (M = N)
+constexpr int KT = TC_KT;     // K rows per stage
 constexpr long long WAIT_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// largest position p in [lo, hi) with P[p] <= u (P a non-decreasing prefix
+// array with P[lo] <= u < P[hi]): the supernode owning work unit u
+__device__ __forceinline__ int find_unit(const int* __restrict__ P, int lo, int hi, int u) {
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (P[mid] <= u)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
 
 // tcgen05 shared-memory descriptor: start >> 4 in bits 0-13, leading (K)
 // core-matrix stride >> 4 in bits 16-29, stride between 8-row groups >> 4 in
@@ -103,79 +120,74 @@ constexpr int STAGES = 3;
 // Staged through shared memory so that global reads and writes are coalesced.
 template <int MODE>
 __global__ void __launch_bounds__(256)
-    k_pack_tc(int tmax, int min_cols, const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+    k_pack_tc(const int* __restrict__ plan, int ns, const int* __restrict__ level_list,
+              const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
               const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ Y,
               int64_t ldx, unsigned char* pk) {
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
-  const int s = blockIdx.y;
-  const int ncol = 3 * qcount[s];
-  const int w = super_ptr[s + 1] - super_ptr[s];
-  const int nk = (w + KT - 1) / KT;
-  const int I = blockIdx.x / nk, kt = blockIdx.x % nk;
-  if (ncol < min_cols || I * TM >= ncol || I >= tmax) return;
-  const float* Ys = Y + fr_ptr[s] * ldx;
-  for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
-    const int k = e / TM, r = e % TM;
-    const int row = kt * KT + k, col = I * TM + r;
-    sy[k][r] = (row < w && col < ncol) ? Ys[(int64_t)row * ldx + col] : 0.f;
-  }
-  __syncthreads();
-  unsigned char* blk = pk + (boff[s] + (int64_t)I * nk + kt) * (int64_t)(TR::PARTS * tile_bytes<MODE>());
-  // 16-byte chunk q of the tile: core matrix (g, j), row r8: elements k = j*C .. j*C + C-1
-  constexpr int C = 16 / TR::EB;
-  constexpr int CHUNKS = TM * KT / C;
-  for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
-    const int cm = q >> 3, r8 = q & 7;                 // core matrix index, row inside it
-    const int g = cm / (KT / C), j = cm % (KT / C);
-    const int r = g * 8 + r8;
-    if constexpr (MODE == ICR_CONTRACT_BF16) {
-      unsigned short h[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sy[j * C + c][r]));
-      *(uint4*)(blk + q * 16) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                                           h[6] | (h[7] << 16));
-    } else {
-      uint32_t hi[4], lo[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float x = sy[j * C + c][r];
-        hi[c] = to_tf32(x);
-        lo[c] = to_tf32(x - __uint_as_float(hi[c]));
-      }
-      *(uint4*)(blk + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      if constexpr (TR::PARTS == 2)
-        *(uint4*)(blk + tile_bytes<MODE>() + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  const int total = plan[ns];
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
+    const int pos = find_unit(plan, 0, ns, u);
+    const int s = level_list[pos];
+    const int ncol = 3 * qcount[s];
+    const int w = super_ptr[s + 1] - super_ptr[s];
+    const int nk = (w + KT - 1) / KT;
+    const int local = u - plan[pos];
+    const int I = local / nk, kt = local % nk;
+    const float* Ys = Y + fr_ptr[s] * ldx;
+    for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
+      const int k = e / TM, r = e % TM;
+      const int row = kt * KT + k, col = I * TM + r;
+      sy[k][r] = (row < w && col < ncol) ? Ys[(int64_t)row * ldx + col] : 0.f;
     }
+    __syncthreads();
+    unsigned char* blk = pk + (boff[s] + (int64_t)I * nk + kt) * (int64_t)(TR::PARTS * tile_bytes<MODE>());
+    // 16-byte chunk q of the tile: core matrix (g, j), row r8: elements k = j*C .. j*C + C-1
+    constexpr int C = 16 / TR::EB;
+    constexpr int CHUNKS = TM * KT / C;
+    for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
+      const int cm = q >> 3, r8 = q & 7;                 // core matrix index, row inside it
+      const int g = cm / (KT / C), j = cm % (KT / C);
+      const int r = g * 8 + r8;
+      if constexpr (MODE == ICR_CONTRACT_BF16) {
+        unsigned short h[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sy[j * C + c][r]));
+        *(uint4*)(blk + q * 16) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                             h[6] | (h[7] << 16));
+      } else {
+        uint32_t hi[4], lo[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float x = sy[j * C + c][r];
+          hi[c] = to_tf32(x);
+          lo[c] = to_tf32(x - __uint_as_float(hi[c]));
+        }
+        *(uint4*)(blk + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        if constexpr (TR::PARTS == 2)
+          *(uint4*)(blk + tile_bytes<MODE>() + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+    __syncthreads();   // sy is refilled by the next unit
   }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(128, 1)
-    k_contract_tc(int ntc, int tmax, int min_cols, const int* __restrict__ super_ptr,
-                  const int* __restrict__ qcount, const int* __restrict__ qidx, const int64_t* __restrict__ boff,
-                  int m, const unsigned char* __restrict__ pk, float* WH, int64_t ldw, int* dev_err) {
+    k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+                  const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
+                  const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
+                  int64_t ldw, int* dev_err) {
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();   // one packed operand block
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block)
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
   __shared__ uint32_t tmem_base;
-  __shared__ int ok_sh;
-  const int s = blockIdx.y;
-  int rem = blockIdx.x, I = 0;
-  while (rem >= ntc - I) {
-    rem -= ntc - I;
-    ++I;
-  }
-  const int J = I + rem;
-  const int ncol = 3 * qcount[s];
-  if (ncol < min_cols || J * TM >= ncol || J >= tmax) return;   // uniform: before any allocation
-  const int w = super_ptr[s + 1] - super_ptr[s];
-  const int nk = (w + KT - 1) / KT;
+  __shared__ int ok_sh, unit_sh;
+  const int total = plan[ns];
+  if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const unsigned char* blkA = pk + (boff[s] + (int64_t)I * nk) * BLK;
-  const unsigned char* blkB = pk + (boff[s] + (int64_t)J * nk) * BLK;
-  const bool same = I == J;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
@@ -194,100 +206,138 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    const uint32_t idesc = instr_desc(TR::TYPE);
-    constexpr int SBO = (KT / (16 / TR::EB)) * 128;
-    const uint32_t bytes = same ? BLK : 2 * BLK;
-    bool ok = true;
-    for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
-      if (kt < nk) {   // load chunk kt
-        const int st = kt % STAGES;
-        if (kt >= STAGES && !mbar_wait(smem_u32(&empty[st]), ((kt / STAGES) - 1) & 1)) {
-          ok = false;
-          break;
-        }
-        unsigned char* dA = smem + st * 2 * BLK;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&full[st])), "r"(bytes));
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                smem_u32(dA)),
-            "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
-            : "memory");
-        if (!same)
+  uint32_t gl = 0, gm = 0;   // loads and MMA chunks issued by this block so far (thread 0)
+  for (;;) {
+    if (tid == 0) unit_sh = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ur = unit_sh;
+    if (ur >= total || !ok_sh) break;   // uniform
+    const int u = total - 1 - ur;
+    const int pos = find_unit(plan, 0, ns, u);
+    const int s = level_list[pos];
+    const int ncol = 3 * qcount[s];
+    const int nI = (ncol + TM - 1) / TM;
+    int rem = u - plan[pos], I = 0;
+    while (rem >= nI - I) {
+      rem -= nI - I;
+      ++I;
+    }
+    const int J = I + rem;
+    const int w = super_ptr[s + 1] - super_ptr[s];
+    const int nk = (w + KT - 1) / KT;
+    const unsigned char* blkA = pk + (boff[s] + (int64_t)I * nk) * BLK;
+    const unsigned char* blkB = pk + (boff[s] + (int64_t)J * nk) * BLK;
+    const bool same = I == J;
+    if (tid == 0) {
+      const uint32_t idesc = instr_desc(TR::TYPE);
+      constexpr int SBO = (KT / (16 / TR::EB)) * 128;
+      const uint32_t bytes = same ? BLK : 2 * BLK;
+      bool ok = true;
+      int nl = 0, nm = 0;   // loads and MMA chunks of this unit
+      for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
+        if (kt < nk) {   // load chunk kt
+          const uint32_t g = gl + kt;
+          const int st = g % STAGES;
+          if (g >= STAGES && !mbar_wait(smem_u32(&empty[st]), ((g / STAGES) - 1) & 1)) {
+            ok = false;
+            break;
+          }
+          unsigned char* dA = smem + st * 2 * BLK;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&full[st])),
+                       "r"(bytes));
           asm volatile(
               "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                  smem_u32(dA + BLK)),
-              "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
+                  smem_u32(dA)),
+              "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
               : "memory");
-      }
-      const int kc = kt - (STAGES - 1);
-      if (kc >= 0) {   // multiply chunk kc
-        const int st = kc % STAGES;
-        if (!mbar_wait(smem_u32(&full[st]), (kc / STAGES) & 1)) {
-          ok = false;
-          break;
+          if (!same)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(dA + BLK)),
+                "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
+                : "memory");
+          ++nl;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const unsigned char* sA = smem + st * 2 * BLK;
-        const unsigned char* sB = same ? sA : sA + BLK;
-#pragma unroll
-        for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
-          const uint32_t off = kk * 256;   // two core matrices along K per MMA
-#pragma unroll
-          for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
-            const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
-            const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
-            const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
-            const uint32_t acc = (kc > 0 || kk > 0 || term > 0) ? 1u : 0u;
-            if constexpr (MODE == ICR_CONTRACT_BF16)
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                      tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            else
-              asm volatile(
-                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                      tmem),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        const int kc = kt - (STAGES - 1);
+        if (kc >= 0) {   // multiply chunk kc
+          const uint32_t g = gm + kc;
+          const int st = g % STAGES;
+          if (!mbar_wait(smem_u32(&full[st]), (g / STAGES) & 1)) {
+            ok = false;
+            break;
           }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&empty[st])));
-      }
-    }
-    // the last commit tracks every MMA issued before it
-    if (ok && !mbar_wait(smem_u32(&empty[(nk - 1) % STAGES]), ((nk - 1) / STAGES) & 1)) ok = false;
-    if (!ok) {
-      ok_sh = 0;
-      atomicExch(dev_err, 1);
-      // let copies already in flight land before the block leaves
-      for (int st = 0; st < STAGES; ++st) mbar_wait(smem_u32(&full[st]), 0);
-    }
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
-  if (ok_sh) {
-    const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread (TMEM lane)
-    const bool row_ok = li < ncol;
-    const int64_t gi = row_ok ? 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3 : 0;
-    for (int c0j = 0; c0j < TM; c0j += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0j;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-      if (!row_ok) continue;
+          asm volatile("tcgen05.fence::after_thread_sync;\n");
+          const unsigned char* sA = smem + st * 2 * BLK;
+          const unsigned char* sB = same ? sA : sA + BLK;
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int lj = J * TM + c0j + j;
-        if (lj >= ncol || li > lj) continue;
-        const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
-        atomicAdd(&WH[gi * ldw + gj], __uint_as_float(v[j]));
+          for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
+            const uint32_t off = kk * 256;   // two core matrices along K per MMA
+#pragma unroll
+            for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
+              const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
+              const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
+              const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
+              const uint32_t acc = (kc > 0 || kk > 0 || term > 0) ? 1u : 0u;
+              if constexpr (MODE == ICR_CONTRACT_BF16)
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+              else
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                        tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              smem_u32(&empty[st])));
+          ++nm;
+        }
+      }
+      // the last commit tracks every MMA issued before it
+      if (ok) {
+        const uint32_t g = gm + nk - 1;
+        if (!mbar_wait(smem_u32(&empty[g % STAGES]), (g / STAGES) & 1)) ok = false;
+      }
+      if (!ok) {
+        ok_sh = 0;
+        atomicExch(dev_err, 1);
+        // let copies already in flight land before the block leaves
+        for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&full[g % STAGES]), (g / STAGES) & 1);
+      }
+      gl += nl;
+      gm += nm;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (ok_sh) {
+      const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread (TMEM lane)
+      const bool row_ok = li < ncol;
+      const int64_t gi = row_ok ? 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3 : 0;
+      for (int c0j = 0; c0j < TM; c0j += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0j;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+        if (!row_ok) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int lj = J * TM + c0j + j;
+          if (lj >= ncol || li > lj) continue;
+          const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
+          atomicAdd(&WH[gi * ldw + gj], __uint_as_float(v[j]));
+        }
       }
     }
+    // the accumulator is read before the next unit's MMAs overwrite it, and
+    // unit_sh before thread 0 takes the next unit
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
@@ -295,28 +345,37 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 template <int MODE>
-int contract_tc_T(Scene* s, int min_cols) {
-  const int m = s->m;
+int contract_tc_T(Scene* s) {
+  const int m = s->m, ns = s->ns;
   const int64_t nr = 3 * (int64_t)m;
-  const int ntc = (int)((nr + TM - 1) / TM);
-  const int npairs = ntc * (ntc + 1) / 2;
   const size_t smem = STAGES * 2 * (size_t)(TcTraits<MODE>::PARTS * tile_bytes<MODE>());
   static bool attr = false;
+  static int occ = 1;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_contract_tc)");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_contract_tc<MODE>, 128, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_contract_tc)");
+    occ = std::max(1, std::min(occ, 4));   // 4 x 128 TMEM columns fill an SM's 512
     attr = true;
   }
-  const int nkmax = (s->wmax + KT - 1) / KT;
-  k_pack_tc<MODE><<<dim3(s->tc_tmax * nkmax, s->ns), 256, 0, s->ctx->stream>>>(
-      s->tc_tmax, min_cols, (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
-      (const int64_t*)s->tc_boff.p, (const float*)s->X.p, s->ldx, (unsigned char*)s->Ypk.p);
+  const int* plan = (const int*)s->plan.p;
+  const int nsm = s->ctx->sm_count;
+  const int tmax = s->tc_tmax;
+  const int64_t ub_pack = (int64_t)ns * tmax * ((s->wmax + KT - 1) / KT);
+  k_pack_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream>>>(
+      plan + PLAN_PACK * (ns + 1), ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+      (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p,
+      s->ldx, (unsigned char*)s->Ypk.p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc");
   ++s->launches;
-  k_contract_tc<MODE><<<dim3(npairs, s->ns), 128, smem, s->ctx->stream>>>(
-      ntc, s->tc_tmax, min_cols, (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
-      (const int64_t*)s->tc_boff.p, m, (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
+  const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2;
+  k_contract_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), 128, smem,
+                        s->ctx->stream>>>(
+      plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + 1, ns, (const int*)s->level_list.p,
+      (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
+      (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_contract_tc");
   ++s->launches;
@@ -325,11 +384,11 @@ int contract_tc_T(Scene* s, int min_cols) {
 
 }  // namespace
 
-int launch_contract_tc(Scene* s, int mode, int min_cols) {
+int launch_contract_tc(Scene* s, int mode) {
   switch (mode) {
-    case ICR_CONTRACT_TF32X3: return contract_tc_T<ICR_CONTRACT_TF32X3>(s, min_cols);
-    case ICR_CONTRACT_TF32: return contract_tc_T<ICR_CONTRACT_TF32>(s, min_cols);
-    case ICR_CONTRACT_BF16: return contract_tc_T<ICR_CONTRACT_BF16>(s, min_cols);
+    case ICR_CONTRACT_TF32X3: return contract_tc_T<ICR_CONTRACT_TF32X3>(s);
+    case ICR_CONTRACT_TF32: return contract_tc_T<ICR_CONTRACT_TF32>(s);
+    case ICR_CONTRACT_BF16: return contract_tc_T<ICR_CONTRACT_BF16>(s);
     default: set_error("launch_contract_tc: mode %d is not a tensor-core mode", mode); return ICR_EINVAL;
   }
 }
