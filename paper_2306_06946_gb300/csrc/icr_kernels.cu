@@ -641,13 +641,11 @@ __global__ void __launch_bounds__(1024, 1)
   };
   for (int i = tid; i < n3; i += nthr) lam[i] = warm ? lam_g[i] : T(0);
   for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
-  for (int i = tid; i < PGS_MAX_BLOCKS / 32; i += nthr) actb[i] = ~0u;
+  for (int i = tid; i < PGS_MAX_BLOCKS / 32; i += nthr) actb[i] = 0u;
   if (tid == 0) {
-    pref[0] = 1;
     pref[1] = 0;
     changed = 0;
   }
-  prefetch(0, 0, tid, nthr);
   __syncthreads();
   if (warm) {
     for (int row = wid; row < n3; row += 32) {
@@ -661,6 +659,19 @@ __global__ void __launch_bounds__(1024, 1)
   } else {
     for (int i = tid; i < n3; i += nthr) r[i] = delta[i];
   }
+  __syncthreads();
+  // a block starts active when one of its contacts has lambda~ != 0 or a
+  // negative normal residual; only active blocks have their rows prefetched
+  for (int bb = wid; bb < nblk; bb += 32) {
+    const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
+    const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
+                                  lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
+    if (__ballot_sync(FULL, a) != 0u && lane == 0) atomicOr(&actb[bb >> 5], 1u << (bb & 31));
+  }
+  __syncthreads();
+  const bool act0 = nblk <= 2 || (actb[0] & 1u);
+  if (act0) prefetch(0, 0, tid, nthr);
+  if (tid == 0) pref[0] = act0 ? 1 : 0;
   cp_async_wait_all();
   __syncthreads();
 
