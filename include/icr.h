@@ -224,16 +224,31 @@ int icr_correct_motion(icr_scene* scene, double* dq_out, int reset);
 /* One time step of the fast scheme (Alg. 3) enqueued entirely on the device,
  * with directions from the scene's obstacle (icr_linearize): p <- p_0, u <- 0,
  * icr_build_WH, then n_newton x (icr_linearize(k), icr_update_W,
- * icr_solve_friction from lambda~ = 0, icr_update_proximity), then
+ * icr_solve_friction (from lambda~ = 0, or warm-started in iteration 1 per
+ * icr_params.warm_start), icr_update_proximity), then
  * icr_correct_motion without a host copy (dq, p, lambda~ stay on the device).
  * Needs a system, a mapping, p_0 and an obstacle; returns once the work is
  * enqueued. */
 int icr_step(icr_scene* scene, int32_t n_newton);
 /* Capture icr_step(scene, n_newton) into a CUDA graph owned by the scene (one
- * plain step runs first so that every kernel is set up).  The context's stream
- * must not be the legacy default stream (ICR_EINVAL).  A later icr_set_mapping
- * invalidates the graph. */
+ * plain step runs first so that every kernel is set up; icr_autotune runs
+ * first when the scene is not tuned).  The context's stream must not be the
+ * legacy default stream (ICR_EINVAL).  A later icr_set_mapping invalidates the
+ * graph. */
 int icr_step_capture(icr_scene* scene, int32_t n_newton);
+/* Autotuner of the forward solve X = L^-1 H^T (the multi-RHS supernodal solve
+ * of Eq. "schur complemnt reformulated").  For every elimination-tree level it
+ * times the level's front products with 64 x 96 CUDA-core tiles and with
+ * 128 x 128 tcgen05 tiles (3xTF32, for fronts at least 64 wide with 64
+ * columns) on the scene's current mapping and keeps the faster (the tensor
+ * cores must win by 3 %).  Synchronises; runs several W_H builds (W_H is left
+ * formed).  Needs a system and a mapping (ICR_ESTATE); not while the stream is
+ * being captured (ICR_ESTATE).  FP64 scenes and the SIMT contraction mode keep
+ * CUDA cores.  tc_levels (may be NULL) receives the number of levels on the
+ * tensor cores.  Until it runs, every level with a front at least 64 wide uses
+ * the tensor cores; icr_set_mapping and a change of contraction mode mark the
+ * scene untuned. */
+int icr_autotune(icr_scene* scene, int32_t* tc_levels);
 /* Launch the captured step on the context's stream (ICR_ESTATE without one). */
 int icr_step_launch(icr_scene* scene);
 /* Wait until the context's stream has finished the scene's work. */

@@ -331,7 +331,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan};
+                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -347,9 +347,12 @@ int icr_set_params(icr_scene* s, const icr_params* params) {
     set_error("precision is fixed when the scene is created");
     return ICR_EINVAL;
   }
+  if (params->contraction != s->params.contraction) s->tuned = false;
   s->params = *params;
   return ICR_OK;
 }
+
+static int upload_tc_super(Scene* s);
 
 int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr, const int64_t* rowpat_ptr,
                    const int32_t* rowpat, const int64_t* val_ptr, const double* Lp, const double* D,
@@ -545,6 +548,39 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   RET(upload(s, s->ctr_ptr, cptr_rows.data(), cptr_rows.size()));
   RET(upload(s, s->ctr_child, crow_child.data(), crow_child.size()));
   RET(upload(s, s->ctr_row, crow_row.data(), crow_row.size()));
+  if (s->prec == ICR_FP32) {
+    // G_s of the supernodes wide enough for the tensor-core forward solve, as
+    // 3xTF32 operand blocks of 128 rows x 32 columns (32 KiB each)
+    std::vector<int64_t> goff(ns + 1, -1);
+    std::vector<int32_t> blocks;
+    int64_t nb = 0;
+    for (int k = 0; k < ns; ++k) {
+      const int w = sp[k + 1] - sp[k];
+      if (w < TC_GEMM_MIN_W) continue;
+      const int nrows = w + (int)(rp[k + 1] - rp[k]);
+      const int nrt = (nrows + TC_TILE - 1) / TC_TILE, nk = (w + TC_KT - 1) / TC_KT;
+      goff[k] = nb;
+      for (int rt = 0; rt < nrt; ++rt)
+        for (int kt = 0; kt < nk; ++kt) {
+          blocks.push_back(k);
+          blocks.push_back(rt);
+          blocks.push_back(kt);
+        }
+      nb += (int64_t)nrt * nk;
+    }
+    RET(dalloc(s, s->gpk_off, (ns + 1) * sizeof(int64_t)));
+    RET(upload(s, s->gpk_off, goff.data(), ns + 1));
+    RET(dalloc(s, s->Gpk, std::max<int64_t>(1, nb) * 32768));
+    if (nb) {
+      DBuf list;
+      RET(dalloc(s, list, blocks.size() * sizeof(int32_t)));
+      const int rc = upload(s, list, blocks.data(), blocks.size());
+      const int rc2 = rc == ICR_OK ? launch_pack_g(s, (const int32_t*)list.p, (int)(nb)) : rc;
+      cudaStreamSynchronize(s->ctx->stream);
+      dfree(s, list);
+      if (rc2 != ICR_OK) return rc2;
+    }
+  }
   CK(cudaStreamSynchronize(s->ctx->stream));
 
   s->n = n;
@@ -556,6 +592,12 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   s->h_val_ptr = vp;
   s->h_fr_ptr = frp;
   s->levels = levs;
+  s->h_level_list = llist;
+  s->tc_level.assign(nlev, 0);
+  for (int l = 0; l < nlev; ++l) s->tc_level[l] = levs[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
+  s->tuned = false;
+  RET(dalloc(s, s->tc_super, ns));
+  RET(upload_tc_super(s));
   s->total_front_rows = frp[ns];
   s->wmax = wmax;
   s->rmax = rmax;
@@ -606,7 +648,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->bitmap, (size_t)ns * words * sizeof(uint32_t)));
   RET(dalloc(s, s->wprefix, (size_t)ns * words * sizeof(int32_t)));
   RET(dalloc(s, s->qcount, ns * sizeof(int32_t)));
-  RET(dalloc(s, s->plan, ((size_t)PLAN_LISTS * (ns + 1) + PLAN_COUNTERS) * sizeof(int32_t)));
+  RET(dalloc(s, s->plan, ((size_t)PLAN_LISTS * (ns + 1) + 2 + s->levels.size()) * sizeof(int32_t)));
   RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qinv, (size_t)ns * mm * sizeof(int32_t)));
@@ -662,6 +704,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   s->has_mapping = true;
   s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
   s->obst_kind = 0;
+  s->tuned = false;
   if (s->step_graph) {
     cudaGraphExecDestroy(s->step_graph);
     s->step_graph = nullptr;
@@ -934,6 +977,85 @@ int icr_correct_motion(icr_scene* s, double* dq_out, int reset) {
   return ICR_OK;
 }
 
+// the per-level forward-solve engine flags, per supernode, for the planner
+static int upload_tc_super(Scene* s) {
+  std::vector<uint8_t> f(s->ns, 0);
+  for (size_t l = 0; l < s->levels.size(); ++l)
+    for (int i = 0; i < s->levels[l].count; ++i) f[s->h_level_list[s->levels[l].first + i]] = s->tc_level[l];
+  CK(cudaMemcpy(s->tc_super.p, f.data(), f.size(), cudaMemcpyHostToDevice));
+  return ICR_OK;
+}
+
+static int autotune(Scene* s) {
+  const int nlev = (int)s->levels.size();
+  cudaStream_t st = s->ctx->stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("autotune: the scene's stream is being captured");
+    return ICR_ESTATE;
+  }
+  std::vector<cudaEvent_t> ev(nlev + 1, nullptr);
+  for (auto& e : ev) {
+    const cudaError_t rc = cudaEventCreate(&e);
+    if (rc != cudaSuccess) {
+      for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+      return cuda_fail(rc, "autotune: cudaEventCreate");
+    }
+  }
+  auto done = [&](int rc) {
+    s->level_events = nullptr;
+    for (auto& x : ev) cudaEventDestroy(x);
+    return rc;
+  };
+  // per level, the better of two timed builds for each engine choice
+  std::vector<double> t[2];
+  for (int cfg = 0; cfg < 2; ++cfg) {
+    t[cfg].assign(nlev, 1e30);
+    for (int l = 0; l < nlev; ++l) s->tc_level[l] = cfg && s->levels[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
+    int rc = upload_tc_super(s);
+    if (rc != ICR_OK) return done(rc);
+    for (int rep = 0; rep < 3; ++rep) {
+      s->level_events = rep ? ev.data() : nullptr;
+      rc = launch_build_WH(s);
+      if (rc != ICR_OK) return done(rc);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return done(cuda_fail(e, "autotune: build"));
+      if (!rep) continue;
+      for (int l = 0; l < nlev; ++l) {
+        float ms = 0.f;
+        const cudaError_t e2 = cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
+        if (e2 != cudaSuccess) return done(cuda_fail(e2, "autotune: cudaEventElapsedTime"));
+        t[cfg][l] = std::min(t[cfg][l], (double)ms);
+      }
+    }
+  }
+  for (int l = 0; l < nlev; ++l)
+    s->tc_level[l] = s->levels[l].wmax >= TC_GEMM_MIN_W && t[1][l] < 0.97 * t[0][l] ? 1 : 0;
+  const int rc = upload_tc_super(s);
+  if (rc != ICR_OK) return done(rc);
+  s->tuned = true;
+  s->has_WH = true;   // every tuning build formed W_H
+  RET(check_device_error(s));
+  return done(ICR_OK);
+}
+
+int icr_autotune(icr_scene* s, int32_t* tc_levels) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "autotune"));
+  RET(set_device(s));
+  int mode = s->params.contraction;
+  if (s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT && s->m > 0) RET(autotune(s));
+  s->tuned = true;
+  if (tc_levels) {
+    int n = 0;
+    for (uint8_t f : s->tc_level) n += s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT ? f : 0;
+    *tc_levels = n;
+  }
+  return ICR_OK;
+}
+
 static int step_enqueue(Scene* s, int n_newton) {
   if (!s->has_mapping || !s->has_system) {
     set_error("step: needs icr_set_system and icr_set_mapping");
@@ -1021,6 +1143,7 @@ int icr_step_capture(icr_scene* s, int32_t n_newton) {
     set_error("step_capture: the context needs its own CUDA stream to capture a graph");
     return ICR_EINVAL;
   }
+  if (!s->tuned) RET(icr_autotune(s, nullptr));
   RET(step_enqueue(s, n_newton));   // a plain step sets every kernel up before capture
   CK(cudaStreamSynchronize(st));
   if (s->step_graph) {

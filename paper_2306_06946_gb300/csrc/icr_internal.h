@@ -35,10 +35,20 @@ struct DBuf {
 // exclusive prefix sum of the work units the supernodes before p contribute to
 // each list.  A kernel over a level range [a, b) of positions covers units
 // plan[a] .. plan[b] - 1; the unit's supernode is found by binary search.
-enum PlanList { PLAN_ASM = 0, PLAN_GEMM = 1, PLAN_SIMT = 2, PLAN_PACK = 3, PLAN_TC = 4, PLAN_LISTS = 5 };
-constexpr int PLAN_COUNTERS = 2;   // dynamic-scheduling counters: SIMT and tensor-core contraction
-constexpr int TC_TILE = 128;       // tensor-core output tile (M = N)
-constexpr int TC_KT = 32;          // front rows per packed operand block
+// Lists: assembly tiles, SIMT front-GEMM tiles, tensor-core front-GEMM tiles,
+// packed F_top blocks, SIMT contraction tile pairs, packed Y blocks,
+// tensor-core contraction tile pairs.  After the lists come the scheduling
+// counters: SIMT contraction, tensor-core contraction, then one per level for
+// the tensor-core front GEMM.
+enum PlanList {
+  PLAN_ASM = 0, PLAN_GEMM = 1, PLAN_GTC = 2, PLAN_FPACK = 3, PLAN_SIMT = 4, PLAN_PACK = 5, PLAN_TC = 6,
+  PLAN_LISTS = 7
+};
+enum PlanCounter { PLAN_CNT_SIMT = 0, PLAN_CNT_TC = 1, PLAN_CNT_GTC = 2 };
+constexpr int TC_TILE = 128;         // tensor-core output tile (M = N)
+constexpr int TC_KT = 32;            // front rows per packed operand block
+constexpr int TC_GEMM_MIN_W = 64;    // fronts at least this wide ...
+constexpr int TC_GEMM_MIN_COLS = 64; // ... and with this many columns take the tensor-core forward solve
 
 // Per-level launch geometry of the supernodal elimination tree.
 struct Level {
@@ -73,7 +83,15 @@ struct Scene {
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, ut, y, dq, stats;
-  DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then PLAN_COUNTERS counters (int32)
+  DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then 2 + levels counters (int32)
+  DBuf Gpk, gpk_off;   // G_s of the wide supernodes as 3xTF32 operand blocks; first block per supernode
+  // forward-solve engine per etree level: 1 puts the level's wide fronts on the
+  // tensor cores (chosen by icr_autotune), mirrored per supernode for the planner
+  std::vector<uint8_t> tc_level;
+  std::vector<int32_t> h_level_list;
+  DBuf tc_super;
+  bool tuned = false;
+  cudaEvent_t* level_events = nullptr;   // while tuning: recorded before every level and after the last
   DBuf dev_err;            // int set by a kernel whose bounded wait ran out
   DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
   int tc_tmax = 0;         // 128-column tiles of the widest possible front
@@ -109,6 +127,8 @@ int launch_correct_motion(Scene* s);
 int launch_linearize(Scene* s, int k);
 // tcgen05 contraction for supernodes with at least min_cols front columns (icr_tc.cu)
 int launch_contract_tc(Scene* s, int mode);
+int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks);
+int launch_front_gemm_tc(Scene* s, int level);
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);
 

@@ -177,19 +177,26 @@ __device__ __forceinline__ int find_pos(const int* __restrict__ P, int lo, int h
 __device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 // Work units per supernode for the lists of one build (PlanList order):
-// assembly and front-GEMM tiles, SIMT contraction tile pairs of fronts
-// narrower than simt_max columns, packed tensor-core operand blocks and
+// assembly tiles; front-GEMM tiles, on the tensor cores (with their packed
+// F_top blocks) for fronts at least TC_GEMM_MIN_W wide with TC_GEMM_MIN_COLS
+// columns when tc_gemm is set and the supernode's level runs on the tensor
+// cores (tc_super), on CUDA cores otherwise; SIMT contraction tile
+// pairs of fronts narrower than simt_max columns; packed operand blocks and
 // tensor-core tile pairs of fronts at least tc_min columns wide.
 __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super_ptr,
                                             const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount,
-                                            int simt_max, int tc_min, int* c) {
+                                            int simt_max, int tc_min, int tc_gemm,
+                                            const unsigned char* __restrict__ tc_super, int* c) {
   const int q = qcount[s];
   const int w = super_ptr[s + 1] - super_ptr[s];
   const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
   const int nt = cdiv(q, TCC);
   const int ncol = 3 * q;
+  const bool tcg = tc_gemm && tc_super[s] && q > 0 && w >= TC_GEMM_MIN_W && ncol >= TC_GEMM_MIN_COLS;
   c[PLAN_ASM] = cdiv(nrows, AR) * nt;
-  c[PLAN_GEMM] = cdiv(nrows, GR) * nt;
+  c[PLAN_GEMM] = tcg ? 0 : cdiv(nrows, GR) * nt;
+  c[PLAN_GTC] = tcg ? cdiv(nrows, TC_TILE) * cdiv(ncol, TC_TILE) : 0;
+  c[PLAN_FPACK] = tcg ? cdiv(ncol, TC_TILE) * cdiv(w, TC_KT) : 0;
   const int ns_ = cdiv(ncol, CT);
   c[PLAN_SIMT] = (q > 0 && ncol < simt_max) ? ns_ * (ns_ + 1) / 2 : 0;
   const int nI = cdiv(ncol, TC_TILE);
@@ -199,19 +206,21 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
 }
 
 // One block: exclusive prefix sums of the per-supernode unit counts over the
-// positions of level_list, and the contraction counters reset to zero.
+// positions of level_list, and the scheduling counters reset to zero.
 __global__ void __launch_bounds__(1024)
     k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
            const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
-           int* plan) {
+           int tc_gemm, const unsigned char* __restrict__ tc_super, int ncounters, int* plan) {
   __shared__ int wsum[PLAN_LISTS][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int per = cdiv(ns, blockDim.x);
   const int p0 = min(ns, tid * per), p1 = min(ns, p0 + per);
-  int tot[PLAN_LISTS] = {0, 0, 0, 0, 0};
+  int tot[PLAN_LISTS];
+#pragma unroll
+  for (int l = 0; l < PLAN_LISTS; ++l) tot[l] = 0;
   for (int p = p0; p < p1; ++p) {
     int c[PLAN_LISTS];
-    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, c);
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, c);
 #pragma unroll
     for (int l = 0; l < PLAN_LISTS; ++l) tot[l] += c[l];
   }
@@ -247,14 +256,14 @@ __global__ void __launch_bounds__(1024)
   for (int l = 0; l < PLAN_LISTS; ++l) off[l] += wsum[l][warp];
   for (int p = p0; p < p1; ++p) {
     int c[PLAN_LISTS];
-    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, c);
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, c);
 #pragma unroll
     for (int l = 0; l < PLAN_LISTS; ++l) {
       plan[l * (ns + 1) + p] = off[l];
       off[l] += c[l];
     }
   }
-  if (tid < PLAN_COUNTERS) plan[PLAN_LISTS * (ns + 1) + tid] = 0;
+  for (int i = tid; i < ncounters; i += blockDim.x) plan[PLAN_LISTS * (ns + 1) + i] = 0;
 }
 
 // Assembly of the fronts of one level (positions [pa, pb) of level_list).
@@ -1112,14 +1121,24 @@ static int build_WH_T(Scene* s) {
   if (mode == ICR_CONTRACT_AUTO) mode = ICR_CONTRACT_TF32X3;
   const int simt_max = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
   const int tc_min = mode == ICR_CONTRACT_SIMT ? (1 << 30) : TC_MIN_COLS;
+  // the forward solve of wide fronts goes to the tensor cores (3xTF32) in FP32
+  // scenes, except in the all-SIMT mode
+  const int tc_gemm = mode != ICR_CONTRACT_SIMT ? 1 : 0;
   int* plan = (int*)s->plan.p;
+  const int nlev = (int)s->levels.size();
   k_plan<<<1, 1024, 0, st>>>(ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
-                             (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, plan);
+                             (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, tc_gemm,
+                             (const unsigned char*)s->tc_super.p, 2 + nlev, plan);
   LAUNCH_OK("k_plan");
   const int nsm = s->ctx->sm_count;
   const int ntiles = (m + TCC - 1) / TCC;
-  for (const Level& lv : s->levels) {
+  for (int li = 0; li < nlev; ++li) {
+    const Level& lv = s->levels[li];
     const int pa = lv.first, pb = lv.first + lv.count;
+    if (s->level_events) {
+      e = cudaEventRecord(s->level_events[li], st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
+    }
     const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + AR - 1) / AR) * ntiles;
     k_assemble<T><<<(unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st>>>(
         plan + PLAN_ASM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
@@ -1133,6 +1152,14 @@ static int build_WH_T(Scene* s) {
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
         (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
     LAUNCH_OK("k_front_gemm");
+    if (tc_gemm && s->tc_level[li] && lv.wmax >= TC_GEMM_MIN_W) {
+      const int rc = launch_front_gemm_tc(s, li);
+      if (rc != ICR_OK) return rc;
+    }
+  }
+  if (s->level_events) {
+    e = cudaEventRecord(s->level_events[nlev], st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
   }
   k_scale<T><<<(s->n + 7) / 8, 256, 0, st>>>(s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                              (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,

@@ -1,10 +1,15 @@
-// Tensor-core (tcgen05) contraction W_H += Y_s^T Y_s for the supernodes whose
-// scaled front Y_s = D_s^-1/2 X_s has at least TC_MIN_COLS columns
-// (Eq. "schur complemnt reformulated": W_H = H A^-1 H^T = X^T D^-1 X).
+// Tensor-core (tcgen05) parts of the W_H build (Eq. "schur complemnt
+// reformulated": W_H = H A^-1 H^T = X^T D^-1 X, X = L^-1 H^T):
+//   * the contraction W_H += Y_s^T Y_s for the supernodes whose scaled front
+//     Y_s = D_s^-1/2 X_s has at least TC_MIN_COLS columns, and
+//   * the forward-solve product of wide fronts, out = G_s F_top with the solve
+//     operator G_s = [L_ss^-1; L_Rs L_ss^-1] (3xTF32 only): rows < w give X_s,
+//     the others are subtracted from the update rows.
 //
-// k_pack_tc writes Y_s once per step as operand blocks (128 front columns x
-// 32 front rows, K-major core-matrix layout: 8 rows x 16 bytes per core matrix,
-// no swizzle), converted to the MMA operand type.
+// Operands are packed into blocks of 128 rows x 32 K (K-major core-matrix
+// layout: 8 rows x 16 bytes per core matrix, no swizzle), converted to the MMA
+// operand type: k_pack_tc packs Y_s (contraction, B = A) or F_top (forward
+// solve, B operand) once per build, k_pack_g packs G_s once per system.
 // k_contract_tc, persistent blocks of 4 warps taking work units (128 x 128
 // output tile pair I <= J of supernode s) from a counter, largest fronts first:
 //   * one thread streams the blocks of tiles I and J through three
@@ -118,24 +123,63 @@ constexpr int STAGES = 3;
 // kt*KT.. of Y_s restricted to columns I*TM.., as PARTS planes of a K-major
 // TM x KT tile (tile row r = front column I*TM + r, tile k = front row kt*KT + k).
 // Staged through shared memory so that global reads and writes are coalesced.
+// Writes the KT x TM staging tile sy (sy[k][r]) as one K-major operand block:
+// PARTS planes of TM x KT, 16-byte chunk q = core matrix (g, j), row r8.
+template <int MODE>
+__device__ __forceinline__ void pack_tile(const float (*sy)[TM + 1], unsigned char* blk) {
+  using TR = TcTraits<MODE>;
+  constexpr int C = 16 / TR::EB;
+  constexpr int CHUNKS = TM * KT / C;
+  for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
+    const int cm = q >> 3, r8 = q & 7;                 // core matrix index, row inside it
+    const int g = cm / (KT / C), j = cm % (KT / C);
+    const int r = g * 8 + r8;
+    if constexpr (MODE == ICR_CONTRACT_BF16) {
+      unsigned short h[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sy[j * C + c][r]));
+      *(uint4*)(blk + q * 16) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
+                                           h[6] | (h[7] << 16));
+    } else {
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float x = sy[j * C + c][r];
+        hi[c] = to_tf32(x);
+        lo[c] = to_tf32(x - __uint_as_float(hi[c]));
+      }
+      *(uint4*)(blk + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      if constexpr (TR::PARTS == 2)
+        *(uint4*)(blk + tile_bytes<MODE>() + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    }
+  }
+}
+
+// Packs, for the work units [plan[pa], plan[pb]) of a list over level_list
+// positions, 128-column x 32-row blocks of a front: unit (s, I, kt) holds rows
+// kt*KT.. of the source restricted to columns I*TM.., as PARTS planes of a
+// K-major TM x KT tile (tile row r = column I*TM + r, tile k = row kt*KT + k).
+// The source is the scaled front Y_s (rows from fr_ptr[s]) or the assembled top
+// rows F_top (rows from super_ptr[s]).  Staged through shared memory so that
+// global reads and writes are coalesced.
 template <int MODE>
 __global__ void __launch_bounds__(256)
-    k_pack_tc(const int* __restrict__ plan, int ns, const int* __restrict__ level_list,
+    k_pack_tc(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
-              const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ Y,
-              int64_t ldx, unsigned char* pk) {
+              const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
+              int from_ftop, int64_t ldx, unsigned char* pk) {
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
-  const int total = plan[ns];
-  for (int u = blockIdx.x; u < total; u += gridDim.x) {   // block-uniform
-    const int pos = find_unit(plan, 0, ns, u);
+  const int u1 = plan[pb];
+  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {   // block-uniform
+    const int pos = find_unit(plan, pa, pb, u);
     const int s = level_list[pos];
     const int ncol = 3 * qcount[s];
     const int w = super_ptr[s + 1] - super_ptr[s];
     const int nk = (w + KT - 1) / KT;
     const int local = u - plan[pos];
     const int I = local / nk, kt = local % nk;
-    const float* Ys = Y + fr_ptr[s] * ldx;
+    const float* Ys = src + (from_ftop ? (int64_t)super_ptr[s] : fr_ptr[s]) * ldx;
     for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
       const int k = e / TM, r = e % TM;
       const int row = kt * KT + k, col = I * TM + r;
@@ -143,70 +187,243 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     unsigned char* blk = pk + (boff[s] + (int64_t)I * nk + kt) * (int64_t)(TR::PARTS * tile_bytes<MODE>());
-    // 16-byte chunk q of the tile: core matrix (g, j), row r8: elements k = j*C .. j*C + C-1
-    constexpr int C = 16 / TR::EB;
-    constexpr int CHUNKS = TM * KT / C;
-    for (int q = threadIdx.x; q < CHUNKS; q += blockDim.x) {
-      const int cm = q >> 3, r8 = q & 7;                 // core matrix index, row inside it
-      const int g = cm / (KT / C), j = cm % (KT / C);
-      const int r = g * 8 + r8;
-      if constexpr (MODE == ICR_CONTRACT_BF16) {
-        unsigned short h[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) h[c] = __bfloat16_as_ushort(__float2bfloat16_rn(sy[j * C + c][r]));
-        *(uint4*)(blk + q * 16) = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16),
-                                             h[6] | (h[7] << 16));
-      } else {
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float x = sy[j * C + c][r];
-          hi[c] = to_tf32(x);
-          lo[c] = to_tf32(x - __uint_as_float(hi[c]));
-        }
-        *(uint4*)(blk + q * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        if constexpr (TR::PARTS == 2)
-          *(uint4*)(blk + tile_bytes<MODE>() + q * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-    }
+    pack_tile<MODE>(sy, blk);
     __syncthreads();   // sy is refilled by the next unit
   }
 }
 
+// Packs the solve operators G_s of the supernodes at least TC_GEMM_MIN_W wide
+// (column-major (w + r) x w panels, ld = w + r) into 128-row x 32-K blocks with
+// two TF32 planes; one CTA per block, the blocks listed by the host as
+// (supernode, row tile, K tile).
+__global__ void __launch_bounds__(256)
+    k_pack_g(const int* __restrict__ blocks, int nblocks, const int* __restrict__ super_ptr,
+             const int64_t* __restrict__ rowpat_ptr, const int64_t* __restrict__ val_ptr,
+             const int64_t* __restrict__ goff, const float* __restrict__ G, unsigned char* pk) {
+  __shared__ float sy[KT][TM + 1];
+  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    const int s = blocks[3 * b], rt = blocks[3 * b + 1], kt = blocks[3 * b + 2];
+    const int w = super_ptr[s + 1] - super_ptr[s];
+    const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+    const int nk = (w + KT - 1) / KT;
+    const float* Gs = G + val_ptr[s];
+    for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
+      const int k = e / TM, r = e % TM;   // consecutive threads: consecutive rows of one column
+      const int row = rt * TM + r, col = kt * KT + k;
+      sy[k][r] = (row < nrows && col < w) ? Gs[(int64_t)col * nrows + row] : 0.f;
+    }
+    __syncthreads();
+    pack_tile<ICR_CONTRACT_TF32X3>(sy, pk + (goff[s] + (int64_t)rt * nk + kt) * (int64_t)(2 * tile_bytes<ICR_CONTRACT_TF32X3>()));
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- pipeline
+// CTA of 5 warps.  Warp 4 (lane 0) streams the nk K-blocks of A and B (B = A
+// when same) through the STAGES-deep shared-memory ring with cp.async.bulk and
+// issues the MMAs (M = N = 128); warps 0-3 own the tile's rows (warp w reads
+// TMEM lanes 32w..32w+31).  The tensor cores accumulate at most PROMOTE_KB
+// K-blocks (128 K) into one of two 128-column TMEM buffers; the row warps then
+// add that partial tile into FP32 registers (IEEE adds) and free the buffer, so
+// the MMA's own accumulation never runs over more than 128 products.  Load,
+// MMA-chunk and buffer counters run over the CTA's whole life: stage or buffer
+// = count % depth, phase parity = (count / depth) & 1.  Every wait is bounded.
+constexpr int PROMOTE_KB = 4;
+constexpr int TC_THREADS = 160;
+constexpr uint32_t TMEM_COLS = 2 * TM;
+
+struct TcBars {
+  uint64_t full[STAGES], empty[STAGES];   // shared-memory ring
+  uint64_t tfull[2], tfree[2];            // TMEM buffers: MMAs done / drained
+  uint64_t fin;                           // teardown: every MMA issued has completed
+};
+
+// warp 4, lane 0
 template <int MODE>
-__global__ void __launch_bounds__(128, 1)
+__device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB, bool same, int nk,
+                           unsigned char* smem, TcBars& br, uint32_t tmem, uint32_t& gl, uint32_t& gm,
+                           uint32_t& gc) {
+  using TR = TcTraits<MODE>;
+  constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
+  const uint32_t idesc = instr_desc(TR::TYPE);
+  constexpr int SBO = (KT / (16 / TR::EB)) * 128;
+  const uint32_t bytes = same ? BLK : 2 * BLK;
+  const int nchunks = (nk + PROMOTE_KB - 1) / PROMOTE_KB;
+  bool ok = true;
+  int nl = 0, nm = 0;
+  for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
+    if (kt < nk) {   // load K-block kt
+      const uint32_t g = gl + kt;
+      const int st = g % STAGES;
+      if (g >= STAGES && !mbar_wait(smem_u32(&br.empty[st]), ((g / STAGES) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      unsigned char* dA = smem + st * 2 * BLK;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&br.full[st])),
+                   "r"(bytes));
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+              smem_u32(dA)),
+          "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
+          : "memory");
+      if (!same)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_u32(dA + BLK)),
+            "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
+            : "memory");
+      ++nl;
+    }
+    const int kc = kt - (STAGES - 1);
+    if (kc >= 0) {   // multiply K-block kc
+      const int ch = kc / PROMOTE_KB, first = kc % PROMOTE_KB == 0;
+      const bool last = kc % PROMOTE_KB == PROMOTE_KB - 1 || kc == nk - 1;
+      const uint32_t gb = gc + ch;                 // buffer use counter of this chunk
+      const uint32_t tb = tmem + (gb & 1) * TM;    // its 128 TMEM columns
+      if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      const uint32_t g = gm + kc;
+      const int st = g % STAGES;
+      if (!mbar_wait(smem_u32(&br.full[st]), (g / STAGES) & 1)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const unsigned char* sA = smem + st * 2 * BLK;
+      const unsigned char* sB = same ? sA : sA + BLK;
+#pragma unroll
+      for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
+        const uint32_t off = kk * 256;   // two core matrices along K per MMA
+#pragma unroll
+        for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
+          const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
+          const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
+          const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
+          const uint32_t acc = (!first || kk > 0 || term > 0) ? 1u : 0u;
+          if constexpr (MODE == ICR_CONTRACT_BF16)
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tb),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          else
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                    tb),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&br.empty[st])));
+      if (last)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&br.tfull[gb & 1])));
+      ++nm;
+    }
+  }
+  if (!ok)   // let copies already in flight land
+    for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&br.full[g % STAGES]), (g / STAGES) & 1);
+  gl += nl;
+  gm += nm;
+  gc += nchunks;
+  return ok;
+}
+
+// warps 0-3: acc[0..127] <- sum over the unit's chunks of the row's TMEM columns
+__device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, uint32_t& gc, float* acc) {
+  const int nchunks = (nk + PROMOTE_KB - 1) / PROMOTE_KB;
+  bool ok = true;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const uint32_t gb = gc + ch;
+    const int fine = ok && mbar_wait(smem_u32(&br.tfull[gb & 1]), (gb >> 1) & 1);
+    if (!__all_sync(0xffffffffu, fine)) {
+      ok = false;
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const uint32_t base = tmem + (gb & 1) * TM + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+    for (int c0j = 0; c0j < TM; c0j += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(base + (uint32_t)c0j));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) acc[c0j + j] = ch == 0 ? __uint_as_float(v[j]) : acc[c0j + j] + __uint_as_float(v[j]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&br.tfree[gb & 1])));
+  }
+  gc += nchunks;
+  return ok;
+}
+
+__device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, int* ok_sh) {
+  const int tid = threadIdx.x;
+  if ((tid >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_base)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.full[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.empty[i])), "r"(1));
+    }
+    for (int i = 0; i < 2; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.tfull[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.tfree[i])), "r"(4));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.fin)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+    *ok_sh = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+}
+
+// every MMA the CTA issued has completed (bounded) before TMEM is freed
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
+  if (threadIdx.x == 128) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        smem_u32(&br.fin)));
+    mbar_wait(smem_u32(&br.fin), 0);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// Contraction: persistent CTAs take units (128 x 128 output tile pair I <= J
+// of supernode s) from a counter, largest fronts first; the row warps add the
+// tile's upper-triangle entries into W_H.
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
                   const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
                   int64_t ldw, int* dev_err) {
   using TR = TcTraits<MODE>;
-  constexpr int BLK = TR::PARTS * tile_bytes<MODE>();   // one packed operand block
+  constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block)
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+  __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
   __shared__ int ok_sh, unit_sh;
   const int total = plan[ns];
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base)),
-                 "r"(TM));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-  if (tid == 0) {
-    for (int i = 0; i < STAGES; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&full[i])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&empty[i])), "r"(1));
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;\n");
-    ok_sh = 1;
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  tc_setup(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
-  uint32_t gl = 0, gm = 0;   // loads and MMA chunks issued by this block so far (thread 0)
+  uint32_t gl = 0, gm = 0, gc = 0;
   for (;;) {
     if (tid == 0) unit_sh = atomicAdd(counter, 1);
     __syncthreads();
@@ -225,138 +442,138 @@ __global__ void __launch_bounds__(128, 1)
     const int J = I + rem;
     const int w = super_ptr[s + 1] - super_ptr[s];
     const int nk = (w + KT - 1) / KT;
-    const unsigned char* blkA = pk + (boff[s] + (int64_t)I * nk) * BLK;
-    const unsigned char* blkB = pk + (boff[s] + (int64_t)J * nk) * BLK;
-    const bool same = I == J;
-    if (tid == 0) {
-      const uint32_t idesc = instr_desc(TR::TYPE);
-      constexpr int SBO = (KT / (16 / TR::EB)) * 128;
-      const uint32_t bytes = same ? BLK : 2 * BLK;
-      bool ok = true;
-      int nl = 0, nm = 0;   // loads and MMA chunks of this unit
-      for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
-        if (kt < nk) {   // load chunk kt
-          const uint32_t g = gl + kt;
-          const int st = g % STAGES;
-          if (g >= STAGES && !mbar_wait(smem_u32(&empty[st]), ((g / STAGES) - 1) & 1)) {
-            ok = false;
-            break;
-          }
-          unsigned char* dA = smem + st * 2 * BLK;
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&full[st])),
-                       "r"(bytes));
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                  smem_u32(dA)),
-              "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
-              : "memory");
-          if (!same)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                    smem_u32(dA + BLK)),
-                "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&full[st]))
-                : "memory");
-          ++nl;
-        }
-        const int kc = kt - (STAGES - 1);
-        if (kc >= 0) {   // multiply chunk kc
-          const uint32_t g = gm + kc;
-          const int st = g % STAGES;
-          if (!mbar_wait(smem_u32(&full[st]), (g / STAGES) & 1)) {
-            ok = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;\n");
-          const unsigned char* sA = smem + st * 2 * BLK;
-          const unsigned char* sB = same ? sA : sA + BLK;
-#pragma unroll
-          for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
-            const uint32_t off = kk * 256;   // two core matrices along K per MMA
-#pragma unroll
-            for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
-              const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
-              const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
-              const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
-              const uint32_t acc = (kc > 0 || kk > 0 || term > 0) ? 1u : 0u;
-              if constexpr (MODE == ICR_CONTRACT_BF16)
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-              else
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                        tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-              smem_u32(&empty[st])));
-          ++nm;
-        }
-      }
-      // the last commit tracks every MMA issued before it
-      if (ok) {
-        const uint32_t g = gm + nk - 1;
-        if (!mbar_wait(smem_u32(&empty[g % STAGES]), (g / STAGES) & 1)) ok = false;
-      }
-      if (!ok) {
+    if (warp == 4) {
+      if (lane == 0 &&
+          !tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk) * BLK, pk + (boff[s] + (int64_t)J * nk) * BLK, I == J,
+                            nk, smem, br, tmem, gl, gm, gc)) {
         ok_sh = 0;
         atomicExch(dev_err, 1);
-        // let copies already in flight land before the block leaves
-        for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&full[g % STAGES]), (g / STAGES) & 1);
       }
-      gl += nl;
-      gm += nm;
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    if (ok_sh) {
-      const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread (TMEM lane)
-      const bool row_ok = li < ncol;
-      const int64_t gi = row_ok ? 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3 : 0;
-      for (int c0j = 0; c0j < TM; c0j += 16) {
-        uint32_t v[16];
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0j;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-        if (!row_ok) continue;
+    } else {
+      float acc[TM];
+      if (tc_drain(nk, br, tmem, warp, lane, gc, acc)) {
+        const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
+        if (li < ncol) {
+          const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int lj = J * TM + c0j + j;
-          if (lj >= ncol || li > lj) continue;
-          const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
-          atomicAdd(&WH[gi * ldw + gj], __uint_as_float(v[j]));
+          for (int j = 0; j < TM; ++j) {
+            const int lj = J * TM + j;
+            if (lj >= ncol || li > lj) continue;
+            const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
+            atomicAdd(&WH[gi * ldw + gj], acc[j]);
+          }
         }
+      } else if (lane == 0) {
+        ok_sh = 0;
+        atomicExch(dev_err, 1);
       }
     }
-    // the accumulator is read before the next unit's MMAs overwrite it, and
-    // unit_sh before thread 0 takes the next unit
-    asm volatile("tcgen05.fence::before_thread_sync;\n");
+    __syncthreads();   // unit_sh is read by all before thread 0 takes the next unit
+  }
+  tc_teardown(tmem, br);
+}
+
+// Forward-solve product of the wide fronts of one level (3xTF32): persistent
+// CTAs take units (supernode s, 128-row tile rt of its w + r front rows,
+// 128-column tile ct of its 3|Q_s| columns) from the level's counter, largest
+// fronts first, and form out = G_s[rt rows, :] F_top[:, ct columns]; rows < w
+// store X_s = out, the update rows take U_s -= out.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_front_gemm_tc(const int* __restrict__ plan, int pa, int pb, int* counter, const int* __restrict__ level_list,
+                    const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                    const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                    const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
+                    const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
+                    int* dev_err) {
+  constexpr int MODE = ICR_CONTRACT_TF32X3;
+  constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) TcBars br;
+  __shared__ uint32_t tmem_base;
+  __shared__ int ok_sh, unit_sh;
+  const int u0 = plan[pa], total = plan[pb] - u0;
+  if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  tc_setup(&tmem_base, br, &ok_sh);
+  const uint32_t tmem = tmem_base;
+  uint32_t gl = 0, gm = 0, gc = 0;
+  for (;;) {
+    if (tid == 0) unit_sh = atomicAdd(counter, 1);
+    __syncthreads();
+    const int ur = unit_sh;
+    if (ur >= total || !ok_sh) break;   // uniform
+    const int u = u0 + total - 1 - ur;
+    const int pos = find_unit(plan, pa, pb, u);
+    const int s = level_list[pos];
+    const int ncol = 3 * qcount[s];
+    const int nJ = (ncol + TM - 1) / TM;
+    const int local = u - plan[pos];
+    const int rt = local / nJ, ct = local % nJ;
+    const int w = super_ptr[s + 1] - super_ptr[s];
+    const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+    const int nk = (w + KT - 1) / KT;
+    if (warp == 4) {
+      if (lane == 0 && !tc_produce<MODE>(gpk + (goff[s] + (int64_t)rt * nk) * BLK,
+                                         fpk + (boff[s] + (int64_t)ct * nk) * BLK, false, nk, smem, br, tmem, gl, gm,
+                                         gc)) {
+        ok_sh = 0;
+        atomicExch(dev_err, 1);
+      }
+    } else {
+      float acc[TM];
+      if (tc_drain(nk, br, tmem, warp, lane, gc, acc)) {
+        const int row = rt * TM + 32 * warp + lane;   // front row owned by this thread
+        const int cmax = ncol - ct * TM;              // columns of this tile inside the front
+        if (row < nrows) {
+          float* F = X + (fr_ptr[s] + row) * ldx + ct * TM;
+#pragma unroll
+          for (int c0j = 0; c0j < TM; c0j += 4) {
+            if (c0j >= cmax) break;
+            if (c0j + 4 <= cmax) {
+              float4* F4 = (float4*)(F + c0j);
+              float4 o = make_float4(acc[c0j], acc[c0j + 1], acc[c0j + 2], acc[c0j + 3]);
+              if (row >= w) {
+                const float4 x = *F4;
+                o = make_float4(x.x - o.x, x.y - o.y, x.z - o.z, x.w - o.w);
+              }
+              *F4 = o;
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (c0j + j < cmax) F[c0j + j] = row < w ? acc[c0j + j] : F[c0j + j] - acc[c0j + j];
+            }
+          }
+        }
+      } else if (lane == 0) {
+        ok_sh = 0;
+        atomicExch(dev_err, 1);
+      }
+    }
     __syncthreads();
   }
-  asm volatile("tcgen05.fence::before_thread_sync;\n");
-  __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TM));
+  tc_teardown(tmem, br);
+}
+
+// dynamic shared memory of a tensor-core CTA: the ring, padded so that at most
+// two CTAs share an SM (2 x 256 TMEM columns fill its 512)
+template <int MODE>
+static size_t tc_smem_bytes() {
+  return std::max<size_t>(STAGES * 2 * (size_t)(TcTraits<MODE>::PARTS * tile_bytes<MODE>()), 100 * 1024);
 }
 
 template <int MODE>
 int contract_tc_T(Scene* s) {
   const int m = s->m, ns = s->ns;
   const int64_t nr = 3 * (int64_t)m;
-  const size_t smem = STAGES * 2 * (size_t)(TcTraits<MODE>::PARTS * tile_bytes<MODE>());
+  const size_t smem = tc_smem_bytes<MODE>();
   static bool attr = false;
   static int occ = 1;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_contract_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_contract_tc)");
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_contract_tc<MODE>, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_contract_tc<MODE>, TC_THREADS, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_contract_tc)");
-    occ = std::max(1, std::min(occ, 4));   // 4 x 128 TMEM columns fill an SM's 512
+    occ = std::max(1, std::min(occ, 2));   // 2 x 256 TMEM columns fill an SM's 512
     attr = true;
   }
   const int* plan = (const int*)s->plan.p;
@@ -364,16 +581,16 @@ int contract_tc_T(Scene* s) {
   const int tmax = s->tc_tmax;
   const int64_t ub_pack = (int64_t)ns * tmax * ((s->wmax + KT - 1) / KT);
   k_pack_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream>>>(
-      plan + PLAN_PACK * (ns + 1), ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
-      (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p,
+      plan + PLAN_PACK * (ns + 1), 0, ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+      (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p, 0,
       s->ldx, (unsigned char*)s->Ypk.p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc");
   ++s->launches;
   const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2;
-  k_contract_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), 128, smem,
+  k_contract_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem,
                         s->ctx->stream>>>(
-      plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + 1, ns, (const int*)s->level_list.p,
+      plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_TC, ns, (const int*)s->level_list.p,
       (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
       (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
   e = cudaGetLastError();
@@ -391,6 +608,51 @@ int launch_contract_tc(Scene* s, int mode) {
     case ICR_CONTRACT_BF16: return contract_tc_T<ICR_CONTRACT_BF16>(s);
     default: set_error("launch_contract_tc: mode %d is not a tensor-core mode", mode); return ICR_EINVAL;
   }
+}
+
+int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks) {
+  if (nblocks == 0) return ICR_OK;
+  k_pack_g<<<(unsigned)std::min(nblocks, 8 * s->ctx->sm_count), 256, 0, s->ctx->stream>>>(
+      blocks, nblocks, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p,
+      (const int64_t*)s->gpk_off.p, (const float*)s->G.p, (unsigned char*)s->Gpk.p);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_pack_g");
+  return ICR_OK;
+}
+
+int launch_front_gemm_tc(Scene* s, int level) {
+  constexpr int MODE = ICR_CONTRACT_TF32X3;
+  const size_t smem = tc_smem_bytes<MODE>();
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(k_front_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm_tc)");
+    attr = true;
+  }
+  const Level& lv = s->levels[level];
+  const int ns = s->ns, pa = lv.first, pb = lv.first + lv.count;
+  int* plan = (int*)s->plan.p;
+  const int nsm = s->ctx->sm_count;
+  const int tmax = s->tc_tmax;
+  const int64_t ub_pack = (int64_t)lv.count * tmax * ((lv.wmax + KT - 1) / KT);
+  k_pack_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream>>>(
+      plan + PLAN_FPACK * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+      (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->Ftop.p, 1,
+      s->ldx, (unsigned char*)s->Ypk.p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc(F_top)");
+  ++s->launches;
+  const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax;
+  k_front_gemm_tc<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream>>>(
+      plan + PLAN_GTC * (ns + 1), pa, pb, plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_GTC + level,
+      (const int*)s->level_list.p, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
+      (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->gpk_off.p,
+      (const unsigned char*)s->Gpk.p, (const int64_t*)s->tc_boff.p, (const unsigned char*)s->Ypk.p, (float*)s->X.p,
+      s->ldx, (int*)s->dev_err.p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "k_front_gemm_tc");
+  ++s->launches;
+  return ICR_OK;
 }
 
 }  // namespace icr

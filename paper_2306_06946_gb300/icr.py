@@ -28,7 +28,7 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_set_obstacle_spheres", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
-           "icr_step_launch", "icr_sync", "icr_serve")
+           "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune")
 
 
 class IcrError(RuntimeError):
@@ -93,6 +93,7 @@ def lib() -> ct.CDLL:
             "icr_step_capture": [P, ct.c_int32],
             "icr_step_launch": [P],
             "icr_sync": [P],
+            "icr_autotune": [P, P],
             "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
         }
         for name, args in sigs.items():
@@ -298,6 +299,13 @@ class Scene:
 
     def step(self, n_newton: int):
         _check(lib().icr_step(self.h, int(n_newton)))
+
+    def autotune(self) -> int:
+        """Per-level choice of the forward-solve engine; returns the number of
+        levels on the tensor cores."""
+        n = ct.c_int32(0)
+        _check(lib().icr_autotune(self.h, ct.byref(n)))
+        return int(n.value)
 
     def step_capture(self, n_newton: int):
         _check(lib().icr_step_capture(self.h, int(n_newton)))

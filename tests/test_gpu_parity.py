@@ -339,3 +339,16 @@ def test_WH_contraction_modes(ctx, name, mode, tol):
     print(f"{name} {mode}: relative Frobenius error of W_H vs FP64 oracle {err:.3e}")
     assert err < tol
     assert np.array_equal(WH, WH.T)
+
+
+# ---------------------------------------------------------------- forward-solve engine autotuner
+def test_autotune_keeps_parity(ctx):
+    from paper_2306_06946_gb300 import icr
+    s = scene("liver_c1")
+    sc = make_scene(ctx, "liver_c1", icr.FP32)
+    n = sc.autotune()
+    assert 0 <= n <= s.factor.sym.nsuper
+    sc.build_WH()
+    assert rel(sc.get("WH"), oracle_WH("liver_c1")) < 1e-5
+    sc64 = make_scene(ctx, "liver_c1", icr.FP64)
+    assert sc64.autotune() == 0
