@@ -113,7 +113,9 @@ enum icr_field {
   ICR_FIELD_U = 7,         /* (3m) double, accumulated sum_k C_k^T lambda~_k */
   ICR_FIELD_REACH_PTR = 8, /* (nsuper + 1) int32, CSR offsets of the reached contacts */
   ICR_FIELD_REACH_IDX = 9, /* (reach_ptr[nsuper]) int32, ascending contact ids per supernode */
-  ICR_FIELD_DQ = 10        /* (n) double, the last corrective motion */
+  ICR_FIELD_DQ = 10,       /* (n) double, the last corrective motion */
+  ICR_FIELD_LAMBDA0 = 11   /* (3m) double, lambda~ of Newton iteration 1 of the last warm-started
+                              device-resident step (the next step's warm start; zero before) */
 };
 
 /* Thread-local text of the last error (never NULL). */

@@ -1103,6 +1103,7 @@ static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
     case ICR_FIELD_WH:
     case ICR_FIELD_W: *count = 9 * m * m; break;
     case ICR_FIELD_LAMBDA:
+    case ICR_FIELD_LAMBDA0:
     case ICR_FIELD_DELTA:
     case ICR_FIELD_P:
     case ICR_FIELD_U: *count = 3 * m; break;
@@ -1220,6 +1221,7 @@ int icr_get(icr_scene* s, int32_t field, void* dst, size_t bytes) {
     case ICR_FIELD_WH: return download_T(s, s->WH, (double*)dst, c);
     case ICR_FIELD_W: return download_T_2d(s, s->W, s->ldw, (double*)dst, 3 * (size_t)s->m, 3 * (size_t)s->m);
     case ICR_FIELD_LAMBDA: return download_T(s, s->lam, (double*)dst, c);
+    case ICR_FIELD_LAMBDA0: return download_T(s, s->lam0, (double*)dst, c);
     case ICR_FIELD_DELTA: return download_T(s, s->delta, (double*)dst, c);
     case ICR_FIELD_C: return download_T(s, s->C, (double*)dst, c);
     case ICR_FIELD_MU: return download_T(s, s->mu, (double*)dst, c);
@@ -1274,6 +1276,7 @@ int icr_set_field(icr_scene* s, int32_t field, const double* src, size_t bytes) 
       break;
     case ICR_FIELD_WH: RET(upload_T(s, s->WH, src, c)); s->has_WH = true; break;
     case ICR_FIELD_LAMBDA: RET(upload_T(s, s->lam, src, c)); s->has_lam = true; break;
+    case ICR_FIELD_LAMBDA0: RET(upload_T(s, s->lam0, src, c)); break;
     case ICR_FIELD_DELTA: RET(upload_T(s, s->delta, src, c)); break;
     case ICR_FIELD_C:
       RET(check_directions(src, s->m));

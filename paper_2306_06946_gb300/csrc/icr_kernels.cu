@@ -586,7 +586,9 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 //       residuals (streaming those rows of W) and prefetch, with cp.async,
 //       the next block's rows of W (its diagonal block and the block to its right).
 // A block whose contacts all have lambda~ = 0 and non-negative normal
-// residuals is a no-op and is passed without reading W.
+// residuals is a no-op and is passed without reading W.  After a block that
+// changed nothing every residual is complete, so the CTA looks ahead (one
+// warp per block) and jumps over the run of no-op blocks that follows.
 // The solve stops when eps <= tol (tol > 0) or after a sweep that changed
 // nothing, a fixed point of the iteration (Alg. 1's test with PGS_error = 0).
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
@@ -626,8 +628,10 @@ __global__ void __launch_bounds__(1024, 1)
   int* nzl = (int*)(dl + 2 * BR);  // 31 x BR: per streaming warp, rows with a non-zero change
   __shared__ T red[32];
   __shared__ int flag;
-  __shared__ int pref[2];            // stage k holds the prefetched rows of its block
-  __shared__ int changed;            // some lambda~ changed in the current sweep
+  __shared__ int pref[2];            // block whose rows stage k holds (-1: none)
+  __shared__ int chg_sweep[2];       // some lambda~ changed in sweep (done & 1)
+  __shared__ int chg_it[2];          // block processed at step t changed some lambda~ (slot t & 1)
+  __shared__ int nxt[2];             // look-ahead result (two slots, alternating)
   __shared__ unsigned actb[PGS_MAX_BLOCKS / 32];   // block had a changing contact in its last visit
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
@@ -652,8 +656,10 @@ __global__ void __launch_bounds__(1024, 1)
   for (int i = tid; i < 2 * BR; i += nthr) dl[i] = T(0);
   for (int i = tid; i < PGS_MAX_BLOCKS / 32; i += nthr) actb[i] = 0u;
   if (tid == 0) {
-    pref[1] = 0;
-    changed = 0;
+    pref[1] = -1;
+    chg_sweep[0] = chg_sweep[1] = 0;
+    chg_it[0] = chg_it[1] = 1;   // no look-ahead before the first block
+    nxt[0] = nxt[1] = nblk;
   }
   __syncthreads();
   if (warm) {
@@ -680,22 +686,75 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   const bool act0 = nblk <= 2 || (actb[0] & 1u);
   if (act0) prefetch(0, 0, tid, nthr);
-  if (tid == 0) pref[0] = act0 ? 1 : 0;
+  if (tid == 0) pref[0] = act0 ? 0 : -1;
   cp_async_wait_all();
   __syncthreads();
 
   // warp 0: lane l holds the residual (q) of contact l of the current block and
   // the pending changes (p) of contact l of the next block
-  T p0 = 0, p1 = 0, p2 = 0, dsum = T(0);
-  int done = 0, b = 0;
+  T p0 = 0, p1 = 0, p2 = 0, dsum = T(0), dlast = T(0);
+  int done = 0, b = 0, pb = -1, look = 0;
+  long t = 0;   // blocks processed (stage parity)
   double eps = 0.0;
-  const long total = (long)sweeps * nblk;
-  for (long t = 0; t < total; ++t) {
+  const bool want_eps = tol > 0.0;
+  while (done < sweeps) {
+    if (!chg_it[(t + 1) & 1]) {   // the previous step's slot
+      // the last block changed nothing: every residual is complete and nothing
+      // is pending, so blocks from b on that start with lambda~ = 0 and
+      // non-negative normal residuals stay unchanged; find the first one that
+      // does not (one warp per block)
+      int* nx = &nxt[look & 1];
+      for (int bb = b + wid; bb < nblk; bb += 32) {
+        const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
+        const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
+                                      lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
+        if (__ballot_sync(FULL, a) != 0u) {
+          if (lane == 0) atomicMin(nx, bb);
+          break;
+        }
+      }
+      __syncthreads();
+      const int nb_ = *nx;
+      if (tid == 0) nxt[(look + 1) & 1] = nblk;   // reset the other slot for the next look-ahead
+      ++look;
+      if (nb_ > b) {
+        for (int bb = b + tid; bb < nb_; bb += nthr) actb[bb >> 5] &= ~(1u << (bb & 31));
+        __syncthreads();
+      }
+      b = nb_;
+      if (b == nblk) {   // the rest of the sweep is unchanged: end of sweep
+        if (want_eps) {
+          T nrm = T(0);
+          for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
+          nrm = warp_sum(nrm);
+          if (lane == 0) red[wid] = nrm;
+          const T ds = wid == 0 ? warp_sum(dsum) : T(0);
+          __syncthreads();
+          if (tid == 0) {
+            T tot = T(0);
+            for (int k = 0; k < 32; ++k) tot += red[k];
+            red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
+          }
+          __syncthreads();
+          eps = (double)red[0];
+        }
+        const int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
+        if (wid == 0) {
+          dlast = dsum;
+          dsum = T(0);
+        }
+        if (tid == 0) chg_sweep[(done + 1) & 1] = 0;
+        ++done;
+        b = 0;
+        __syncthreads();
+        if (brk) break;
+        continue;
+      }
+    }
     const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0;
     const int bn = b + 1 == nblk ? 0 : b + 1;
     const int stg = (int)(t & 1);
     const int dc = stg;
-    const int pb = t > 0 ? (b == 0 ? nblk - 1 : b - 1) : -1;
     if (wid == 0) {
       const T* WDc = WD + stg * BR * BR;
       const T* WRc = WR + stg * BR * BR;
@@ -723,7 +782,7 @@ __global__ void __launch_bounds__(1024, 1)
         else
           actb[b >> 5] &= ~(1u << (b & 31));
       }
-      if (any && !pref[stg]) {
+      if (any && pref[stg] != b) {
         // rows not prefetched: warp 0 fetches them now
         T* D = WD + stg * BR * BR;
         T* Rr = WR + stg * BR * BR;
@@ -809,7 +868,11 @@ __global__ void __launch_bounds__(1024, 1)
         r[R0 + 3 * lane + 1] = q1;
         r[R0 + 3 * lane + 2] = q2;
       }
-      if (__any_sync(FULL, e0 != T(0) || e1 != T(0) || e2 != T(0)) && lane == 0) changed = 1;
+      const bool chg = __any_sync(FULL, e0 != T(0) || e1 != T(0) || e2 != T(0));
+      if (lane == 0) {
+        chg_it[t & 1] = chg ? 1 : 0;
+        if (chg) chg_sweep[done & 1] = 1;
+      }
       if (lane < BC) {                // lanes without a change write zeros
         dl[dc * BR + 3 * lane] = e0;
         dl[dc * BR + 3 * lane + 1] = e1;
@@ -818,7 +881,7 @@ __global__ void __launch_bounds__(1024, 1)
       if (bn == b) p0 = p1 = p2 = T(0);   // single block: the residual already has them
     } else {
       const int t2 = tid - 32, n2 = nthr - 32;
-      if (t + 1 < total) {
+      {
         // prefetch the next block's rows when it has a non-zero lambda~ or
         // changed in its last visit (data no streaming warp writes, so every
         // warp takes the same decision); a block that needs rows it did not
@@ -831,7 +894,7 @@ __global__ void __launch_bounds__(1024, 1)
           need = __ballot_sync(FULL, nz) != 0u;
         }
         if (need) prefetch(bn, 1 - stg, t2, n2);
-        if (t2 == 0) pref[1 - stg] = need ? 1 : 0;
+        if (t2 == 0) pref[1 - stg] = need ? bn : -1;
       }
       if (pb >= 0) {
         // fold the previous block's non-zero changes into every row but this
@@ -865,33 +928,53 @@ __global__ void __launch_bounds__(1024, 1)
       cp_async_wait_all();
     }
     __syncthreads();
+    pb = b;
+    ++t;
     if (bn == 0) {
-      // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i||  (Alg. 1)
-      T nrm = T(0);
-      for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
-      nrm = warp_sum(nrm);
-      if (lane == 0) red[wid] = nrm;
-      const T ds = wid == 0 ? warp_sum(dsum) : T(0);
-      __syncthreads();
-      if (tid == 0) {
-        T tot = T(0);
-        for (int k = 0; k < 32; ++k) tot += red[k];
-        const T e = tot > T(0) ? sqrt(ds / tot) : T(0);
-        red[0] = e;
-        // stop at eps <= tol, or after a sweep that changed nothing (a fixed
-        // point: every later sweep would repeat it exactly)
-        flag = (!changed || (tol > 0.0 && (double)e <= tol)) ? 1 : 0;
-        changed = 0;
+      // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i|| (Alg. 1),
+      // formed here only when a positive tol needs it
+      if (want_eps) {
+        T nrm = T(0);
+        for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
+        nrm = warp_sum(nrm);
+        if (lane == 0) red[wid] = nrm;
+        const T ds = wid == 0 ? warp_sum(dsum) : T(0);
+        __syncthreads();
+        if (tid == 0) {
+          T tot = T(0);
+          for (int k = 0; k < 32; ++k) tot += red[k];
+          red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
+        }
+        __syncthreads();
+        eps = (double)red[0];
       }
-      __syncthreads();
-      eps = (double)red[0];
-      dsum = T(0);
+      // stop at eps <= tol, or after a sweep that changed nothing (a fixed
+      // point: every later sweep would repeat it exactly)
+      const int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
+      if (wid == 0) {
+        dlast = dsum;
+        dsum = T(0);
+      }
+      if (tid == 0) chg_sweep[(done + 1) & 1] = 0;
       ++done;
-      const int brk = flag;
       __syncthreads();
       if (brk) break;
     }
     b = bn;
+  }
+  // eps of the last sweep, for the statistics
+  {
+    T nrm = T(0);
+    for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
+    nrm = warp_sum(nrm);
+    if (lane == 0) red[wid] = nrm;
+    const T ds = wid == 0 ? warp_sum(dlast) : T(0);
+    __syncthreads();
+    if (tid == 0) {
+      T tot = T(0);
+      for (int k = 0; k < 32; ++k) tot += red[k];
+      eps = tot > T(0) ? (double)sqrt(ds / tot) : 0.0;
+    }
   }
   for (int i = tid; i < n3; i += nthr) lam_g[i] = lam[i];
   if (tid == 0) {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libicr.so")
 OK, EINVAL, ENOTSPD, ESTATE, ENOMEM, ENOCONV, ETIMEOUT, ECUDA = range(8)
 FP32, FP64 = 0, 1
 FIELD = {"WH": 0, "W": 1, "LAMBDA": 2, "P": 3, "DELTA": 4, "C": 5, "MU": 6, "U": 7,
-         "REACH_PTR": 8, "REACH_IDX": 9, "DQ": 10}
+         "REACH_PTR": 8, "REACH_IDX": 9, "DQ": 10, "LAMBDA0": 11}
 _INT_FIELDS = {"REACH_PTR", "REACH_IDX"}
 
 # every symbol include/icr.h declares
