@@ -798,6 +798,7 @@ __global__ void __launch_bounds__(1024, 1)
         cp_async_commit();
         cp_async_wait_all();
         __syncwarp();
+        if (lane == 0) pref[stg] = b;
       }
       if (any && valid) {
         const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
@@ -894,7 +895,9 @@ __global__ void __launch_bounds__(1024, 1)
           need = __ballot_sync(FULL, nz) != 0u;
         }
         if (need) prefetch(bn, 1 - stg, t2, n2);
-        if (t2 == 0) pref[1 - stg] = need ? bn : -1;
+        // a stage not refilled keeps the rows it holds: a block that comes back
+        // to the same stage (the next sweep's first active block) reuses them
+        if (t2 == 0 && need) pref[1 - stg] = bn;
       }
       if (pb >= 0) {
         // fold the previous block's non-zero changes into every row but this
