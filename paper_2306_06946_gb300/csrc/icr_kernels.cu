@@ -609,6 +609,20 @@ __device__ __forceinline__ double rsqrt_t<double>(double x) {
 
 static constexpr int PGS_MAX_BLOCKS = 1024;   // contact blocks per scene (m <= 1024 BC)
 
+// acc[q] += w[q] * d for one 16-byte chunk of a W row (16-byte aligned)
+__device__ __forceinline__ void fma_chunk(float* acc, const float* w, float d) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(w));
+  acc[0] += v.x * d;
+  acc[1] += v.y * d;
+  acc[2] += v.z * d;
+  acc[3] += v.w * d;
+}
+__device__ __forceinline__ void fma_chunk(double* acc, const double* w, double d) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(w));
+  acc[0] += v.x * d;
+  acc[1] += v.y * d;
+}
+
 template <class T, int BC>
 __global__ void __launch_bounds__(1024, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
@@ -915,16 +929,30 @@ __global__ void __launch_bounds__(1024, 1)
         }
         __syncwarp();
         if (cnt > 0) {
-          for (int j = t2; j < n3; j += n2) {
-            if ((j >= R0 && j < R0 + 3 * nb) || (j >= pR0 && j < pR0 + pnr)) continue;
-            T acc = T(0);
-            const T* Wc = W + (int64_t)pR0 * ldw + j;
-#pragma unroll 8
-            for (int k = 0; k < cnt; ++k) {
-              const int i = lst[k];
-              acc += Wc[(int64_t)i * ldw] * dlp[i];
+          // rows in 16-byte chunks (block starts are multiples of the chunk, so a
+          // chunk is inside or outside a block; W's padding columns are zero)
+          const int nch = (n3 + CH - 1) / CH;
+          for (int c = t2; c < nch; c += n2) {
+            const int j0 = c * CH;
+            if ((j0 >= R0 && j0 < R0 + 3 * nb) || (j0 >= pR0 && j0 < pR0 + pnr)) continue;
+            T acc[CH];
+#pragma unroll
+            for (int q = 0; q < CH; ++q) acc[q] = T(0);
+            const T* Wc = W + (int64_t)pR0 * ldw + j0;
+            constexpr int UNR = sizeof(T) == 4 ? 8 : 4;   // loads in flight per group, within 64 registers
+            for (int k0 = 0; k0 < cnt; k0 += UNR) {
+              // a whole group is issued at once (predicated), so a short tail
+              // does not fall back to one load latency per row
+#pragma unroll
+              for (int u = 0; u < UNR; ++u)
+                if (k0 + u < cnt) {
+                  const int i = lst[k0 + u];
+                  fma_chunk(acc, Wc + (int64_t)i * ldw, dlp[i]);
+                }
             }
-            r[j] += acc;
+#pragma unroll
+            for (int q = 0; q < CH; ++q)
+              if (j0 + q < n3) r[j0 + q] += acc[q];
           }
         }
       }
