@@ -604,6 +604,9 @@ template <>
 __device__ __forceinline__ double rsqrt_t<double>(double x) {
   return 1.0 / sqrt(x);
 }
+// correctly rounded reciprocal (the value of 1 / x)
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
 
 
 
@@ -816,64 +819,59 @@ __global__ void __launch_bounds__(1024, 1)
       }
       if (any && valid) {
         const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
-        iWnn = T(1) / Wo[0];
+        iWnn = rcp_t(Wo[0]);
         Wt1n = Wo[BR];
         Wt2n = Wo[2 * BR];
-        iwt = T(1) / (T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
+        iwt = rcp_t(T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
         mua = mu[a0 + lane];
       }
-      // A contact with lambda~ = 0 and a non-negative normal residual is left
-      // unchanged by the local rule (lambda_n stays 0, so lambda_t is zeroed):
-      // the sweep visits contacts in order but jumps over such contacts, which
-      // gives exactly the iterate of visiting them.
-      int i = any ? -1 : nb;
-      while (i < nb) {
-        const unsigned act =
-            __ballot_sync(FULL, valid && lane > i && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0)));
+      // Every lane forms the update its own contact would take from its current
+      // residual (the local rule); the next contact in order whose update is
+      // not zero is applied and folded into every lane's residual.  The contacts
+      // passed over have zero updates (among them every contact with lambda~ = 0
+      // and a non-negative normal residual), so the iterate is exactly that of
+      // visiting them in order.
+      int i = -1;
+      while (any) {
+        // without branches: lanes past the block hold zeros and get zero updates
+        T ln = l0 - q0 * iWnn;
+        ln = ln > T(0) ? ln : T(0);
+        const T dn = ln - l0;
+        const T rt1 = q1 + Wt1n * dn, rt2 = q2 + Wt2n * dn;
+        T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
+        const T lim = mua * ln;
+        const T s2 = lt1 * lt1 + lt2 * lt2;
+        const bool out = s2 > lim * lim;            // outside the friction disc: project
+        const T sc = lim * rsqrt_t(out ? s2 : T(1));
+        lt1 = ln <= T(0) ? T(0) : (out ? lt1 * sc : lt1);
+        lt2 = ln <= T(0) ? T(0) : (out ? lt2 * sc : lt2);
+        const T c0 = ln - l0, c1 = lt1 - l1, c2 = lt2 - l2;
+        const unsigned act = __ballot_sync(FULL, valid && lane > i && (c0 != T(0) || c1 != T(0) || c2 != T(0)));
         if (act == 0u) break;
         i = __ffs(act) - 1;
-        T d0 = T(0), d1 = T(0), d2 = T(0);
+        // couplings W[3i+c, 3l+q] (this block) and W[3i+c, next block's 3l+q]
+        const T* Wl = WDc + (3 * i) * BR + 3 * ll;
+        const T* Xl = WRc + (3 * i) * BR + 3 * ll;
+        const T w00 = Wl[0], w01 = Wl[1], w02 = Wl[2], w10 = Wl[BR], w11 = Wl[BR + 1], w12 = Wl[BR + 2],
+                w20 = Wl[2 * BR], w21 = Wl[2 * BR + 1], w22 = Wl[2 * BR + 2];
+        const T x00 = Xl[0], x01 = Xl[1], x02 = Xl[2], x10 = Xl[BR], x11 = Xl[BR + 1], x12 = Xl[BR + 2],
+                x20 = Xl[2 * BR], x21 = Xl[2 * BR + 1], x22 = Xl[2 * BR + 2];
+        const T d0 = __shfl_sync(FULL, c0, i), d1 = __shfl_sync(FULL, c1, i), d2 = __shfl_sync(FULL, c2, i);
         if (lane == i) {
-          T ln = l0 - q0 * iWnn;
-          ln = ln > T(0) ? ln : T(0);
-          const T dn = ln - l0;
-          const T rt1 = q1 + Wt1n * dn, rt2 = q2 + Wt2n * dn;
-          T lt1 = l1 - rt1 * iwt, lt2 = l2 - rt2 * iwt;
-          const T lim = mua * ln;
-          const T s2 = lt1 * lt1 + lt2 * lt2;
-          if (ln <= T(0)) {
-            lt1 = T(0);
-            lt2 = T(0);
-          } else if (s2 > lim * lim) {
-            const T sc = lim * rsqrt_t(s2);
-            lt1 *= sc;
-            lt2 *= sc;
-          }
-          d0 = ln - l0;
-          d1 = lt1 - l1;
-          d2 = lt2 - l2;
-          e0 = d0;
-          e1 = d1;
-          e2 = d2;
           l0 = ln;
           l1 = lt1;
           l2 = lt2;
+          e0 = d0;
+          e1 = d1;
+          e2 = d2;
           dsum += d0 * d0 + d1 * d1 + d2 * d2;
         }
-        d0 = __shfl_sync(FULL, d0, i);
-        d1 = __shfl_sync(FULL, d1, i);
-        d2 = __shfl_sync(FULL, d2, i);
-        if (d0 != T(0) || d1 != T(0) || d2 != T(0)) {
-          // couplings W[3i+c, 3l+q] (this block) and W[3i+c, next block's 3l+q]
-          const T* Wl = WDc + (3 * i) * BR + 3 * ll;
-          q0 += Wl[0] * d0 + Wl[BR] * d1 + Wl[2 * BR] * d2;
-          q1 += Wl[1] * d0 + Wl[BR + 1] * d1 + Wl[2 * BR + 1] * d2;
-          q2 += Wl[2] * d0 + Wl[BR + 2] * d1 + Wl[2 * BR + 2] * d2;
-          const T* Xl = WRc + (3 * i) * BR + 3 * ll;
-          p0 += Xl[0] * d0 + Xl[BR] * d1 + Xl[2 * BR] * d2;
-          p1 += Xl[1] * d0 + Xl[BR + 1] * d1 + Xl[2 * BR + 1] * d2;
-          p2 += Xl[2] * d0 + Xl[BR + 2] * d1 + Xl[2 * BR + 2] * d2;
-        }
+        q0 += w00 * d0 + w10 * d1 + w20 * d2;
+        q1 += w01 * d0 + w11 * d1 + w21 * d2;
+        q2 += w02 * d0 + w12 * d1 + w22 * d2;
+        p0 += x00 * d0 + x10 * d1 + x20 * d2;
+        p1 += x01 * d0 + x11 * d1 + x21 * d2;
+        p2 += x02 * d0 + x12 * d1 + x22 * d2;
       }
       if (valid) {
         lam[R0 + 3 * lane] = l0;
