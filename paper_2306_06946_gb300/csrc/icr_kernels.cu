@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(1024, 1)
       if (tid == 0) nxt[(look + 1) & 1] = nblk;   // reset the other slot for the next look-ahead
       ++look;
       if (nb_ > b) {
-        for (int bb = b + tid; bb < nb_; bb += nthr) actb[bb >> 5] &= ~(1u << (bb & 31));
+        for (int bb = b + tid; bb < nb_; bb += nthr) atomicAnd(&actb[bb >> 5], ~(1u << (bb & 31)));
         __syncthreads();
       }
       b = nb_;
