@@ -390,18 +390,15 @@ def run_icr(args):
                + h_tool.nbytes)
         d2h = h_dq.nbytes
 
+        # each step: the step's inputs from pinned host buffers, the captured
+        # step graph (it reads the scene's buffers), the corrective motion back
         def e2e_step():
             sc.set_mapping(h_nodes, h_bary)
             sc.set_proximity(h_p0)
             sc.set_obstacle_spheres(h_spheres, h_tool, h_anch)
             sc.set_field("MU", h_mu)
-            sc.build_WH()
-            for k in range(scene.n_newton):
-                sc.linearize(k)
-                sc.update_W()
-                sc.solve_friction(warm_start=False)
-                sc.update_proximity()
-            sc.correct_motion(want_dq=True, reset=True, out=h_dq)
+            sc.step_launch()
+            sc.get("DQ", out=h_dq)
 
         for _ in range(2):
             e2e_step()

@@ -235,8 +235,10 @@ int icr_step(icr_scene* scene, int32_t n_newton);
 /* Capture icr_step(scene, n_newton) into a CUDA graph owned by the scene (one
  * plain step runs first so that every kernel is set up; icr_autotune runs
  * first when the scene is not tuned).  The context's stream must not be the
- * legacy default stream (ICR_EINVAL).  A later icr_set_mapping invalidates the
- * graph. */
+ * legacy default stream (ICR_EINVAL).  The graph reads the scene's device
+ * buffers, so new inputs of the same shape (icr_set_mapping with the same
+ * contact count, icr_set_proximity, the obstacle, icr_set_field) are stepped
+ * by launching it again. */
 int icr_step_capture(icr_scene* scene, int32_t n_newton);
 /* Autotuner of the forward solve X = L^-1 H^T (the multi-RHS supernodal solve
  * of Eq. "schur complemnt reformulated").  For every elimination-tree level it
@@ -251,7 +253,10 @@ int icr_step_capture(icr_scene* scene, int32_t n_newton);
  * the tensor cores; icr_set_mapping and a change of contraction mode mark the
  * scene untuned. */
 int icr_autotune(icr_scene* scene, int32_t* tc_levels);
-/* Launch the captured step on the context's stream (ICR_ESTATE without one). */
+/* Launch the captured step on the context's stream.  ICR_ESTATE without a
+ * captured step, without a mapping and an obstacle, or when the graph is stale:
+ * a buffer was reallocated, or the contact count, the obstacle kind or the
+ * parameters differ from the capture (capture again). */
 int icr_step_launch(icr_scene* scene);
 /* Wait until the context's stream has finished the scene's work. */
 int icr_sync(icr_scene* scene);

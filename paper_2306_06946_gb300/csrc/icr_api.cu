@@ -57,6 +57,7 @@ int dalloc(Scene* s, DBuf& b, size_t bytes) {
   }
   b.bytes = bytes;
   c->in_use += bytes;
+  ++s->alloc_epoch;
   return ICR_OK;
 }
 
@@ -212,6 +213,24 @@ static void compute_G(int ns, const std::vector<int32_t>& sp, const std::vector<
 }
 
 namespace icr {
+int check_step_graph(Scene* s, const char* where) {
+  if (!s->step_graph) {
+    set_error("%s: no captured step (icr_step_capture)", where);
+    return ICR_ESTATE;
+  }
+  if (!s->has_mapping || s->obst_kind == 0) {
+    set_error("%s: the step needs a mapping and an obstacle", where);
+    return ICR_ESTATE;
+  }
+  if (s->graph_epoch != s->alloc_epoch || s->graph_m != s->m || s->graph_obst != s->obst_kind ||
+      std::memcmp(&s->graph_params, &s->params, sizeof(icr_params)) != 0) {
+    set_error("%s: the captured step is stale (buffers, contact count, obstacle or parameters changed); "
+              "capture it again", where);
+    return ICR_ESTATE;
+  }
+  return ICR_OK;
+}
+
 int check_device_error(Scene* s) {
   if (!s->dev_err.p) return ICR_OK;
   int h = 0;
@@ -705,10 +724,6 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
   s->obst_kind = 0;
   s->tuned = false;
-  if (s->step_graph) {
-    cudaGraphExecDestroy(s->step_graph);
-    s->step_graph = nullptr;
-  }
   return ICR_OK;
 }
 
@@ -1163,6 +1178,11 @@ int icr_step_capture(icr_scene* s, int32_t n_newton) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  s->graph_epoch = s->alloc_epoch;
+  s->graph_m = s->m;
+  s->graph_obst = s->obst_kind;
+  s->graph_newton = n_newton;
+  s->graph_params = s->params;
   const cudaError_t e2 = cudaGraphInstantiate(&s->step_graph, g, 0);
   cudaGraphDestroy(g);
   if (e2 != cudaSuccess) {
@@ -1174,10 +1194,7 @@ int icr_step_capture(icr_scene* s, int32_t n_newton) {
 
 int icr_step_launch(icr_scene* s) {
   RET(check_scene(s));
-  if (!s->step_graph) {
-    set_error("step_launch: no captured step (icr_step_capture)");
-    return ICR_ESTATE;
-  }
+  RET(check_step_graph(s, "step_launch"));
   RET(set_device(s));
   CK(cudaGraphLaunch(s->step_graph, s->ctx->stream));
   s->launches += s->graph_kernels;

@@ -98,6 +98,12 @@ struct Scene {
   uint64_t launches = 0;   // kernels launched by this scene
   cudaGraphExec_t step_graph = nullptr;   // captured icr_step
   uint64_t graph_kernels = 0;             // kernels in the captured step
+  // the graph holds device addresses and launch shapes: it stays valid while no
+  // buffer has been reallocated (alloc_epoch), and the contact count, obstacle
+  // kind, parameters and Newton count are those it was captured with
+  uint64_t alloc_epoch = 0, graph_epoch = 0;
+  int graph_m = -1, graph_obst = -1, graph_newton = -1;
+  icr_params graph_params{};
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
 
   // ---- obstacle (device linearisation)
@@ -129,6 +135,7 @@ int launch_linearize(Scene* s, int k);
 int launch_contract_tc(Scene* s, int mode);
 int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks);
 int launch_front_gemm_tc(Scene* s, int level);
+int check_step_graph(Scene* s, const char* where);
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);
 

@@ -54,10 +54,12 @@ extern "C" int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32
   }
   int device = -1;
   for (int i = 0; i < n_scenes; ++i) {
-    if (!scenes[i] || !scenes[i]->step_graph) {
-      set_error("serve: scene %d has no captured step (icr_step_capture)", i);
-      return ICR_ESTATE;
+    if (!scenes[i]) {
+      set_error("serve: scene %d is NULL", i);
+      return ICR_EINVAL;
     }
+    const int rc = check_step_graph(scenes[i], "serve");
+    if (rc != ICR_OK) return rc;
     if (device < 0) device = scenes[i]->ctx->device;
     if (scenes[i]->ctx->device != device) {
       set_error("serve: all scenes must live on one device");

@@ -321,10 +321,17 @@ class Scene:
         _check(lib().icr_field_bytes(self.h, FIELD[field], ct.byref(v)))
         return int(v.value)
 
-    def get(self, field: str) -> np.ndarray:
+    def get(self, field: str, out: np.ndarray | None = None) -> np.ndarray:
+        """Copy a field to the host (into ``out`` when given: a contiguous
+        array of the field's dtype and size, e.g. pinned memory)."""
         nb = self.field_bytes(field)
         dt = np.int32 if field in _INT_FIELDS else np.float64
-        a = np.empty(nb // np.dtype(dt).itemsize, dtype=dt)
+        if out is None:
+            a = np.empty(nb // np.dtype(dt).itemsize, dtype=dt)
+        else:
+            a = out
+            if a.dtype != dt or a.nbytes != nb or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"out must be a contiguous {np.dtype(dt).name} array of {nb} bytes")
         _check(lib().icr_get(self.h, FIELD[field], _ptr(a), nb))
         if field in ("WH", "W"):
             a = a.reshape(3 * self.m, 3 * self.m)

@@ -205,3 +205,52 @@ def test_two_sphere_obstacle_errors(batch, torch_mod):
     import ctypes as ct
     sc.params.warm_start = 2
     assert icr.lib().icr_set_params(sc.h, ct.byref(sc.params)) == icr.EINVAL
+
+
+def test_captured_step_follows_new_inputs_and_detects_stale_graphs(batch, torch_mod):
+    """A captured step reads the scene's buffers: loading the same-shape inputs
+    again and relaunching reproduces the step; a different contact count makes
+    the graph stale (ICR_ESTATE) until it is captured again."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    s, s2 = batch[0], batch[1]
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    sc = icr.Scene(ctx, precision=icr.FP32, n_sweeps=s.n_sweeps)
+    driver.load_system(sc, s.factor)
+
+    def load(x):
+        driver.load_contacts(sc, x.nodes, x.bary, x.p0)
+        driver.load_obstacle(sc, x.obstacle)
+        sc.set_field("MU", x.mu)
+
+    load(s)
+    sc.step_capture(s.n_newton)
+    sc.sync()
+    first = sc.get("DQ")
+    load(s)                      # same inputs again, same shape: the graph is still valid
+    sc.step_launch()
+    sc.sync()
+    assert rel(sc.get("DQ"), first) < 1e-5
+    sub = scenegen_subset(s, max(1, s.m // 2))
+    load(sub)                    # fewer contacts: stale
+    with pytest.raises(icr.IcrError) as e:
+        sc.step_launch()
+    assert e.value.code == icr.ESTATE
+    sc.step_capture(sub.n_newton)
+    sc.sync()
+    assert np.all(np.isfinite(sc.get("DQ")))
+
+
+def scenegen_subset(s, m):
+    """The first m contacts of a scene (same system and obstacle kind)."""
+    import copy
+    t = copy.copy(s)
+    t.nodes, t.bary, t.p0, t.mu = s.nodes[:m], s.bary[:m], s.p0[:m], s.mu[:m]
+    ob = copy.copy(s.obstacle)
+    ob.anchors = s.obstacle.anchors[:m]
+    if ob.kind == "sphere":
+        ob.tool = s.obstacle.tool[:m]
+    else:
+        ob.normals = s.obstacle.normals[:, :m]
+    t.obstacle = ob
+    return t
