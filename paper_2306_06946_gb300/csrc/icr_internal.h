@@ -136,6 +136,46 @@ int launch_contract_tc(Scene* s, int mode);
 int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks);
 int launch_front_gemm_tc(Scene* s, int level);
 int check_step_graph(Scene* s, const char* where);
+
+// Kernel launches of the time step use programmatic dependent launch outside
+// graph capture: a kernel's CTAs may be scheduled while the previous kernel on
+// the stream finishes.  Every library kernel therefore starts with pdl_entry():
+// griddepcontrol.wait returns once the preceding kernels have completed and
+// their writes are visible, and launch_dependents lets the next kernel be
+// scheduled early.  Without a programmatic dependency both return at once.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <class... KArgs, class... Args>
+cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  // inside a captured graph the nodes are already launched back to back, and
+  // programmatic edges measured slower there: plain edges when capturing
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+// launch through pdl_launch, check it and count it in the scene `s` in scope
+#define PDL(where, ...)                                \
+  do {                                                 \
+    const cudaError_t e_ = pdl_launch(__VA_ARGS__);    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    ++s->launches;                                     \
+  } while (0)
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);
 

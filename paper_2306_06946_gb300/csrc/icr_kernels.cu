@@ -75,6 +75,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // first supernode already marked for its contact: whoever marked it walks on.
 __global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
                              const int* __restrict__ parent, int ns, uint32_t* bitmap, int words) {
+  pdl_entry();
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 4 * m) return;
   int a = t >> 2;
@@ -92,6 +93,7 @@ __global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __
 // list the contacts in ascending order.
 __global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
                              int* qidx) {
+  pdl_entry();
   extern __shared__ int sh[];
   int s = blockIdx.x;
   int w = threadIdx.x;
@@ -120,6 +122,7 @@ __global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int
 __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
                                   int m, const int* __restrict__ parent, const int* __restrict__ qcount,
                                   const int* __restrict__ qidx, int* qpos) {
+  pdl_entry();
   int s = blockIdx.y;
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= qcount[s]) return;
@@ -137,6 +140,7 @@ __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int
 // contact of its parent's list (-1 when the contact does not reach c).
 __global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __restrict__ qcount,
                             const int* __restrict__ qpos, int* qinv) {
+  pdl_entry();
   const int c = blockIdx.x;
   const int p = parent[c];
   if (p < 0) return;
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(1024)
     k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
            const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
            int tc_gemm, const unsigned char* __restrict__ tc_super, int ncounters, int* plan) {
+  pdl_entry();
   __shared__ int wsum[PLAN_LISTS][32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int per = cdiv(ns, blockDim.x);
@@ -279,6 +284,7 @@ __global__ void __launch_bounds__(AR * TCOLS)
                const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
                const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
                const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
+  pdl_entry();
   const int u1 = plan[pb];
   for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {
     const int pos = find_pos(plan, pa, pb, u);
@@ -420,6 +426,7 @@ __global__ void __launch_bounds__(256)
                  const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                  const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
                  const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sG = (T*)smraw;                 // 2 x KB x GLD
   T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
@@ -447,6 +454,7 @@ template <class T>
 __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                         const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                         const double* __restrict__ dinvsqrt, T* X, int64_t ldx) {
+  pdl_entry();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -470,6 +478,7 @@ __global__ void __launch_bounds__(256)
                const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
                const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
                const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
+  pdl_entry();
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
   __shared__ int unit_sh;
@@ -541,6 +550,7 @@ __global__ void __launch_bounds__(256)
 
 template <class T>
 __global__ void k_symmetrize(int nr, T* A) {
+  pdl_entry();
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
   if (j < i) A[(int64_t)i * nr + j] = A[(int64_t)j * nr + i];
@@ -549,6 +559,7 @@ __global__ void k_symmetrize(int nr, T* A) {
 // ------------------------------------------------------------------ a6 W = C W_H C^T
 template <class T>
 __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw) {
+  pdl_entry();
   const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
   if (a >= m || b >= m || a > b) return;
   const int64_t ld = 3 * (int64_t)m;
@@ -630,6 +641,7 @@ template <class T, int BC>
 __global__ void __launch_bounds__(1024, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
           const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
+  pdl_entry();
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
   constexpr int RCH = BR / CH;                 // 16-byte copies per block row
@@ -1026,6 +1038,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 template <class T>
 __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
                                const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
+  pdl_entry();
   const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= m) return;
@@ -1063,6 +1076,7 @@ __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, cons
 // ------------------------------------------------------------------ a8 proximity update
 template <class T>
 __global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u) {
+  pdl_entry();
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const T l0 = lam[3 * a], l1 = lam[3 * a + 1], l2 = lam[3 * a + 2];
@@ -1076,6 +1090,7 @@ __global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ l
 
 template <class T>
 __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp) {
+  pdl_entry();
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= 3 * m) return;
@@ -1092,6 +1107,7 @@ __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ 
 // ------------------------------------------------------------------ a9 corrective motion
 template <class T>
 __global__ void k_cast_u(int n, const double* __restrict__ u, T* ut) {
+  pdl_entry();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) ut[i] = (T)u[i];
 }
@@ -1103,6 +1119,7 @@ __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __rest
                      const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                      const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
                      const T* __restrict__ ut, const double* __restrict__ dinvsqrt, T* y) {
+  pdl_entry();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -1123,6 +1140,7 @@ __global__ void __launch_bounds__(256)
     k_bsolve(const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
              const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
              const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const T* __restrict__ y, T* dq) {
+  pdl_entry();
   const int s = level_list[lvl_first + blockIdx.x / nchunk];
   const int k = (blockIdx.x % nchunk) * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -1144,6 +1162,7 @@ template <class T>
 __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
                             const double* __restrict__ anchors, const double* __restrict__ spheres,
                             const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta) {
+  pdl_entry();
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
@@ -1202,20 +1221,19 @@ static int build_WH_T(Scene* s) {
   if (m == 0) return ICR_OK;
   cudaError_t e = cudaMemsetAsync(s->bitmap.p, 0, (size_t)ns * words * sizeof(uint32_t), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset bitmap");
-  k_reach_mark<<<(4 * m + 255) / 256, 256, 0, st>>>((const int*)s->nodes.p, m, (const int*)s->node_super.p,
+  PDL("k_reach_mark", k_reach_mark, (4 * m + 255) / 256, 256, 0, st,
+      (const int*)s->nodes.p, m, (const int*)s->node_super.p,
                                                      (const int*)s->parent.p, ns, (uint32_t*)s->bitmap.p, words);
-  LAUNCH_OK("k_reach_mark");
   const int bt = ((words + 31) / 32) * 32;
-  k_reach_rows<<<ns, bt, bt * sizeof(int), st>>>((const uint32_t*)s->bitmap.p, words, m, (int*)s->wprefix.p,
+  PDL("k_reach_rows", k_reach_rows, ns, bt, bt * sizeof(int), st,
+      (const uint32_t*)s->bitmap.p, words, m, (int*)s->wprefix.p,
                                                   (int*)s->qcount.p, (int*)s->qidx.p);
-  LAUNCH_OK("k_reach_rows");
-  k_reach_parentpos<<<dim3((m + 255) / 256, ns), 256, 0, st>>>(
+  PDL("k_reach_parentpos", k_reach_parentpos, dim3((m + 255) / 256, ns), 256, 0, st,
       (const uint32_t*)s->bitmap.p, (const int*)s->wprefix.p, words, m, (const int*)s->parent.p,
       (const int*)s->qcount.p, (const int*)s->qidx.p, (int*)s->qpos.p);
-  LAUNCH_OK("k_reach_parentpos");
-  k_reach_inv<<<ns, 256, 0, st>>>(m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
+  PDL("k_reach_inv", k_reach_inv, ns, 256, 0, st,
+      m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
                                   (int*)s->qinv.p);
-  LAUNCH_OK("k_reach_inv");
   static bool gemm_attr = false;
   static int gemm_occ = 1;
   if (!gemm_attr) {
@@ -1238,10 +1256,10 @@ static int build_WH_T(Scene* s) {
   const int tc_gemm = mode != ICR_CONTRACT_SIMT ? 1 : 0;
   int* plan = (int*)s->plan.p;
   const int nlev = (int)s->levels.size();
-  k_plan<<<1, 1024, 0, st>>>(ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+  PDL("k_plan", k_plan, 1, 1024, 0, st,
+      ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
                              (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, tc_gemm,
                              (const unsigned char*)s->tc_super.p, 2 + nlev, plan);
-  LAUNCH_OK("k_plan");
   const int nsm = s->ctx->sm_count;
   const int ntiles = (m + TCC - 1) / TCC;
   for (int li = 0; li < nlev; ++li) {
@@ -1252,18 +1270,16 @@ static int build_WH_T(Scene* s) {
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
     }
     const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + AR - 1) / AR) * ntiles;
-    k_assemble<T><<<(unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st>>>(
+    PDL("k_assemble", k_assemble<T>, (unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st,
         plan + PLAN_ASM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
         (const int*)s->ctr_child.p, (const int*)s->ctr_row.p, (const int*)s->nodes.p, (const T*)s->bary.p,
         (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qinv.p, m, X, (T*)s->Ftop.p, ldx);
-    LAUNCH_OK("k_assemble");
     const int64_t ub_g = (int64_t)lv.count * ((lv.wmax + lv.rmax + GR - 1) / GR) * ntiles;
-    k_front_gemm<T><<<(unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st>>>(
+    PDL("k_front_gemm", k_front_gemm<T>, (unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st,
         plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
         (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
-    LAUNCH_OK("k_front_gemm");
     if (tc_gemm && s->tc_level[li] && lv.wmax >= TC_GEMM_MIN_W) {
       const int rc = launch_front_gemm_tc(s, li);
       if (rc != ICR_OK) return rc;
@@ -1273,28 +1289,27 @@ static int build_WH_T(Scene* s) {
     e = cudaEventRecord(s->level_events[nlev], st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
   }
-  k_scale<T><<<(s->n + 7) / 8, 256, 0, st>>>(s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
+  PDL("k_scale", k_scale<T>, (s->n + 7) / 8, 256, 0, st,
+      s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                              (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
                                              (const double*)s->dinvsqrt.p, X, ldx);
-  LAUNCH_OK("k_scale");
   const int64_t nr = 3 * (int64_t)m;
   e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
   if (e != cudaSuccess) return cuda_fail(e, "memset WH");
   {
     const int64_t ntc = (nr + CT - 1) / CT;
     const int64_t ub = (int64_t)ns * (ntc * (ntc + 1) / 2);
-    k_contract<T><<<(unsigned)std::min<int64_t>(ub, 4 * nsm), 256, 0, st>>>(
+    PDL("k_contract", k_contract<T>, (unsigned)std::min<int64_t>(ub, 4 * nsm), 256, 0, st,
         plan + PLAN_SIMT * (ns + 1), plan + PLAN_LISTS * (ns + 1), ns, (const int*)s->level_list.p,
         (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, m,
         X, ldx, (T*)s->WH.p, nr);
-    LAUNCH_OK("k_contract");
   }
   if (mode != ICR_CONTRACT_SIMT) {
     const int rc = launch_contract_tc(s, mode);
     if (rc != ICR_OK) return rc;
   }
-  k_symmetrize<T><<<dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st>>>((int)nr, (T*)s->WH.p);
-  LAUNCH_OK("k_symmetrize");
+  PDL("k_symmetrize", k_symmetrize<T>, dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st,
+      (int)nr, (T*)s->WH.p);
   return ICR_OK;
 }
 
@@ -1305,8 +1320,8 @@ static int update_W_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   dim3 grid((m + 15) / 16, (m + 15) / 16);
-  k_update_W<T><<<grid, dim3(16, 16), 0, s->ctx->stream>>>(m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw);
-  LAUNCH_OK("k_update_W");
+  PDL("k_update_W", k_update_W<T>, grid, dim3(16, 16), 0, s->ctx->stream,
+      m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw);
   return ICR_OK;
 }
 
@@ -1332,14 +1347,14 @@ static int pgs_T(Scene* s, int warm, int want_res) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
     attr_bytes = smem;
   }
-  k_pgs<T, BC><<<1, 1024, smem, st>>>(m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
+  PDL("k_pgs", k_pgs<T, BC>, 1, 1024, smem, st,
+      m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
                                       (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
-  LAUNCH_OK("k_pgs");
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
-    k_pgs_residual<T><<<(m + 7) / 8, 256, 0, st>>>(m, (const T*)s->W.p, s->ldw, (const T*)s->delta.p, (const T*)s->mu.p,
+    PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,
+        m, (const T*)s->W.p, s->ldw, (const T*)s->delta.p, (const T*)s->mu.p,
                                                    (const T*)s->lam.p, rel, ds);
-    LAUNCH_OK("k_pgs_residual");
   }
   return ICR_OK;
 }
@@ -1354,11 +1369,11 @@ static int prox_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   double* u = (double*)s->u.p;
-  k_prox_u<T><<<(m + 127) / 128, 128, 0, st>>>(m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u);
-  LAUNCH_OK("k_prox_u");
-  k_prox_p<T><<<(3 * m + 7) / 8, 256, 0, st>>>(m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p,
+  PDL("k_prox_u", k_prox_u<T>, (m + 127) / 128, 128, 0, st,
+      m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u);
+  PDL("k_prox_p", k_prox_p<T>, (3 * m + 7) / 8, 256, 0, st,
+      m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p,
                                                u + 3 * (size_t)m);
-  LAUNCH_OK("k_prox_p");
   return ICR_OK;
 }
 
@@ -1373,21 +1388,21 @@ static int correct_T(Scene* s) {
     if (e != cudaSuccess) return cuda_fail(e, "memset dq");
     return ICR_OK;
   }
-  k_cast_u<T><<<(3 * m + 255) / 256, 256, 0, st>>>(3 * m, (const double*)s->u.p, (T*)s->ut.p);
-  LAUNCH_OK("k_cast_u");
-  k_xu<T><<<(n + 7) / 8, 256, 0, st>>>(n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
+  PDL("k_cast_u", k_cast_u<T>, (3 * m + 255) / 256, 256, 0, st,
+      3 * m, (const double*)s->u.p, (T*)s->ut.p);
+  PDL("k_xu", k_xu<T>, (n + 7) / 8, 256, 0, st,
+      n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
                                        m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinvsqrt.p,
                                        (T*)s->y.p);
-  LAUNCH_OK("k_xu");
   for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
     const Level& lv = s->levels[l];
     const int nchunk = (lv.wmax + 7) / 8;
-    k_bsolve<T><<<lv.count * nchunk, 256, 0, st>>>((const int*)s->level_list.p, lv.first, nchunk,
+    PDL("k_bsolve", k_bsolve<T>, lv.count * nchunk, 256, 0, st,
+        (const int*)s->level_list.p, lv.first, nchunk,
                                                    (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
                                                    (const int*)s->rowpat.p, (const int64_t*)s->val_ptr.p,
                                                    (const T*)s->G.p, (const T*)s->y.p, (T*)s->dq.p);
-    LAUNCH_OK("k_bsolve");
   }
   return ICR_OK;
 }
@@ -1399,10 +1414,9 @@ static int linearize_T(Scene* s, int k) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   const double* nk = s->obst_kind == 1 ? (const double*)s->obst_normals.p + (size_t)k * m * 3 : nullptr;
-  k_linearize<T><<<(m + 127) / 128, 128, 0, s->ctx->stream>>>(
+  PDL("k_linearize", k_linearize<T>, (m + 127) / 128, 128, 0, s->ctx->stream,
       m, s->obst_kind, nk, (const double*)s->obst_anchors.p, (const double*)s->obst_spheres.p,
       (const int*)s->obst_of.p, (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p);
-  LAUNCH_OK("k_linearize");
   return ICR_OK;
 }
 

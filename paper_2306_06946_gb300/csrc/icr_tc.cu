@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(256)
               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
               const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
               int from_ftop, int64_t ldx, unsigned char* pk) {
+  pdl_entry();
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
   const int u1 = plan[pb];
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(256)
     k_pack_g(const int* __restrict__ blocks, int nblocks, const int* __restrict__ super_ptr,
              const int64_t* __restrict__ rowpat_ptr, const int64_t* __restrict__ val_ptr,
              const int64_t* __restrict__ goff, const float* __restrict__ G, unsigned char* pk) {
+  pdl_entry();
   __shared__ float sy[KT][TM + 1];
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
     const int s = blocks[3 * b], rt = blocks[3 * b + 1], kt = blocks[3 * b + 2];
@@ -412,6 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
                   int64_t ldw, int* dev_err) {
+  pdl_entry();
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block)
@@ -485,6 +488,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
                     const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
                     int* dev_err) {
+  pdl_entry();
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -580,22 +584,15 @@ int contract_tc_T(Scene* s) {
   const int nsm = s->ctx->sm_count;
   const int tmax = s->tc_tmax;
   const int64_t ub_pack = (int64_t)ns * tmax * ((s->wmax + KT - 1) / KT);
-  k_pack_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream>>>(
+  PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_PACK * (ns + 1), 0, ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p, 0,
       s->ldx, (unsigned char*)s->Ypk.p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc");
-  ++s->launches;
   const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2;
-  k_contract_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem,
-                        s->ctx->stream>>>(
+  PDL("k_contract_tc", k_contract_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_TC, ns, (const int*)s->level_list.p,
       (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
       (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "k_contract_tc");
-  ++s->launches;
   return ICR_OK;
 }
 
@@ -635,23 +632,17 @@ int launch_front_gemm_tc(Scene* s, int level) {
   const int nsm = s->ctx->sm_count;
   const int tmax = s->tc_tmax;
   const int64_t ub_pack = (int64_t)lv.count * tmax * ((lv.wmax + KT - 1) / KT);
-  k_pack_tc<MODE><<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream>>>(
+  PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_FPACK * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->Ftop.p, 1,
       s->ldx, (unsigned char*)s->Ypk.p);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "k_pack_tc(F_top)");
-  ++s->launches;
   const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax;
-  k_front_gemm_tc<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream>>>(
+  PDL("k_front_gemm_tc", k_front_gemm_tc, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_GTC * (ns + 1), pa, pb, plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_GTC + level,
       (const int*)s->level_list.p, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->gpk_off.p,
       (const unsigned char*)s->Gpk.p, (const int64_t*)s->tc_boff.p, (const unsigned char*)s->Ypk.p, (float*)s->X.p,
       s->ldx, (int*)s->dev_err.p);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "k_front_gemm_tc");
-  ++s->launches;
   return ICR_OK;
 }
 
