@@ -637,6 +637,16 @@ __device__ __forceinline__ void fma_chunk(double* acc, const double* w, double d
   acc[1] += v.y * d;
 }
 
+// clears bits [lo, hi) of a bit array, one atomic per 32-bit word
+__device__ __forceinline__ void clear_bits(unsigned* bits, int lo, int hi, int tid, int nthr) {
+  for (int w = (lo >> 5) + tid; w <= ((hi - 1) >> 5) && lo < hi; w += nthr) {
+    const int a = max(lo, w << 5) - (w << 5), e = min(hi, (w + 1) << 5) - (w << 5);   // bits [a, e) of word w
+    const unsigned msk = (e - a == 32) ? ~0u : (((1u << (e - a)) - 1u) << a);
+    atomicAnd(&bits[w], ~msk);
+  }
+}
+
+
 template <class T, int BC>
 __global__ void __launch_bounds__(1024, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
@@ -660,7 +670,9 @@ __global__ void __launch_bounds__(1024, 1)
   __shared__ int pref[2];            // block whose rows stage k holds (-1: none)
   __shared__ int chg_sweep[2];       // some lambda~ changed in sweep (done & 1)
   __shared__ int chg_it[2];          // block processed at step t changed some lambda~ (slot t & 1)
-  __shared__ int nxt[2];             // look-ahead result (two slots, alternating)
+  __shared__ int nxt[2][2];          // look-ahead results (two slots, alternating): from b on, from 0
+  __shared__ T cst[2][5][BC];        // per-contact local-rule constants of the block in stage k
+  __shared__ int cst_blk[2];         // block whose constants cst[k] holds (-1: none)
   __shared__ unsigned actb[PGS_MAX_BLOCKS / 32];   // block had a changing contact in its last visit
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
@@ -688,7 +700,8 @@ __global__ void __launch_bounds__(1024, 1)
     pref[1] = -1;
     chg_sweep[0] = chg_sweep[1] = 0;
     chg_it[0] = chg_it[1] = 1;   // no look-ahead before the first block
-    nxt[0] = nxt[1] = nblk;
+    nxt[0][0] = nxt[0][1] = nxt[1][0] = nxt[1][1] = nblk;
+    cst_blk[0] = cst_blk[1] = -1;
   }
   __syncthreads();
   if (warm) {
@@ -723,33 +736,33 @@ __global__ void __launch_bounds__(1024, 1)
   // the pending changes (p) of contact l of the next block
   T p0 = 0, p1 = 0, p2 = 0, dsum = T(0), dlast = T(0);
   int done = 0, b = 0, pb = -1, look = 0;
+  bool known = false;   // b was found by a look-ahead: no second look needed
   long t = 0;   // blocks processed (stage parity)
   double eps = 0.0;
   const bool want_eps = tol > 0.0;
   while (done < sweeps) {
-    if (!chg_it[(t + 1) & 1]) {   // the previous step's slot
+    if (!known && !chg_it[(t + 1) & 1]) {   // the previous step's slot
       // the last block changed nothing: every residual is complete and nothing
-      // is pending, so blocks from b on that start with lambda~ = 0 and
-      // non-negative normal residuals stay unchanged; find the first one that
-      // does not (one warp per block)
-      int* nx = &nxt[look & 1];
-      for (int bb = b + wid; bb < nblk; bb += 32) {
+      // is pending, so blocks that hold lambda~ = 0 and non-negative normal
+      // residuals stay unchanged.  One warp per block finds the first other
+      // block from b on, and the first from 0 on (the next sweep's start when
+      // this sweep has none left).
+      int* nx = nxt[look & 1];
+      for (int bb = wid; bb < nblk; bb += 32) {
         const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
         const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
                                       lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
-        if (__ballot_sync(FULL, a) != 0u) {
-          if (lane == 0) atomicMin(nx, bb);
-          break;
+        if (__ballot_sync(FULL, a) != 0u && lane == 0) {
+          if (bb >= b) atomicMin(&nx[0], bb);
+          atomicMin(&nx[1], bb);
         }
       }
       __syncthreads();
-      const int nb_ = *nx;
-      if (tid == 0) nxt[(look + 1) & 1] = nblk;   // reset the other slot for the next look-ahead
+      const int nb_ = nx[0], nw_ = nx[1];
+      if (tid == 0) nxt[(look + 1) & 1][0] = nxt[(look + 1) & 1][1] = nblk;   // the other slot, for the next look-ahead
       ++look;
-      if (nb_ > b) {
-        for (int bb = b + tid; bb < nb_; bb += nthr) atomicAnd(&actb[bb >> 5], ~(1u << (bb & 31)));
-        __syncthreads();
-      }
+      // blocks passed over hold no active contact (a prefetch hint, no barrier needed)
+      clear_bits(actb, b, nb_, tid, nthr);
       b = nb_;
       if (b == nblk) {   // the rest of the sweep is unchanged: end of sweep
         if (want_eps) {
@@ -767,19 +780,31 @@ __global__ void __launch_bounds__(1024, 1)
           __syncthreads();
           eps = (double)red[0];
         }
-        const int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
+        int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
         if (wid == 0) {
           dlast = dsum;
           dsum = T(0);
         }
         if (tid == 0) chg_sweep[(done + 1) & 1] = 0;
         ++done;
-        b = 0;
+        if (!brk && nw_ == nblk && done < sweeps) {
+          // no block can change in the next sweep: it is a sweep without
+          // change, after which the iteration stops at its fixed point
+          if (wid == 0) {
+            dlast = T(0);
+          }
+          ++done;
+          brk = 1;
+        }
+        clear_bits(actb, 0, nw_, tid, nthr);
+        b = nw_;
+        known = true;   // the next sweep starts at a block that may change
         __syncthreads();
         if (brk) break;
         continue;
       }
     }
+    known = false;
     const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0;
     const int bn = b + 1 == nblk ? 0 : b + 1;
     const int stg = (int)(t & 1);
@@ -807,9 +832,9 @@ __global__ void __launch_bounds__(1024, 1)
       const bool any = __ballot_sync(FULL, valid && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0))) != 0u;
       if (lane == 0) {
         if (any)
-          actb[b >> 5] |= 1u << (b & 31);
+          atomicOr(&actb[b >> 5], 1u << (b & 31));
         else
-          actb[b >> 5] &= ~(1u << (b & 31));
+          atomicAnd(&actb[b >> 5], ~(1u << (b & 31)));
       }
       if (any && pref[stg] != b) {
         // rows not prefetched: warp 0 fetches them now
@@ -827,15 +852,39 @@ __global__ void __launch_bounds__(1024, 1)
         cp_async_commit();
         cp_async_wait_all();
         __syncwarp();
-        if (lane == 0) pref[stg] = b;
+        if (lane == 0) {
+          pref[stg] = b;
+          cst_blk[stg] = -1;
+        }
       }
-      if (any && valid) {
-        const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
-        iWnn = rcp_t(Wo[0]);
-        Wt1n = Wo[BR];
-        Wt2n = Wo[2 * BR];
-        iwt = rcp_t(T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
-        mua = mu[a0 + lane];
+      if (any) {
+        // the local rule's constants, kept with the stage's rows: a block that
+        // comes back to the same stage reuses them
+        if (cst_blk[stg] == b) {
+          if (valid) {
+            iWnn = cst[stg][0][lane];
+            Wt1n = cst[stg][1][lane];
+            Wt2n = cst[stg][2][lane];
+            iwt = cst[stg][3][lane];
+            mua = cst[stg][4][lane];
+          }
+        } else {
+          if (valid) {
+            const T* Wo = WDc + (3 * lane) * BR + 3 * lane;
+            iWnn = rcp_t(Wo[0]);
+            Wt1n = Wo[BR];
+            Wt2n = Wo[2 * BR];
+            iwt = rcp_t(T(0.5) * (Wo[BR + 1] + Wo[2 * BR + 2]));
+            mua = mu[a0 + lane];
+            cst[stg][0][lane] = iWnn;
+            cst[stg][1][lane] = Wt1n;
+            cst[stg][2][lane] = Wt2n;
+            cst[stg][3][lane] = iwt;
+            cst[stg][4][lane] = mua;
+          }
+          __syncwarp();
+          if (lane == 0) cst_blk[stg] = b;
+        }
       }
       // Every lane forms the update its own contact would take from its current
       // residual (the local rule); the next contact in order whose update is
@@ -921,7 +970,10 @@ __global__ void __launch_bounds__(1024, 1)
         if (need) prefetch(bn, 1 - stg, t2, n2);
         // a stage not refilled keeps the rows it holds: a block that comes back
         // to the same stage (the next sweep's first active block) reuses them
-        if (t2 == 0 && need) pref[1 - stg] = bn;
+        if (t2 == 0 && need) {
+          pref[1 - stg] = bn;
+          cst_blk[1 - stg] = -1;
+        }
       }
       if (pb >= 0) {
         // fold the previous block's non-zero changes into every row but this
@@ -939,6 +991,11 @@ __global__ void __launch_bounds__(1024, 1)
         }
         __syncwarp();
         if (cnt > 0) {
+          // rows in 16-byte chunks (block starts are multiples of the chunk, so a
+          // chunk is inside or outside a block; W's padding columns are zero).
+          // When the chunks are fewer than the threads, KS consecutive lanes
+          // share a chunk, each taking every KS-th changed row, and add their
+          // partial sums with shuffles.
           // rows in 16-byte chunks (block starts are multiples of the chunk, so a
           // chunk is inside or outside a block; W's padding columns are zero)
           const int nch = (n3 + CH - 1) / CH;
