@@ -251,8 +251,19 @@ int icr_step_capture(icr_scene* scene, int32_t n_newton);
  * CUDA cores.  tc_levels (may be NULL) receives the number of levels on the
  * tensor cores.  Until it runs, every level with a front at least 64 wide uses
  * the tensor cores; icr_set_mapping and a change of contraction mode mark the
- * scene untuned. */
-int icr_autotune(icr_scene* scene, int32_t* tc_levels);
+ * scene untuned.  Each level's time is the median of 5 builds per engine, the
+ * engines alternating; level_ms (may be NULL when max_levels = 0) receives,
+ * for the first max_levels levels (leaves first), the CUDA-core and the
+ * tensor-core time in ms (the same value twice for levels too narrow for the
+ * tensor cores). */
+int icr_autotune(icr_scene* scene, int32_t* tc_levels, double* level_ms, int32_t max_levels);
+/* Fix the forward-solve plan instead of tuning it: for every etree level
+ * (n_levels = icr_forward_levels, leaves first) 1 puts the level's wide fronts
+ * on the tensor cores (where they qualify, FP32 scenes outside the SIMT
+ * contraction mode), 0 keeps CUDA cores.  Marks the scene tuned.  Needs a
+ * system (ICR_ESTATE); ICR_EINVAL on a wrong count or a flag other than 0/1. */
+int icr_set_forward_plan(icr_scene* scene, const uint8_t* tc_levels, int32_t n_levels);
+int icr_forward_levels(icr_scene* scene, int32_t* n_levels);
 /* Launch the captured step on the context's stream.  ICR_ESTATE without a
  * captured step, without a mapping and an obstacle, or when the graph is stale:
  * a buffer was reallocated, or the contact count, the obstacle kind or the

@@ -1001,7 +1001,7 @@ static int upload_tc_super(Scene* s) {
   return ICR_OK;
 }
 
-static int autotune(Scene* s) {
+static int autotune(Scene* s, double* level_ms, int max_levels) {
   const int nlev = (int)s->levels.size();
   cudaStream_t st = s->ctx->stream;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -1024,48 +1024,104 @@ static int autotune(Scene* s) {
     for (auto& x : ev) cudaEventDestroy(x);
     return rc;
   };
-  // per level, the better of two timed builds for each engine choice
-  std::vector<double> t[2];
-  for (int cfg = 0; cfg < 2; ++cfg) {
-    t[cfg].assign(nlev, 1e30);
+  auto configure = [&](int cfg) {
     for (int l = 0; l < nlev; ++l) s->tc_level[l] = cfg && s->levels[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
-    int rc = upload_tc_super(s);
-    if (rc != ICR_OK) return done(rc);
-    for (int rep = 0; rep < 3; ++rep) {
-      s->level_events = rep ? ev.data() : nullptr;
+    return upload_tc_super(s);
+  };
+  // per level and engine, the median of REPS timed builds; the two engines
+  // alternate so that clock and cache drift affect both alike
+  constexpr int REPS = 5;
+  std::vector<double> samp[2];
+  samp[0].assign((size_t)nlev * REPS, 0.0);
+  samp[1].assign((size_t)nlev * REPS, 0.0);
+  for (int rep = -1; rep < REPS; ++rep) {
+    for (int cfg = 0; cfg < 2; ++cfg) {
+      int rc = configure(cfg);
+      if (rc != ICR_OK) return done(rc);
+      s->level_events = rep >= 0 ? ev.data() : nullptr;   // rep -1 warms up
       rc = launch_build_WH(s);
       if (rc != ICR_OK) return done(rc);
       const cudaError_t e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) return done(cuda_fail(e, "autotune: build"));
-      if (!rep) continue;
+      if (rep < 0) continue;
       for (int l = 0; l < nlev; ++l) {
         float ms = 0.f;
         const cudaError_t e2 = cudaEventElapsedTime(&ms, ev[l], ev[l + 1]);
         if (e2 != cudaSuccess) return done(cuda_fail(e2, "autotune: cudaEventElapsedTime"));
-        t[cfg][l] = std::min(t[cfg][l], (double)ms);
+        samp[cfg][(size_t)l * REPS + rep] = ms;
       }
     }
   }
-  for (int l = 0; l < nlev; ++l)
-    s->tc_level[l] = s->levels[l].wmax >= TC_GEMM_MIN_W && t[1][l] < 0.97 * t[0][l] ? 1 : 0;
+  for (int l = 0; l < nlev; ++l) {
+    double med[2];
+    for (int cfg = 0; cfg < 2; ++cfg) {
+      std::vector<double> v(samp[cfg].begin() + (size_t)l * REPS, samp[cfg].begin() + (size_t)(l + 1) * REPS);
+      std::nth_element(v.begin(), v.begin() + REPS / 2, v.end());
+      med[cfg] = v[REPS / 2];
+    }
+    s->tc_level[l] = s->levels[l].wmax >= TC_GEMM_MIN_W && med[1] < 0.97 * med[0] ? 1 : 0;
+    if (level_ms && l < max_levels) {
+      level_ms[2 * l] = med[0];
+      level_ms[2 * l + 1] = s->levels[l].wmax >= TC_GEMM_MIN_W ? med[1] : med[0];
+    }
+  }
   const int rc = upload_tc_super(s);
   if (rc != ICR_OK) return done(rc);
+
   s->tuned = true;
   s->has_WH = true;   // every tuning build formed W_H
   RET(check_device_error(s));
   return done(ICR_OK);
 }
 
-int icr_autotune(icr_scene* s, int32_t* tc_levels) {
+int icr_set_forward_plan(icr_scene* s, const uint8_t* tc_levels, int32_t n_levels) {
+  RET(check_scene(s));
+  if (!s->has_system) {
+    set_error("set_forward_plan: call icr_set_system first");
+    return ICR_ESTATE;
+  }
+  const int nlev = (int)s->levels.size();
+  if (n_levels != nlev || !tc_levels) {
+    set_error("set_forward_plan: tc_levels must hold one flag per etree level (%d)", nlev);
+    return ICR_EINVAL;
+  }
+  for (int l = 0; l < nlev; ++l)
+    if (tc_levels[l] > 1) {
+      set_error("set_forward_plan: flag %d of level %d is not 0 or 1", tc_levels[l], l);
+      return ICR_EINVAL;
+    }
+  RET(set_device(s));
+  for (int l = 0; l < nlev; ++l) s->tc_level[l] = tc_levels[l] && s->levels[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
+  RET(upload_tc_super(s));
+  s->tuned = true;
+  return ICR_OK;
+}
+
+int icr_forward_levels(icr_scene* s, int32_t* n_levels) {
+  RET(check_scene(s));
+  if (!s->has_system || !n_levels) {
+    set_error("forward_levels: needs a system and an output");
+    return s->has_system ? ICR_EINVAL : ICR_ESTATE;
+  }
+  *n_levels = (int32_t)s->levels.size();
+  return ICR_OK;
+}
+
+int icr_autotune(icr_scene* s, int32_t* tc_levels, double* level_ms, int32_t max_levels) {
   RET(check_scene(s));
   RET(need_mapping(s, "autotune"));
   RET(set_device(s));
-  int mode = s->params.contraction;
-  if (s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT && s->m > 0) RET(autotune(s));
+  if (max_levels < 0 || (max_levels > 0 && !level_ms)) {
+    set_error("autotune: level_ms needs room for 2 x max_levels doubles");
+    return ICR_EINVAL;
+  }
+  const int mode = s->params.contraction;
+  const bool tunable = s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT && s->m > 0;
+  if (tunable) RET(autotune(s, level_ms, max_levels));
   s->tuned = true;
   if (tc_levels) {
     int n = 0;
-    for (uint8_t f : s->tc_level) n += s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT ? f : 0;
+    for (uint8_t f : s->tc_level) n += tunable ? f : 0;
     *tc_levels = n;
   }
   return ICR_OK;
@@ -1159,7 +1215,7 @@ int icr_step_capture(icr_scene* s, int32_t n_newton) {
     set_error("step_capture: the context needs its own CUDA stream to capture a graph");
     return ICR_EINVAL;
   }
-  if (!s->tuned) RET(icr_autotune(s, nullptr));
+  if (!s->tuned) RET(icr_autotune(s, nullptr, nullptr, 0));
   RET(step_enqueue(s, n_newton));   // a plain step sets every kernel up before capture
   CK(cudaStreamSynchronize(st));
   if (s->step_graph) {

@@ -271,6 +271,37 @@ __global__ void __launch_bounds__(1024)
   for (int i = tid; i < ncounters; i += blockDim.x) plan[PLAN_LISTS * (ns + 1) + i] = 0;
 }
 
+// Entry (row, column 3*kl + d) of supernode s's front: its H^T entry (rows < w)
+// plus the children's update entries listed for that row (extend-add as a
+// gather, children in ascending order).
+template <class T>
+__device__ __forceinline__ T assemble_entry(int s, int row, int kl, int d, int c0, int w, int m,
+                                           const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+                                           const int* __restrict__ ctr_ptr, const int* __restrict__ ctr_child,
+                                           const int* __restrict__ ctr_row, const int* __restrict__ nodes,
+                                           const T* __restrict__ bary, const int* __restrict__ qidx,
+                                           const int* __restrict__ qinv, const T* X, int64_t ldx) {
+  T v = T(0);
+  if (row < w && (c0 + row) % 3 == d) {
+    // column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
+    const int node = (c0 + row) / 3;
+    const int a = qidx[(size_t)s * m + kl];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (nodes[4 * a + i] == node) v += bary[4 * a + i];
+  }
+  const int64_t fr = fr_ptr[s] + row;
+  for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
+    const int c = ctr_child[e];
+    const int jl = qinv[(size_t)c * m + kl];
+    if (jl >= 0) {
+      const int wc = super_ptr[c + 1] - super_ptr[c];
+      v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
+    }
+  }
+  return v;
+}
+
 // Assembly of the fronts of one level (positions [pa, pb) of level_list).
 // Work unit (supernode, AR-row tile, TCC-contact tile); one thread per front
 // element: its H^T entry, plus the children's update entries listed for that
@@ -300,29 +331,12 @@ __global__ void __launch_bounds__(AR * TCOLS)
     const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
     const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
     if (row >= nrows || col >= ncols) continue;
-    const int kl = k0 + col / 3, d = col % 3;
-    T v = T(0);
-    if (row < w && (c0 + row) % 3 == d) {
-      // column 3k+d of contact a holds bary[a,i] at DOF 3*node_i + d
-      const int node = (c0 + row) / 3;
-      const int a = qidx[(size_t)s * m + kl];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (nodes[4 * a + i] == node) v += bary[4 * a + i];
-    }
-    const int64_t fr = fr_ptr[s] + row;
-    for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
-      const int c = ctr_child[e];
-      const int jl = qinv[(size_t)c * m + kl];
-      if (jl >= 0) {
-        const int wc = super_ptr[c + 1] - super_ptr[c];
-        v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
-      }
-    }
+    const T v = assemble_entry<T>(s, row, k0 + col / 3, col % 3, c0, w, m, super_ptr, fr_ptr, ctr_ptr, ctr_child,
+                                  ctr_row, nodes, bary, qidx, qinv, X, ldx);
     if (row < w)
       Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
     else
-      X[fr * ldx + 3 * k0 + col] = v;
+      X[(fr_ptr[s] + row) * ldx + 3 * k0 + col] = v;
   }
 }
 

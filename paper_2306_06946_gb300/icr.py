@@ -28,7 +28,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_set_obstacle_spheres", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
-           "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune")
+           "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
+           "icr_set_forward_plan", "icr_forward_levels")
 
 
 class IcrError(RuntimeError):
@@ -93,7 +94,9 @@ def lib() -> ct.CDLL:
             "icr_step_capture": [P, ct.c_int32],
             "icr_step_launch": [P],
             "icr_sync": [P],
-            "icr_autotune": [P, P],
+            "icr_autotune": [P, P, P, ct.c_int32],
+            "icr_set_forward_plan": [P, P, ct.c_int32],
+            "icr_forward_levels": [P, P],
             "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
         }
         for name, args in sigs.items():
@@ -300,12 +303,26 @@ class Scene:
     def step(self, n_newton: int):
         _check(lib().icr_step(self.h, int(n_newton)))
 
-    def autotune(self) -> int:
+    def autotune(self, level_times: bool = False):
         """Per-level choice of the forward-solve engine; returns the number of
-        levels on the tensor cores."""
+        levels on the tensor cores (and, with ``level_times``, an array of
+        [CUDA-core ms, tensor-core ms] per etree level)."""
         n = ct.c_int32(0)
-        _check(lib().icr_autotune(self.h, ct.byref(n)))
+        nlev = self.forward_levels()
+        lv = np.zeros(2 * nlev) if level_times else None
+        _check(lib().icr_autotune(self.h, ct.byref(n), _ptr(lv), nlev if level_times else 0))
+        if not level_times:
+            return int(n.value)
+        return int(n.value), lv.reshape(nlev, 2)
+
+    def forward_levels(self) -> int:
+        n = ct.c_int32(0)
+        _check(lib().icr_forward_levels(self.h, ct.byref(n)))
         return int(n.value)
+
+    def set_forward_plan(self, tc_levels):
+        f = _arr(tc_levels, np.uint8)
+        _check(lib().icr_set_forward_plan(self.h, _ptr(f), int(f.size)))
 
     def step_capture(self, n_newton: int):
         _check(lib().icr_step_capture(self.h, int(n_newton)))

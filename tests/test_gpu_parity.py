@@ -352,3 +352,23 @@ def test_autotune_keeps_parity(ctx):
     assert rel(sc.get("WH"), oracle_WH("liver_c1")) < 1e-5
     sc64 = make_scene(ctx, "liver_c1", icr.FP64)
     assert sc64.autotune() == 0
+
+
+# ---------------------------------------------------------------- forward-solve plans
+@pytest.mark.parametrize("name", ["beam_mid", "liver_c1"])
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
+def test_forward_plans_keep_parity(ctx, name, prec, tol):
+    """Every plan of the forward solve (tensor cores or CUDA cores per level,
+    alternating) forms the same W_H."""
+    from paper_2306_06946_gb300 import icr
+    sc = make_scene(ctx, name, prec)
+    nlev = sc.forward_levels()
+    assert nlev >= 2
+    for plan in [np.zeros(nlev), np.ones(nlev), np.arange(nlev) % 2, 1 - np.arange(nlev) % 2]:
+        sc.set_forward_plan(plan.astype(np.uint8))
+        sc.build_WH()
+        assert rel(sc.get("WH"), oracle_WH(name)) < tol, plan
+    for bad in [np.zeros(nlev + 1), np.full(nlev, 2)]:
+        with pytest.raises(icr.IcrError) as e:
+            sc.set_forward_plan(bad.astype(np.uint8))
+        assert e.value.code == icr.EINVAL
