@@ -56,6 +56,8 @@ int dalloc(Scene* s, DBuf& b, size_t bytes) {
     return ICR_ENOMEM;
   }
   b.bytes = bytes;
+  static uint64_t generation = 0;
+  b.gen = ++generation;
   c->in_use += bytes;
   ++s->alloc_epoch;
   return ICR_OK;
@@ -350,7 +352,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->ut, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super};
+                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -684,7 +686,6 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->p0, 3 * mm * sizeof(double)));
   RET(dalloc(s, s->u, 6 * mm * sizeof(double)));   // u (3m) then the last increment dp (3m)
   RET(dalloc(s, s->uk, 3 * mm * T));
-  RET(dalloc(s, s->ut, 3 * mm * T));
   RET(dalloc(s, s->y, s->n * T));
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
@@ -693,29 +694,31 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
     // tensor-core operand blocks: per supernode ceil(3m/128) column tiles x
     // ceil(w/32) row chunks, 32 KiB each (two TF32 planes)
     const int tmax = std::max(1, (int)((3 * (int64_t)m + 127) / 128));
-    std::vector<int64_t> boff(ns + 1, 0);
-    for (int k = 0; k < ns; ++k) boff[k + 1] = boff[k] + (int64_t)tmax * ((s->h_super_ptr[k + 1] - s->h_super_ptr[k] + 31) / 32);
-    RET(dalloc(s, s->tc_boff, (ns + 1) * sizeof(int64_t)));
-    RET(upload(s, s->tc_boff, boff.data(), ns + 1));
-    RET(dalloc(s, s->Ypk, (size_t)boff[ns] * 32768));
-    s->tc_tmax = tmax;
+    if (tmax != s->tc_tmax || !s->tc_boff.p) {   // the block offsets depend on the tile count only
+      std::vector<int64_t> boff(ns + 1, 0);
+      for (int k = 0; k < ns; ++k)
+        boff[k + 1] = boff[k] + (int64_t)tmax * ((s->h_super_ptr[k + 1] - s->h_super_ptr[k] + 31) / 32);
+      RET(dalloc(s, s->tc_boff, (ns + 1) * sizeof(int64_t)));
+      RET(upload(s, s->tc_boff, boff.data(), ns + 1));
+      CK(cudaStreamSynchronize(s->ctx->stream));   // boff is a local vector
+      RET(dalloc(s, s->Ypk, (size_t)boff[ns] * 32768));
+      s->tc_tmax = tmax;
+    }
   }
   if (m) {
     RET(upload(s, s->nodes, nodes, 4 * (size_t)m));
     RET(upload_T(s, s->bary, bary, 4 * (size_t)m));
   }
   cudaStream_t st = s->ctx->stream;
-  CK(cudaMemsetAsync(s->W.p, 0, 3 * mm * (size_t)ldw * T, st));   // padding columns stay 0
-  CK(cudaMemsetAsync(s->lam.p, 0, 3 * mm * T, st));
-  CK(cudaMemsetAsync(s->lam0.p, 0, 3 * mm * T, st));
-  CK(cudaMemsetAsync(s->mu.p, 0, mm * T, st));
-  CK(cudaMemsetAsync(s->delta.p, 0, 3 * mm * T, st));
-  CK(cudaMemsetAsync(s->C.p, 0, 9 * mm * T, st));
-  CK(cudaMemsetAsync(s->p.p, 0, 3 * mm * sizeof(double), st));
-  CK(cudaMemsetAsync(s->p0.p, 0, 3 * mm * sizeof(double), st));
-  CK(cudaMemsetAsync(s->u.p, 0, 6 * mm * sizeof(double), st));
-  CK(cudaMemsetAsync(s->stats.p, 0, sizeof(PgsDevStats), st));
-  CK(cudaMemsetAsync(s->dev_err.p, 0, sizeof(int), st));
+  // W's padding columns stay zero (update_W writes the 3m x 3m part); a new
+  // mapping resets the contact state in one launch
+  if (s->W_zeroed != s->W.gen || s->W_zeroed_ld != ldw || s->W_zeroed_rows != 3 * (int64_t)mm) {
+    CK(cudaMemsetAsync(s->W.p, 0, 3 * mm * (size_t)ldw * T, st));
+    s->W_zeroed = s->W.gen;
+    s->W_zeroed_ld = ldw;
+    s->W_zeroed_rows = 3 * (int64_t)mm;
+  }
+  RET(launch_reset_contacts(s, (int)mm));
   s->m = m;
   s->words = words;
   s->ldx = ldx;

@@ -28,6 +28,7 @@ struct Ctx {
 struct DBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  uint64_t gen = 0;   // allocation generation (changes with every cudaMalloc behind it)
 };
 
 // Work lists of one W_H build, written on the device by the planner right
@@ -82,7 +83,7 @@ struct Scene {
   int64_t ldx = 0;     // leading dimension (columns) of every front
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
-  DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, ut, y, dq, stats;
+  DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, y, dq, stats;
   DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then 2 + levels counters (int32)
   DBuf Gpk, gpk_off;   // G_s of the wide supernodes as 3xTF32 operand blocks; first block per supernode
   // forward-solve engine per etree level: 1 puts the level's wide fronts on the
@@ -95,6 +96,8 @@ struct Scene {
   DBuf dev_err;            // int set by a kernel whose bounded wait ran out
   DBuf Ypk, tc_boff;       // packed tensor-core operand blocks and each supernode's first block
   int tc_tmax = 0;         // 128-column tiles of the widest possible front
+  uint64_t W_zeroed = 0;   // allocation generation of W whose padding is known to be zero, for ld and rows
+  int64_t W_zeroed_ld = 0, W_zeroed_rows = 0;
   uint64_t launches = 0;   // kernels launched by this scene
   cudaGraphExec_t step_graph = nullptr;   // captured icr_step
   uint64_t graph_kernels = 0;             // kernels in the captured step
@@ -135,6 +138,9 @@ int launch_linearize(Scene* s, int k);
 int launch_contract_tc(Scene* s, int mode);
 int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks);
 int launch_front_gemm_tc(Scene* s, int level);
+// zero lambda~, its warm start, mu, delta, C, p, p_0, u, the PGS stats and the
+// device error word of mm contacts in one launch
+int launch_reset_contacts(Scene* s, int mm);
 int check_step_graph(Scene* s, const char* where);
 
 // Kernel launches of the time step use programmatic dependent launch outside

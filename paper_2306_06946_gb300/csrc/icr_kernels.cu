@@ -16,7 +16,8 @@
 //   a6  k_update_W     W = C W_H C^T, one 3x3 block pair per thread
 //   a7  k_pgs          projected Gauss-Seidel (Eq. "PGS"), one CTA
 //       k_pgs_residual FP64 complementarity / cone residuals
-//   a8  k_prox_*       p += W_H C^T lambda~, u += C^T lambda~
+//   a8  k_prox         p += W_H C^T lambda~, u += C^T lambda~ (k_prox_u and
+//                      k_prox_p when C^T lambda~ does not fit shared memory)
 // End of step:
 //   a9  k_xu, k_bsolve dq = L^-T D^-1 X u, the backward solve as
 //                      dq_s = G_s^T [y_s; -dq_R] per level, top-down
@@ -1159,6 +1160,38 @@ __global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ l
   }
 }
 
+// u_k = C_k^T lambda~_k and p += W_H u_k in one launch: every CTA forms u_k in
+// shared memory (12 flops per contact), CTA 0 also adds it to u (FP64), and
+// each warp takes one row of W_H.
+template <class T>
+__global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
+                       double* u, double* p, double* dp) {
+  pdl_entry();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* uk = (T*)smraw;   // 3m
+  for (int a = threadIdx.x; a < m; a += blockDim.x) {
+    const T l0 = lam[3 * a], l1 = lam[3 * a + 1], l2 = lam[3 * a + 2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const T v = C[9 * a + j] * l0 + C[9 * a + 3 + j] * l1 + C[9 * a + 6 + j] * l2;
+      uk[3 * a + j] = v;
+      if (blockIdx.x == 0) u[3 * a + j] += (double)v;
+    }
+  }
+  __syncthreads();
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= 3 * m) return;
+  const T* Wr = WH + (int64_t)i * 3 * m;
+  T acc = T(0);
+  for (int j = lane; j < 3 * m; j += 32) acc += Wr[j] * uk[j];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    p[i] += (double)acc;
+    dp[i] = (double)acc;
+  }
+}
+
 template <class T>
 __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp) {
   pdl_entry();
@@ -1176,20 +1209,13 @@ __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ 
 }
 
 // ------------------------------------------------------------------ a9 corrective motion
-template <class T>
-__global__ void k_cast_u(int n, const double* __restrict__ u, T* ut) {
-  pdl_entry();
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) ut[i] = (T)u[i];
-}
-
 // y = D^-1 X u = D^-1/2 (Y u), one warp per DOF row (Y holds the scaled front
 // rows, restricted to the contacts reaching them)
 template <class T>
 __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                      const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                      const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
-                     const T* __restrict__ ut, const double* __restrict__ dinvsqrt, T* y) {
+                     const double* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
   pdl_entry();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -1199,7 +1225,7 @@ __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __rest
   const T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
   const int* q = qidx + (size_t)s * m;
   T acc = T(0);
-  for (int c = lane; c < ncol; c += 32) acc += F[c] * ut[3 * q[c / 3] + c % 3];
+  for (int c = lane; c < ncol; c += 32) acc += F[c] * (T)u[3 * q[c / 3] + c % 3];
   acc = warp_sum(acc);
   if (lane == 0) y[row] = (T)(dinvsqrt[row] * (double)acc);
 }
@@ -1440,12 +1466,56 @@ static int prox_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   double* u = (double*)s->u.p;
+  const size_t smem = 3 * (size_t)m * sizeof(T);
+  if (smem <= 48 * 1024) {   // u_k fits the default shared memory: one launch
+    PDL("k_prox", k_prox<T>, (3 * m + 15) / 16, 512, smem, st, m, (const T*)s->C.p, (const T*)s->lam.p,
+        (const T*)s->WH.p, u, (double*)s->p.p, u + 3 * (size_t)m);
+    return ICR_OK;
+  }
   PDL("k_prox_u", k_prox_u<T>, (m + 127) / 128, 128, 0, st,
       m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u);
   PDL("k_prox_p", k_prox_p<T>, (3 * m + 7) / 8, 256, 0, st,
       m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p,
                                                u + 3 * (size_t)m);
   return ICR_OK;
+}
+
+// one thread per contact: its entries of every per-contact buffer
+template <class T>
+__global__ void k_reset_contacts(int mm, T* lam, T* lam0, T* mu, T* delta, T* C, double* p, double* p0, double* u,
+                                 int* stats, int nstats, int* dev_err) {
+  pdl_entry();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < mm) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      lam[3 * a + j] = T(0);
+      lam0[3 * a + j] = T(0);
+      delta[3 * a + j] = T(0);
+      p[3 * a + j] = 0.0;
+      p0[3 * a + j] = 0.0;
+      u[3 * a + j] = 0.0;
+      u[3 * (size_t)mm + 3 * a + j] = 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) C[9 * a + j] = T(0);
+    mu[a] = T(0);
+  }
+  if (a < nstats) stats[a] = 0;
+  if (a == 0) *dev_err = 0;
+}
+
+template <class T>
+static int reset_T(Scene* s, int mm) {
+  const int nstats = (int)(sizeof(PgsDevStats) / sizeof(int));
+  PDL("k_reset_contacts", k_reset_contacts<T>, (std::max(mm, nstats) + 255) / 256, 256, 0, s->ctx->stream, mm,
+      (T*)s->lam.p, (T*)s->lam0.p, (T*)s->mu.p, (T*)s->delta.p, (T*)s->C.p, (double*)s->p.p, (double*)s->p0.p,
+      (double*)s->u.p, (int*)s->stats.p, nstats, (int*)s->dev_err.p);
+  return ICR_OK;
+}
+
+int launch_reset_contacts(Scene* s, int mm) {
+  return s->prec == ICR_FP64 ? reset_T<double>(s, mm) : reset_T<float>(s, mm);
 }
 
 int launch_update_proximity(Scene* s) { return s->prec == ICR_FP64 ? prox_T<double>(s) : prox_T<float>(s); }
@@ -1459,12 +1529,10 @@ static int correct_T(Scene* s) {
     if (e != cudaSuccess) return cuda_fail(e, "memset dq");
     return ICR_OK;
   }
-  PDL("k_cast_u", k_cast_u<T>, (3 * m + 255) / 256, 256, 0, st,
-      3 * m, (const double*)s->u.p, (T*)s->ut.p);
   PDL("k_xu", k_xu<T>, (n + 7) / 8, 256, 0, st,
       n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
-                                       m, (const T*)s->X.p, s->ldx, (const T*)s->ut.p, (const double*)s->dinvsqrt.p,
+                                       m, (const T*)s->X.p, s->ldx, (const double*)s->u.p, (const double*)s->dinvsqrt.p,
                                        (T*)s->y.p);
   for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
     const Level& lv = s->levels[l];
