@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -174,6 +175,44 @@ cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
   cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+
+// Per-device set-up of a kernel's dynamic shared-memory limit (the attribute
+// belongs to the current device); thread-safe, a driver call only when the
+// limit grows.  `room` (may be NULL) receives the dynamic bytes the device
+// allows next to the kernel's static shared memory.
+struct SmemLimit {
+  std::atomic<int> bytes[64];
+};
+template <class K>
+cudaError_t ensure_smem(K kernel, SmemLimit& lim, int device, int bytes, int* room = nullptr) {
+  if (room) {
+    int optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    *room = optin - (int)fa.sharedSizeBytes;
+  }
+  const bool cached = device >= 0 && device < 64;
+  if (cached && lim.bytes[device].load() >= bytes) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && cached) {
+    int cur = lim.bytes[device].load();
+    while (cur < bytes && !lim.bytes[device].compare_exchange_weak(cur, bytes)) {
+    }
+  }
+  return e;
+}
+
+// Per-device cache of an occupancy figure (0: not yet known).
+struct DevInt {
+  std::atomic<int> v[64];
+  int get(int device) const { return device >= 0 && device < 64 ? v[device].load() : 0; }
+  void put(int device, int x) {
+    if (device >= 0 && device < 64) v[device].store(x);
+  }
+};
 
 // launch through pdl_launch, check it and count it in the scene `s` in scope
 #define PDL(where, ...)                                \

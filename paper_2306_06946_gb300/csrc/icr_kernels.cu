@@ -1331,15 +1331,17 @@ static int build_WH_T(Scene* s) {
   PDL("k_reach_inv", k_reach_inv, ns, 256, 0, st,
       m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
                                   (int*)s->qinv.p);
-  static bool gemm_attr = false;
-  static int gemm_occ = 1;
-  if (!gemm_attr) {
-    e = cudaFuncSetAttribute(k_front_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem_bytes<T>());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
+  static SmemLimit gemm_lim;
+  static DevInt gemm_occ_dev;
+  const int dev = s->ctx->device;
+  e = ensure_smem(k_front_gemm<T>, gemm_lim, dev, (int)gemm_smem_bytes<T>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
+  int gemm_occ = gemm_occ_dev.get(dev);
+  if (gemm_occ == 0) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gemm_occ, k_front_gemm<T>, 256, gemm_smem_bytes<T>());
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_front_gemm)");
     gemm_occ = std::max(1, gemm_occ);
-    gemm_attr = true;
+    gemm_occ_dev.put(dev, gemm_occ);
   }
   // contraction: FP32 scenes put fronts of TC_MIN_COLS or more columns on the
   // tensor cores (unless SIMT is asked for), the rest on CUDA cores
@@ -1433,17 +1435,21 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (e != cudaSuccess) return cuda_fail(e, "memset stats");
   if (m == 0) return ICR_OK;
   const size_t smem = pgs_smem_bytes<T, BC>(m);
-  // the opt-in limit (227 KiB) covers static plus dynamic shared memory
-  if (smem > 226 * 1024 || (m + BC - 1) / BC > PGS_MAX_BLOCKS) {
-    set_error("solve_friction: %d contacts exceed the single-CTA PGS shared-memory capacity", m);
+  // the opt-in limit covers static plus dynamic shared memory
+  static SmemLimit pgs_lim;
+  int room = 0;
+  if ((m + BC - 1) / BC > PGS_MAX_BLOCKS) {
+    set_error("solve_friction: %d contacts exceed the single-CTA PGS block capacity", m);
     return ICR_EINVAL;
   }
-  static size_t attr_bytes = 48 * 1024;
-  if (smem > attr_bytes) {
-    e = cudaFuncSetAttribute(k_pgs<T, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
-    attr_bytes = smem;
+  e = ensure_smem(k_pgs<T, BC>, pgs_lim, s->ctx->device, 0, &room);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes(k_pgs)");
+  if (smem > (size_t)room) {
+    set_error("solve_friction: %d contacts need %zu bytes of shared memory, the device allows %d", m, smem, room);
+    return ICR_EINVAL;
   }
+  e = ensure_smem(k_pgs<T, BC>, pgs_lim, s->ctx->device, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
   PDL("k_pgs", k_pgs<T, BC>, 1, 1024, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
                                       (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);

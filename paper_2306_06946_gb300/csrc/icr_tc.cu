@@ -570,15 +570,17 @@ int contract_tc_T(Scene* s) {
   const int m = s->m, ns = s->ns;
   const int64_t nr = 3 * (int64_t)m;
   const size_t smem = tc_smem_bytes<MODE>();
-  static bool attr = false;
-  static int occ = 1;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_contract_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_contract_tc)");
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_contract_tc<MODE>, TC_THREADS, smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_contract_tc)");
+  static SmemLimit lim;
+  static DevInt occ_dev;
+  const int dev = s->ctx->device;
+  cudaError_t e0 = ensure_smem(k_contract_tc<MODE>, lim, dev, (int)smem);
+  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaFuncSetAttribute(k_contract_tc)");
+  int occ = occ_dev.get(dev);
+  if (occ == 0) {
+    e0 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_contract_tc<MODE>, TC_THREADS, smem);
+    if (e0 != cudaSuccess) return cuda_fail(e0, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_contract_tc)");
     occ = std::max(1, std::min(occ, 2));   // 2 x 256 TMEM columns fill an SM's 512
-    attr = true;
+    occ_dev.put(dev, occ);
   }
   const int* plan = (const int*)s->plan.p;
   const int nsm = s->ctx->sm_count;
@@ -620,12 +622,9 @@ int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks) {
 int launch_front_gemm_tc(Scene* s, int level) {
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   const size_t smem = tc_smem_bytes<MODE>();
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_front_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm_tc)");
-    attr = true;
-  }
+  static SmemLimit lim;
+  const cudaError_t e0 = ensure_smem(k_front_gemm_tc, lim, s->ctx->device, (int)smem);
+  if (e0 != cudaSuccess) return cuda_fail(e0, "cudaFuncSetAttribute(k_front_gemm_tc)");
   const Level& lv = s->levels[level];
   const int ns = s->ns, pa = lv.first, pb = lv.first + lv.count;
   int* plan = (int*)s->plan.p;
