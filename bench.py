@@ -20,6 +20,11 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+# concurrent scenes run on separate streams; the default of 8 hardware work
+# queues would serialise streams that share a queue (must be set before the
+# CUDA context exists)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import statistics
 import subprocess
 import sys
