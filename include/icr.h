@@ -69,12 +69,15 @@ typedef struct icr_ctx icr_ctx;       /* one device + one CUDA stream + an HBM b
 typedef struct icr_scene icr_scene;   /* one deformable body with its contacts */
 
 /* How the contraction W_H = Y^T Y (Y = D^-1/2 L^-1 H^T) is computed in an FP32
- * scene.  FP64 scenes always use FP64 SIMT arithmetic. */
+ * scene.  FP64 scenes always use FP64 SIMT arithmetic.  In the three
+ * tensor-core modes the forward solve of the wide fronts also runs on the
+ * tensor cores, always in 3xTF32, in the etree levels icr_autotune assigns
+ * them; tensor-core partial sums are added into FP32 registers every 128 K. */
 enum icr_contraction {
   ICR_CONTRACT_AUTO = 0,    /* FP32 scenes: ICR_CONTRACT_TF32X3 */
-  ICR_CONTRACT_SIMT = 1,    /* FP32 CUDA cores */
-  ICR_CONTRACT_TF32X3 = 2,  /* tensor cores, each operand split into two TF32 parts, three products
-                               (FP32-level error) */
+  ICR_CONTRACT_SIMT = 1,    /* FP32 CUDA cores for the contraction and the forward solve */
+  ICR_CONTRACT_TF32X3 = 2,  /* tensor cores, each operand split into a TF32 part and a TF32 remainder,
+                               three products (W_H within 3e-6 of FP64 at 60k DOF, CUDA cores 3e-7) */
   ICR_CONTRACT_TF32 = 3,    /* tensor cores, TF32 operands, FP32 accumulation */
   ICR_CONTRACT_BF16 = 4     /* tensor cores, BF16 operands, FP32 accumulation */
 };
@@ -156,7 +159,8 @@ int icr_set_system(icr_scene* scene, int32_t n, int32_t nsuper, const int32_t* s
  * (Eq. "geometrical mapping"; Eq. "isolate directions" keeps it apart from
  * the directions).  nodes (m x 4) int32 node ids in factor order, bary
  * (m x 4) double weights, each >= 0 and summing to 1 within 1e-12.
- * m = 0 is allowed.  Resets lambda~, u and the proximity positions to 0. */
+ * m = 0 is allowed.  Resets lambda~ (and its warm start), mu, the directions,
+ * the gaps, u and the proximity positions to 0. */
 int icr_set_mapping(icr_scene* scene, int32_t m, const int32_t* nodes, const double* bary);
 
 /* Proximity positions p (m x 3 double) after the free motion: the start of the
@@ -280,7 +284,10 @@ int icr_sync(icr_scene* scene);
  * request starts on a free slot as soon as its scene has no step in flight, so
  * requests that arrive while others run on the GPU overlap with them.
  * latency_s[r] receives arrival-to-completion seconds, *makespan_s (may be
- * NULL) the time until the last completion.  ICR_ETIMEOUT after timeout_s. */
+ * NULL) the time until the last completion.  ICR_ETIMEOUT after timeout_s.
+ * Slots only overlap on the GPU when the process has as many hardware work
+ * queues (environment variable CUDA_DEVICE_MAX_CONNECTIONS, read when CUDA
+ * starts; 8 by default): streams that share a queue run one after another. */
 int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene, const double* req_arrival_s,
               int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s);
 
