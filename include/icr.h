@@ -36,6 +36,9 @@
  * synchronise that stream before returning; the others return once the work
  * is enqueued.
  *
+ * Threads: a context and its scenes are used by one host thread at a time;
+ * different contexts may be used from different threads.
+ *
  * Errors: every call returns ICR_OK or one of the codes below and leaves a
  * message for icr_last_error() (thread-local).
  */

@@ -56,7 +56,7 @@ int dalloc(Scene* s, DBuf& b, size_t bytes) {
     return ICR_ENOMEM;
   }
   b.bytes = bytes;
-  static uint64_t generation = 0;
+  static std::atomic<uint64_t> generation{0};
   b.gen = ++generation;
   c->in_use += bytes;
   ++s->alloc_epoch;

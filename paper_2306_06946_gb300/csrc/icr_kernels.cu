@@ -681,7 +681,6 @@ __global__ void __launch_bounds__(1024, 1)
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
   int* nzl = (int*)(dl + 2 * BR);  // 31 x BR: per streaming warp, rows with a non-zero change
   __shared__ T red[32];
-  __shared__ int flag;
   __shared__ int pref[2];            // block whose rows stage k holds (-1: none)
   __shared__ int chg_sweep[2];       // some lambda~ changed in sweep (done & 1)
   __shared__ int chg_it[2];          // block processed at step t changed some lambda~ (slot t & 1)
