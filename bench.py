@@ -354,11 +354,14 @@ def run_icr(args):
     # ---- sweeps each PGS launch of the step runs (the solve stops at a fixed point)
     sc.reset_proximity()
     sc.build_WH()
-    sweeps = []
+    sweeps, s_only, folds = [], [], []
     for k in range(scene.n_newton):
         sc.linearize(k)
         sc.update_W()
-        sweeps.append(int(sc.solve_friction(warm_start=False, stats=True)["sweeps"]))
+        st = sc.solve_friction(warm_start=False, stats=True)
+        sweeps.append(int(st["sweeps"]))
+        s_only.append(int(st["sweeps_s_only"]))
+        folds.append(int(st["deferred_folds"]))
         sc.update_proximity()
     sc.correct_motion(want_dq=False, reset=True)
 
@@ -371,11 +374,12 @@ def run_icr(args):
     pgs_s = phase_ms["pgs"] / 1e3
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
     achieved = pgs_bytes / pgs_s / 1e9
-    traffic = profiled_traffic("template <class T, int BC>\n__global__ void __launch_bounds__(1024, 1)\n    k_pgs(",
+    traffic = profiled_traffic("static constexpr int PGS_MAX_BLOCKS",
                                "template <class T, int BC>\nstatic size_t pgs_smem_bytes", "k_pgs_liver_c1.md")
     roofline = {"kernel": "k_pgs", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "algorithmic_bytes": pgs_bytes, "sweeps_per_launch": sweeps,
+                "s_only_sweeps_per_launch": s_only, "deferred_folds_per_launch": folds,
                 "ns_per_contact_visit": pgs_s * 1e9 / (mean_sweeps * scene.m),
                 "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
 

@@ -106,6 +106,9 @@ typedef struct icr_pgs_stats {
   double res_cone;      /* FP64 max(0, ||lambda_t|| - mu lambda_n) */
   double res_stick;     /* FP64 max ||delta_t|| over sticking contacts */
   double res_slip;      /* FP64 max misalignment of delta_t against -lambda_t over slipping contacts */
+  int32_t sweeps_s_only;  /* sweeps that visited only the blocks of contacts that may change (the
+                             others provably keep lambda~ = 0; see icr_solve_friction) */
+  int32_t deferred_folds; /* folds of those sweeps' changes into the other contacts' residuals */
 } icr_pgs_stats;
 
 enum icr_field {
@@ -214,6 +217,13 @@ int icr_update_W(icr_scene* scene);
  * lambda_t is projected on the disc ||lambda_t|| <= mu lambda_n.
  * The solve stops after n_sweeps, when eps <= tol (tol > 0), or after a sweep
  * that changed no lambda~ (a fixed point: every later sweep would repeat it).
+ * A contact with lambda~ = 0 and r_n >= 0 is left unchanged by the local rule,
+ * so a sweep passes over it; after a sweep the contacts that may change (S,
+ * in blocks of 32, FP64 16) are swept alone while the sum of |changes| since
+ * the last complete residual stays below min r_n / max_j |W[n, j]| over the
+ * others (their r_n then stays non-negative), and those changes reach the
+ * others' residuals in one deferred fold: the iterate is that of full sweeps,
+ * up to the rounding of the residuals.
  * warm_start = 0 starts from lambda~ = 0, 1 from the last solve's lambda~.
  * stats (may be NULL) receives the sweep count, eps and FP64 residuals (this
  * synchronises).  Returns ICR_ENOCONV (non-fatal) when tol > 0 and eps > tol

@@ -352,7 +352,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super};
+                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super, &s->wcoup};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -686,6 +686,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->p0, 3 * mm * sizeof(double)));
   RET(dalloc(s, s->u, 6 * mm * sizeof(double)));   // u (3m) then the last increment dp (3m)
   RET(dalloc(s, s->uk, 3 * mm * T));
+  RET(dalloc(s, s->wcoup, mm * T));
   RET(dalloc(s, s->y, s->n * T));
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
@@ -959,6 +960,8 @@ int icr_solve_friction(icr_scene* s, int warm_start, icr_pgs_stats* stats) {
   stats->res_cone = r[1];
   stats->res_stick = r[2];
   stats->res_slip = r[3];
+  stats->sweeps_s_only = d.s_only;
+  stats->deferred_folds = d.folds;
   if (s->params.tol > 0 && d.eps > s->params.tol && s->m > 0) {
     set_error("solve_friction: eps %g above tol %g after %d sweeps", d.eps, s->params.tol, d.sweeps);
     return ICR_ENOCONV;
@@ -1348,6 +1351,7 @@ int icr_set_field(icr_scene* s, int32_t field, const double* src, size_t bytes) 
   switch (field) {
     case ICR_FIELD_W:
       RET(upload_T_2d(s, s->W, s->ldw, src, 3 * (size_t)s->m, 3 * (size_t)s->m));
+      RET(launch_wcoup(s));
       s->has_W = true;
       break;
     case ICR_FIELD_WH: RET(upload_T(s, s->WH, src, c)); s->has_WH = true; break;

@@ -85,6 +85,7 @@ struct Scene {
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, y, dq, stats;
+  DBuf wcoup;   // per contact: max |W[3a, j]| over the other contacts' columns j
   DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then 2 + levels counters (int32)
   DBuf Gpk, gpk_off;   // G_s of the wide supernodes as 3xTF32 operand blocks; first block per supernode
   // forward-solve engine per etree level: 1 puts the level's wide fronts on the
@@ -124,6 +125,7 @@ void dfree(Scene* s, DBuf& b);
 struct PgsDevStats {
   int32_t sweeps;
   int32_t n_sep, n_stick, n_slip;
+  int32_t s_only, folds;   // sweeps over S only; deferred folds
   double eps;
   unsigned long long res_bits[4];   // normal, cone, stick, slip as non-negative double bits
 };
@@ -131,6 +133,7 @@ struct PgsDevStats {
 // ---- launchers (icr_kernels.cu); every one enqueues on s->ctx->stream
 int launch_build_WH(Scene* s);
 int launch_update_W(Scene* s);
+int launch_wcoup(Scene* s);   // wcoup of a W given directly
 int launch_pgs(Scene* s, int warm_start, int want_residuals);
 int launch_update_proximity(Scene* s);
 int launch_correct_motion(Scene* s);

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "icr_internal.h"
 
@@ -572,33 +573,84 @@ __global__ void k_symmetrize(int nr, T* A) {
 }
 
 // ------------------------------------------------------------------ a6 W = C W_H C^T
+// Also raises wcoup[a] to the largest |W[3a, j]| over the columns j of the
+// other contacts (the normal row's coupling to them; wcoup is zeroed before the
+// launch), the bound PGS uses to pass over separated contacts.
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) { atomicMax(addr, __float_as_uint(v)); }
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
 template <class T>
-__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw) {
+using bits_t = typename std::conditional<sizeof(T) == 4, unsigned, unsigned long long>::type;
+__device__ __forceinline__ unsigned to_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ unsigned long long to_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ float from_bits(unsigned u) { return __uint_as_float(u); }
+__device__ __forceinline__ double from_bits(unsigned long long u) { return __longlong_as_double((long long)u); }
+// max of non-negative values that keeps a NaN (its bits order above +inf)
+template <class T>
+__device__ __forceinline__ T nmax(T a, T b) {
+  return a != a ? a : ((b > a || b != b) ? b : a);
+}
+
+template <class T>
+__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw, T* wcoup) {
   pdl_entry();
-  const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
-  if (a >= m || b >= m || a > b) return;
-  const int64_t ld = 3 * (int64_t)m;
-  T M[3][3], Ca[3][3], Cb[3][3], t[3][3];
+  __shared__ bits_t<T> mxa[16], mxb[16];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int b = blockIdx.x * 16 + tx, a = blockIdx.y * 16 + ty;
+  if (ty == 0) mxb[tx] = 0;
+  if (tx == 0) mxa[ty] = 0;
+  __syncthreads();
+  if (a < m && b < m && a <= b) {
+    const int64_t ld = 3 * (int64_t)m;
+    T M[3][3], Ca[3][3], Cb[3][3], t[3][3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
-      Ca[i][j] = C[9 * a + 3 * i + j];
-      Cb[i][j] = C[9 * b + 3 * i + j];
+      for (int j = 0; j < 3; ++j) {
+        M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
+        Ca[i][j] = C[9 * a + 3 * i + j];
+        Cb[i][j] = C[9 * b + 3 * i + j];
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) t[i][j] = M[i][0] * Cb[j][0] + M[i][1] * Cb[j][1] + M[i][2] * Cb[j][2];
+    T ra = T(0), rb = T(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        T v = Ca[i][0] * t[0][j] + Ca[i][1] * t[1][j] + Ca[i][2] * t[2][j];
+        W[(3 * a + i) * ldw + 3 * b + j] = v;
+        W[(3 * b + j) * ldw + 3 * a + i] = v;
+        if (i == 0) ra = nmax(ra, fabs(v));   // W[3a, 3b + j]
+        if (j == 0) rb = nmax(rb, fabs(v));   // W[3b, 3a + i]
+      }
+    if (a != b) {
+      atomic_max_nonneg(&mxa[ty], ra);
+      atomic_max_nonneg(&mxb[tx], rb);
     }
+  }
+  __syncthreads();
+  const int ga = blockIdx.y * 16 + tx, gb = blockIdx.x * 16 + tx;
+  if (ty == 0 && ga < m && mxa[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + ga, mxa[tx]);
+  if (ty == 1 && gb < m && mxb[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + gb, mxb[tx]);
+}
+
+// wcoup of a W given directly: one warp per contact's normal row
+template <class T>
+__global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wcoup) {
+  pdl_entry();
+  const int a = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (a >= m) return;
+  const T* row = W + (int64_t)(3 * a) * ldw;
+  T mx = T(0);
+  for (int j = lane; j < 3 * m; j += 32)
+    if (j / 3 != a) mx = nmax(mx, fabs(row[j]));
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) t[i][j] = M[i][0] * Cb[j][0] + M[i][1] * Cb[j][1] + M[i][2] * Cb[j][2];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      T v = Ca[i][0] * t[0][j] + Ca[i][1] * t[1][j] + Ca[i][2] * t[2][j];
-      W[(3 * a + i) * ldw + 3 * b + j] = v;
-      W[(3 * b + j) * ldw + 3 * a + i] = v;
-    }
+  for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(FULL, mx, o));
+  if (lane == 0) wcoup[a] = mx;
 }
 
 // ------------------------------------------------------------------ a7 PGS
@@ -637,6 +689,9 @@ __device__ __forceinline__ double rcp_t(double x) { return __drcp_rn(x); }
 
 
 static constexpr int PGS_MAX_BLOCKS = 1024;   // contact blocks per scene (m <= 1024 BC)
+static constexpr int PGS_THREADS = 512;       // one CTA: warp 0 solves, the others stream
+static constexpr int PGS_WARPS = PGS_THREADS / 32;
+static constexpr int PGS_MAX_DEFER = 16;      // most blocks that may change while the others are passed over
 
 // acc[q] += w[q] * d for one 16-byte chunk of a W row (16-byte aligned)
 __device__ __forceinline__ void fma_chunk(float* acc, const float* w, float d) {
@@ -661,11 +716,160 @@ __device__ __forceinline__ void clear_bits(unsigned* bits, int lo, int hi, int t
   }
 }
 
+// State of the S-only sweeps (deferred folds), in shared memory.
+template <class T>
+struct PgsDefer {
+  int slist[PGS_MAX_DEFER];            // the blocks of S in ascending order
+  unsigned sbits[PGS_MAX_BLOCKS / 32]; // S as a bit set
+  int on, ns;                          // S-only sweeps start; |S|
+  int xf[2];                           // leave them after step t (slot t & 1)
+  T nb[PGS_MAX_DEFER];                 // sum of |D| over block slist[k]
+  T th;                                // the bound sum |D| must stay below
+  bits_t<T> thq;                       // theta being formed (bits of a non-negative value)
+  int cnt;                             // entries of the compact list of non-zero D
+  int sweeps, folds;                   // statistics: S-only sweeps, deferred folds
+  int xs[2];                           // sweeps warp 0 ended itself in step t (slot t & 1)
+};
+
+// Entered with every residual complete, at the end of a sweep.  S = the
+// blocks that may change in the next sweep; every other contact has
+// lambda~ = 0 and r_n >= 0 and keeps lambda~ = 0 while r_n stays
+// non-negative.  The changes D of S move its r_n by at most wcoup * sum |D|,
+// so while sum |D| stays below theta = min r_n / wcoup over those contacts,
+// sweeps can visit S only and fold S's changes into S's rows; the other rows
+// wait for one fold of D.  Returns |S| when the S-only sweeps start, else 0.
+// Out of line: its temporaries stay out of the solve loop's registers.
+template <class T, int BC>
+__device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam, const T* r,
+                                            const T* __restrict__ wcoup, T* dacc, T dlast) {
+  constexpr int BR = 3 * BC;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nblk = (m + BC - 1) / BC;
+  if (tid < PGS_MAX_BLOCKS / 32) d->sbits[tid] = 0u;
+  if (tid == 0) d->thq = to_bits(T(INFINITY));
+  __syncthreads();
+  for (int bb = wid; bb < nblk; bb += PGS_WARPS) {
+    const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
+    const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
+                                  lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
+    if (__ballot_sync(FULL, a) != 0u) {
+      if (lane == 0) atomicOr(&d->sbits[bb >> 5], 1u << (bb & 31));
+    } else {
+      T v = T(INFINITY);
+      if (lane < nbb) {
+        const T rn = r[i0 + 3 * lane], wm = wcoup[bb * BC + lane];
+        v = (wm > T(0) && rn > T(0)) ? rn / wm : (wm == T(0) ? T(INFINITY) : T(0));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+      if (lane == 0) atomicMin(&d->thq, to_bits(v));
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const unsigned wd = d->sbits[lane];
+    const int c = __popc(wd);
+    int off = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, off, o);
+      if (lane >= o) off += y;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= c;
+    const T th = from_bits(d->thq);
+    // started only when the last sweep's change ||d||_2 (<= ||d||_1) would
+    // fit twice into the bound: a start that ends within its first sweep
+    // costs a fold more than the sweep it saves
+    const T ds = warp_sum(dlast);
+    const bool on = total <= PGS_MAX_DEFER && total < nblk && th > T(0) && ds <= T(0.25) * th * th;
+    if (on) {
+      for (unsigned w = wd; w != 0u; w &= w - 1u) d->slist[off++] = lane * 32 + __ffs(w) - 1;
+      for (int i = lane; i < total * BR; i += 32) dacc[i] = T(0);
+      if (lane < total) d->nb[lane] = T(0);
+    }
+    if (lane == 0) {
+      d->on = on ? 1 : 0;
+      d->ns = total;
+      d->th = th * T(1.0 - 1.0 / 1024.0);   // margin for the rounding of the bound
+    }
+  }
+  __syncthreads();
+  return d->on ? d->ns : 0;
+}
+
+// Leaves the S-only sweeps after block pb, whose changes are dlp: they are
+// folded into the rows of S (its successor's pending share included, which
+// warp 0 drops) and the deferred changes D of S into every other row.  Then
+// every residual is complete.  Out of line, like pgs_defer_enter.
+template <class T, int BC>
+__device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int nsd, const T* dlp,
+                                             const T* __restrict__ W, int64_t ldw, T* r, const T* dacc,
+                                             int* nzl, int* drow, T* dval) {
+  constexpr int BR = 3 * BC;
+  constexpr int CH = 16 / (int)sizeof(T);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
+  const int n3 = 3 * m;
+  const int pR0 = 3 * pb * BC, pnr = 3 * min(BC, m - pb * BC);
+  int cnt = 0;
+  if (wid == 0) {
+    // compact list of the non-zero D rows, in order
+    for (int k = 0; k < nsd; ++k) {
+      const int R = 3 * d->slist[k] * BC;
+      for (int w0 = 0; w0 < BR; w0 += 32) {
+        const T v = w0 + lane < BR ? dacc[k * BR + w0 + lane] : T(0);
+        const bool nz = v != T(0);
+        const unsigned msk = __ballot_sync(FULL, nz);
+        if (nz) {
+          const int q = cnt + __popc(msk & ((1u << lane) - 1u));
+          drow[q] = R + w0 + lane;
+          dval[q] = v;
+        }
+        cnt += __popc(msk);
+      }
+    }
+    if (lane == 0) d->cnt = cnt;
+  } else {
+    int* lst = nzl + (wid - 1) * BR;
+#pragma unroll
+    for (int w0 = 0; w0 < BR; w0 += 32) {
+      const bool nz = w0 + lane < pnr && dlp[w0 + lane] != T(0);
+      const unsigned msk = __ballot_sync(FULL, nz);
+      if (nz) lst[cnt + __popc(msk & ((1u << lane) - 1u))] = w0 + lane;
+      cnt += __popc(msk);
+    }
+  }
+  __syncthreads();
+  if (wid > 0) {
+    const int t2 = tid - 32, n2 = nthr - 32, nd = d->cnt;
+    const int* lst = nzl + (wid - 1) * BR;
+    const int nch = (n3 + CH - 1) / CH;
+    for (int c = t2; c < nch; c += n2) {
+      const int j0 = c * CH;
+      if (j0 >= pR0 && j0 < pR0 + pnr) continue;
+      const int blk = j0 / BR;
+      T acc[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) acc[q] = T(0);
+      if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) {
+        const T* Wc = W + (int64_t)pR0 * ldw + j0;
+        for (int k = 0; k < cnt; ++k) fma_chunk(acc, Wc + (int64_t)lst[k] * ldw, dlp[lst[k]]);
+      } else {
+        for (int k = 0; k < nd; ++k) fma_chunk(acc, W + (int64_t)drow[k] * ldw + j0, dval[k]);
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q)
+        if (j0 + q < n3) r[j0 + q] += acc[q];
+    }
+  }
+  __syncthreads();
+}
+
 
 template <class T, int BC>
-__global__ void __launch_bounds__(1024, 1)
+__global__ void __launch_bounds__(PGS_THREADS, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-          const T* __restrict__ mu, T* lam_g, int warm, PgsDevStats* st) {
+          const T* __restrict__ mu, const T* __restrict__ wcoup, T* lam_g, int warm, PgsDevStats* st) {
   pdl_entry();
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
@@ -679,21 +883,24 @@ __global__ void __launch_bounds__(1024, 1)
   T* lam = WR + 2 * BR * BR;       // 3m
   T* r = lam + 3 * m;              // 3m
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
-  int* nzl = (int*)(dl + 2 * BR);  // 31 x BR: per streaming warp, rows with a non-zero change
-  __shared__ T red[32];
+  T* dacc = dl + 2 * BR;           // PGS_MAX_DEFER x BR: changes of the blocks in S not yet folded elsewhere
+  int* nzl = (int*)(dacc + PGS_MAX_DEFER * BR);  // (PGS_WARPS - 1) x BR: per streaming warp, rows with a non-zero change
+  __shared__ T red[PGS_WARPS];
   __shared__ int pref[2];            // block whose rows stage k holds (-1: none)
+  __shared__ int psuc[2];            // the block whose columns stage k's WR holds
   __shared__ int chg_sweep[2];       // some lambda~ changed in sweep (done & 1)
   __shared__ int chg_it[2];          // block processed at step t changed some lambda~ (slot t & 1)
   __shared__ int nxt[2][2];          // look-ahead results (two slots, alternating): from b on, from 0
   __shared__ T cst[2][5][BC];        // per-contact local-rule constants of the block in stage k
   __shared__ int cst_blk[2];         // block whose constants cst[k] holds (-1: none)
   __shared__ unsigned actb[PGS_MAX_BLOCKS / 32];   // block had a changing contact in its last visit
+  __shared__ PgsDefer<T> dfs;       // S-only sweeps (deferred folds)
+  static_assert(PGS_MAX_BLOCKS / 32 == 32 && PGS_MAX_DEFER <= 32, "one warp scans the block bits");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
   const int n3 = 3 * m;
   const int nblk = (m + BC - 1) / BC;
-  // W[rows of block bn, cols of blocks bn and bn+1] -> stage k
-  auto prefetch = [&](int bn, int k, int t0, int nt) {
-    const int bn1 = (bn + 1) % nblk;
+  // W[rows of block bn, cols of block bn and of its successor bn1] -> stage k
+  auto prefetch = [&](int bn, int bn1, int k, int t0, int nt) {
     const int n0 = 3 * bn * BC, nnr = 3 * min(BC, m - bn * BC), c1 = 3 * bn1 * BC;
     T* D = WD + k * BR * BR;
     T* Rr = WR + k * BR * BR;
@@ -712,6 +919,12 @@ __global__ void __launch_bounds__(1024, 1)
   for (int i = tid; i < PGS_MAX_BLOCKS / 32; i += nthr) actb[i] = 0u;
   if (tid == 0) {
     pref[1] = -1;
+    psuc[0] = 1 % nblk;
+    psuc[1] = -1;
+    dfs.on = dfs.ns = 0;
+    dfs.sweeps = dfs.folds = 0;
+    dfs.xs[0] = dfs.xs[1] = 0;
+    dfs.xf[0] = dfs.xf[1] = 0;
     chg_sweep[0] = chg_sweep[1] = 0;
     chg_it[0] = chg_it[1] = 1;   // no look-ahead before the first block
     nxt[0][0] = nxt[0][1] = nxt[1][0] = nxt[1][1] = nblk;
@@ -719,7 +932,7 @@ __global__ void __launch_bounds__(1024, 1)
   }
   __syncthreads();
   if (warm) {
-    for (int row = wid; row < n3; row += 32) {
+    for (int row = wid; row < n3; row += PGS_WARPS) {
       const T* Wr = W + (int64_t)row * ldw;
       T acc = T(0);
 #pragma unroll 4
@@ -733,7 +946,7 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   // a block starts active when one of its contacts has lambda~ != 0 or a
   // negative normal residual; only active blocks have their rows prefetched
-  for (int bb = wid; bb < nblk; bb += 32) {
+  for (int bb = wid; bb < nblk; bb += PGS_WARPS) {
     const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
     const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
                                   lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
@@ -741,7 +954,7 @@ __global__ void __launch_bounds__(1024, 1)
   }
   __syncthreads();
   const bool act0 = nblk <= 2 || (actb[0] & 1u);
-  if (act0) prefetch(0, 0, tid, nthr);
+  if (act0) prefetch(0, 1 % nblk, 0, tid, nthr);
   if (tid == 0) pref[0] = act0 ? 0 : -1;
   cp_async_wait_all();
   __syncthreads();
@@ -751,18 +964,39 @@ __global__ void __launch_bounds__(1024, 1)
   T p0 = 0, p1 = 0, p2 = 0, dsum = T(0), dlast = T(0);
   int done = 0, b = 0, pb = -1, look = 0;
   bool known = false;   // b was found by a look-ahead: no second look needed
-  long t = 0;   // blocks processed (stage parity)
-  double eps = 0.0;
-  const bool want_eps = tol > 0.0;
+  unsigned t = 0;   // blocks processed (its parity selects double-buffered slots)
+  const bool want_eps = tol > 0.0;   // eps of a sweep is formed into red[0]
+  // S-only sweeps: |S| (0: off), position of b in slist, may start in this sweep
+  int nsd = 0, kpos = 0, tryd = 1;
   while (done < sweeps) {
-    if (!known && !chg_it[(t + 1) & 1]) {   // the previous step's slot
+    if (nsd && dfs.xf[(t + 1) & 1]) {   // set in the previous step
+      // the changes of S may now be large enough to change a contact outside
+      // S: fold what was deferred, then go on in order after pb
+      if (wid == 0) p0 = p1 = p2 = T(0);
+      pgs_defer_leave<T, BC>(&dfs, m, pb, nsd, dl + (1 - (int)(t & 1)) * BR, W, ldw, r, dacc, nzl,
+                             (int*)WD, WR);   // scratch in stage 0
+      if (tid == 0) {
+        ++dfs.folds;
+        dfs.xf[0] = dfs.xf[1] = 0;
+        pref[0] = -1;
+        cst_blk[0] = -1;
+        chg_it[(t + 1) & 1] = 0;   // nothing pending: look ahead from b
+      }
+      __syncthreads();
+      nsd = tryd = 0;   // again from the end of this sweep
+      b = pb + 1;
+      pb = -1;
+      known = false;
+      continue;
+    }
+    if (!nsd && !known && !chg_it[(t + 1) & 1]) {   // the previous step's slot
       // the last block changed nothing: every residual is complete and nothing
       // is pending, so blocks that hold lambda~ = 0 and non-negative normal
       // residuals stay unchanged.  One warp per block finds the first other
       // block from b on, and the first from 0 on (the next sweep's start when
       // this sweep has none left).
       int* nx = nxt[look & 1];
-      for (int bb = wid; bb < nblk; bb += 32) {
+      for (int bb = wid; bb < nblk; bb += PGS_WARPS) {
         const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
         const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
                                       lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
@@ -778,6 +1012,14 @@ __global__ void __launch_bounds__(1024, 1)
       // blocks passed over hold no active contact (a prefetch hint, no barrier needed)
       clear_bits(actb, b, nb_, tid, nthr);
       b = nb_;
+      if (tryd && b < nblk) {
+        // every residual is complete: the rest of the sweep and the next
+        // sweeps may visit S only, starting at b (the first block of S from b)
+        tryd = 0;
+        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, wid == 0 ? dlast : T(0));
+        kpos = 0;
+        while (kpos < nsd - 1 && dfs.slist[kpos] != b) ++kpos;
+      }
       if (b == nblk) {   // the rest of the sweep is unchanged: end of sweep
         if (want_eps) {
           T nrm = T(0);
@@ -788,13 +1030,12 @@ __global__ void __launch_bounds__(1024, 1)
           __syncthreads();
           if (tid == 0) {
             T tot = T(0);
-            for (int k = 0; k < 32; ++k) tot += red[k];
+            for (int k = 0; k < PGS_WARPS; ++k) tot += red[k];
             red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
           }
           __syncthreads();
-          eps = (double)red[0];
         }
-        int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
+        int brk = !chg_sweep[done & 1] || (want_eps && (double)red[0] <= tol);
         if (wid == 0) {
           dlast = dsum;
           dsum = T(0);
@@ -811,6 +1052,12 @@ __global__ void __launch_bounds__(1024, 1)
           brk = 1;
         }
         clear_bits(actb, 0, nw_, tid, nthr);
+        tryd = 1;
+        if (!brk && nw_ < nblk && done < sweeps) {
+          tryd = 0;
+          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, wid == 0 ? dlast : T(0));
+          kpos = 0;
+        }
         b = nw_;
         known = true;   // the next sweep starts at a block that may change
         __syncthreads();
@@ -820,9 +1067,14 @@ __global__ void __launch_bounds__(1024, 1)
     }
     known = false;
     const int a0 = b * BC, nb = min(BC, m - a0), R0 = 3 * a0;
-    const int bn = b + 1 == nblk ? 0 : b + 1;
-    const int stg = (int)(t & 1);
-    const int dc = stg;
+    // the next block visited: the next one in order, or the next one of S
+    const int bn = nsd ? dfs.slist[kpos + 1 == nsd ? 0 : kpos + 1] : (b + 1 == nblk ? 0 : b + 1);
+    const int dc = (int)(t & 1);   // slot of this block's changes in dl
+    // stage of this block's rows: alternating, so that the next block's rows
+    // can be prefetched into the other one; when S is one block, whichever
+    // stage holds it (nothing is prefetched then)
+    int stg = dc;
+    if (nsd == 1 && pref[stg] != b && pref[1 - stg] == b) stg = 1 - stg;
     if (wid == 0) {
       const T* WDc = WD + stg * BR * BR;
       const T* WRc = WR + stg * BR * BR;
@@ -850,7 +1102,7 @@ __global__ void __launch_bounds__(1024, 1)
         else
           atomicAnd(&actb[b >> 5], ~(1u << (b & 31)));
       }
-      if (any && pref[stg] != b) {
+      if (any && (pref[stg] != b || (bn != b && psuc[stg] != bn))) {
         // rows not prefetched: warp 0 fetches them now
         T* D = WD + stg * BR * BR;
         T* Rr = WR + stg * BR * BR;
@@ -868,6 +1120,7 @@ __global__ void __launch_bounds__(1024, 1)
         __syncwarp();
         if (lane == 0) {
           pref[stg] = b;
+          psuc[stg] = bn;
           cst_blk[stg] = -1;
         }
       }
@@ -906,8 +1159,12 @@ __global__ void __launch_bounds__(1024, 1)
       // passed over have zero updates (among them every contact with lambda~ = 0
       // and a non-negative normal residual), so the iterate is exactly that of
       // visiting them in order.
+      int xs = 0;          // sweeps warp 0 ends itself (S is this block alone)
+      bool lv = false;     // the bound on the changes of S ran out
+      bool chg;
+      for (bool go = any;;) {
       int i = -1;
-      while (any) {
+      while (go) {
         // without branches: lanes past the block hold zeros and get zero updates
         T ln = l0 - q0 * iWnn;
         ln = ln > T(0) ? ln : T(0);
@@ -929,8 +1186,6 @@ __global__ void __launch_bounds__(1024, 1)
         const T* Xl = WRc + (3 * i) * BR + 3 * ll;
         const T w00 = Wl[0], w01 = Wl[1], w02 = Wl[2], w10 = Wl[BR], w11 = Wl[BR + 1], w12 = Wl[BR + 2],
                 w20 = Wl[2 * BR], w21 = Wl[2 * BR + 1], w22 = Wl[2 * BR + 2];
-        const T x00 = Xl[0], x01 = Xl[1], x02 = Xl[2], x10 = Xl[BR], x11 = Xl[BR + 1], x12 = Xl[BR + 2],
-                x20 = Xl[2 * BR], x21 = Xl[2 * BR + 1], x22 = Xl[2 * BR + 2];
         const T d0 = __shfl_sync(FULL, c0, i), d1 = __shfl_sync(FULL, c1, i), d2 = __shfl_sync(FULL, c2, i);
         if (lane == i) {
           l0 = ln;
@@ -944,9 +1199,53 @@ __global__ void __launch_bounds__(1024, 1)
         q0 += w00 * d0 + w10 * d1 + w20 * d2;
         q1 += w01 * d0 + w11 * d1 + w21 * d2;
         q2 += w02 * d0 + w12 * d1 + w22 * d2;
-        p0 += x00 * d0 + x10 * d1 + x20 * d2;
-        p1 += x01 * d0 + x11 * d1 + x21 * d2;
-        p2 += x02 * d0 + x12 * d1 + x22 * d2;
+        if (bn != b) {   // pending changes for the next block (none when it is this block)
+          const T x00 = Xl[0], x01 = Xl[1], x02 = Xl[2], x10 = Xl[BR], x11 = Xl[BR + 1], x12 = Xl[BR + 2],
+                  x20 = Xl[2 * BR], x21 = Xl[2 * BR + 1], x22 = Xl[2 * BR + 2];
+          p0 += x00 * d0 + x10 * d1 + x20 * d2;
+          p1 += x01 * d0 + x11 * d1 + x21 * d2;
+          p2 += x02 * d0 + x12 * d1 + x22 * d2;
+        }
+      }
+      if (nsd) {
+        // accumulate this visit's changes into D and test the bound: the
+        // blocks outside S up to the next block of S see the state after it
+        T* Dk = dacc + kpos * BR;
+        T part = T(0);
+        if (valid) {
+          const T D0 = Dk[3 * lane] + e0, D1 = Dk[3 * lane + 1] + e1, D2 = Dk[3 * lane + 2] + e2;
+          Dk[3 * lane] = D0;
+          Dk[3 * lane + 1] = D1;
+          Dk[3 * lane + 2] = D2;
+          part = fabs(D0) + fabs(D1) + fabs(D2);
+        }
+        part = warp_sum(part);
+        T tot = lane < nsd ? (lane == kpos ? part : dfs.nb[lane]) : T(0);
+        tot = warp_sum(tot);
+        lv = !(tot <= dfs.th);
+        if (lane == 0) {
+          dfs.nb[kpos] = part;
+          if (lv) dfs.xf[t & 1] = 1;
+        }
+      }
+      chg = __any_sync(FULL, e0 != T(0) || e1 != T(0) || e2 != T(0));
+      // When S is this block alone, the visit ends a sweep.  Warp 0 ends it
+      // and starts the next one itself, residuals kept in registers, while
+      // the other warps wait at the barrier; the main loop ends the last
+      // sweep (no change, eps <= tol, the sweep cap or the bound running out).
+      if (nsd != 1 || !chg || lv || done + xs + 1 >= sweeps) break;
+      if (want_eps) {
+        // lambda~ outside S is zero, so ||lambda^i|| is this block's
+        T nl = valid ? l0 * l0 + l1 * l1 + l2 * l2 : T(0);
+        nl = warp_sum(nl);
+        const T ds = warp_sum(dsum);
+        if ((nl > T(0) ? (double)sqrt(ds / nl) : 0.0) <= tol) break;
+      }
+      dlast = dsum;
+      dsum = T(0);
+      ++xs;
+      e0 = e1 = e2 = T(0);
+      go = __ballot_sync(FULL, valid && (l0 != T(0) || l1 != T(0) || l2 != T(0) || q0 < T(0))) != 0u;
       }
       if (valid) {
         lam[R0 + 3 * lane] = l0;
@@ -956,10 +1255,15 @@ __global__ void __launch_bounds__(1024, 1)
         r[R0 + 3 * lane + 1] = q1;
         r[R0 + 3 * lane + 2] = q2;
       }
-      const bool chg = __any_sync(FULL, e0 != T(0) || e1 != T(0) || e2 != T(0));
       if (lane == 0) {
         chg_it[t & 1] = chg ? 1 : 0;
-        if (chg) chg_sweep[done & 1] = 1;
+        if (xs) {
+          chg_sweep[(done + xs) & 1] = chg ? 1 : 0;   // the slot of the sweep now running
+          dfs.sweeps += xs;
+        } else if (chg) {
+          chg_sweep[done & 1] = 1;
+        }
+        dfs.xs[t & 1] = xs;
       }
       if (lane < BC) {                // lanes without a change write zeros
         dl[dc * BR + 3 * lane] = e0;
@@ -975,17 +1279,19 @@ __global__ void __launch_bounds__(1024, 1)
         // warp takes the same decision); a block that needs rows it did not
         // get has them fetched by warp 0
         const int nbn = min(BC, m - bn * BC), bn0 = 3 * bn * BC;
-        bool need = nblk <= 2 || ((actb[bn >> 5] >> (bn & 31)) & 1u);
-        if (!need) {
+        bool need = nsd > 1 || (!nsd && (nblk <= 2 || ((actb[bn >> 5] >> (bn & 31)) & 1u)));
+        if (!need && !nsd) {
           const bool nz = lane < nbn && (lam[bn0 + 3 * lane] != T(0) || lam[bn0 + 3 * lane + 1] != T(0) ||
                                          lam[bn0 + 3 * lane + 2] != T(0));
           need = __ballot_sync(FULL, nz) != 0u;
         }
-        if (need) prefetch(bn, 1 - stg, t2, n2);
+        const int bn1 = nsd ? dfs.slist[(kpos + 2) % nsd] : (bn + 1) % nblk;
+        if (need) prefetch(bn, bn1, 1 - stg, t2, n2);
         // a stage not refilled keeps the rows it holds: a block that comes back
         // to the same stage (the next sweep's first active block) reuses them
         if (t2 == 0 && need) {
           pref[1 - stg] = bn;
+          psuc[1 - stg] = bn1;
           cst_blk[1 - stg] = -1;
         }
       }
@@ -1006,15 +1312,12 @@ __global__ void __launch_bounds__(1024, 1)
         __syncwarp();
         if (cnt > 0) {
           // rows in 16-byte chunks (block starts are multiples of the chunk, so a
-          // chunk is inside or outside a block; W's padding columns are zero).
-          // When the chunks are fewer than the threads, KS consecutive lanes
-          // share a chunk, each taking every KS-th changed row, and add their
-          // partial sums with shuffles.
-          // rows in 16-byte chunks (block starts are multiples of the chunk, so a
-          // chunk is inside or outside a block; W's padding columns are zero)
-          const int nch = (n3 + CH - 1) / CH;
+          // chunk is inside or outside a block; W's padding columns are zero);
+          // during S-only sweeps only the rows of S
+          const int nch = nsd ? nsd * RCH : (n3 + CH - 1) / CH;
           for (int c = t2; c < nch; c += n2) {
-            const int j0 = c * CH;
+            const int j0 = nsd ? 3 * dfs.slist[c / RCH] * BC + (c % RCH) * CH : c * CH;
+            if (j0 >= n3) continue;
             if ((j0 >= R0 && j0 < R0 + 3 * nb) || (j0 >= pR0 && j0 < pR0 + pnr)) continue;
             T acc[CH];
 #pragma unroll
@@ -1041,8 +1344,10 @@ __global__ void __launch_bounds__(1024, 1)
     }
     __syncthreads();
     pb = b;
+    const bool leave = nsd && dfs.xf[t & 1];
+    done += dfs.xs[t & 1];   // sweeps warp 0 ended itself
     ++t;
-    if (bn == 0) {
+    if (bn <= b && !leave) {
       // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i|| (Alg. 1),
       // formed here only when a positive tol needs it
       if (want_eps) {
@@ -1054,27 +1359,32 @@ __global__ void __launch_bounds__(1024, 1)
         __syncthreads();
         if (tid == 0) {
           T tot = T(0);
-          for (int k = 0; k < 32; ++k) tot += red[k];
+          for (int k = 0; k < PGS_WARPS; ++k) tot += red[k];
           red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
         }
         __syncthreads();
-        eps = (double)red[0];
       }
       // stop at eps <= tol, or after a sweep that changed nothing (a fixed
       // point: every later sweep would repeat it exactly)
-      const int brk = !chg_sweep[done & 1] || (want_eps && eps <= tol);
+      const int brk = !chg_sweep[done & 1] || (want_eps && (double)red[0] <= tol);
       if (wid == 0) {
         dlast = dsum;
         dsum = T(0);
       }
-      if (tid == 0) chg_sweep[(done + 1) & 1] = 0;
+      if (tid == 0) {
+        chg_sweep[(done + 1) & 1] = 0;
+        if (nsd) ++dfs.sweeps;
+      }
       ++done;
+      tryd = 1;
       __syncthreads();
       if (brk) break;
     }
     b = bn;
+    if (nsd) kpos = kpos + 1 == nsd ? 0 : kpos + 1;
   }
   // eps of the last sweep, for the statistics
+  double eps = 0.0;
   {
     T nrm = T(0);
     for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
@@ -1084,7 +1394,7 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
     if (tid == 0) {
       T tot = T(0);
-      for (int k = 0; k < 32; ++k) tot += red[k];
+      for (int k = 0; k < PGS_WARPS; ++k) tot += red[k];
       eps = tot > T(0) ? (double)sqrt(ds / tot) : 0.0;
     }
   }
@@ -1092,17 +1402,15 @@ __global__ void __launch_bounds__(1024, 1)
   if (tid == 0) {
     st->sweeps = done;
     st->eps = eps;
+    st->s_only = dfs.sweeps;
+    st->folds = dfs.folds;
   }
 }
 
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
-  return (4 * BR * BR + 6 * (size_t)m + 2 * BR) * sizeof(T) + 31 * BR * sizeof(int);
-}
-
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
-  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR + PGS_MAX_DEFER * BR) * sizeof(T) + (PGS_WARPS - 1) * BR * sizeof(int);
 }
 
 // FP64 residuals of the final iterate: one warp per contact.
@@ -1418,12 +1726,25 @@ static int update_W_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   dim3 grid((m + 15) / 16, (m + 15) / 16);
+  cudaError_t e = cudaMemsetAsync(s->wcoup.p, 0, (size_t)m * sizeof(T), s->ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset wcoup");
   PDL("k_update_W", k_update_W<T>, grid, dim3(16, 16), 0, s->ctx->stream,
-      m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw);
+      m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw, (T*)s->wcoup.p);
   return ICR_OK;
 }
 
 int launch_update_W(Scene* s) { return s->prec == ICR_FP64 ? update_W_T<double>(s) : update_W_T<float>(s); }
+
+template <class T>
+static int wcoup_T(Scene* s) {
+  const int m = s->m;
+  if (m == 0) return ICR_OK;
+  PDL("k_wcoup", k_wcoup<T>, (unsigned)((m + 7) / 8), 256, 0, s->ctx->stream,
+      m, (const T*)s->W.p, s->ldw, (T*)s->wcoup.p);
+  return ICR_OK;
+}
+
+int launch_wcoup(Scene* s) { return s->prec == ICR_FP64 ? wcoup_T<double>(s) : wcoup_T<float>(s); }
 
 template <class T, int BC>
 static int pgs_T(Scene* s, int warm, int want_res) {
@@ -1449,9 +1770,9 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   }
   e = ensure_smem(k_pgs<T, BC>, pgs_lim, s->ctx->device, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
-  PDL("k_pgs", k_pgs<T, BC>, 1, 1024, smem, st,
+  PDL("k_pgs", k_pgs<T, BC>, 1, PGS_THREADS, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
-                                      (const T*)s->delta.p, (const T*)s->mu.p, (T*)s->lam.p, warm, ds);
+      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wcoup.p, (T*)s->lam.p, warm, ds);
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
     PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,
