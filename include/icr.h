@@ -64,7 +64,8 @@ enum icr_status {
 };
 
 enum icr_precision {
-  ICR_FP32 = 0,      /* L, X, W_H, W and the PGS sweeps in FP32; D^-1/2 applied in FP64 */
+  ICR_FP32 = 0,      /* L, X, W_H, W, the tangent frames and the PGS sweeps in FP32; gaps, p and u
+                        accumulated in FP64 */
   ICR_FP64 = 1       /* everything in FP64 */
 };
 

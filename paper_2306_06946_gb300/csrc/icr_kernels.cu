@@ -476,9 +476,11 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
   if (row >= n) return;
   const int s = dof_super[row];
   const int ncol = 3 * qcount[s];
-  const double ds = dinvsqrt[row];
+  // in the FP32 path D^-1/2 is rounded to FP32 first (one more rounding of
+  // the product, within an FP32 ulp; FP64 arithmetic is a slow path here)
+  const T ds = (T)dinvsqrt[row];
   T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
-  for (int c = lane; c < ncol; c += 32) F[c] = (T)(ds * (double)F[c]);
+  for (int c = lane; c < ncol; c += 32) F[c] *= ds;
 }
 
 // ------------------------------------------------------------------ a4 contraction
@@ -1517,24 +1519,35 @@ __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ 
 
 // ------------------------------------------------------------------ a9 corrective motion
 // y = D^-1 X u = D^-1/2 (Y u), one warp per DOF row (Y holds the scaled front
-// rows, restricted to the contacts reaching them)
+// rows, restricted to the contacts reaching them); u in the working precision
 template <class T>
 __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                      const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                      const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
-                     const double* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
+                     const T* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
   pdl_entry();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const int s = dof_super[row];
-  const int ncol = 3 * qcount[s];
+  const int nq = qcount[s];
   const T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
   const int* q = qidx + (size_t)s * m;
   T acc = T(0);
-  for (int c = lane; c < ncol; c += 32) acc += F[c] * (T)u[3 * q[c / 3] + c % 3];
+  for (int k = lane; k < nq; k += 32) {
+    const T* ua = u + 3 * q[k];
+    acc += F[3 * k] * ua[0] + F[3 * k + 1] * ua[1] + F[3 * k + 2] * ua[2];
+  }
   acc = warp_sum(acc);
   if (lane == 0) y[row] = (T)(dinvsqrt[row] * (double)acc);
+}
+
+// u in the working precision for k_xu
+template <class T>
+__global__ void k_u_round(int n3, const double* __restrict__ u, T* ut) {
+  pdl_entry();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n3) ut[i] = (T)u[i];
 }
 
 // Backward solve L^T dq = y for the supernodes of one level (top-down):
@@ -1561,7 +1574,11 @@ __global__ void __launch_bounds__(256)
 }
 
 // ------------------------------------------------------------------ linearisation
-// C rows n, t1, t2 and the gaps from the current proximity positions (FP64).
+// C rows n, t1, t2 and the gaps from the current proximity positions.  The
+// normal, the choice of the tangent axis and the normal gap are formed in
+// FP64 (the gap is a small difference of large distances); in the FP32 path
+// the tangent frame and the tangential gaps are formed in FP32, the precision
+// C and delta are stored in (FP64 arithmetic is a slow path on this part).
 template <class T>
 __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
                             const double* __restrict__ anchors, const double* __restrict__ spheres,
@@ -1570,20 +1587,30 @@ __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
-  double n0, n1, n2, dist = 0.0, radius = 0.0;
+  const double rx = px - anchors[3 * a], ry = py - anchors[3 * a + 1], rz = pz - anchors[3 * a + 2];
+  double n0, n1, n2, dn;
   if (kind == 1) {
     n0 = normals_k[3 * a];
     n1 = normals_k[3 * a + 1];
     n2 = normals_k[3 * a + 2];
+    dn = n0 * rx + n1 * ry + n2 * rz;
   } else {
     const double* sp = spheres + 4 * sphere_of[a];
-    radius = sp[3];
     const double dx = px - sp[0], dy = py - sp[1], dz = pz - sp[2];
-    dist = sqrt(dx * dx + dy * dy + dz * dz);
-    n0 = dx / dist;
-    n1 = dy / dist;
-    n2 = dz / dist;
+    const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+    if (sizeof(T) == 8) {
+      n0 = dx / dist;
+      n1 = dy / dist;
+      n2 = dz / dist;
+    } else {
+      const double inv = 1.0 / dist;
+      n0 = dx * inv;
+      n1 = dy * inv;
+      n2 = dz * inv;
+    }
+    dn = dist - sp[3];
   }
+  // tangent t1 = n x e, e the axis of the smallest |n| component; t2 = n x t1
   int ax = 0;
   double best = fabs(n0);
   if (fabs(n1) < best) {
@@ -1591,28 +1618,28 @@ __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_
     best = fabs(n1);
   }
   if (fabs(n2) < best) ax = 2;
-  const double e0 = ax == 0, e1 = ax == 1, e2 = ax == 2;
-  double t10 = n1 * e2 - n2 * e1, t11 = n2 * e0 - n0 * e2, t12 = n0 * e1 - n1 * e0;
-  const double nt = sqrt(t10 * t10 + t11 * t11 + t12 * t12);
+  const T m0 = (T)n0, m1 = (T)n1, m2 = (T)n2;
+  const T e0 = ax == 0, e1 = ax == 1, e2 = ax == 2;
+  T t10 = m1 * e2 - m2 * e1, t11 = m2 * e0 - m0 * e2, t12 = m0 * e1 - m1 * e0;
+  const T nt = sqrt(t10 * t10 + t11 * t11 + t12 * t12);
   t10 /= nt;
   t11 /= nt;
   t12 /= nt;
-  const double t20 = n1 * t12 - n2 * t11, t21 = n2 * t10 - n0 * t12, t22 = n0 * t11 - n1 * t10;
-  const double rx = px - anchors[3 * a], ry = py - anchors[3 * a + 1], rz = pz - anchors[3 * a + 2];
-  const double dn = kind == 1 ? n0 * rx + n1 * ry + n2 * rz : dist - radius;
+  const T t20 = m1 * t12 - m2 * t11, t21 = m2 * t10 - m0 * t12, t22 = m0 * t11 - m1 * t10;
+  const T qx = (T)rx, qy = (T)ry, qz = (T)rz;
   T* Ca = C + 9 * a;
-  Ca[0] = (T)n0;
-  Ca[1] = (T)n1;
-  Ca[2] = (T)n2;
-  Ca[3] = (T)t10;
-  Ca[4] = (T)t11;
-  Ca[5] = (T)t12;
-  Ca[6] = (T)t20;
-  Ca[7] = (T)t21;
-  Ca[8] = (T)t22;
+  Ca[0] = m0;
+  Ca[1] = m1;
+  Ca[2] = m2;
+  Ca[3] = t10;
+  Ca[4] = t11;
+  Ca[5] = t12;
+  Ca[6] = t20;
+  Ca[7] = t21;
+  Ca[8] = t22;
   delta[3 * a] = (T)dn;
-  delta[3 * a + 1] = (T)(t10 * rx + t11 * ry + t12 * rz);
-  delta[3 * a + 2] = (T)(t20 * rx + t21 * ry + t22 * rz);
+  delta[3 * a + 1] = t10 * qx + t11 * qy + t12 * qz;
+  delta[3 * a + 2] = t20 * qx + t21 * qy + t22 * qz;
 }
 
 // ------------------------------------------------------------------ launchers
@@ -1855,10 +1882,15 @@ static int correct_T(Scene* s) {
     if (e != cudaSuccess) return cuda_fail(e, "memset dq");
     return ICR_OK;
   }
+  const T* uw = (const T*)s->u.p;   // FP64: u as it is
+  if (sizeof(T) == 4) {
+    PDL("k_u_round", k_u_round<T>, (3 * m + 255) / 256, 256, 0, st, 3 * m, (const double*)s->u.p, (T*)s->uk.p);
+    uw = (const T*)s->uk.p;
+  }
   PDL("k_xu", k_xu<T>, (n + 7) / 8, 256, 0, st,
       n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
-                                       m, (const T*)s->X.p, s->ldx, (const double*)s->u.p, (const double*)s->dinvsqrt.p,
+                                       m, (const T*)s->X.p, s->ldx, uw, (const double*)s->dinvsqrt.p,
                                        (T*)s->y.p);
   for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
     const Level& lv = s->levels[l];
