@@ -352,7 +352,7 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super, &s->wcoup};
+                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super, &s->wcoup, &s->level_first};
   for (DBuf* b : all) dfree(s, *b);
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
@@ -619,6 +619,12 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   s->tuned = false;
   RET(dalloc(s, s->tc_super, ns));
   RET(upload_tc_super(s));
+  {
+    std::vector<int32_t> lf(nlev + 1, 0);
+    for (int l = 0; l < nlev; ++l) lf[l + 1] = levs[l].first + levs[l].count;
+    RET(dalloc(s, s->level_first, (nlev + 1) * sizeof(int32_t)));
+    RET(upload(s, s->level_first, lf.data(), nlev + 1));
+  }
   s->total_front_rows = frp[ns];
   s->wmax = wmax;
   s->rmax = rmax;
@@ -669,7 +675,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->bitmap, (size_t)ns * words * sizeof(uint32_t)));
   RET(dalloc(s, s->wprefix, (size_t)ns * words * sizeof(int32_t)));
   RET(dalloc(s, s->qcount, ns * sizeof(int32_t)));
-  RET(dalloc(s, s->plan, ((size_t)PLAN_LISTS * (ns + 1) + 2 + s->levels.size()) * sizeof(int32_t)));
+  RET(dalloc(s, s->plan, ((size_t)PLAN_LISTS * (ns + 1) + 3 + 2 * s->levels.size()) * sizeof(int32_t)));
   RET(dalloc(s, s->qidx, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qpos, (size_t)ns * mm * sizeof(int32_t)));
   RET(dalloc(s, s->qinv, (size_t)ns * mm * sizeof(int32_t)));

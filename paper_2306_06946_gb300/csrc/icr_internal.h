@@ -51,6 +51,16 @@ constexpr int TC_TILE = 128;         // tensor-core output tile (M = N)
 constexpr int TC_KT = 32;            // front rows per packed operand block
 constexpr int TC_GEMM_MIN_W = 64;    // fronts at least this wide ...
 constexpr int TC_GEMM_MIN_COLS = 64; // ... and with this many columns take the tensor-core forward solve
+constexpr int TC_PART_KB = 4;        // fewest K blocks in a part of a split tensor-core unit
+constexpr int TC_MAX_SPLIT = 8;      // most K parts of a tensor-core unit
+constexpr int PLAN_MAX_LEV = 128;    // levels with their own K split (deeper ones are not split)
+// K parts of a tensor-core unit over nk K blocks, given the split factor of
+// its list (k_plan: about one unit per SM when the list has few tiles)
+__host__ __device__ inline int tc_parts(int split, int nk) {
+  const int most = nk / TC_PART_KB;
+  const int n = split < most ? split : most;
+  return n < 1 ? 1 : n;
+}
 
 // Per-level launch geometry of the supernodal elimination tree.
 struct Level {
@@ -86,7 +96,8 @@ struct Scene {
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, y, dq, stats;
   DBuf wcoup;   // per contact: max |W[3a, j]| over the other contacts' columns j
-  DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, then 2 + levels counters (int32)
+  DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, 2 + levels counters, levels + 1 K splits (int32)
+  DBuf level_first;   // (levels + 1) offsets of the levels in level_list
   DBuf Gpk, gpk_off;   // G_s of the wide supernodes as 3xTF32 operand blocks; first block per supernode
   // forward-solve engine per etree level: 1 puts the level's wide fronts on the
   // tensor cores (chosen by icr_autotune), mirrored per supernode for the planner

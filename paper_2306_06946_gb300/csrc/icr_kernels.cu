@@ -188,11 +188,15 @@ __device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
 // columns when tc_gemm is set and the supernode's level runs on the tensor
 // cores (tc_super), on CUDA cores otherwise; SIMT contraction tile
 // pairs of fronts narrower than simt_max columns; packed operand blocks and
-// tensor-core tile pairs of fronts at least tc_min columns wide.
+// tensor-core tile pairs of fronts at least tc_min columns wide.  Tensor-core
+// units are split over K into tc_parts(gsplit or tsplit, K blocks) parts
+// (gsplit: the level's front GEMM, tsplit: the contraction; 0 counts the
+// unsplit tiles).
 __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super_ptr,
                                             const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount,
                                             int simt_max, int tc_min, int tc_gemm,
-                                            const unsigned char* __restrict__ tc_super, int* c) {
+                                            const unsigned char* __restrict__ tc_super, int gsplit, int tsplit,
+                                            int* c) {
   const int q = qcount[s];
   const int w = super_ptr[s + 1] - super_ptr[s];
   const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
@@ -201,33 +205,64 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
   const bool tcg = tc_gemm && tc_super[s] && q > 0 && w >= TC_GEMM_MIN_W && ncol >= TC_GEMM_MIN_COLS;
   c[PLAN_ASM] = cdiv(nrows, AR) * nt;
   c[PLAN_GEMM] = tcg ? 0 : cdiv(nrows, GR) * nt;
-  c[PLAN_GTC] = tcg ? cdiv(nrows, TC_TILE) * cdiv(ncol, TC_TILE) : 0;
+  const int nkb = cdiv(w, TC_KT);   // K blocks of a tensor-core unit
+  c[PLAN_GTC] = tcg ? cdiv(nrows, TC_TILE) * cdiv(ncol, TC_TILE) * tc_parts(gsplit, nkb) : 0;
   c[PLAN_FPACK] = tcg ? cdiv(ncol, TC_TILE) * cdiv(w, TC_KT) : 0;
   const int ns_ = cdiv(ncol, CT);
   c[PLAN_SIMT] = (q > 0 && ncol < simt_max) ? ns_ * (ns_ + 1) / 2 : 0;
   const int nI = cdiv(ncol, TC_TILE);
   const bool tc = q > 0 && ncol >= tc_min;
   c[PLAN_PACK] = tc ? nI * cdiv(w, TC_KT) : 0;
-  c[PLAN_TC] = tc ? nI * (nI + 1) / 2 : 0;
+  c[PLAN_TC] = tc ? nI * (nI + 1) / 2 * tc_parts(tsplit, nkb) : 0;
 }
 
 // One block: exclusive prefix sums of the per-supernode unit counts over the
-// positions of level_list, and the scheduling counters reset to zero.
+// positions of level_list, and the scheduling counters reset to zero.  First
+// the K split factors: a level's tensor-core front GEMM, and the
+// tensor-core contraction, with fewer tiles than target (one per SM) split
+// their units over K into about target / tiles parts (plan counters area,
+// after the 2 + nlev counters: nlev level factors, then the contraction's).
 __global__ void __launch_bounds__(1024)
     k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
            const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
-           int tc_gemm, const unsigned char* __restrict__ tc_super, int ncounters, int* plan) {
+           int tc_gemm, const unsigned char* __restrict__ tc_super, const int* __restrict__ level_first, int nlev,
+           int target, int* plan) {
   pdl_entry();
   __shared__ int wsum[PLAN_LISTS][32];
+  __shared__ int tiles[PLAN_MAX_LEV + 1];   // unsplit tensor-core tiles per level; [PLAN_MAX_LEV]: contraction
+  __shared__ int split[PLAN_MAX_LEV + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int per = cdiv(ns, blockDim.x);
   const int p0 = min(ns, tid * per), p1 = min(ns, p0 + per);
+  const int nl = min(nlev, PLAN_MAX_LEV);
+  for (int l = tid; l <= PLAN_MAX_LEV; l += blockDim.x) tiles[l] = 0;
+  __syncthreads();
+  int lv0 = 0;   // level of position p0
+  while (lv0 + 1 < nlev && level_first[lv0 + 1] <= p0) ++lv0;
+  for (int p = p0, lv = lv0; p < p1; ++p) {
+    while (lv + 1 < nlev && level_first[lv + 1] <= p) ++lv;
+    int c[PLAN_LISTS];
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, 1, 1, c);
+    if (c[PLAN_GTC] && lv < nl) atomicAdd(&tiles[lv], c[PLAN_GTC]);
+    if (c[PLAN_TC]) atomicAdd(&tiles[PLAN_MAX_LEV], c[PLAN_TC]);
+  }
+  __syncthreads();
+  for (int l = tid; l <= PLAN_MAX_LEV; l += blockDim.x) {
+    const int t = tiles[l];
+    split[l] = t > 0 ? max(1, min(TC_MAX_SPLIT, target / t)) : 1;
+  }
+  __syncthreads();
+  int* splits = plan + PLAN_LISTS * (ns + 1) + 2 + nlev;
+  for (int l = tid; l <= nlev; l += blockDim.x) splits[l] = l == nlev ? split[PLAN_MAX_LEV] : (l < nl ? split[l] : 1);
+  const int tsplit = split[PLAN_MAX_LEV];
   int tot[PLAN_LISTS];
 #pragma unroll
   for (int l = 0; l < PLAN_LISTS; ++l) tot[l] = 0;
-  for (int p = p0; p < p1; ++p) {
+  for (int p = p0, lv = lv0; p < p1; ++p) {
+    while (lv + 1 < nlev && level_first[lv + 1] <= p) ++lv;
     int c[PLAN_LISTS];
-    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, c);
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super,
+                lv < nl ? split[lv] : 1, tsplit, c);
 #pragma unroll
     for (int l = 0; l < PLAN_LISTS; ++l) tot[l] += c[l];
   }
@@ -261,16 +296,18 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
 #pragma unroll
   for (int l = 0; l < PLAN_LISTS; ++l) off[l] += wsum[l][warp];
-  for (int p = p0; p < p1; ++p) {
+  for (int p = p0, lv = lv0; p < p1; ++p) {
+    while (lv + 1 < nlev && level_first[lv + 1] <= p) ++lv;
     int c[PLAN_LISTS];
-    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, c);
+    plan_counts(level_list[p], super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super,
+                lv < nl ? split[lv] : 1, tsplit, c);
 #pragma unroll
     for (int l = 0; l < PLAN_LISTS; ++l) {
       plan[l * (ns + 1) + p] = off[l];
       off[l] += c[l];
     }
   }
-  for (int i = tid; i < ncounters; i += blockDim.x) plan[PLAN_LISTS * (ns + 1) + i] = 0;
+  for (int i = tid; i < 2 + nlev; i += blockDim.x) plan[PLAN_LISTS * (ns + 1) + i] = 0;
 }
 
 // Entry (row, column 3*kl + d) of supernode s's front: its H^T entry (rows < w)
@@ -1692,7 +1729,8 @@ static int build_WH_T(Scene* s) {
   PDL("k_plan", k_plan, 1, 1024, 0, st,
       ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
                              (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, tc_gemm,
-                             (const unsigned char*)s->tc_super.p, 2 + nlev, plan);
+                             (const unsigned char*)s->tc_super.p, (const int*)s->level_first.p, nlev,
+                             s->ctx->sm_count, plan);
   const int nsm = s->ctx->sm_count;
   const int ntiles = (m + TCC - 1) / TCC;
   for (int li = 0; li < nlev; ++li) {

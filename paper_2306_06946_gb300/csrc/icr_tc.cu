@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(256)
     k_pack_tc(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
               const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
-              int from_ftop, int64_t ldx, unsigned char* pk) {
+              int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
   pdl_entry();
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
@@ -181,10 +181,14 @@ __global__ void __launch_bounds__(256)
     const int local = u - plan[pos];
     const int I = local / nk, kt = local % nk;
     const float* Ys = src + (from_ftop ? (int64_t)super_ptr[s] : fr_ptr[s]) * ldx;
+    // F_top: the product's rows < w (X_s) are accumulated over K parts
+    float* Xz = from_ftop ? X + fr_ptr[s] * ldx : nullptr;
     for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
       const int k = e / TM, r = e % TM;
       const int row = kt * KT + k, col = I * TM + r;
-      sy[k][r] = (row < w && col < ncol) ? Ys[(int64_t)row * ldx + col] : 0.f;
+      const bool in = row < w && col < ncol;
+      sy[k][r] = in ? Ys[(int64_t)row * ldx + col] : 0.f;
+      if (Xz && in) Xz[(int64_t)row * ldx + col] = 0.f;
     }
     __syncthreads();
     unsigned char* blk = pk + (boff[s] + (int64_t)I * nk + kt) * (int64_t)(TR::PARTS * tile_bytes<MODE>());
@@ -413,17 +417,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
                   const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
-                  int64_t ldw, int* dev_err) {
+                  int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p) {
   pdl_entry();
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
-  extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block)
+  extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block), then the list's prefix
   __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
   __shared__ int ok_sh, unit_sh;
   const int total = plan[ns];
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tsplit = *tsplit_p;
+  // the unit search reads the list's prefix sums from shared memory when they fit
+  const int* plan_s = plan;
+  if (cache_plan) {
+    int* ps = reinterpret_cast<int*>(smem + STAGES * 2 * BLK);
+    for (int i = tid; i <= ns; i += TC_THREADS) ps[i] = plan[i];
+    plan_s = ps;
+  }
   tc_setup(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
@@ -433,28 +445,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int ur = unit_sh;
     if (ur >= total || !ok_sh) break;   // uniform
     const int u = total - 1 - ur;
-    const int pos = find_unit(plan, 0, ns, u);
+    const int pos = find_unit(plan_s, 0, ns, u);
     const int s = level_list[pos];
     const int ncol = 3 * qcount[s];
     const int nI = (ncol + TM - 1) / TM;
-    int rem = u - plan[pos], I = 0;
+    const int w = super_ptr[s + 1] - super_ptr[s];
+    const int nk = (w + KT - 1) / KT;
+    const int nsk = tc_parts(tsplit, nk);   // unit = (tile pair, K part)
+    const int kc = (u - plan_s[pos]) % nsk;
+    int rem = (u - plan_s[pos]) / nsk, I = 0;
     while (rem >= nI - I) {
       rem -= nI - I;
       ++I;
     }
     const int J = I + rem;
-    const int w = super_ptr[s + 1] - super_ptr[s];
-    const int nk = (w + KT - 1) / KT;
+    const int k0 = kc * nk / nsk, nku = (kc + 1) * nk / nsk - k0;
     if (warp == 4) {
-      if (lane == 0 &&
-          !tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk) * BLK, pk + (boff[s] + (int64_t)J * nk) * BLK, I == J,
-                            nk, smem, br, tmem, gl, gm, gc)) {
+      if (lane == 0 && !tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK,
+                                         pk + (boff[s] + (int64_t)J * nk + k0) * BLK, I == J, nku, smem, br, tmem,
+                                         gl, gm, gc)) {
         ok_sh = 0;
         atomicExch(dev_err, 1);
       }
     } else {
       float acc[TM];
-      if (tc_drain(nk, br, tmem, warp, lane, gc, acc)) {
+      if (tc_drain(nku, br, tmem, warp, lane, gc, acc)) {
         const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
         if (li < ncol) {
           const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
@@ -487,7 +502,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                     const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
                     const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
-                    int* dev_err) {
+                    int* dev_err, const int* __restrict__ gsplit_p) {
   pdl_entry();
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
@@ -498,6 +513,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int u0 = plan[pa], total = plan[pb] - u0;
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gsplit = *gsplit_p;
   tc_setup(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
@@ -511,24 +527,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int s = level_list[pos];
     const int ncol = 3 * qcount[s];
     const int nJ = (ncol + TM - 1) / TM;
-    const int local = u - plan[pos];
-    const int rt = local / nJ, ct = local % nJ;
     const int w = super_ptr[s + 1] - super_ptr[s];
     const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
     const int nk = (w + KT - 1) / KT;
+    const int nsk = tc_parts(gsplit, nk);   // unit = (tile, K part)
+    const int local = (u - plan[pos]) / nsk, kc = (u - plan[pos]) % nsk;
+    const int rt = local / nJ, ct = local % nJ;
+    const int k0 = kc * nk / nsk, nku = (kc + 1) * nk / nsk - k0;
     if (warp == 4) {
-      if (lane == 0 && !tc_produce<MODE>(gpk + (goff[s] + (int64_t)rt * nk) * BLK,
-                                         fpk + (boff[s] + (int64_t)ct * nk) * BLK, false, nk, smem, br, tmem, gl, gm,
-                                         gc)) {
+      if (lane == 0 && !tc_produce<MODE>(gpk + (goff[s] + (int64_t)rt * nk + k0) * BLK,
+                                         fpk + (boff[s] + (int64_t)ct * nk + k0) * BLK, false, nku, smem, br, tmem,
+                                         gl, gm, gc)) {
         ok_sh = 0;
         atomicExch(dev_err, 1);
       }
     } else {
       float acc[TM];
-      if (tc_drain(nk, br, tmem, warp, lane, gc, acc)) {
+      if (tc_drain(nku, br, tmem, warp, lane, gc, acc)) {
         const int row = rt * TM + 32 * warp + lane;   // front row owned by this thread
         const int cmax = ncol - ct * TM;              // columns of this tile inside the front
-        if (row < nrows) {
+        if (row < nrows && nsk > 1) {
+          // K parts add up: X_s (zeroed when F_top was packed) += out, U_s -= out
+          float* F = X + (fr_ptr[s] + row) * ldx + ct * TM;
+          const float sg = row < w ? 1.f : -1.f;
+#pragma unroll
+          for (int c0j = 0; c0j < TM; c0j += 4) {
+            if (c0j >= cmax) break;
+            if (c0j + 4 <= cmax) {
+              atomicAdd((float4*)(F + c0j),
+                        make_float4(sg * acc[c0j], sg * acc[c0j + 1], sg * acc[c0j + 2], sg * acc[c0j + 3]));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                if (c0j + j < cmax) atomicAdd(F + c0j + j, sg * acc[c0j + j]);
+            }
+          }
+        } else if (row < nrows) {
           float* F = X + (fr_ptr[s] + row) * ldx + ct * TM;
 #pragma unroll
           for (int c0j = 0; c0j < TM; c0j += 4) {
@@ -569,7 +603,10 @@ template <int MODE>
 int contract_tc_T(Scene* s) {
   const int m = s->m, ns = s->ns;
   const int64_t nr = 3 * (int64_t)m;
-  const size_t smem = tc_smem_bytes<MODE>();
+  // the ring, then the contraction list's prefix sums (up to 24 KiB of them)
+  const size_t ring = (size_t)STAGES * 2 * TcTraits<MODE>::PARTS * tile_bytes<MODE>();
+  const int cache_plan = (ns + 1) * (int)sizeof(int) <= 24 * 1024;
+  const size_t smem = std::max(tc_smem_bytes<MODE>(), ring + (cache_plan ? (size_t)(ns + 1) * sizeof(int) : 0));
   static SmemLimit lim;
   static DevInt occ_dev;
   const int dev = s->ctx->device;
@@ -589,12 +626,14 @@ int contract_tc_T(Scene* s) {
   PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_PACK * (ns + 1), 0, ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p, 0,
-      s->ldx, (unsigned char*)s->Ypk.p);
-  const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2;
+      s->ldx, (unsigned char*)s->Ypk.p, (float*)nullptr);
+  const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2 * TC_MAX_SPLIT;
+  const int nlev = (int)s->levels.size();
   PDL("k_contract_tc", k_contract_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_TC, ns, (const int*)s->level_list.p,
       (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
-      (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p);
+      (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p, cache_plan,
+      plan + PLAN_LISTS * (ns + 1) + 2 + 2 * nlev);
   return ICR_OK;
 }
 
@@ -634,14 +673,15 @@ int launch_front_gemm_tc(Scene* s, int level) {
   PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_FPACK * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->Ftop.p, 1,
-      s->ldx, (unsigned char*)s->Ypk.p);
-  const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax;
+      s->ldx, (unsigned char*)s->Ypk.p, (float*)s->X.p);
+  const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax * TC_MAX_SPLIT;
+  const int nlev = (int)s->levels.size();
   PDL("k_front_gemm_tc", k_front_gemm_tc, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_GTC * (ns + 1), pa, pb, plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_GTC + level,
       (const int*)s->level_list.p, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->gpk_off.p,
       (const unsigned char*)s->Gpk.p, (const int64_t*)s->tc_boff.p, (const unsigned char*)s->Ypk.p, (float*)s->X.p,
-      s->ldx, (int*)s->dev_err.p);
+      s->ldx, (int*)s->dev_err.p, plan + PLAN_LISTS * (ns + 1) + 2 + nlev + level);
   return ICR_OK;
 }
 
