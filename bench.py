@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--modes", default="simt,tf32x3,tf32,bf16", help="precision_c3: FP32 contraction modes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nvtx-step", action="store_true",
+                    help="after the timed steps, replay one more step inside an NVTX range named 'step' "
+                         "(for a per-step kernel list: ncu --nvtx --nvtx-include step/)")
     return ap.parse_args()
 
 
@@ -321,6 +324,11 @@ def run_icr(args):
     if dist is not None:
         dist.barrier()
     launches = sc.launches() - l0
+    if args.nvtx_step:
+        torch.cuda.nvtx.range_push("step")
+        step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(ms)
     if dist is not None:

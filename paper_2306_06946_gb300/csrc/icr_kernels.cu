@@ -693,19 +693,23 @@ __global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wcoup) {
 }
 
 // ------------------------------------------------------------------ a7 PGS
-// One CTA of 1024 threads.  The residual r = delta + W lambda~ of every row is
-// kept in shared memory.  Contacts are taken in blocks of BC; for each block,
-// with one barrier per block:
+// One CTA of PGS_THREADS threads.  The residual r = delta + W lambda~ of every
+// row is kept in shared memory.  Contacts are taken in blocks of BC; for each
+// block, with one barrier per block:
 //       warp 0 runs the block's contacts in order (lane = contact); the lane
 //       of contact i solves it and every lane folds the change into its own
-//       residual and into the next block's contact of the same lane, while warps
-//       1..31 fold the previous block's non-zero changes into all other
+//       residual and into the next block's contact of the same lane, while the
+//       other warps fold the previous block's non-zero changes into all other
 //       residuals (streaming those rows of W) and prefetch, with cp.async,
 //       the next block's rows of W (its diagonal block and the block to its right).
 // A block whose contacts all have lambda~ = 0 and non-negative normal
 // residuals is a no-op and is passed without reading W.  After a block that
 // changed nothing every residual is complete, so the CTA looks ahead (one
 // warp per block) and jumps over the run of no-op blocks that follows.
+// With every residual complete, sweeps may visit only the blocks that can
+// change (S-only sweeps, pgs_defer_enter), folding their changes into the
+// other rows later in one pass, while a bound shows that no other contact
+// can change.
 // The solve stops when eps <= tol (tol > 0) or after a sweep that changed
 // nothing, a fixed point of the iteration (Alg. 1's test with PGS_error = 0).
 // Visiting order, residual definition and local rule are those of Eq. "PGS"
