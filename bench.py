@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--modes", default="simt,tf32x3,tf32,bf16", help="precision_c3: FP32 contraction modes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tc-levels", default=None,
+                    help="liver_c1: comma list, per etree level (leaves first) 1 = forward solve on tcgen05; "
+                         "fixes the plan instead of autotuning (a profiler distorts the autotuner's timings)")
     ap.add_argument("--nvtx-step", action="store_true",
                     help="after the timed steps, replay one more step inside an NVTX range named 'step' "
                          "(for a per-step kernel list: ncu --nvtx --nvtx-include step/)")
@@ -298,7 +301,12 @@ def run_icr(args):
     # one time step (reset p and u, W_H build, n_newton x (linearise, W update,
     # PGS from zero, proximity update), corrective motion), captured once as a
     # CUDA graph after the per-level engine choice and replayed each step
-    tc_levels = sc.autotune()
+    if args.tc_levels:
+        plan = [int(x) for x in args.tc_levels.split(",")]
+        sc.set_forward_plan(plan)
+        tc_levels = int(sum(plan))
+    else:
+        tc_levels = sc.autotune()
     sc.step_capture(scene.n_newton)
 
     def step():
@@ -474,7 +482,7 @@ def run_icr(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {**workload_config(scene), "parallelism": f"replicas x{world}",
                        "execution": f"captured step graph replayed per step; forward solve on tcgen05 in "
-                                    f"{tc_levels} etree levels (autotuned), CUDA cores elsewhere"},
+                                    f"{tc_levels} etree levels ({'fixed' if args.tc_levels else 'autotuned'}), CUDA cores elsewhere"},
             "latency_ms": {"p50": float(statistics.median(ms)),
                            "p99": float(ms_sorted[int(round(0.99 * (len(ms) - 1)))])},
             "phase_ms": phase_ms,
