@@ -167,8 +167,11 @@ __global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __
 // order).  Rows < w go to Ftop, rows >= w to the front's update rows.
 static constexpr int AR = 4;   // front rows per assembly block
 
-// largest position p in [lo, hi) with P[p] <= u, for a non-decreasing prefix
-// array P with P[lo] <= u < P[hi]: the supernode that owns work unit u
+
+__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// The position p in [lo, hi) with P[p] <= u < P[p + 1], for a non-decreasing
+// prefix array P with P[lo] <= u < P[hi]: the supernode that owns work unit u.
 __device__ __forceinline__ int find_pos(const int* __restrict__ P, int lo, int hi, int u) {
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -180,7 +183,18 @@ __device__ __forceinline__ int find_pos(const int* __restrict__ P, int lo, int h
   return lo;
 }
 
-__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
+// find_pos by the whole block, for kernels with few, large units: thread t
+// tests position lo + t (+ multiples of the block size), one round of loads
+// instead of log2 dependent ones.  Block-uniform call; sh is a shared int.
+__device__ __forceinline__ int block_find_pos(const int* __restrict__ P, int lo, int hi, int u, int* sh) {
+  const int nt = blockDim.x * blockDim.y, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  for (int p = lo + tid; p < hi; p += nt)
+    if (P[p] <= u && u < P[p + 1]) *sh = p;   // exactly one p: P non-decreasing, P[lo] <= u < P[hi]
+  __syncthreads();
+  const int r = *sh;
+  __syncthreads();   // sh is reused by the next search
+  return r;
+}
 
 // Work units per supernode for the lists of one build (PlanList order):
 // assembly tiles; front-GEMM tiles, on the tensor cores (with their packed
@@ -483,9 +497,10 @@ __global__ void __launch_bounds__(256)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sG = (T*)smraw;                 // 2 x KB x GLD
   T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
+  __shared__ int pos_sh;
   const int u1 = plan[pb];
   for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {   // block-uniform
-    const int pos = find_pos(plan, pa, pb, u);
+    const int pos = block_find_pos(plan, pa, pb, u, &pos_sh);
     const int s = level_list[pos];
     const int nq = qcount[s];
     const int local = u - plan[pos];
@@ -536,7 +551,7 @@ __global__ void __launch_bounds__(256)
   pdl_entry();
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
-  __shared__ int unit_sh;
+  __shared__ int unit_sh, pos_sh;
   const int total = plan[ns];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (;;) {
@@ -546,7 +561,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (ur >= total) break;
     const int u = total - 1 - ur;
-    const int pos = find_pos(plan, 0, ns, u);
+    const int pos = block_find_pos(plan, 0, ns, u, &pos_sh);
     const int s = level_list[pos];
     const int ncol = 3 * qcount[s];
     const int nt = cdiv(ncol, CT);
