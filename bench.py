@@ -411,17 +411,17 @@ def run_icr(args):
         h_dq = pin(np.zeros(scene.n), np.float64)
         h_spheres = pin(np.concatenate([scene.obstacle.centers, scene.obstacle.radii[:, None]], axis=1), np.float64)
         h_tool = pin(scene.obstacle.tool, np.int32)
-        h2d = (h_nodes.nbytes + h_bary.nbytes + h_p0.nbytes + h_anch.nbytes + h_mu.nbytes + h_spheres.nbytes
-               + h_tool.nbytes)
+        # one staged copy per step (icr_set_step_inputs): nodes, sphere ids, bary and mu
+        # in FP32, p0, anchors and spheres in FP64, each part 16-byte aligned
+        al = lambda x: (x + 15) // 16 * 16
+        m_, ns_ = scene.m, h_spheres.shape[0]
+        h2d = al(16 * m_) + al(4 * m_) + al(16 * m_) + al(4 * m_) + al(24 * m_) + al(24 * m_) + al(32 * ns_)
         d2h = h_dq.nbytes
 
         # each step: the step's inputs from pinned host buffers, the captured
         # step graph (it reads the scene's buffers), the corrective motion back
         def e2e_step():
-            sc.set_mapping(h_nodes, h_bary)
-            sc.set_proximity(h_p0)
-            sc.set_obstacle_spheres(h_spheres, h_tool, h_anch)
-            sc.set_field("MU", h_mu)
+            sc.set_step_inputs(h_nodes, h_bary, h_p0, h_mu, h_spheres, h_tool, h_anch)
             sc.step_launch()
             sc.get("DQ", out=h_dq)
 

@@ -200,6 +200,18 @@ int icr_set_obstacle_sphere(icr_scene* scene, const double* center, double radiu
  * n_spheres = 1.  Copies its inputs; ICR_EINVAL on a bad radius or index. */
 int icr_set_obstacle_spheres(icr_scene* scene, int32_t n_spheres, const double* spheres,
                              const int32_t* contact_sphere, const double* anchors);
+/* A time step's inputs in one call: the same as icr_set_mapping(m, nodes,
+ * bary), icr_set_proximity(p0), icr_set_obstacle_spheres(n_spheres, spheres,
+ * contact_sphere, anchors) and icr_set_field(ICR_FIELD_MU, mu), with the same
+ * checks and errors.  When the scene already holds m contacts and n_spheres
+ * spheres, the inputs travel in one host-to-device copy through a pinned
+ * staging buffer of the scene (two slots; a slot is reused only after its
+ * previous copy has completed) and one kernel resets the contact state, so a
+ * captured step graph stays valid; otherwise it makes the four calls.  The
+ * host arrays may be released when the call returns. */
+int icr_set_step_inputs(icr_scene* scene, int32_t m, const int32_t* nodes, const double* bary, const double* p0,
+                        const double* mu, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
+                        const double* anchors);
 int icr_linearize(icr_scene* scene, int32_t k);
 
 /* W_H = H A^-1 H^T = X^T D^-1 X with X = L^-1 H^T (Eq. "schur complemnt

@@ -354,6 +354,14 @@ int icr_scene_destroy(icr_scene* s) {
                  &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
                  &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super, &s->wcoup, &s->level_first};
   for (DBuf* b : all) dfree(s, *b);
+  if (s->stage_dev.p) {
+    cudaFree(s->stage_dev.p);
+    s->ctx->in_use -= s->stage_dev.bytes;
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (s->stage_host[k]) cudaFreeHost(s->stage_host[k]);
+    if (s->stage_ev[k]) cudaEventDestroy(s->stage_ev[k]);
+  }
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
@@ -633,8 +641,8 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   return ICR_OK;
 }
 
-int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double* bary) {
-  RET(check_scene(s));
+// the checks of icr_set_mapping
+static int check_mapping(const Scene* s, int32_t m, const int32_t* nodes, const double* bary) {
   if (!s->has_system) {
     set_error("set_mapping: call icr_set_system first");
     return ICR_ESTATE;
@@ -663,6 +671,12 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
       return ICR_EINVAL;
     }
   }
+  return ICR_OK;
+}
+
+int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double* bary) {
+  RET(check_scene(s));
+  RET(check_mapping(s, m, nodes, bary));
   RET(set_device(s));
   const int ns = s->ns;
   const int words = std::max(1, (m + 31) / 32);
@@ -857,11 +871,9 @@ int icr_set_obstacle_plane(icr_scene* s, int32_t n_iters, const double* normals,
   return ICR_OK;
 }
 
-int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
-                             const double* anchors) {
-  RET(check_scene(s));
-  RET(need_mapping(s, "set_obstacle_spheres"));
-  const int m = s->m;
+// the checks of icr_set_obstacle_spheres for m contacts
+static int check_spheres(int m, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
+                         const double* anchors) {
   if (n_spheres <= 0 || !spheres || (m && (!anchors || !contact_sphere))) {
     set_error("set_obstacle_spheres: need n_spheres > 0, the spheres, each contact's sphere and anchors");
     return ICR_EINVAL;
@@ -878,6 +890,15 @@ int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* sphe
       set_error("set_obstacle_spheres: contact %d names sphere %d of %d", a, contact_sphere[a], n_spheres);
       return ICR_EINVAL;
     }
+  return ICR_OK;
+}
+
+int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
+                             const double* anchors) {
+  RET(check_scene(s));
+  RET(need_mapping(s, "set_obstacle_spheres"));
+  const int m = s->m;
+  RET(check_spheres(m, n_spheres, spheres, contact_sphere, anchors));
   RET(set_device(s));
   RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)m * 3) * sizeof(double)));
   RET(dalloc(s, s->obst_spheres, (size_t)n_spheres * 4 * sizeof(double)));
@@ -885,6 +906,106 @@ int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* sphe
   RET(upload(s, s->obst_anchors, anchors, (size_t)m * 3));
   RET(upload(s, s->obst_spheres, spheres, (size_t)n_spheres * 4));
   if (m) RET(upload(s, s->obst_of, contact_sphere, (size_t)m));
+  s->obst_kind = 2;
+  s->obst_iters = 0;
+  return ICR_OK;
+}
+
+int icr_set_step_inputs(icr_scene* s, int32_t m, const int32_t* nodes, const double* bary, const double* p0,
+                        const double* mu, int32_t n_spheres, const double* spheres, const int32_t* contact_sphere,
+                        const double* anchors) {
+  RET(check_scene(s));
+  const bool fast = s->has_mapping && m > 0 && m == s->m && n_spheres > 0 && s->obst_kind == 2 &&
+                    s->obst_spheres.bytes >= (size_t)n_spheres * 4 * sizeof(double) &&
+                    s->W_zeroed == s->W.gen && s->W_zeroed_ld == s->ldw && s->W_zeroed_rows == 3 * (int64_t)m;
+  if (!fast) {
+    RET(icr_set_mapping(s, m, nodes, bary));
+    RET(icr_set_proximity(s, p0));
+    RET(icr_set_obstacle_spheres(s, n_spheres, spheres, contact_sphere, anchors));
+    return icr_set_field(s, ICR_FIELD_MU, mu, (size_t)m * sizeof(double));
+  }
+  RET(check_mapping(s, m, nodes, bary));
+  if (!p0 || !mu) {
+    set_error("set_step_inputs: p0 and mu must not be NULL");
+    return ICR_EINVAL;
+  }
+  for (int i = 0; i < 3 * m; ++i)
+    if (!std::isfinite(p0[i])) {
+      set_error("set_proximity: p[%d] is not finite", i);
+      return ICR_EINVAL;
+    }
+  RET(check_spheres(m, n_spheres, spheres, contact_sphere, anchors));
+  for (int a = 0; a < m; ++a)
+    if (!std::isfinite(mu[a])) {
+      set_error("set_field: value %d is not finite", a);
+      return ICR_EINVAL;
+    }
+  RET(set_device(s));
+  // staging layout (bytes, 16-byte aligned parts): nodes, sphere ids, bary, mu, p0, anchors, spheres
+  const size_t T = s->tsize;
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  int64_t off[7];
+  off[0] = 0;
+  off[1] = (int64_t)al((size_t)off[0] + 16 * (size_t)m);
+  off[2] = (int64_t)al((size_t)off[1] + 4 * (size_t)m);
+  off[3] = (int64_t)al((size_t)off[2] + 4 * T * (size_t)m);
+  off[4] = (int64_t)al((size_t)off[3] + T * (size_t)m);
+  off[5] = (int64_t)al((size_t)off[4] + 24 * (size_t)m);
+  off[6] = (int64_t)al((size_t)off[5] + 24 * (size_t)m);
+  const size_t total = al((size_t)off[6] + 32 * (size_t)n_spheres);
+  if (s->stage_bytes < total) {
+    for (int k = 0; k < 2; ++k) {
+      if (s->stage_used[k]) CK(cudaEventSynchronize(s->stage_ev[k]));
+      if (s->stage_host[k]) cudaFreeHost(s->stage_host[k]);
+      s->stage_host[k] = nullptr;
+      s->stage_used[k] = false;
+      if (!s->stage_ev[k]) CK(cudaEventCreateWithFlags(&s->stage_ev[k], cudaEventDisableTiming));
+    }
+    CK(cudaStreamSynchronize(s->ctx->stream));   // the device buffer may be in use
+    if (s->stage_dev.p) {
+      cudaFree(s->stage_dev.p);
+      s->ctx->in_use -= s->stage_dev.bytes;
+      s->stage_dev.p = nullptr;
+      s->stage_dev.bytes = 0;
+      s->stage_bytes = 0;
+    }
+    // outside dalloc: a captured step graph does not read it, so it stays valid
+    Ctx* c = s->ctx;
+    if (c->budget && c->in_use + total > c->budget) {
+      set_error("set_step_inputs: staging %zu bytes exceeds the context HBM budget", total);
+      return ICR_ENOMEM;
+    }
+    CK(cudaMalloc(&s->stage_dev.p, total));
+    s->stage_dev.bytes = total;
+    s->ctx->in_use += total;
+    for (int k = 0; k < 2; ++k) CK(cudaHostAlloc((void**)&s->stage_host[k], total, cudaHostAllocDefault));
+    s->stage_bytes = total;
+  }
+  const int slot = s->stage_slot;
+  s->stage_slot ^= 1;
+  if (s->stage_used[slot]) CK(cudaEventSynchronize(s->stage_ev[slot]));   // its last copy has left
+  unsigned char* h = s->stage_host[slot];
+  std::memcpy(h + off[0], nodes, 16 * (size_t)m);
+  std::memcpy(h + off[1], contact_sphere, 4 * (size_t)m);
+  if (s->prec == ICR_FP64) {
+    std::memcpy(h + off[2], bary, 32 * (size_t)m);
+    std::memcpy(h + off[3], mu, 8 * (size_t)m);
+  } else {
+    float* b = (float*)(h + off[2]);
+    for (int i = 0; i < 4 * m; ++i) b[i] = (float)bary[i];
+    float* u = (float*)(h + off[3]);
+    for (int i = 0; i < m; ++i) u[i] = (float)mu[i];
+  }
+  std::memcpy(h + off[4], p0, 24 * (size_t)m);
+  std::memcpy(h + off[5], anchors, 24 * (size_t)m);
+  std::memcpy(h + off[6], spheres, 32 * (size_t)n_spheres);
+  CK(cudaMemcpyAsync(s->stage_dev.p, h, total, cudaMemcpyHostToDevice, s->ctx->stream));
+  CK(cudaEventRecord(s->stage_ev[slot], s->ctx->stream));
+  s->stage_used[slot] = true;
+  RET(launch_unpack_inputs(s, n_spheres, off));
+  // the state icr_set_mapping leaves, then the obstacle's
+  s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
+  s->tuned = false;
   s->obst_kind = 2;
   s->obst_iters = 0;
   return ICR_OK;

@@ -98,6 +98,13 @@ struct Scene {
   DBuf wcoup;   // per contact: max |W[3a, j]| over the other contacts' columns j
   DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, 2 + levels counters, levels + 1 K splits (int32)
   DBuf level_first;   // (levels + 1) offsets of the levels in level_list
+  // icr_set_step_inputs: device staging buffer, two pinned host slots, their copy events
+  DBuf stage_dev;
+  unsigned char* stage_host[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  bool stage_used[2] = {false, false};
+  int stage_slot = 0;
   DBuf Gpk, gpk_off;   // G_s of the wide supernodes as 3xTF32 operand blocks; first block per supernode
   // forward-solve engine per etree level: 1 puts the level's wide fronts on the
   // tensor cores (chosen by icr_autotune), mirrored per supernode for the planner
@@ -145,6 +152,9 @@ struct PgsDevStats {
 int launch_build_WH(Scene* s);
 int launch_update_W(Scene* s);
 int launch_wcoup(Scene* s);   // wcoup of a W given directly
+// scatter a packed staging buffer into the per-contact inputs and reset the
+// contact state (offsets in bytes: nodes, sphere ids, bary, mu, p0, anchors, spheres)
+int launch_unpack_inputs(Scene* s, int n_spheres, const int64_t* off);
 int launch_pgs(Scene* s, int warm_start, int want_residuals);
 int launch_update_proximity(Scene* s);
 int launch_correct_motion(Scene* s);

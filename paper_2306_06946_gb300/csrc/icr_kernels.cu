@@ -1915,6 +1915,64 @@ __global__ void k_reset_contacts(int mm, T* lam, T* lam0, T* mu, T* delta, T* C,
   if (a == 0) *dev_err = 0;
 }
 
+// one thread per contact: the inputs of icr_set_step_inputs from the staging
+// buffer, and the contact state reset as in k_reset_contacts
+template <class T>
+__global__ void k_unpack_inputs(int m, int nsph, const unsigned char* __restrict__ stg, int64_t o_nodes,
+                                int64_t o_of, int64_t o_bary, int64_t o_mu, int64_t o_p0, int64_t o_anch,
+                                int64_t o_sph, int* nodes, int* sphere_of, T* bary, T* mu, double* p, double* p0,
+                                double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C, double* u,
+                                int* stats, int nstats, int* dev_err) {
+  pdl_entry();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a < m) {
+    const int* sn = (const int*)(stg + o_nodes);
+    const T* sb = (const T*)(stg + o_bary);
+    const double* sp = (const double*)(stg + o_p0);
+    const double* sa = (const double*)(stg + o_anch);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      nodes[4 * a + j] = sn[4 * a + j];
+      bary[4 * a + j] = sb[4 * a + j];
+    }
+    sphere_of[a] = ((const int*)(stg + o_of))[a];
+    mu[a] = ((const T*)(stg + o_mu))[a];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      p[3 * a + j] = sp[3 * a + j];
+      p0[3 * a + j] = sp[3 * a + j];
+      anchors[3 * a + j] = sa[3 * a + j];
+      lam[3 * a + j] = T(0);
+      lam0[3 * a + j] = T(0);
+      delta[3 * a + j] = T(0);
+      u[3 * a + j] = 0.0;
+      u[3 * (size_t)m + 3 * a + j] = 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) C[9 * a + j] = T(0);
+  }
+  if (a < 4 * nsph) spheres[a] = ((const double*)(stg + o_sph))[a];
+  if (a < nstats) stats[a] = 0;
+  if (a == 0) *dev_err = 0;
+}
+
+template <class T>
+static int unpack_T(Scene* s, int nsph, const int64_t* o) {
+  const int m = s->m;
+  const int nstats = (int)(sizeof(PgsDevStats) / sizeof(int));
+  const int n = std::max(std::max(m, 4 * nsph), nstats);
+  PDL("k_unpack_inputs", k_unpack_inputs<T>, (n + 255) / 256, 256, 0, s->ctx->stream, m, nsph,
+      (const unsigned char*)s->stage_dev.p, o[0], o[1], o[2], o[3], o[4], o[5], o[6], (int*)s->nodes.p,
+      (int*)s->obst_of.p, (T*)s->bary.p, (T*)s->mu.p, (double*)s->p.p, (double*)s->p0.p,
+      (double*)s->obst_anchors.p, (double*)s->obst_spheres.p, (T*)s->lam.p, (T*)s->lam0.p, (T*)s->delta.p,
+      (T*)s->C.p, (double*)s->u.p, (int*)s->stats.p, nstats, (int*)s->dev_err.p);
+  return ICR_OK;
+}
+
+int launch_unpack_inputs(Scene* s, int n_spheres, const int64_t* off) {
+  return s->prec == ICR_FP64 ? unpack_T<double>(s, n_spheres, off) : unpack_T<float>(s, n_spheres, off);
+}
+
 template <class T>
 static int reset_T(Scene* s, int mm) {
   const int nstats = (int)(sizeof(PgsDevStats) / sizeof(int));

@@ -25,7 +25,7 @@ _INT_FIELDS = {"REACH_PTR", "REACH_IDX"}
 EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes_in_use", "icr_scene_create",
            "icr_scene_destroy", "icr_set_params", "icr_set_system", "icr_set_mapping", "icr_set_proximity",
            "icr_reset_proximity", "icr_scene_launches", "icr_update_directions", "icr_set_obstacle_plane", "icr_set_obstacle_sphere",
-           "icr_set_obstacle_spheres", "icr_linearize",
+           "icr_set_obstacle_spheres", "icr_set_step_inputs", "icr_linearize",
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
            "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
@@ -81,6 +81,7 @@ def lib() -> ct.CDLL:
             "icr_set_obstacle_plane": [P, ct.c_int32, P, P],
             "icr_set_obstacle_sphere": [P, P, ct.c_double, P],
             "icr_set_obstacle_spheres": [P, ct.c_int32, P, P, P],
+            "icr_set_step_inputs": [P, ct.c_int32, P, P, P, P, ct.c_int32, P, P, P],
             "icr_linearize": [P, ct.c_int32],
             "icr_build_WH": [P],
             "icr_update_W": [P],
@@ -262,6 +263,18 @@ class Scene:
         sp = _arr(spheres, np.float64).reshape(-1, 4)
         _check(lib().icr_set_obstacle_spheres(self.h, int(sp.shape[0]), _ptr(sp),
                                               _ptr(_arr(contact_sphere, np.int32)), _ptr(_arr(anchors, np.float64))))
+
+    def set_step_inputs(self, nodes, bary, p0, mu, spheres, contact_sphere, anchors):
+        """A time step's inputs in one call (mapping, proximity positions, sphere
+        tools, friction): one host-to-device copy when the contact count is
+        unchanged."""
+        nd = _arr(nodes, np.int32).reshape(-1, 4)
+        sp = _arr(spheres, np.float64).reshape(-1, 4)
+        _check(lib().icr_set_step_inputs(self.h, int(nd.shape[0]), _ptr(nd), _ptr(_arr(bary, np.float64)),
+                                         _ptr(_arr(p0, np.float64)), _ptr(_arr(mu, np.float64)), int(sp.shape[0]),
+                                         _ptr(sp), _ptr(_arr(contact_sphere, np.int32)),
+                                         _ptr(_arr(anchors, np.float64))))
+        self.m = int(nd.shape[0])
 
     def linearize(self, k: int):
         _check(lib().icr_linearize(self.h, int(k)))

@@ -254,3 +254,64 @@ def scenegen_subset(s, m):
         ob.normals = s.obstacle.normals[:, :m]
     t.obstacle = ob
     return t
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
+def test_step_inputs_in_one_call_equal_the_single_calls(batch, torch_mod, prec, tol):
+    """icr_set_step_inputs (first call: the four single calls; later calls:
+    one staged copy) gives the steps the single calls give, and a captured
+    step graph stays valid across it."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    a, b = batch[0], batch[2]
+    assert a.obstacle.kind == "sphere"
+
+    def spheres(s):
+        ob = s.obstacle
+        return np.concatenate([np.asarray(ob.centers, dtype=np.float64).reshape(-1, 3),
+                               np.asarray(ob.radii, dtype=np.float64).reshape(-1, 1)], axis=1)
+
+    def single(s, inputs):
+        ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+        sc = icr.Scene(ctx, precision=prec, n_sweeps=s.n_sweeps)
+        driver.load_system(sc, s.factor)
+        nodes, bary, p0, mu, sph, tool, anch = inputs
+        sc.set_mapping(nodes, bary)
+        sc.set_proximity(p0)
+        sc.set_obstacle_spheres(sph, tool, anch)
+        sc.set_field("MU", mu)
+        sc.step(s.n_newton)
+        sc.sync()
+        return sc.get("DQ")
+
+    ins_a = (a.nodes, a.bary, a.p0, a.mu, spheres(a), a.obstacle.tool, a.obstacle.anchors)
+    # the same contacts moved: other proximity positions and friction, same count
+    rng = np.random.default_rng(4)
+    ins_b = (a.nodes, a.bary, np.asarray(a.p0) + 1e-4 * rng.standard_normal(np.shape(a.p0)), 0.5 * np.asarray(a.mu),
+             spheres(a), a.obstacle.tool, a.obstacle.anchors)
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    sc = icr.Scene(ctx, precision=prec, n_sweeps=a.n_sweeps)
+    driver.load_system(sc, a.factor)
+    sc.set_step_inputs(*ins_a)              # no mapping yet: the single calls
+    sc.step_capture(a.n_newton)
+    sc.sync()
+    assert rel(sc.get("DQ"), single(a, ins_a)) < tol
+    for ins in (ins_b, ins_a):              # same count: one staged copy, the graph stays valid
+        sc.set_step_inputs(*ins)
+        sc.step_launch()
+        sc.sync()
+        assert rel(sc.get("DQ"), single(a, ins)) < tol
+    # checks of the single calls apply on the staged path too
+    bad = np.array(a.bary, dtype=np.float64).copy()
+    bad[0, 0] += 0.5
+    for args in [(a.nodes, bad) + ins_a[2:],
+                 ins_a[:3] + (np.full(a.m, np.nan),) + ins_a[4:],
+                 ins_a[:5] + (np.full(a.m, 7),) + ins_a[6:]]:
+        with pytest.raises(icr.IcrError) as e:
+            sc.set_step_inputs(*args)
+        assert e.value.code == icr.EINVAL
+    # another contact count: the single calls again, then a new capture
+    sc.set_step_inputs(b.nodes, b.bary, b.p0, b.mu, spheres(b), b.obstacle.tool, b.obstacle.anchors)
+    sc.step(b.n_newton)
+    sc.sync()
+    assert np.all(np.isfinite(sc.get("DQ")))
