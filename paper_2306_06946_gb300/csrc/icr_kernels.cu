@@ -799,7 +799,7 @@ struct PgsDefer {
 // Out of line: its temporaries stay out of the solve loop's registers.
 template <class T, int BC>
 __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam, const T* r,
-                                            const T* __restrict__ wcoup, T* dacc, T dlast) {
+                                            const T* __restrict__ wcoup, T* dacc, T* dsnap) {
   constexpr int BR = 3 * BC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nblk = (m + BC - 1) / BC;
@@ -836,14 +836,10 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
     const int total = __shfl_sync(FULL, off, 31);
     off -= c;
     const T th = from_bits(d->thq);
-    // started only when the last sweep's change ||d||_2 (<= ||d||_1) would
-    // fit twice into the bound: a start that ends within its first sweep
-    // costs a fold more than the sweep it saves
-    const T ds = warp_sum(dlast);
-    const bool on = total <= PGS_MAX_DEFER && total < nblk && th > T(0) && ds <= T(0.25) * th * th;
+    const bool on = total <= PGS_MAX_DEFER && total < nblk && th > T(0);
     if (on) {
       for (unsigned w = wd; w != 0u; w &= w - 1u) d->slist[off++] = lane * 32 + __ffs(w) - 1;
-      for (int i = lane; i < total * BR; i += 32) dacc[i] = T(0);
+      for (int i = lane; i < total * BR; i += 32) dacc[i] = dsnap[i] = T(0);
       if (lane < total) d->nb[lane] = T(0);
     }
     if (lane == 0) {
@@ -854,6 +850,63 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
   }
   __syncthreads();
   return d->on ? d->ns : 0;
+}
+
+// The bound on the changes of S since the last base ran out: every contact
+// outside S gets its normal residual with all deferred changes D,
+// r_n + W[n, S] D (W's symmetry: column n of the rows of D).  If all stay
+// positive, no contact outside S changes at its passed-over visit, and the
+// bound starts again from this base (dsnap = D, theta from these residuals):
+// returns 1.  Else returns 0 (the caller leaves the S-only sweeps).  The list
+// of D's non-zero rows is built in drow / dval (stage 0's space).
+template <class T, int BC>
+__device__ __noinline__ int pgs_defer_recheck(PgsDefer<T>* d, int m, int nsd, const T* __restrict__ W, int64_t ldw,
+                                              const T* r, const T* dacc, T* dsnap, const T* __restrict__ wcoup,
+                                              int* drow, T* dval) {
+  constexpr int BR = 3 * BC;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
+  if (wid == 0) {
+    int cnt = 0;
+    for (int k = 0; k < nsd; ++k) {
+      const int R = 3 * d->slist[k] * BC;
+      for (int w0 = 0; w0 < BR; w0 += 32) {
+        const T v = w0 + lane < BR ? dacc[k * BR + w0 + lane] : T(0);
+        const bool nz = v != T(0);
+        const unsigned msk = __ballot_sync(FULL, nz);
+        if (nz) {
+          const int q = cnt + __popc(msk & ((1u << lane) - 1u));
+          drow[q] = R + w0 + lane;
+          dval[q] = v;
+        }
+        cnt += __popc(msk);
+      }
+    }
+    if (lane == 0) {
+      d->cnt = cnt;
+      d->thq = to_bits(T(INFINITY));
+    }
+  }
+  __syncthreads();
+  const int nd = d->cnt;
+  for (int a = tid; a < m; a += nthr) {
+    const int blk = a / BC;
+    if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) continue;
+    T v = r[3 * a];
+    for (int k = 0; k < nd; ++k) v += W[(int64_t)drow[k] * ldw + 3 * a] * dval[k];
+    const T wm = wcoup[a];
+    const T q = (wm > T(0) && v > T(0)) ? v / wm : (wm == T(0) && v > T(0) ? T(INFINITY) : T(0));
+    atomicMin(&d->thq, to_bits(q));
+  }
+  __syncthreads();
+  const T th = from_bits(d->thq);
+  const int ok = th > T(0);
+  if (ok) {
+    for (int i = tid; i < nsd * BR; i += nthr) dsnap[i] = dacc[i];
+    if (tid < nsd) d->nb[tid] = T(0);
+    if (tid == 0) d->th = th * T(1.0 - 1.0 / 1024.0);
+  }
+  __syncthreads();
+  return ok;
 }
 
 // Leaves the S-only sweeps after block pb, whose changes are dlp: they are
@@ -942,7 +995,8 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
   T* r = lam + 3 * m;              // 3m
   T* dl = r + 3 * m;               // 2 x BR: lambda~ changes of the last two blocks
   T* dacc = dl + 2 * BR;           // PGS_MAX_DEFER x BR: changes of the blocks in S not yet folded elsewhere
-  int* nzl = (int*)(dacc + PGS_MAX_DEFER * BR);  // (PGS_WARPS - 1) x BR: per streaming warp, rows with a non-zero change
+  T* dsnap = dacc + PGS_MAX_DEFER * BR;   // PGS_MAX_DEFER x BR: dacc at the bound's base
+  int* nzl = (int*)(dsnap + PGS_MAX_DEFER * BR);  // (PGS_WARPS - 1) x BR: per streaming warp, rows with a non-zero change
   __shared__ T red[PGS_WARPS];
   __shared__ int pref[2];            // block whose rows stage k holds (-1: none)
   __shared__ int psuc[2];            // the block whose columns stage k's WR holds
@@ -1024,12 +1078,68 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
   bool known = false;   // b was found by a look-ahead: no second look needed
   unsigned t = 0;   // blocks processed (its parity selects double-buffered slots)
   const bool want_eps = tol > 0.0;   // eps of a sweep is formed into red[0]
-  // S-only sweeps: |S| (0: off), position of b in slist, may start in this sweep
-  int nsd = 0, kpos = 0, tryd = 1;
+  // S-only sweeps: |S| (0: off), position of b in slist, may start in this
+  // sweep; a sweep end waits for a recheck; S-block visits since the bound's base
+  int nsd = 0, kpos = 0, tryd = 1, since = 0;
+  bool pend = false;
+  // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i|| (Alg. 1),
+  // formed only when a positive tol needs it; returns 1 to stop at eps <= tol
+  // or after a sweep that changed nothing (a fixed point: every later sweep
+  // would repeat it exactly)
+  auto end_sweep = [&]() -> int {
+    if (want_eps) {
+      T nrm = T(0);
+      for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
+      nrm = warp_sum(nrm);
+      if (lane == 0) red[wid] = nrm;
+      const T ds = wid == 0 ? warp_sum(dsum) : T(0);
+      __syncthreads();
+      if (tid == 0) {
+        T tot = T(0);
+        for (int k = 0; k < PGS_WARPS; ++k) tot += red[k];
+        red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
+      }
+      __syncthreads();
+    }
+    const int brk = !chg_sweep[done & 1] || (want_eps && (double)red[0] <= tol);
+    if (wid == 0) {
+      dlast = dsum;
+      dsum = T(0);
+    }
+    if (tid == 0) {
+      chg_sweep[(done + 1) & 1] = 0;
+      if (nsd) ++dfs.sweeps;
+    }
+    ++done;
+    tryd = 1;
+    __syncthreads();
+    return brk;
+  };
   while (done < sweeps) {
     if (nsd && dfs.xf[(t + 1) & 1]) {   // set in the previous step
-      // the changes of S may now be large enough to change a contact outside
-      // S: fold what was deferred, then go on in order after pb
+      // The bound on the changes of S ran out after block pb.  When it lasted
+      // a round of S, the passed-over contacts' normal residuals are formed
+      // with the deferred changes: if none would change, the S-only sweeps
+      // go on from this new base.  Else fold what was deferred and go on in
+      // order after pb.
+      const int ok = since >= nsd ? pgs_defer_recheck<T, BC>(&dfs, m, nsd, W, ldw, r, dacc, dsnap, wcoup, (int*)WD, WR)
+                                  : 0;   // the list is built in stage 0
+      __syncthreads();   // every thread has read the flag before it is cleared
+      if (tid == 0) {
+        dfs.xf[0] = dfs.xf[1] = 0;
+        pref[0] = -1;
+        cst_blk[0] = -1;
+      }
+      __syncthreads();
+      if (ok) {
+        since = 0;
+        if (pend) {
+          pend = false;
+          if (end_sweep()) break;
+        }
+        continue;
+      }
+      pend = false;
       if (wid == 0) p0 = p1 = p2 = T(0);
       pgs_defer_leave<T, BC>(&dfs, m, pb, nsd, dl + (1 - (int)(t & 1)) * BR, W, ldw, r, dacc, nzl,
                              (int*)WD, WR);   // scratch in stage 0
@@ -1074,8 +1184,8 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         // every residual is complete: the rest of the sweep and the next
         // sweeps may visit S only, starting at b (the first block of S from b)
         tryd = 0;
-        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, wid == 0 ? dlast : T(0));
-        kpos = 0;
+        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, dsnap);
+        kpos = since = 0;
         while (kpos < nsd - 1 && dfs.slist[kpos] != b) ++kpos;
       }
       if (b == nblk) {   // the rest of the sweep is unchanged: end of sweep
@@ -1113,8 +1223,8 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         tryd = 1;
         if (!brk && nw_ < nblk && done < sweeps) {
           tryd = 0;
-          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, wid == 0 ? dlast : T(0));
-          kpos = 0;
+          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, dsnap);
+          kpos = since = 0;
         }
         b = nw_;
         known = true;   // the next sweep starts at a block that may change
@@ -1269,13 +1379,14 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         // accumulate this visit's changes into D and test the bound: the
         // blocks outside S up to the next block of S see the state after it
         T* Dk = dacc + kpos * BR;
+        const T* Sk = dsnap + kpos * BR;
         T part = T(0);
         if (valid) {
           const T D0 = Dk[3 * lane] + e0, D1 = Dk[3 * lane + 1] + e1, D2 = Dk[3 * lane + 2] + e2;
           Dk[3 * lane] = D0;
           Dk[3 * lane + 1] = D1;
           Dk[3 * lane + 2] = D2;
-          part = fabs(D0) + fabs(D1) + fabs(D2);
+          part = fabs(D0 - Sk[3 * lane]) + fabs(D1 - Sk[3 * lane + 1]) + fabs(D2 - Sk[3 * lane + 2]);
         }
         part = warp_sum(part);
         T tot = lane < nsd ? (lane == kpos ? part : dfs.nb[lane]) : T(0);
@@ -1405,41 +1516,13 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
     const bool leave = nsd && dfs.xf[t & 1];
     done += dfs.xs[t & 1];   // sweeps warp 0 ended itself
     ++t;
-    if (bn <= b && !leave) {
-      // end of a sweep: eps = ||lambda^i - lambda^(i-1)|| / ||lambda^i|| (Alg. 1),
-      // formed here only when a positive tol needs it
-      if (want_eps) {
-        T nrm = T(0);
-        for (int i = tid; i < n3; i += nthr) nrm += lam[i] * lam[i];
-        nrm = warp_sum(nrm);
-        if (lane == 0) red[wid] = nrm;
-        const T ds = wid == 0 ? warp_sum(dsum) : T(0);
-        __syncthreads();
-        if (tid == 0) {
-          T tot = T(0);
-          for (int k = 0; k < PGS_WARPS; ++k) tot += red[k];
-          red[0] = tot > T(0) ? sqrt(ds / tot) : T(0);
-        }
-        __syncthreads();
-      }
-      // stop at eps <= tol, or after a sweep that changed nothing (a fixed
-      // point: every later sweep would repeat it exactly)
-      const int brk = !chg_sweep[done & 1] || (want_eps && (double)red[0] <= tol);
-      if (wid == 0) {
-        dlast = dsum;
-        dsum = T(0);
-      }
-      if (tid == 0) {
-        chg_sweep[(done + 1) & 1] = 0;
-        if (nsd) ++dfs.sweeps;
-      }
-      ++done;
-      tryd = 1;
-      __syncthreads();
-      if (brk) break;
-    }
+    pend = leave && bn <= b;   // the sweep ends once the passed-over blocks are shown unchanged
+    if (bn <= b && !leave && end_sweep()) break;
     b = bn;
-    if (nsd) kpos = kpos + 1 == nsd ? 0 : kpos + 1;
+    if (nsd) {
+      kpos = kpos + 1 == nsd ? 0 : kpos + 1;
+      ++since;
+    }
   }
   // eps of the last sweep, for the statistics
   double eps = 0.0;
@@ -1468,7 +1551,8 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
 template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
-  return (4 * BR * BR + 6 * (size_t)m + 2 * BR + PGS_MAX_DEFER * BR) * sizeof(T) + (PGS_WARPS - 1) * BR * sizeof(int);
+  return (4 * BR * BR + 6 * (size_t)m + 2 * BR + 2 * PGS_MAX_DEFER * BR) * sizeof(T) +
+         (PGS_WARPS - 1) * BR * sizeof(int);
 }
 
 // FP64 residuals of the final iterate: one warp per contact.
