@@ -1064,7 +1064,19 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
                                   lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
     if (__ballot_sync(FULL, a) != 0u && lane == 0) atomicOr(&actb[bb >> 5], 1u << (bb & 31));
   }
-  __syncthreads();
+  // No block holds a contact with lambda~ != 0 or a negative normal residual:
+  // the first sweep changes nothing, a fixed point (lambda~ = 0) after one
+  // sweep, as the loop below would find.
+  if (!__syncthreads_or(tid < PGS_MAX_BLOCKS / 32 && actb[tid] != 0u)) {
+    for (int i = tid; i < n3; i += nthr) lam_g[i] = T(0);
+    if (tid == 0) {
+      st->sweeps = sweeps > 0 ? 1 : 0;
+      st->eps = 0.0;
+      st->s_only = 0;
+      st->folds = 0;
+    }
+    return;
+  }
   const bool act0 = nblk <= 2 || (actb[0] & 1u);
   if (act0) prefetch(0, 1 % nblk, 0, tid, nthr);
   if (tid == 0) pref[0] = act0 ? 0 : -1;
@@ -1628,9 +1640,16 @@ __global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam
     }
   }
   __syncthreads();
+  bool nz = false;
+  for (int a = threadIdx.x; a < 3 * m; a += blockDim.x) nz |= uk[a] != T(0);
+  nz = __syncthreads_or(nz);
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= 3 * m) return;
+  if (!nz) {   // C^T lambda~ = 0: p stays, dp = 0 (no row of W_H is read)
+    if (lane == 0) dp[i] = 0.0;
+    return;
+  }
   const T* Wr = WH + (int64_t)i * 3 * m;
   T acc = T(0);
   for (int j = lane; j < 3 * m; j += 32) acc += Wr[j] * uk[j];
