@@ -517,7 +517,7 @@ static size_t gemm_smem_bytes() {
 
 // ------------------------------------------------------------------ a3 pivot scaling
 // Y = D^-1/2 X in place on the first w rows of every front (one warp per DOF
-// row), the product taken in FP64 and rounded once to T.
+// row), with D^-1/2 in the working precision.
 template <class T>
 __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                         const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
