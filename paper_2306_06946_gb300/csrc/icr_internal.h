@@ -51,7 +51,7 @@ constexpr int TC_TILE = 128;         // tensor-core output tile (M = N)
 constexpr int TC_KT = 32;            // front rows per packed operand block
 constexpr int TC_GEMM_MIN_W = 64;    // fronts at least this wide ...
 constexpr int TC_GEMM_MIN_COLS = 64; // ... and with this many columns take the tensor-core forward solve
-constexpr int TC_PART_KB = 4;        // fewest K blocks in a part of a split tensor-core unit
+constexpr int TC_PART_KB = 2;        // fewest K blocks in a part of a split tensor-core unit
 constexpr int TC_MAX_SPLIT = 8;      // most K parts of a tensor-core unit
 constexpr int PLAN_MAX_LEV = 128;    // levels with their own K split (deeper ones are not split)
 // K parts of a tensor-core unit over nk K blocks, given the split factor of

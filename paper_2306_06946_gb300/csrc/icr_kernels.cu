@@ -649,23 +649,29 @@ __device__ __forceinline__ T nmax(T a, T b) {
 template <class T>
 __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw, T* wcoup) {
   pdl_entry();
+  if (blockIdx.x < blockIdx.y) return;   // the block pairs of the upper triangle only (uniform)
   __shared__ bits_t<T> mxa[16], mxb[16];
-  const int tx = threadIdx.x, ty = threadIdx.y;
+  __shared__ T sC[2][16][9];             // directions of the block's a and b contacts
+  __shared__ T tile[48][49];             // W[3b + j, 3a + i] of the block, for coalesced mirror rows
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
   const int b = blockIdx.x * 16 + tx, a = blockIdx.y * 16 + ty;
   if (ty == 0) mxb[tx] = 0;
   if (tx == 0) mxa[ty] = 0;
+  for (int e = tid; e < 2 * 16 * 9; e += 256) {
+    const int w = e / 144, k = (e % 144) / 9, q = e % 9;
+    const int c = (w == 0 ? blockIdx.y : blockIdx.x) * 16 + k;
+    sC[w][k][q] = c < m ? C[9 * c + q] : T(0);
+  }
   __syncthreads();
   if (a < m && b < m && a <= b) {
     const int64_t ld = 3 * (int64_t)m;
-    T M[3][3], Ca[3][3], Cb[3][3], t[3][3];
+    T M[3][3], t[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
-        Ca[i][j] = C[9 * a + 3 * i + j];
-        Cb[i][j] = C[9 * b + 3 * i + j];
-      }
+      for (int j = 0; j < 3; ++j) M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
+    const T(*Ca)[3] = reinterpret_cast<const T(*)[3]>(&sC[0][ty][0]);
+    const T(*Cb)[3] = reinterpret_cast<const T(*)[3]>(&sC[1][tx][0]);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -677,7 +683,8 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
       for (int j = 0; j < 3; ++j) {
         T v = Ca[i][0] * t[0][j] + Ca[i][1] * t[1][j] + Ca[i][2] * t[2][j];
         W[(3 * a + i) * ldw + 3 * b + j] = v;
-        W[(3 * b + j) * ldw + 3 * a + i] = v;
+        if (a == b) W[(3 * b + j) * ldw + 3 * a + i] = v;   // the diagonal block, made symmetric
+        tile[3 * tx + j][3 * ty + i] = v;
         if (i == 0) ra = nmax(ra, fabs(v));   // W[3a, 3b + j]
         if (j == 0) rb = nmax(rb, fabs(v));   // W[3b, 3a + i]
       }
@@ -687,6 +694,12 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
     }
   }
   __syncthreads();
+  // the mirror W[3b + j, 3a + i] (a < b), 48 consecutive columns per row
+  for (int e = tid; e < 48 * 48; e += 256) {
+    const int rr = e / 48, cc = e % 48;
+    const int bg = blockIdx.x * 16 + rr / 3, ag = blockIdx.y * 16 + cc / 3;
+    if (bg < m && ag < bg) W[(3 * bg + rr % 3) * ldw + 3 * ag + cc % 3] = tile[rr][cc];
+  }
   const int ga = blockIdx.y * 16 + tx, gb = blockIdx.x * 16 + tx;
   if (ty == 0 && ga < m && mxa[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + ga, mxa[tx]);
   if (ty == 1 && gb < m && mxb[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + gb, mxb[tx]);
