@@ -231,12 +231,14 @@ int icr_update_W(icr_scene* scene);
  * The solve stops after n_sweeps, when eps <= tol (tol > 0), or after a sweep
  * that changed no lambda~ (a fixed point: every later sweep would repeat it).
  * A contact with lambda~ = 0 and r_n >= 0 is left unchanged by the local rule,
- * so a sweep passes over it; after a sweep the contacts that may change (S,
- * in blocks of 32, FP64 16) are swept alone while the sum of |changes| since
- * the last complete residual stays below min r_n / max_j |W[n, j]| over the
- * others (their r_n then stays non-negative), and those changes reach the
- * others' residuals in one deferred fold: the iterate is that of full sweeps,
- * up to the rounding of the residuals.
+ * so a sweep passes over it; once every residual is complete, the contacts
+ * that may change (S, in blocks of 32, FP64 16) are swept alone while the sum
+ * of |changes| since the bound's base stays below min r_n / max_j |W[n, j]|
+ * over the others (their r_n then stays non-negative).  When it runs out, the
+ * others' normal residuals are formed with the deferred changes: all positive,
+ * the bound starts again from there; else the changes reach the others'
+ * residuals in one deferred fold and full sweeps resume.  The iterate is that
+ * of full sweeps, up to the rounding of the residuals.
  * warm_start = 0 starts from lambda~ = 0, 1 from the last solve's lambda~.
  * stats (may be NULL) receives the sweep count, eps and FP64 residuals (this
  * synchronises).  Returns ICR_ENOCONV (non-fatal) when tol > 0 and eps > tol
