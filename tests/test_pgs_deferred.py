@@ -10,10 +10,7 @@ iterate is that of plain sweeps; these cases drive both the S-only sweeps and
 their ends (the bound running out, |S| above the block limit, the last block
 in S, an exact fixed point) and compare with the oracle on the same W.
 
-W is a dense SPD matrix kron(K, M): K an exponential kernel over random
-contact positions on a line (coupling that decays with distance, as between
-contacts on a body), M a fixed 3x3 SPD block; negative normal gaps make the
-chosen contacts active, the others have positive gaps drawn log-uniformly.
+The instances are those of tests/pgs_cases.py.
 """
 import numpy as np
 import pytest
@@ -21,43 +18,9 @@ import pytest
 from oracle import pgs as pg
 
 from gpu_helpers import rel, scene
+from pgs_cases import CASES
 
 pytestmark = pytest.mark.gpu
-
-
-def synth(m, active, gaps, seed, ell=0.05):
-    rng = np.random.default_rng(seed)
-    x = np.sort(rng.uniform(0.0, 1.0, m))
-    K = np.exp(-np.abs(x[:, None] - x[None, :]) / ell)
-    M = np.array([[1.0, 0.3, -0.2], [0.3, 0.8, 0.1], [-0.2, 0.1, 0.7]])
-    W = np.kron(K, M)
-    delta = np.zeros(3 * m)
-    lo, hi = gaps
-    delta[0::3] = np.exp(rng.uniform(np.log(lo), np.log(hi), m))
-    delta[3 * np.asarray(active)] = -rng.uniform(0.01, 0.03, len(active))
-    delta[1::3] = 0.01 * rng.standard_normal(m)
-    delta[2::3] = 0.01 * rng.standard_normal(m)
-    mu = rng.uniform(0.2, 0.5, m)
-    return W, delta, mu
-
-
-def many_active():
-    act = sorted([32 * k + 3 for k in range(20)] + [32 * k + 10 for k in range(20)])
-    W, d, mu = synth(700, act, (0.05, 0.1), 7)
-    d[3 * np.asarray(act)] = -0.05
-    return W, d, mu
-
-
-# name -> (W, delta, mu) and what the S-only sweeps must do: "run" (S-only
-# sweeps), "leave" (S-only sweeps and deferred folds), "off" (|S| > 16 blocks)
-CASES = {
-    "one_block": (lambda: synth(100, [0, 3, 5, 9, 14, 20], (0.05, 0.1), 7), "run"),
-    "three_blocks": (lambda: synth(200, [1, 4, 70, 75, 170, 180], (0.05, 0.1), 7), "run"),
-    "small_gaps": (lambda: synth(200, [1, 4, 70, 75, 170, 180], (1e-4, 0.1), 11), "leave"),
-    "last_block": (lambda: synth(150, [2, 130, 140, 149], (0.02, 0.1), 7), "run"),
-    "fixed_point": (lambda: synth(64, [5], (0.05, 0.1), 3), "fixed"),
-    "many_blocks": (many_active, "off"),
-}
 
 
 @pytest.fixture(scope="module")
