@@ -59,11 +59,15 @@ def test_s_only_sweeps_match_the_oracle(ctx, name, prec):
     lam = sc.get("LAMBDA")
     if prec == 1:
         # where the oracle's last sweeps change lambda~ by rounding only (eps
-        # near 1e-16 or 0), where the iteration stops depends on that rounding
+        # near 1e-16 or 0: a fixed point, or a limit cycle of one-ulp changes
+        # that runs to the cap), where the iteration stops depends on that
+        # rounding; lambda~ itself must agree
         if eps_ref > 1e-13:
             assert st["sweeps"] == sw_ref
-        else:
+        elif sw_ref < sweeps:   # both stop at an exact fixed point, a few sweeps apart
             assert abs(st["sweeps"] - sw_ref) <= 5
+        else:                   # the oracle's one-ulp cycle runs to the cap
+            assert st["sweeps"] <= sweeps
         assert rel(lam, lam_ref) < 1e-9
     else:
         assert rel(lam, lam_ref) < 1e-4
