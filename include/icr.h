@@ -101,12 +101,14 @@ typedef struct icr_pgs_stats {
   int32_t sweeps;       /* sweeps run */
   int32_t n_separated;  /* contacts with lambda_n = 0 */
   int32_t n_stick;      /* contacts strictly inside the friction cone */
-  int32_t n_slip;       /* contacts on the cone */
+  int32_t n_slip;       /* contacts on the cone (||lambda_t|| >= mu lambda_n (1 - rel), rel = 1e-9 in FP64
+                           scenes and 1e-5 in FP32 scenes; a loaded frictionless contact counts here) */
   double eps;           /* ||lambda^i - lambda^(i-1)|| / ||lambda^i|| of the last sweep (Alg. 1) */
   double res_normal;    /* FP64 max |min(delta_n, lambda_n)| at the end */
   double res_cone;      /* FP64 max(0, ||lambda_t|| - mu lambda_n) */
   double res_stick;     /* FP64 max ||delta_t|| over sticking contacts */
-  double res_slip;      /* FP64 max misalignment of delta_t against -lambda_t over slipping contacts */
+  double res_slip;      /* FP64 max misalignment of delta_t against -lambda_t over slipping contacts with
+                           lambda_t != 0 (with mu lambda_n = 0 the sliding is free) */
   int32_t sweeps_s_only;  /* sweeps that visited only the blocks of contacts that may change (the
                              others provably keep lambda~ = 0; see icr_solve_friction) */
   int32_t deferred_folds; /* folds of those sweeps' changes into the other contacts' residuals */

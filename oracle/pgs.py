@@ -64,12 +64,17 @@ def pgs(W: np.ndarray, delta: np.ndarray, mu: np.ndarray, lam0=None, sweeps: int
     return lam, done, eps
 
 
-def residuals(W: np.ndarray, delta: np.ndarray, lam: np.ndarray, mu: np.ndarray) -> dict:
+def residuals(W: np.ndarray, delta: np.ndarray, lam: np.ndarray, mu: np.ndarray, rel: float = 1e-9) -> dict:
     """Complementarity and friction residuals of a solution (max over contacts).
 
-    normal: |min(delta_n, lambda_n)|; cone: max(0, ||lambda_t|| - mu lambda_n);
-    stick (inside the cone): ||delta_t||; slip (on the cone): the part of
-    delta_t not anti-parallel to lambda_t plus any component along it.
+    With d = delta + W lambda~ (the gaps the solution leaves):
+    normal: |min(d_n, lambda_n)| (Eq. "signorini's law"); cone:
+    max(0, ||lambda_t|| - mu lambda_n) (Eq. "coulomb's law", disc reading);
+    stick (lambda_n > 0 inside the cone): ||d_t||, the sliding a sticking
+    contact must not have; slip (on the cone within ``rel``, as ``classify``
+    decides): the part of d_t not anti-parallel to lambda_t plus any component
+    along it (maximal dissipation: a slipping contact slides against its
+    friction force).
     """
     d = (delta + W @ lam).reshape(-1, 3)
     L = lam.reshape(-1, 3)
@@ -77,13 +82,17 @@ def residuals(W: np.ndarray, delta: np.ndarray, lam: np.ndarray, mu: np.ndarray)
     nt = np.linalg.norm(L[:, 1:], axis=1)
     lim = mu * L[:, 0]
     cone = np.maximum(0.0, nt - lim)
-    on_cone = (L[:, 0] > 0) & (nt >= lim * (1 - 1e-9)) & (nt > 0)
+    # the same states as classify(): on the cone (slip) when ||lambda_t|| >=
+    # mu lambda_n (1 - rel), which includes a frictionless contact (mu = 0)
+    on_cone = (L[:, 0] > 0) & (nt >= lim * (1 - rel))
     stick = (L[:, 0] > 0) & ~on_cone
     res_stick = np.where(stick, np.linalg.norm(d[:, 1:], axis=1), 0.0)
     that = np.where(nt[:, None] > 0, L[:, 1:] / np.where(nt > 0, nt, 1.0)[:, None], 0.0)
     along = np.einsum("ij,ij->i", d[:, 1:], that)
     perp = np.linalg.norm(d[:, 1:] - along[:, None] * that, axis=1)
-    res_slip = np.where(on_cone, perp + np.maximum(0.0, along), 0.0)
+    # with a zero friction force (mu lambda_n = 0) Coulomb's law leaves the
+    # sliding d_t free: no slip residual
+    res_slip = np.where(on_cone & (nt > 0), perp + np.maximum(0.0, along), 0.0)
     return {"normal": float(normal.max(initial=0.0)), "cone": float(cone.max(initial=0.0)),
             "stick": float(res_stick.max(initial=0.0)), "slip": float(res_slip.max(initial=0.0))}
 

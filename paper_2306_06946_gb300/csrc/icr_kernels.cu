@@ -1603,16 +1603,20 @@ __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, cons
   const double nt = hypot(L1, L2);
   atomic_max_nonneg(&st->res_bits[0], fabs(fmin(d[0], L0)));
   atomic_max_nonneg(&st->res_bits[1], fmax(0.0, nt - lim));
-  const bool on_cone = L0 > 0 && nt >= lim * (1.0 - rel) && nt > 0;
+  // slip: on the cone within rel, which includes a frictionless contact
+  // (mu lambda_n = 0, lambda_t = 0) whose sliding Coulomb's law leaves free
+  const bool on_cone = L0 > 0 && nt >= lim * (1.0 - rel);
   const bool stick = L0 > 0 && !on_cone;
   if (L0 <= 0) {
     atomicAdd(&st->n_sep, 1);
   } else if (on_cone) {
     atomicAdd(&st->n_slip, 1);
-    const double tx = L1 / nt, ty = L2 / nt;
-    const double along = d[1] * tx + d[2] * ty;
-    const double px = d[1] - along * tx, py = d[2] - along * ty;
-    atomic_max_nonneg(&st->res_bits[3], hypot(px, py) + fmax(0.0, along));
+    if (nt > 0) {
+      const double tx = L1 / nt, ty = L2 / nt;
+      const double along = d[1] * tx + d[2] * ty;
+      const double px = d[1] - along * tx, py = d[2] - along * ty;
+      atomic_max_nonneg(&st->res_bits[3], hypot(px, py) + fmax(0.0, along));
+    }
   } else if (stick) {
     atomicAdd(&st->n_stick, 1);
     atomic_max_nonneg(&st->res_bits[2], hypot(d[1], d[2]));

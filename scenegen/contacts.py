@@ -80,8 +80,12 @@ class SphereObstacle:
         return C, delta
 
 
-def plane_contacts(rng, X, T, m, n_newton, tilt_sigma=0.05, gap_mm=0.5, slip_mm=0.05):
-    """Contacts inside tets that have a face on z = min z (the beam's bottom)."""
+def plane_contacts(rng, X, T, m, n_newton, tilt_sigma=0.05, gap_mm=0.5, slip_mm=0.05, gap_range_mm=None):
+    """Contacts inside tets that have a face on z = min z (the beam's bottom).
+
+    Normal gaps are uniform in (-gap_mm, gap_mm) mm, or in gap_range_mm =
+    (lo, hi) mm when given; tangential free slips uniform in (-slip_mm,
+    slip_mm) mm per axis."""
     zmin = X[:, 2].min()
     on = np.isclose(X[T, 2], zmin)
     cand = np.nonzero(on.sum(axis=1) >= 3)[0]
@@ -92,7 +96,8 @@ def plane_contacts(rng, X, T, m, n_newton, tilt_sigma=0.05, gap_mm=0.5, slip_mm=
     theta = rng.normal(0.0, tilt_sigma, size=(n_newton, m))
     phi = rng.uniform(0.0, 2.0 * np.pi, size=(n_newton, m))
     normals = np.stack([np.sin(theta) * np.sin(phi), -np.sin(theta) * np.cos(phi), np.cos(theta)], axis=2)
-    g = rng.uniform(-gap_mm, gap_mm, size=m) * 1e-3
+    lo, hi = (-gap_mm, gap_mm) if gap_range_mm is None else gap_range_mm
+    g = rng.uniform(lo, hi, size=m) * 1e-3
     s = rng.uniform(-slip_mm, slip_mm, size=(m, 2)) * 1e-3
     anchors = p0 - np.stack([s[:, 0], s[:, 1], g], axis=1)
     return nodes, bary, p0, PlaneObstacle(normals=normals, anchors=anchors)

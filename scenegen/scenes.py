@@ -18,6 +18,10 @@ Named workloads:
   tissue_c3 the same ellipsoid meshed to ~20,000 nodes (~60k DOF) with 1,500
             contacts split between two 0.02 m sphere tools, one pressed into
             its top (+z) and one into its +x end, seed 3
+  press_c1  contact-dense scene of the C1 size: a 60 x 10 x 5-node beam
+            (9,000 DOF, 0.01 m) held at its top face by 1e4 N/m grounding
+            springs and pressed 0.2-0.3 mm into a plane along its bottom face,
+            300 contacts with mu uniform in 0.1-0.6, 5 Newton x 50 sweeps, seed 5
 """
 from __future__ import annotations
 
@@ -85,6 +89,22 @@ def beam_scene(nodes_xyz=(20, 4, 4), spacing=0.01, m=40, seed=0, n_newton=3, n_s
     nodes, bary, p0, obst = ct.plane_contacts(rng, X, T, m, n_newton)
     return Scene(name or f"beam{nodes_xyz}", X, T, A, F, nodes, bary, np.full(m, float(mu)), p0, obst,
                  n_newton, n_sweeps, h)
+
+
+def press_scene(nodes_xyz=(60, 10, 5), spacing=0.01, m=300, seed=5, n_newton=5, n_sweeps=50,
+                mu_range=(0.1, 0.6), gap_range_mm=(-0.3, -0.2), slip_mm=0.05, ground_k=1e4, leaf_nodes=24,
+                h=0.01, name=None) -> Scene:
+    """A beam held at its top face by grounding springs and pressed into a
+    plane along its bottom face: normal gaps all negative, so most contacts
+    carry load, with sticking and slipping ones mixed (mu per contact)."""
+    rng = np.random.default_rng(seed)
+    X, T = beam(nodes_xyz, spacing)
+    X, T, blocks = _permute(X, T, leaf_nodes)
+    top = np.nonzero(np.isclose(X[:, 2], X[:, 2].max()))[0]
+    A, F = _system(X, T, blocks, h=h, anchor_nodes=top, anchor_k=ground_k)
+    nodes, bary, p0, obst = ct.plane_contacts(rng, X, T, m, n_newton, slip_mm=slip_mm, gap_range_mm=gap_range_mm)
+    mu = rng.uniform(mu_range[0], mu_range[1], size=m)
+    return Scene(name or f"press{nodes_xyz}", X, T, A, F, nodes, bary, mu, p0, obst, n_newton, n_sweeps, h)
 
 
 def ellipsoid_scene(semi=(0.075, 0.05, 0.04), target_nodes=3000, m=300, seed=1, n_newton=5,
@@ -164,4 +184,8 @@ def tissue_c3() -> Scene:
                            name="tissue_c3")
 
 
-NAMED = {"beam_c0": beam_c0, "liver_c1": liver_c1, "tissue_c3": tissue_c3}
+def press_c1() -> Scene:
+    return press_scene(name="press_c1")
+
+
+NAMED = {"beam_c0": beam_c0, "liver_c1": liver_c1, "tissue_c3": tissue_c3, "press_c1": press_c1}

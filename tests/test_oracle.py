@@ -278,27 +278,133 @@ def test_newton_fixed_directions_accumulate(tiny):
 
 
 # ---------------------------------------------------------------- reach
-def test_reach_matches_bruteforce_structure():
-    s = scenegen.beam_scene(nodes_xyz=(6, 3, 3), m=10, seed=5, leaf_nodes=4)
-    F = s.factor
-    sym = F.sym
-    L = F.to_sparse_L().toarray()
-    H = dl.mapping_matrix(s.nodes, s.bary, s.n).toarray()
-    X = np.linalg.solve(L, H.T)
-    reach = rc.contact_reach(sym.parent, sym.super_ptr, s.nodes)
+def _reach_mismatches(reach, scene) -> int:
+    """Supernodes whose contact list differs from the contacts with a non-zero
+    in the supernode's rows of X = L^-1 H^T, formed densely by forward
+    substitution on the fixture's unit lower factor (exact zeros stay zero:
+    every product of a structural zero is an exact zero)."""
+    import scipy.linalg as sla
+    sym = scene.factor.sym
+    L = scene.factor.to_sparse_L().toarray()
+    H = dl.mapping_matrix(scene.nodes, scene.bary, scene.n).toarray()
+    X = sla.solve_triangular(L, H.T, lower=True, unit_diagonal=True)
     sod = rc.supernode_of_dof(sym.super_ptr)
-    for a in range(s.m):
-        for d in range(3):
-            rows = np.nonzero(np.abs(X[:, 3 * a + d]) > 0)[0]
-            hit = set(sod[rows].tolist())
-            pred = {sn for sn in range(sym.nsuper) if a in reach[sn]}
-            assert hit <= pred
-            # the supernodes owning the contact's nodes and the root are reached
-            own = {int(sod[3 * nd]) for nd in s.nodes[a] if s.bary[a, list(s.nodes[a]).index(nd)] > 0}
-            assert own <= hit
-    roots = np.nonzero(sym.parent < 0)[0]
-    for r in roots:
-        assert len(reach[r]) == s.m
+    bad = 0
+    for sn in range(sym.nsuper):
+        rows = sod == sn
+        hit = [a for a in range(scene.m) if np.any(X[rows, 3 * a:3 * a + 3] != 0)]
+        bad += hit != list(reach[sn])
+    return bad
+
+
+@pytest.fixture(scope="module")
+def reach_scenes():
+    # random barycentric weights: no cancellation in L^-1 H^T
+    return [scenegen.beam_scene(nodes_xyz=(6, 3, 3), m=10, seed=5, leaf_nodes=4),
+            scenegen.ellipsoid_scene(target_nodes=500, m=60, seed=4, leaf_nodes=8)]
+
+
+def test_reach_equals_nonzero_structure(reach_scenes):
+    for s in reach_scenes:
+        sym = s.factor.sym
+        reach = rc.contact_reach(sym.parent, sym.super_ptr, s.nodes)
+        assert _reach_mismatches(reach, s) == 0, s.name
+        assert sum(len(r) for r in reach) < sym.nsuper * s.m      # not every contact everywhere
+
+
+def test_reach_pin_catches_planted_mistakes(reach_scenes):
+    s = reach_scenes[1]
+    sym = s.factor.sym
+    reach = rc.contact_reach(sym.parent, sym.super_ptr, s.nodes)
+    # over-reach: every contact reaches every supernode
+    assert _reach_mismatches([list(range(s.m))] * sym.nsuper, s) > 0
+    # over-reach by one: contact 0 added to one supernode off its etree paths
+    off = next(sn for sn in range(sym.nsuper) if 0 not in reach[sn])
+    planted = [list(r) for r in reach]
+    planted[off] = sorted(planted[off] + [0])
+    assert _reach_mismatches(planted, s) == 1
+    # under-reach: the walk stops below the root
+    roots = set(np.nonzero(sym.parent < 0)[0].tolist())
+    planted = [[] if sn in roots else list(r) for sn, r in enumerate(reach)]
+    assert _reach_mismatches(planted, s) == len(roots)
+
+
+# ---------------------------------------------------------------- PGS residuals and states
+# Single contacts with a chosen lambda~, the gaps d = delta + W lambda~ it
+# leaves and mu; each with its residuals and state written down by hand from
+# Eqs. "signorini's law" and "coulomb's law" (disc reading) and maximal
+# dissipation.  W is a random non-symmetric 3x3 block, so delta = d - W lambda~
+# is only right if the residual is formed with W lambda~ (not W^T lambda~).
+RES_CASES = [
+    # name, lambda~, d, mu, {normal, cone, stick, slip}, state
+    ("stick", (1.0, 0.1, 0.0), (0.0, 0.3, -0.4), 0.5, dict(stick=0.5), pg.STICK),
+    ("slip_aligned", (1.0, 0.3, 0.4), (0.0, -1.2, -1.6), 0.5, dict(), pg.SLIP),
+    ("slip_misaligned", (1.0, 0.3, 0.4), (0.0, -1.4, -1.45), 0.5, dict(slip=0.25), pg.SLIP),
+    ("slip_with_force", (1.0, 0.3, 0.4), (0.0, 0.06, 0.08), 0.5, dict(slip=0.1), pg.SLIP),
+    ("cone_violated", (1.0, 0.6, 0.8), (0.0, -0.6, -0.8), 0.5, dict(cone=0.5), pg.SLIP),
+    ("separated_open", (0.0, 0.0, 0.0), (0.2, 5.0, 5.0), 0.5, dict(), pg.SEPARATED),
+    ("separated_penetrating", (0.0, 0.0, 0.0), (-0.2, 0.0, 0.0), 0.5, dict(normal=0.2), pg.SEPARATED),
+    ("loaded_open", (0.3, 0.0, 0.0), (0.1, 0.0, 0.0), 0.5, dict(normal=0.1), pg.STICK),
+    ("frictionless_sliding", (1.0, 0.0, 0.0), (0.0, 0.7, 0.0), 0.0, dict(), pg.SLIP),
+]
+
+
+def _res_case(lam, d, mu, residuals=pg.residuals):
+    W = np.random.default_rng(7).normal(size=(3, 3)) + 3 * np.eye(3)
+    lam = np.asarray(lam, dtype=np.float64)
+    delta = np.asarray(d, dtype=np.float64) - W @ lam
+    return residuals(W, delta, lam, np.array([mu]))
+
+
+def _residual_pin_failures(residuals=pg.residuals, classify=pg.classify):
+    bad = []
+    for name, lam, d, mu, want, state in RES_CASES:
+        got = _res_case(lam, d, mu, residuals)
+        for key in ("normal", "cone", "stick", "slip"):
+            if abs(got[key] - want.get(key, 0.0)) > 1e-12:
+                bad.append((name, key, got[key]))
+        if classify(np.asarray(lam, dtype=np.float64), np.array([mu]))[0] != state:
+            bad.append((name, "state"))
+    return bad
+
+
+def test_residuals_and_states_on_hand_built_contacts():
+    assert _residual_pin_failures() == []
+    # several contacts at once: the maxima over contacts, W block-diagonal
+    k = len(RES_CASES)
+    W = np.zeros((3 * k, 3 * k))
+    lam = np.zeros(3 * k)
+    d = np.zeros(3 * k)
+    for i, (_, l, dd, _, _, _) in enumerate(RES_CASES):
+        W[3 * i:3 * i + 3, 3 * i:3 * i + 3] = np.random.default_rng(i).normal(size=(3, 3)) + 3 * np.eye(3)
+        lam[3 * i:3 * i + 3] = l
+        d[3 * i:3 * i + 3] = dd
+    mu = np.array([c[3] for c in RES_CASES])
+    got = pg.residuals(W, d - W @ lam, lam, mu)
+    assert got == pytest.approx({"normal": 0.2, "cone": 0.5, "stick": 0.5, "slip": 0.25}, abs=1e-12)
+    assert pg.classify(lam, mu).tolist() == [c[5] for c in RES_CASES]
+
+
+def test_residual_pins_catch_planted_mistakes():
+    swapped = lambda lam, mu, rel=1e-9: np.choose(pg.classify(lam, mu, rel), [0, 2, 1])   # stick <-> slip
+    assert _residual_pin_failures(classify=swapped)
+    transposed = lambda W, delta, lam, mu, rel=1e-9: pg.residuals(W.T, delta, lam, mu, rel)
+    assert _residual_pin_failures(residuals=transposed)
+
+    def no_dissipation(W, delta, lam, mu, rel=1e-9):      # slip residual without the along term
+        r = pg.residuals(W, delta, lam, mu, rel)
+        d = (delta + W @ lam).reshape(-1, 3)
+        if lam[0] > 0 and np.linalg.norm(lam[1:]) > 0:
+            t = lam[1:] / np.linalg.norm(lam[1:])
+            r["slip"] = float(np.linalg.norm(d[0, 1:] - (d[0, 1:] @ t) * t))
+        return r
+    assert _residual_pin_failures(residuals=no_dissipation)
+
+
+def test_classification_margin():
+    lam = np.array([1.0, 0.3, 0.4 * (1 - 1e-7)])      # ||lambda_t|| just inside mu lambda_n = 0.5
+    assert pg.classify(lam, np.array([0.5]))[0] == pg.STICK
+    assert pg.classify(lam, np.array([0.5]), rel=1e-5)[0] == pg.SLIP
 
 
 # ---------------------------------------------------------------- paper table
@@ -319,3 +425,14 @@ def test_paper_table_arithmetic():
         rt.append(st["total"] / fa["total"])
     assert abs(np.mean(rn) - t["speedup_newton"]) < 0.01
     assert abs(np.mean(rt) - t["speedup_total"]) < 0.02
+
+
+def test_solver_orderings_agree(beam_c0):
+    # the column ordering of the sparse LU changes rounding only
+    s = beam_c0
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    a = dl.compliance_mapping(dl.SystemSolver(s.A), H)
+    b = dl.compliance_mapping(dl.SystemSolver(s.A, ordering="NATURAL"), H)
+    Ainv = np.linalg.inv(s.A.toarray())
+    ref = H.toarray() @ Ainv @ H.T.toarray()
+    assert _rel(a, ref) < 1e-12 and _rel(b, ref) < 1e-12
