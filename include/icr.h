@@ -321,6 +321,24 @@ int icr_sync(icr_scene* scene);
 int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene, const double* req_arrival_s,
               int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s);
 
+/* Which paths the last icr_build_WH took, read back from the device work
+ * lists (synchronises; needs icr_build_WH, ICR_ESTATE otherwise).  Diagnostic:
+ * the paper has no counterpart; it shows which kernels a workload exercises. */
+typedef struct icr_build_info_t {
+  int32_t levels;              /* elimination-tree levels */
+  int32_t tc_levels;           /* levels whose wide fronts ran the forward solve on tcgen05 */
+  int32_t gemm_tc_units;       /* tensor-core front-GEMM work units (tiles x K parts) */
+  int32_t gemm_tc_split_max;   /* largest K split of a level's tensor-core front GEMM (1: none split) */
+  int32_t gemm_simt_units;     /* CUDA-core front-GEMM tiles */
+  int32_t contract_tc_units;   /* tensor-core contraction units (tile pairs x K parts) */
+  int32_t contract_tc_split;   /* K split of the tensor-core contraction (1: unsplit) */
+  int32_t contract_simt_units; /* CUDA-core contraction tile pairs */
+  int32_t prox_split;          /* 1: the proximity update runs as two launches (C^T lambda~ does not fit
+                                  the default shared memory: 3m x element size > 48 KiB) */
+  int64_t reach_nnz;           /* sum over supernodes of the contacts reaching them */
+} icr_build_info_t;
+int icr_build_info(icr_scene* scene, icr_build_info_t* out);
+
 /* Copy a field to host memory as double (float fields) or int32 (index fields).
  * `bytes` must equal the field's size; ICR_EINVAL otherwise. */
 int icr_get(icr_scene* scene, int32_t field, void* dst, size_t bytes);

@@ -77,6 +77,17 @@ def compliance_mapping(solver: SystemSolver, H: sp.spmatrix) -> np.ndarray:
     return np.asarray(H @ Z)
 
 
+def compliance_columns(A: sp.spmatrix, nodes: np.ndarray, bary: np.ndarray, cols: np.ndarray,
+                       ordering: str = "COLAMD") -> np.ndarray:
+    """Columns ``cols`` of W_H = H A^-1 H^T: H (A^-1 H^T[:, cols]), the
+    definition restricted to some columns (one process's share when W_H is
+    formed by column blocks in parallel)."""
+    n = A.shape[0]
+    H = mapping_matrix(nodes, bary, n)
+    Z = SystemSolver(A, ordering).solve(H.T[:, cols].toarray())
+    return np.asarray(H @ Z)
+
+
 def delassus_fast(C: np.ndarray, WH: np.ndarray) -> np.ndarray:
     """W = C W_H C^T (Eq. "schur complemnt reformulated"; Alg. 3 step 2)."""
     Cm = direction_matrix(C)

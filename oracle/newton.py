@@ -45,11 +45,15 @@ def standard_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0
     return {"dq": q, "p": p, "iters": hist}
 
 
-def fast_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0, lam0=None, solver=None):
+def fast_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0, lam0=None, solver=None, WH=None):
+    """``WH`` (optional): W_H = H A^-1 H^T already formed by the caller, e.g.
+    from column blocks of dl.compliance_mapping solved in parallel (W_H is
+    column-separable); formed here otherwise."""
     n = A.shape[0]
     solver = solver or dl.SystemSolver(A)
     H = dl.mapping_matrix(nodes, bary, n)
-    WH = dl.compliance_mapping(solver, H)
+    if WH is None:
+        WH = dl.compliance_mapping(solver, H)
     p = np.array(p0, dtype=np.float64).reshape(-1)
     u = np.zeros(H.shape[0])
     hist = []

@@ -1125,6 +1125,48 @@ int icr_correct_motion(icr_scene* s, double* dq_out, int reset) {
   return ICR_OK;
 }
 
+int icr_build_info(icr_scene* s, icr_build_info_t* out) {
+  RET(check_scene(s));
+  if (!out) {
+    set_error("build_info: out must not be NULL");
+    return ICR_EINVAL;
+  }
+  if (!s->has_WH) {
+    set_error("build_info: needs icr_build_WH first");
+    return ICR_ESTATE;
+  }
+  RET(set_device(s));
+  *out = icr_build_info_t{};
+  out->levels = (int32_t)s->levels.size();
+  out->prox_split = 3 * (size_t)s->m * s->tsize > 48 * 1024 ? 1 : 0;
+  if (s->m == 0) return ICR_OK;
+  const int ns = s->ns, nlev = (int)s->levels.size();
+  const size_t words = (size_t)PLAN_LISTS * (ns + 1) + 3 + 2 * (size_t)nlev;
+  std::vector<int32_t> plan(words);
+  std::vector<int32_t> qc(ns);
+  CK(cudaMemcpyAsync(plan.data(), s->plan.p, words * sizeof(int32_t), cudaMemcpyDeviceToHost, s->ctx->stream));
+  CK(cudaMemcpyAsync(qc.data(), s->qcount.p, ns * sizeof(int32_t), cudaMemcpyDeviceToHost, s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  auto P = [&](int list, int pos) { return plan[(size_t)list * (ns + 1) + pos]; };
+  const int32_t* splits = plan.data() + (size_t)PLAN_LISTS * (ns + 1) + 2 + nlev;
+  out->gemm_tc_split_max = 1;
+  for (int li = 0; li < nlev; ++li) {
+    const Level& lv = s->levels[li];
+    const int units = P(PLAN_GTC, lv.first + lv.count) - P(PLAN_GTC, lv.first);
+    if (units > 0) {
+      ++out->tc_levels;
+      out->gemm_tc_split_max = std::max(out->gemm_tc_split_max, splits[li]);
+    }
+  }
+  out->gemm_tc_units = P(PLAN_GTC, ns);
+  out->gemm_simt_units = P(PLAN_GEMM, ns);
+  out->contract_tc_units = P(PLAN_TC, ns);
+  out->contract_tc_split = out->contract_tc_units > 0 ? splits[nlev] : 1;
+  out->contract_simt_units = P(PLAN_SIMT, ns);
+  for (int i = 0; i < ns; ++i) out->reach_nnz += qc[i];
+  return ICR_OK;
+}
+
 // the per-level forward-solve engine flags, per supernode, for the planner
 static int upload_tc_super(Scene* s) {
   std::vector<uint8_t> f(s->ns, 0);

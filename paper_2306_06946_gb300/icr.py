@@ -29,7 +29,7 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
            "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
-           "icr_set_forward_plan", "icr_forward_levels")
+           "icr_set_forward_plan", "icr_forward_levels", "icr_build_info")
 
 
 class IcrError(RuntimeError):
@@ -44,6 +44,13 @@ CONTRACT = {"auto": 0, "simt": 1, "tf32x3": 2, "tf32": 3, "bf16": 4}
 class Params(ct.Structure):
     _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double),
                 ("contraction", ct.c_int32), ("warm_start", ct.c_int32)]
+
+
+class BuildInfo(ct.Structure):
+    _fields_ = [("levels", ct.c_int32), ("tc_levels", ct.c_int32), ("gemm_tc_units", ct.c_int32),
+                ("gemm_tc_split_max", ct.c_int32), ("gemm_simt_units", ct.c_int32),
+                ("contract_tc_units", ct.c_int32), ("contract_tc_split", ct.c_int32),
+                ("contract_simt_units", ct.c_int32), ("prox_split", ct.c_int32), ("reach_nnz", ct.c_int64)]
 
 
 class PgsStats(ct.Structure):
@@ -99,6 +106,7 @@ def lib() -> ct.CDLL:
             "icr_autotune": [P, P, P, ct.c_int32],
             "icr_set_forward_plan": [P, P, ct.c_int32],
             "icr_forward_levels": [P, P],
+            "icr_build_info": [P, ct.POINTER(BuildInfo)],
             "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
         }
         for name, args in sigs.items():
@@ -337,6 +345,12 @@ class Scene:
     def set_forward_plan(self, tc_levels):
         f = _arr(tc_levels, np.uint8)
         _check(lib().icr_set_forward_plan(self.h, _ptr(f), int(f.size)))
+
+    def build_info(self) -> dict:
+        """Which paths the last W_H build took (icr_build_info)."""
+        b = BuildInfo()
+        _check(lib().icr_build_info(self.h, ct.byref(b)))
+        return {f: int(getattr(b, f)) for f, _ in BuildInfo._fields_}
 
     def step_capture(self, n_newton: int):
         _check(lib().icr_step_capture(self.h, int(n_newton)))

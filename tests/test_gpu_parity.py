@@ -10,8 +10,8 @@ import pytest
 from oracle import delassus as dl
 from oracle import pgs as pg
 
-from gpu_helpers import (classify, make_scene, margin_mask, oracle_fast, oracle_reach, oracle_WH, rel,
-                         scene)
+from gpu_helpers import (as_stored, classify, make_scene, margin_mask, oracle_fast, oracle_reach, oracle_WH,
+                         per_contact_error, rel, scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +91,7 @@ def test_W_matches_oracle(ctx, name, prec, tol):
 
 
 # ---------------------------------------------------------------- a7 PGS on a given W
-@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1"])
+@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1", "press_c1"])
 def test_pgs_fp64_matches_oracle_exactly_in_classification(ctx, name):
     from paper_2306_06946_gb300 import icr
     s = scene(name)
@@ -110,10 +110,12 @@ def test_pgs_fp64_matches_oracle_exactly_in_classification(ctx, name):
     assert abs(st["eps"] - eps_ref) <= 1e-6 * max(eps_ref, 1e-12) + 1e-12 or (st["eps"] < 1e-15 and eps_ref < 1e-15)
     cls = classify(lam_ref, s.mu)
     assert st["n_separated"] == int((cls == 0).sum())
-    assert st["n_slip"] + st["n_stick"] == int((cls > 0).sum())
+    assert st["n_stick"] == int((cls == 1).sum())
+    assert st["n_slip"] == int((cls == 2).sum())
+    assert per_contact_error(lam, lam_ref, s.mu) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1"])
+@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1", "press_c1"])
 def test_pgs_fp32_matches_oracle(ctx, name):
     from paper_2306_06946_gb300 import icr
     s = scene(name)
@@ -129,6 +131,37 @@ def test_pgs_fp32_matches_oracle(ctx, name):
     assert rel(lam, lam_ref) < 1e-4
     ok = margin_mask(lam_ref, s.mu)
     assert np.array_equal(classify(lam, s.mu, 1e-5)[ok], classify(lam_ref, s.mu)[ok])
+    assert per_contact_error(lam, lam_ref, s.mu) < 1e-4
+
+
+# ---------------------------------------------------------------- a7 FP64 residual check
+@pytest.mark.parametrize("name", ["beam_c0", "beam_mid", "liver_c1", "press_c1"])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_pgs_residual_stats_match_oracle(ctx, name, prec):
+    """The device's FP64 residuals and per-state counts equal the oracle's
+    residuals() and classify() evaluated on the same stored W, gaps, mu and
+    the solve's lambda~, each one separately."""
+    s = scene(name)
+    C, delta = s.linearize(s.p0, 0)
+    W = dl.delassus_fast(C, oracle_WH(name))
+    sc = make_scene(ctx, name, prec)
+    sc.set_field("W", W)
+    sc.set_field("DELTA", delta)
+    sc.set_field("MU", s.mu)
+    st = sc.solve_friction(stats=True)
+    lam = sc.get("LAMBDA")
+    rel_ = 1e-9 if prec == 1 else 1e-5
+    Ws, ds, mus = as_stored(W, prec), as_stored(delta, prec), as_stored(s.mu, prec)
+    ref = pg.residuals(Ws, ds, lam, mus, rel_)
+    scale = max(np.abs(ds).max(), 1e-300)
+    for key in ("normal", "cone", "stick", "slip"):
+        assert abs(st["res_" + key] - ref[key]) <= 1e-9 * max(ref[key], 1e-6 * scale), key
+    cls = pg.classify(lam, mus, rel_)
+    assert st["n_separated"] == int((cls == pg.SEPARATED).sum())
+    assert st["n_stick"] == int((cls == pg.STICK).sum())
+    assert st["n_slip"] == int((cls == pg.SLIP).sum())
+    if name == "press_c1":     # contact-dense: most contacts carry load, sticking and slipping mixed
+        assert st["n_stick"] + st["n_slip"] >= 150 and st["n_stick"] >= 10 and st["n_slip"] >= 10
 
 
 def test_pgs_tol_stops_at_the_oracle_sweep(ctx):
@@ -221,7 +254,8 @@ def test_proximity_and_correction_match_oracle(ctx, name, prec, tol):
 
 # ---------------------------------------------------------------- full step (Alg. 3)
 @pytest.mark.parametrize("name,prec", [("beam_c0", 1), ("beam_c0", 0), ("beam_mid", 0), ("liver_c1", 1),
-                                       ("liver_c1", 0), ("tools2", 1), ("tools2", 0)])
+                                       ("liver_c1", 0), ("tools2", 1), ("tools2", 0), ("press_c1", 1),
+                                       ("press_c1", 0)])
 def test_newton_step_matches_oracle(ctx, name, prec):
     from paper_2306_06946_gb300 import driver
     s = scene(name)
@@ -229,6 +263,7 @@ def test_newton_step_matches_oracle(ctx, name, prec):
     sc = make_scene(ctx, name, prec)
     sc.build_WH()
     lam_scale = max(np.linalg.norm(it["lam"]) for it in ref["iters"])
+    lam_big = max(np.abs(it["lam"]).max() for it in ref["iters"])
     disp_ref = ref["p"].reshape(-1) - s.p0.reshape(-1)
     lam_tol = 1e-9 if prec == 1 else 1e-4
     for k, it in enumerate(ref["iters"]):
@@ -239,6 +274,10 @@ def test_newton_step_matches_oracle(ctx, name, prec):
         sc.solve_friction()
         lam = sc.get("LAMBDA")
         assert np.linalg.norm(lam - it["lam"]) <= lam_tol * lam_scale, f"iteration {k}"
+        # per contact, away from state boundaries, against the step's largest entry
+        ok = margin_mask(it["lam"], s.mu)
+        if ok.any():
+            assert np.abs(lam - it["lam"]).reshape(-1, 3)[ok].max() <= lam_tol * lam_big, f"iteration {k}"
         if prec == 1:
             assert np.array_equal(classify(lam, s.mu), classify(it["lam"], s.mu))
         sc.update_proximity()

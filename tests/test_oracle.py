@@ -436,3 +436,19 @@ def test_solver_orderings_agree(beam_c0):
     Ainv = np.linalg.inv(s.A.toarray())
     ref = H.toarray() @ Ainv @ H.T.toarray()
     assert _rel(a, ref) < 1e-12 and _rel(b, ref) < 1e-12
+
+
+def test_column_blocks_form_WH(beam_c0):
+    # W_H assembled from column blocks equals W_H formed at once, and the
+    # fast scheme given it repeats the fast scheme that forms it
+    s = beam_c0
+    H = dl.mapping_matrix(s.nodes, s.bary, s.n)
+    whole = dl.compliance_mapping(dl.SystemSolver(s.A), H)
+    cols = np.array_split(np.arange(3 * s.m), 3)
+    blocks = np.hstack([dl.compliance_columns(s.A, s.nodes, s.bary, c, "NATURAL") for c in cols])
+    assert _rel(blocks, whole) < 1e-12
+    kw = dict(A=s.A, nodes=s.nodes, bary=s.bary, mu=s.mu, p0=s.p0, linearize=s.linearize,
+              n_newton=s.n_newton, sweeps=s.n_sweeps)
+    a = nw.fast_scheme(**kw)
+    b = nw.fast_scheme(**kw, WH=blocks)
+    assert _rel(b["dq"], a["dq"]) < 1e-11
