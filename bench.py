@@ -1,23 +1,27 @@
 #!/usr/bin/env python3
 """Constraint steps/s of the fast implicit constraint-resolution scheme.
 
-One step = one time step of Alg. 3 on the liver workload (ellipsoid of
-0.15 x 0.1 x 0.08 m with 3,000 nodes / 9,000 DOF, 300 contacts against a
-sphere tool, 5 Newton iterations x 50 PGS sweeps, FP32):
-build W_H (reach, supernodal forward solve, FP64 pivot scaling,
-contraction), then 5 x (device linearisation of the directions, W = C W_H C^T,
-PGS, proximity update), then the corrective motion dq = A^-1 H^T u.
+One step = one time step of Alg. 3 on the largest workload that fits one GPU,
+tissue_c3: an ellipsoid of 0.15 x 0.1 x 0.08 m meshed to 20,000 nodes
+(60,075 DOF) with 1,500 contacts split between two 0.02 m sphere tools,
+5 Newton iterations x 50 PGS sweeps, FP32 with the 3xTF32 tensor-core
+contraction: build W_H (reach, supernodal forward solve, pivot scaling,
+contraction), then 5 x (device linearisation of the directions,
+W = C W_H C^T, PGS, proximity update), then the corrective motion
+dq = A^-1 H^T u.  The line also carries the C1-size liver scene (300
+contacts) and the contact-dense press_c1 scene as extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl icr|reference]
 
 --impl icr (default) times libicr on the GPU; under torchrun every rank runs
 its own replica of the workload on its own GPU (no collective on the data
 path) and rank 0 prints one JSON line.  --impl reference times the FP64 CPU
-oracle on the host cores on the same workload.
+oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 
@@ -39,15 +43,30 @@ if ROOT not in sys.path:
 
 METRIC = "constraint steps/sec (W_H build+W update+PGS) at stated err vs FP64; p50/p99 lat"
 UNIT = "steps/s"
-WORKLOAD = "liver_c1"
+WORKLOAD = "tissue_c3"
+EXTRA_WORKLOADS = ("liver_c1", "press_c1")
 L2_FLUSH_BYTES = 512 << 20
+ORACLE_SAMPLE_COLUMNS = 48      # W_H columns the oracle solves for the CPU baseline and the parity sample
+TF32_PER_BF16 = 1.1 / 2.25      # nominal dense tensor rates of the part (TF32 / BF16)
+
+DESCR = {
+    "tissue_c3": "tissue_c3: ellipsoid 0.15x0.1x0.08 m, {N} nodes / {n} DOF, {m} contacts split between two "
+                 "0.02 m sphere tools (top and +x end, pressed 6 mm, sliding 0.05 m/s), {k} Newton x {s} PGS "
+                 "sweeps, seed 3",
+    "liver_c1": "liver_c1: ellipsoid 0.15x0.1x0.08 m, {N} nodes / {n} DOF, {m} contacts vs a 0.02 m sphere tool, "
+                "{k} Newton x {s} PGS sweeps, seed 1",
+    "press_c1": "press_c1: beam 60x10x5 nodes ({n} DOF) held at its top, pressed 0.2-0.3 mm into a plane, {m} "
+                "contacts (most loaded, stick and slip mixed), mu U(0.1, 0.6), {k} Newton x {s} PGS sweeps, seed 5",
+}
+
+
+def describe(name, scene) -> str:
+    return DESCR[name].format(N=scene.X.shape[0], n=scene.n, m=scene.m, k=scene.n_newton, s=scene.n_sweeps)
 
 
 def workload_config(scene) -> dict:
     return {
-        "workload": f"{WORKLOAD}: ellipsoid 0.15x0.1x0.08 m, {scene.X.shape[0]} nodes / {scene.n} DOF, "
-                    f"{scene.m} contacts vs 0.02 m sphere tool, {scene.n_newton} Newton x {scene.n_sweeps} PGS "
-                    f"sweeps, seed 1",
+        "workload": describe(WORKLOAD, scene),
         "n_dof": scene.n,
         "contacts": scene.m,
         "newton_iterations": scene.n_newton,
@@ -63,8 +82,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["icr", "reference"], default="icr")
-    ap.add_argument("--workload", choices=["liver_c1", "batch_c2", "precision_c3", "serve_c4"], default="liver_c1",
-                    help="liver_c1 is the bench line; the others print their own line")
+    ap.add_argument("--workload", choices=["tissue_c3", "batch_c2", "precision_c3", "serve_c4"],
+                    default="tissue_c3", help="tissue_c3 is the bench line; the others print their own line")
     ap.add_argument("--scenes", type=int, default=64, help="batch_c2: number of scenes")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve_c4: mean arrivals per second")
     ap.add_argument("--duration", type=float, default=3.0, help="serve_c4: seconds of arrivals")
@@ -73,9 +92,11 @@ def parse():
     ap.add_argument("--modes", default="simt,tf32x3,tf32,bf16", help="precision_c3: FP32 contraction modes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="leave out the liver_c1 and press_c1 keys")
+    ap.add_argument("--no-parity", action="store_true", help="leave out the parity figures of the timed run")
     ap.add_argument("--tc-levels", default=None,
-                    help="liver_c1: comma list, per etree level (leaves first) 1 = forward solve on tcgen05; "
-                         "fixes the plan instead of autotuning (a profiler distorts the autotuner's timings)")
+                    help="comma list, per etree level (leaves first) 1 = forward solve on tcgen05; fixes the "
+                         "plan instead of autotuning (a profiler distorts the autotuner's timings)")
     ap.add_argument("--nvtx-step", action="store_true",
                     help="after the timed steps, replay one more step inside an NVTX range named 'step' "
                          "(for a per-step kernel list: ncu --nvtx --nvtx-include step/)")
@@ -153,22 +174,34 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def profiled_traffic(kernel_marker: str, end_marker: str, profile: str):
-    """DRAM bytes per launch recorded by the ncu capture in ``profiles/``, or
-    None when the kernel's source has changed since that capture."""
-    import hashlib
+# kernel -> the source file it is defined in (the ncu figures stay valid while that file is unchanged)
+KERNEL_SOURCE = {"k_pgs": "icr_kernels.cu", "k_front_gemm": "icr_kernels.cu", "k_contract": "icr_kernels.cu",
+                 "k_update_W": "icr_kernels.cu", "k_assemble": "icr_kernels.cu", "k_front_gemm_tc": "icr_tc.cu",
+                 "k_contract_tc": "icr_tc.cu", "k_pack_tc": "icr_tc.cu"}
+
+
+def source_sha(kernel: str) -> str | None:
+    f = KERNEL_SOURCE.get(kernel)
+    if f is None:
+        return None
     try:
-        src = open(os.path.join(ROOT, "paper_2306_06946_gb300", "csrc", "icr_kernels.cu")).read()
-        a, b = src.index(kernel_marker), src.index(end_marker)
-        h = hashlib.sha256(src[a:b].encode()).hexdigest()
-        rec = {}
-        for line in open(os.path.join(ROOT, "profiles", profile)):
-            if ":" in line and line.split(":")[0] in ("dram_bytes_per_launch", "kernel_source_sha256"):
-                k, v = line.split(":", 1)
-                rec[k.strip()] = v.strip()
-        if rec.get("kernel_source_sha256") == h:
-            return int(rec["dram_bytes_per_launch"])
-    except (OSError, ValueError, KeyError):
+        data = open(os.path.join(ROOT, "paper_2306_06946_gb300", "csrc", f), "rb").read()
+    except OSError:
+        return None
+    return hashlib.sha256(data).hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of ``kernel`` from the ncu summary
+    profiles/traffic_<workload>.md (lines "kernel | bytes per launch | source
+    sha"), or None when the kernel's source file has changed since."""
+    sha = source_sha(kernel)
+    try:
+        for line in open(os.path.join(ROOT, "profiles", f"traffic_{workload}.md")):
+            f = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(f) >= 3 and f[0] == kernel and f[2] == sha:
+                return int(float(f[1]))
+    except (OSError, ValueError):
         pass
     return None
 
@@ -188,62 +221,43 @@ def oracle_threads() -> int:
         return os.cpu_count() or 1
 
 
-def oracle_step(scene, solver, newton_iters=None):
-    """One FP64 oracle time step (fast scheme, Alg. 3); ``newton_iters`` limits
-    the Newton iterations for a bounded sample."""
-    from oracle import newton as nw
-    k = scene.n_newton if newton_iters is None else newton_iters
-    return nw.fast_scheme(scene.A, scene.nodes, scene.bary, scene.mu, scene.p0, scene.linearize, k,
-                          scene.n_sweeps, solver=solver)
-
-
-def time_oracle(scene, steps: int, warmup: int, budget_s: float):
-    """Time the oracle; when the full steps would not fit ``budget_s`` each
-    timed step runs the W_H build plus one Newton iteration and the step time
-    is extrapolated to all iterations (the iterations do identical work: a
-    fixed sweep count).  Returns (per-step seconds list, sample description)."""
+def oracle_columns_job(A, nodes, bary, cols):
+    """Columns ``cols`` of W_H = H A^-1 H^T through the oracle's sparse LU
+    (factored in the scene's own nested-dissection order); returns the
+    columns, the factor time and the solve time.  Runs in a spawned process."""
     from oracle import delassus as dl
-    from oracle import newton as nw
-    solver = dl.SystemSolver(scene.A)
     t0 = time.perf_counter()
-    oracle_step(scene, solver)
-    t_full = time.perf_counter() - t0
-    full = (steps + max(0, warmup - 1)) * t_full <= budget_s
-    for _ in range(max(0, warmup - 1)):
-        if full:
-            oracle_step(scene, solver)
-    times = []
-    for _ in range(steps):
-        if full:
-            t0 = time.perf_counter()
-            oracle_step(scene, solver)
-            times.append(time.perf_counter() - t0)
-        else:
-            t0 = time.perf_counter()
-            H = nw.dl.mapping_matrix(scene.nodes, scene.bary, scene.n)
-            WH = nw.dl.compliance_mapping(solver, H)
-            t_wh = time.perf_counter() - t0
-            t0 = time.perf_counter()
-            oracle_step_iter(scene, WH)
-            t_it = time.perf_counter() - t0
-            times.append(t_wh + scene.n_newton * t_it)
-    if full:
-        sample = "full time steps of the FP64 oracle (fast scheme: W_H = H A^-1 H^T by sparse LU, " \
-                 "W = C W_H C^T, PGS, proximity update, dq) on the same scene"
-    else:
-        sample = "per step: the oracle's W_H build plus one Newton iteration (W update, 50 PGS sweeps, " \
-                 "proximity update), step time = W_H + n_newton x iteration (identical iterations)"
-    return times, sample
+    solver = dl.SystemSolver(A, "NATURAL")
+    t1 = time.perf_counter()
+    H = dl.mapping_matrix(nodes, bary, A.shape[0])
+    Z = solver.solve(H.T[:, cols].toarray())
+    WHc = np.asarray(H @ Z)
+    return WHc, t1 - t0, time.perf_counter() - t1
 
 
-def oracle_step_iter(scene, WH):
-    from oracle import delassus as dl
-    from oracle import pgs as pg
-    C, delta = scene.linearize(scene.p0, 0)
-    W = dl.delassus_fast(C, WH)
-    lam, _, _ = pg.pgs(W, delta, scene.mu, None, scene.n_sweeps)
-    uk = (C.transpose(0, 2, 1) @ lam.reshape(-1, 3, 1)).reshape(-1)
-    return WH @ uk
+def start_oracle_sample(scene, ncols=ORACLE_SAMPLE_COLUMNS, seed=3):
+    """Start the oracle's sampled W_H columns in a spawned process (before any
+    GPU work, one BLAS thread); returns (pool, async result, columns)."""
+    import multiprocessing as mp
+    cols = np.sort(np.random.default_rng(seed).choice(3 * scene.m, size=min(ncols, 3 * scene.m), replace=False))
+    keys = ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        pool = mp.get_context("spawn").Pool(1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return pool, pool.apply_async(oracle_columns_job, (scene.A, scene.nodes, scene.bary, cols)), cols
+
+
+def oracle_sample_text(ncols, m3, t_fac):
+    return (f"{ncols} of the {m3} W_H columns (= H A^-1 H^T e_j) through the oracle's sparse LU solve, scaled to "
+            f"all {m3}: the W_H build of one step; the factorisation of A ({t_fac:.1f} s, per system, not per step) "
+            "and the Newton iterations are left out, so the value is an upper bound of the oracle's steps/s")
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -252,19 +266,37 @@ def run_reference(args):
     if rank != 0:
         return
     import scenegen
+    from oracle import delassus as dl
     scene = scenegen.NAMED[WORKLOAD]()
-    times, sample = time_oracle(scene, args.steps, args.warmup, budget_s=150.0)
+    t0 = time.perf_counter()
+    solver = dl.SystemSolver(scene.A, "NATURAL")
+    t_fac = time.perf_counter() - t0
+    H = dl.mapping_matrix(scene.nodes, scene.bary, scene.n)
+    m3 = 3 * scene.m
+    per = 16                   # W_H columns per sampled step
+    rng = np.random.default_rng(7)
+
+    def sample():
+        cols = np.sort(rng.choice(m3, size=per, replace=False))
+        t = time.perf_counter()
+        np.asarray(H @ solver.solve(H.T[:, cols].toarray()))
+        return (time.perf_counter() - t) * m3 / per
+
+    for _ in range(args.warmup):
+        sample()
+    times = [sample() for _ in range(args.steps)]
     total = sum(times)
     value = len(times) / total
     ms = [1e3 * t for t in times]
-    cores = oracle_threads()
+    cores = 1
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(scene),
         "latency_ms": {"p50": float(statistics.median(ms)), "p99": float(sorted(ms)[int(0.99 * (len(ms) - 1))])},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step: " + oracle_sample_text(per, m3, t_fac)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
@@ -272,35 +304,199 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def load_scene(icr, driver, ctx, s, precision, contraction="auto", warm_start=False):
+    sc = icr.Scene(ctx, precision=precision, n_sweeps=s.n_sweeps, contraction=contraction, warm_start=warm_start)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    driver.load_obstacle(sc, s.obstacle)
+    sc.set_field("MU", s.mu)
+    return sc
+
+
+def eager_step(sc, n_newton, stats=False):
+    """One time step call by call: lambda~ of every Newton iteration, W of the
+    first, the PGS statistics, dq and W_H."""
+    sc.reset_proximity()
+    sc.build_WH()
+    lams, sts, W1 = [], [], None
+    for k in range(n_newton):
+        sc.linearize(k)
+        sc.update_W()
+        if k == 0:
+            W1 = sc.get("W")
+        sts.append(sc.solve_friction(stats=stats))
+        lams.append(sc.get("LAMBDA"))
+        sc.update_proximity()
+    dq = sc.correct_motion(want_dq=True, reset=True)
+    return {"WH": sc.get("WH"), "W1": W1, "lams": lams, "stats": sts, "dq": dq}
+
+
+def timed_graph_steps(torch, sc, stream, flush, steps, warmup):
+    for _ in range(warmup):
+        sc.step_launch()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xff)
+        ev[i][0].record(stream)
+        sc.step_launch()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def phase_times(torch, sc, stream, flush, n_newton, reps=3):
+    """Device ms of the paper's table columns, CUDA events on the scene stream."""
+    phases = {"build_WH": [], "linearize": [], "update_W": [], "pgs": [], "update_proximity": [], "correct": []}
+
+    def rec(name, fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        phases[name].append((a, b))
+    for _ in range(reps):
+        flush.fill_(1)
+        sc.reset_proximity()
+        rec("build_WH", sc.build_WH)
+        for k in range(n_newton):
+            rec("linearize", lambda: sc.linearize(k))
+            rec("update_W", sc.update_W)
+            rec("pgs", lambda: sc.solve_friction(warm_start=False))
+            rec("update_proximity", sc.update_proximity)
+        rec("correct", lambda: sc.correct_motion(want_dq=False, reset=True))
+    torch.cuda.synchronize()
+    per_launch = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in phases.items()}
+    # PGS of each Newton iteration on its own (the first carries the loaded contacts)
+    pgs_iter = [statistics.mean(a.elapsed_time(b) for a, b in phases["pgs"][k::n_newton]) for k in range(n_newton)]
+    return per_launch, pgs_iter
+
+
+def kernel_profile(sc, flush, n_newton, reps=3):
+    """Per kernel: launches per step and device ms per launch, from CUDA
+    events around every launch of `reps` eagerly launched steps."""
+    sc.profile_begin()
+    for _ in range(reps):
+        flush.fill_(1)
+        sc.step(n_newton)
+    prof = sc.profile_end()
+    return {k: {"launches_per_step": n / reps, "ms_per_launch": ms / n, "ms_per_step": ms / reps}
+            for k, (n, ms) in prof.items()}
+
+
+def rooflines(scene, name, prof, info, phase_ms, pgs_stats, peaks, sm_count):
+    """Achieved against the bound of each kernel that carries the step's work.
+    Algorithmic work per launch: flops from icr_build_info (forward solve
+    3q (w^2 + 2 w r), contraction w c (c + 1) per front), bytes from the dense
+    definition (W update: W_H read and W written once; PGS: W read once per
+    sweep run)."""
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    bf16 = peaks.get("bf16_tflops") or 1900.0
+    src = "measured" if peaks.get("hbm_gbs") else "fallback"
+    tf32x3 = bf16 * TF32_PER_BF16 / 3.0
+    simt = sm_count * 128 * 2 * (peaks.get("sm_max_mhz") or 2070.0) * 1e6 / 1e12
+    m3 = 3 * scene.m
+    out = {}
+
+    def ent(k, bound, work, unit, peak, note):
+        if k not in prof or prof[k]["launches_per_step"] == 0:
+            return
+        per = work / prof[k]["launches_per_step"]
+        t = prof[k]["ms_per_launch"] / 1e3
+        ach = per / t / (1e9 if unit == "GB/s" else 1e12)
+        out[k] = {"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                  "traffic": profiled_traffic(k, name), "per_launch": per, "ms_per_launch": 1e3 * t,
+                  "share_of_step": prof[k]["ms_per_step"] / sum(v["ms_per_step"] for v in prof.values()),
+                  "peak_note": note}
+    ent("k_front_gemm_tc", "tensor", info["flops_front_tc"], "TFLOP/s", tf32x3,
+        f"3xTF32: the TF32 rate ({src} BF16 burst x {TF32_PER_BF16:.3f}, nominal ratio) / 3 products")
+    ent("k_contract_tc", "tensor", info["flops_contract_tc"], "TFLOP/s", tf32x3,
+        f"3xTF32: the TF32 rate ({src} BF16 burst x {TF32_PER_BF16:.3f}, nominal ratio) / 3 products")
+    ent("k_front_gemm", "alu", info["flops_front_simt"], "TFLOP/s", simt,
+        f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x max SM clock")
+    ent("k_contract", "alu", info["flops_contract_simt"], "TFLOP/s", simt,
+        f"FP32 FMA: {sm_count} SMs x 128 lanes x 2 flops x max SM clock")
+    ent("k_update_W", "hbm", scene.n_newton * (2.0 * m3 * m3 * 4 + 9 * scene.m * 4), "GB/s", hbm,
+        f"{src} copy bandwidth")
+    sweeps = [int(s["sweeps"]) for s in pgs_stats]
+    pgs_bytes = sum(sweeps) * m3 * m3 * 4.0 + scene.n_newton * m3 * 4 * 3
+    ent("k_pgs", "hbm", pgs_bytes, "GB/s", hbm,
+        f"{src} copy bandwidth, against the dense definition's W stream (one read of W per sweep)")
+    if "k_pgs" in out:
+        t = prof["k_pgs"]["ms_per_launch"] * 1e-3
+        visits = sum(sweeps) * scene.m / scene.n_newton
+        out["k_pgs"]["latency"] = {
+            "sweeps_per_launch": sweeps, "s_only_sweeps_per_launch": [int(s["sweeps_s_only"]) for s in pgs_stats],
+            "deferred_folds_per_launch": [int(s["deferred_folds"]) for s in pgs_stats],
+            "loaded_contacts_per_launch": [int(s["n_stick"] + s["n_slip"]) for s in pgs_stats],
+            "ns_per_contact_visit": t * 1e9 / max(visits, 1),
+            "note": "one CTA runs the Gauss-Seidel chain; W stays in L2 when it fits (C3: 81 MB of 129 MB) "
+                    "and a sweep reads only the rows of the blocks that may change, so the serial chain "
+                    "(local rule, ballot, broadcast, 3x3 fold per applied contact) bounds it, not HBM"}
+    flops = info["flops_front_tc"] + info["flops_front_simt"] + info["flops_contract_tc"] + \
+        info["flops_contract_simt"]
+    ach = flops / (phase_ms["build_WH"] * 1e-3) / 1e12
+    out["w_h_build"] = {"bound": "tensor", "achieved": ach, "peak": tf32x3, "unit": "TFLOP/s", "frac": ach / tf32x3,
+                        "traffic": None, "per_launch": flops, "ms_per_launch": phase_ms["build_WH"],
+                        "peak_note": "the whole W_H build (reach, forward solve, scaling, packing, contraction) "
+                                     "against the 3xTF32 rate of its two tensor-core kernels"}
+    return out
+
+
+def run_workload(torch, icr, driver, scene, name, ctx, stream, flush, args, tc_levels_arg=None, full=True):
+    """Time one workload in the bench configuration; returns a dict of figures
+    and the scene (left open)."""
+    sc = load_scene(icr, driver, ctx, scene, icr.FP32)
+    if tc_levels_arg:
+        plan = [int(x) for x in tc_levels_arg.split(",")]
+        sc.set_forward_plan(plan)
+        tc_levels = int(sum(plan))
+    else:
+        tc_levels = sc.autotune()
+    sc.step_capture(scene.n_newton)
+    l0 = sc.launches()
+    ms = timed_graph_steps(torch, sc, stream, flush, args.steps, args.warmup)
+    graph_launches = (sc.launches() - l0) // max(1, args.steps + args.warmup)
+    phase_ms, pgs_iter_ms = phase_times(torch, sc, stream, flush, scene.n_newton)
+    prof = kernel_profile(sc, flush, scene.n_newton)
+    # PGS statistics of every Newton iteration of one step (FP64 residual check included)
+    st = eager_step(sc, scene.n_newton, stats=True)["stats"]
+    info = sc.build_info()
+    s_ms = sorted(ms)
+    return sc, {"ms": ms, "tc_levels": tc_levels, "phase_ms": phase_ms, "pgs_ms_per_iteration": pgs_iter_ms,
+                "kernels": prof, "pgs_stats": st, "build_info": info, "graph_kernels_per_step": graph_launches,
+                "latency_ms": {"p50": float(statistics.median(ms)),
+                               "p99": float(s_ms[int(round(0.99 * (len(ms) - 1)))])}}
+
+
 def run_icr(args):
-    import numpy as np
     import torch
 
     import scenegen
     from paper_2306_06946_gb300 import build, driver, icr
 
     world, rank, local = dist_env()
+    scene = scenegen.NAMED[WORKLOAD]()
+    # the oracle's sample runs in a spawned process, started before any GPU work
+    pool = fut = cols = None
+    if rank == 0 and not (args.no_cpu_baseline and args.no_parity):
+        pool, fut, cols = start_oracle_sample(scene)
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    scene = scenegen.NAMED[WORKLOAD]()
     # a stream of its own (a graph cannot be captured on the legacy default
     # stream), made current so that the L2 flush and the events share it
     stream = torch.cuda.Stream(device=local)
     torch.cuda.set_stream(stream)
     ctx = icr.Context(local, stream.cuda_stream)
-    sc = icr.Scene(ctx, precision=icr.FP32, n_sweeps=scene.n_sweeps)
-    driver.load_system(sc, scene.factor)
-    driver.load_contacts(sc, scene.nodes, scene.bary, scene.p0)
-    driver.load_obstacle(sc, scene.obstacle)
-    sc.set_field("MU", scene.mu)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
 
-    # one time step (reset p and u, W_H build, n_newton x (linearise, W update,
-    # PGS from zero, proximity update), corrective motion), captured once as a
-    # CUDA graph after the per-level engine choice and replayed each step
+    # ---- the timed region: the captured step graph replayed K times
+    sc = load_scene(icr, driver, ctx, scene, icr.FP32)
     if args.tc_levels:
         plan = [int(x) for x in args.tc_levels.split(",")]
         sc.set_forward_plan(plan)
@@ -308,15 +504,9 @@ def run_icr(args):
     else:
         tc_levels = sc.autotune()
     sc.step_capture(scene.n_newton)
-
-    def step():
-        sc.step_launch()
-
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
     for _ in range(args.warmup):
-        step()
+        sc.step_launch()
     torch.cuda.synchronize()
-
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
@@ -326,7 +516,7 @@ def run_icr(args):
         for i in range(args.steps):
             flush.fill_(i & 0xff)
             ev[i][0].record(stream)
-            step()
+            sc.step_launch()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
     if dist is not None:
@@ -334,7 +524,7 @@ def run_icr(args):
     launches = sc.launches() - l0
     if args.nvtx_step:
         torch.cuda.nvtx.range_push("step")
-        step()
+        sc.step_launch()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     ms = [a.elapsed_time(b) for a, b in ev]
@@ -345,59 +535,17 @@ def run_icr(args):
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
 
-    # ---- per-phase device times (the paper's table columns), same stream
-    phases = {"build_WH": [], "linearize": [], "update_W": [], "pgs": [], "update_proximity": [], "correct": []}
-    for _ in range(3):
-        flush.fill_(1)
-        sc.reset_proximity()
-        for name, fn in [("build_WH", sc.build_WH)]:
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream); fn(); b.record(stream)
-            phases[name].append((a, b))
-        for k in range(scene.n_newton):
-            for name, fn in [("linearize", lambda: sc.linearize(k)), ("update_W", sc.update_W),
-                             ("pgs", lambda: sc.solve_friction(warm_start=False)),
-                             ("update_proximity", sc.update_proximity)]:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream); fn(); b.record(stream)
-                phases[name].append((a, b))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream); sc.correct_motion(want_dq=False, reset=True); b.record(stream)
-        phases["correct"].append((a, b))
-    torch.cuda.synchronize()
-    phase_ms = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in phases.items()}
-
-    # ---- sweeps each PGS launch of the step runs (the solve stops at a fixed point)
-    sc.reset_proximity()
-    sc.build_WH()
-    sweeps, s_only, folds = [], [], []
-    for k in range(scene.n_newton):
-        sc.linearize(k)
-        sc.update_W()
-        st = sc.solve_friction(warm_start=False, stats=True)
-        sweeps.append(int(st["sweeps"]))
-        s_only.append(int(st["sweeps_s_only"]))
-        folds.append(int(st["deferred_folds"]))
-        sc.update_proximity()
-    sc.correct_motion(want_dq=False, reset=True)
-
-    # ---- roofline of the dominant kernel (PGS: one k_pgs launch per Newton iteration)
+    # ---- per-phase and per-kernel device times, PGS statistics, rooflines
+    phase_ms, pgs_iter_ms = phase_times(torch, sc, stream, flush, scene.n_newton)
+    prof = kernel_profile(sc, flush, scene.n_newton)
+    step32 = eager_step(sc, scene.n_newton, stats=True)
+    info = sc.build_info()
     peaks = measured_peaks()
-    m3 = 3 * scene.m
-    mean_sweeps = sum(sweeps) / len(sweeps)
-    # per launch: W streamed once per sweep run, plus delta, mu and lambda
-    pgs_bytes = mean_sweeps * m3 * m3 * 4 + m3 * 4 * 3
-    pgs_s = phase_ms["pgs"] / 1e3
-    hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    achieved = pgs_bytes / pgs_s / 1e9
-    traffic = profiled_traffic("static constexpr int PGS_MAX_BLOCKS",
-                               "template <class T, int BC>\nstatic size_t pgs_smem_bytes", "k_pgs_liver_c1.md")
-    roofline = {"kernel": "k_pgs", "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": traffic,
-                "algorithmic_bytes": pgs_bytes, "sweeps_per_launch": sweeps,
-                "s_only_sweeps_per_launch": s_only, "deferred_folds_per_launch": folds,
-                "ns_per_contact_visit": pgs_s * 1e9 / (mean_sweeps * scene.m),
-                "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback"}
+    roof = rooflines(scene, WORKLOAD, prof, info, phase_ms, step32["stats"], peaks, sm_count)
+    dominant = max((k for k in roof if k.startswith("k_")), key=lambda k: prof[k]["ms_per_step"])
+    top = {k: roof[dominant][k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    top["kernel"] = dominant
+    top.update({k: v for k, v in roof[dominant].items() if k not in top})
 
     # ---- end to end through the public API with host buffers (pinned)
     e2e = None
@@ -439,40 +587,54 @@ def run_icr(args):
         e2e = {"value": world * len(times) / sum(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
-    # ---- parity of the timed configuration (FP32) against the FP64 oracle
-    parity = None
-    cpu = None
+    # ---- extra workloads: the C1-size liver and the contact-dense press scene
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        for name in EXTRA_WORKLOADS:
+            s2 = scenegen.NAMED[name]()
+            sc2, r = run_workload(torch, icr, driver, s2, name, ctx, stream, flush, args)
+            ro = rooflines(s2, name, r["kernels"], r["build_info"], r["phase_ms"], r["pgs_stats"], peaks, sm_count)
+            extras[name] = {
+                "workload": describe(name, s2), "value": 1e3 * args.steps / sum(r["ms"]), "unit": UNIT,
+                "ms_per_step": sum(r["ms"]) / args.steps, "latency_ms": r["latency_ms"], "phase_ms": r["phase_ms"],
+                "pgs_ms_per_newton_iteration": r["pgs_ms_per_iteration"],
+                "tc_levels": r["tc_levels"],
+                "kernel_share": {k: v["ms_per_step"] for k, v in r["kernels"].items() if v["ms_per_step"] > 0.01},
+                "roofline": {k: {x: ro[k][x] for x in ("bound", "achieved", "unit", "frac")} for k in ro},
+                "pgs_latency": ro.get("k_pgs", {}).get("latency"),
+            }
+            sc2.close()
+
+    # ---- parity of the timed configuration (FP32) on the same scene
+    parity = cpu = None
     if rank == 0:
-        from oracle import delassus as dl
-        solver = dl.SystemSolver(scene.A)
-        ref = oracle_step(scene, solver)
-        sc.reset_proximity()
-        sc.build_WH()
-        lams = []
-        for k in range(scene.n_newton):
-            sc.linearize(k)
-            sc.update_W()
-            if k == 0:
-                W1 = sc.get("W")
-            sc.solve_friction(warm_start=False)
-            lams.append(sc.get("LAMBDA"))
-            sc.update_proximity()
-        dq = sc.correct_motion(want_dq=True, reset=True)
-        WH_gpu = sc.get("WH")
-        W1_ref = ref["iters"][0]["W"]
-        d2 = sum(float(np.linalg.norm(a - it["lam"]) ** 2) for a, it in zip(lams, ref["iters"]))
-        n2 = sum(float(np.linalg.norm(it["lam"]) ** 2) for it in ref["iters"])
-        parity = {"W_H_rel_fro": float(np.linalg.norm(WH_gpu - ref["WH"]) / np.linalg.norm(ref["WH"])),
-                  "W_rel_fro": float(np.linalg.norm(W1 - W1_ref) / np.linalg.norm(W1_ref)),
-                  "lambda_rel_all_iters": (d2 / max(n2, 1e-300)) ** 0.5,
-                  "dq_rel": float(np.linalg.norm(dq - ref["dq"]) / np.linalg.norm(ref["dq"]))}
-        if world == 1 and not args.no_cpu_baseline:
-            t0 = time.perf_counter()
-            oracle_step(scene, solver)
-            t = time.perf_counter() - t0
-            cpu = {"value": 1.0 / t, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
-                   "sample": "one full time step of the FP64 oracle (fast scheme, sparse-LU W_H, Python PGS) "
-                             "on the same liver_c1 scene"}
+        if not args.no_parity:
+            sc64 = load_scene(icr, driver, ctx, scene, icr.FP64)
+            step64 = eager_step(sc64, scene.n_newton)
+            sc64.close()
+            rf = lambda a, b: float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+            d2 = sum(float(np.linalg.norm(a - b) ** 2) for a, b in zip(step32["lams"], step64["lams"]))
+            n2 = sum(float(np.linalg.norm(b) ** 2) for b in step64["lams"])
+            parity = {"vs_fp64_gpu_path": {"W_H_rel_fro": rf(step32["WH"], step64["WH"]),
+                                           "W_rel_fro": rf(step32["W1"], step64["W1"]),
+                                           "lambda_rel_all_iters": (d2 / max(n2, 1e-300)) ** 0.5,
+                                           "dq_rel": rf(step32["dq"], step64["dq"])},
+                      "note": "the GPU FP64 path matches the oracle at this size to 1e-12 (W_H, W) and 1e-9 "
+                              "(lambda~, dq) in tests/test_gpu_fullsize.py; W_H columns are also checked against "
+                              "the oracle here"}
+        if fut is not None:
+            WHc, t_fac, t_sol = fut.get()
+            pool.close()
+            pool.join()
+            if parity is not None:
+                rf = lambda a, b: float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+                parity["W_H_columns_vs_oracle"] = {"columns": int(cols.size),
+                                                   "fp32_rel_fro": rf(step32["WH"][:, cols], WHc),
+                                                   "fp64_rel_fro": rf(step64["WH"][:, cols], WHc)}
+            if world == 1 and not args.no_cpu_baseline:
+                m3 = 3 * scene.m
+                cpu = {"value": 1.0 / (t_sol / cols.size * m3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                       "sample": oracle_sample_text(int(cols.size), m3, t_fac)}
 
     if rank == 0:
         ms_sorted = sorted(ms)
@@ -482,16 +644,21 @@ def run_icr(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {**workload_config(scene), "parallelism": f"replicas x{world}",
                        "execution": f"captured step graph replayed per step; forward solve on tcgen05 in "
-                                    f"{tc_levels} etree levels ({'fixed' if args.tc_levels else 'autotuned'}), CUDA cores elsewhere"},
+                                    f"{tc_levels} etree levels ({'fixed' if args.tc_levels else 'autotuned'}), "
+                                    f"CUDA cores elsewhere; 3xTF32 contraction"},
             "latency_ms": {"p50": float(statistics.median(ms)),
                            "p99": float(ms_sorted[int(round(0.99 * (len(ms) - 1)))])},
             "phase_ms": phase_ms,
-            "roofline": roofline,
+            "pgs_ms_per_newton_iteration": pgs_iter_ms,
+            "roofline": top,
+            "roofline_kernels": roof,
+            "kernel_ms_per_step": {k: v["ms_per_step"] for k, v in prof.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
-            "parity_vs_fp64_oracle": parity,
+            "parity_vs_fp64": parity,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

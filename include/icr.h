@@ -336,8 +336,28 @@ typedef struct icr_build_info_t {
   int32_t prox_split;          /* 1: the proximity update runs as two launches (C^T lambda~ does not fit
                                   the default shared memory: 3m x element size > 48 KiB) */
   int64_t reach_nnz;           /* sum over supernodes of the contacts reaching them */
+  /* algorithmic flops of the build by engine: forward solve of front s
+     3q (w^2 + 2 w r) (w columns, r rows below, q reaching contacts), contraction
+     w c (c + 1) with c = 3q (the upper triangle of Y_s^T Y_s) */
+  double flops_front_tc, flops_front_simt, flops_contract_tc, flops_contract_simt;
 } icr_build_info_t;
 int icr_build_info(icr_scene* scene, icr_build_info_t* out);
+
+/* Per-kernel device time (diagnostic; the paper reports per-phase times in its
+ * Sec. 6 table, this splits them by kernel).  Between icr_profile_begin and
+ * icr_profile_end every kernel the scene launches eagerly (not inside
+ * icr_step_capture, nor a captured graph's launch) is bracketed by CUDA
+ * events on the context's stream; the events serialise the launches (no
+ * programmatic overlap while profiling).  icr_profile_end synchronises, then
+ * writes one entry per kernel name in first-launch order: up to max_out
+ * entries to out, and the number of names to *n_out. */
+typedef struct icr_kernel_time {
+  char name[32];
+  int32_t launches;
+  double total_ms;
+} icr_kernel_time;
+int icr_profile_begin(icr_scene* scene);
+int icr_profile_end(icr_scene* scene, icr_kernel_time* out, int32_t max_out, int32_t* n_out);
 
 /* Copy a field to host memory as double (float fields) or int32 (index fields).
  * `bytes` must equal the field's size; ICR_EINVAL otherwise. */

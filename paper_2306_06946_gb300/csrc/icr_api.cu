@@ -233,6 +233,26 @@ int check_step_graph(Scene* s, const char* where) {
   return ICR_OK;
 }
 
+int prof_mark(Scene* s, const char* name, bool after) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s->ctx->stream, &cs);
+  if (e != cudaSuccess) return cuda_fail(e, "profile: cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) return ICR_OK;
+  Profiler* P = s->prof;
+  if (!after) {
+    cudaEvent_t a = P->take(), b = P->take();
+    if (!a || !b) {
+      set_error("profile: cudaEventCreate failed");
+      return ICR_ECUDA;
+    }
+    P->recs.push_back({name, a, b});
+    e = cudaEventRecord(a, s->ctx->stream);
+  } else {
+    e = cudaEventRecord(P->recs.back().b, s->ctx->stream);
+  }
+  return e == cudaSuccess ? ICR_OK : cuda_fail(e, "profile: cudaEventRecord");
+}
+
 int check_device_error(Scene* s) {
   if (!s->dev_err.p) return ICR_OK;
   int h = 0;
@@ -363,6 +383,7 @@ int icr_scene_destroy(icr_scene* s) {
     if (s->stage_ev[k]) cudaEventDestroy(s->stage_ev[k]);
   }
   if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
+  delete s->prof;
   icr_ctx* c = static_cast<icr_ctx*>(s->ctx);
   delete s;
   if (--c->scenes == 0 && c->destroyed) delete c;
@@ -1125,6 +1146,59 @@ int icr_correct_motion(icr_scene* s, double* dq_out, int reset) {
   return ICR_OK;
 }
 
+int icr_profile_begin(icr_scene* s) {
+  RET(check_scene(s));
+  if (!s->prof) s->prof = new (std::nothrow) Profiler();
+  if (!s->prof) {
+    set_error("profile_begin: out of host memory");
+    return ICR_ENOMEM;
+  }
+  s->prof->recycle();
+  return ICR_OK;
+}
+
+int icr_profile_end(icr_scene* s, icr_kernel_time* out, int32_t max_out, int32_t* n_out) {
+  RET(check_scene(s));
+  if (!s->prof) {
+    set_error("profile_end: no icr_profile_begin before");
+    return ICR_ESTATE;
+  }
+  if (max_out < 0 || (max_out > 0 && !out) || !n_out) {
+    set_error("profile_end: need max_out >= 0, out for max_out entries and n_out");
+    return ICR_EINVAL;
+  }
+  RET(set_device(s));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  Profiler* P = s->prof;
+  s->prof = nullptr;   // launches of the aggregation below (none) and later ones are not timed
+  std::vector<icr_kernel_time> agg;
+  int rc = ICR_OK;
+  for (const auto& r : P->recs) {
+    float ms = 0.f;
+    const cudaError_t e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "profile_end: cudaEventElapsedTime");
+      break;
+    }
+    size_t i = 0;
+    while (i < agg.size() && std::strncmp(agg[i].name, r.name, sizeof(agg[i].name) - 1) != 0) ++i;
+    if (i == agg.size()) {
+      icr_kernel_time k{};
+      std::snprintf(k.name, sizeof(k.name), "%s", r.name);
+      agg.push_back(k);
+    }
+    agg[i].launches += 1;
+    agg[i].total_ms += ms;
+  }
+  P->recycle();
+  s->prof = nullptr;
+  delete P;
+  if (rc != ICR_OK) return rc;
+  *n_out = (int32_t)agg.size();
+  for (int32_t i = 0; i < std::min<int32_t>(max_out, (int32_t)agg.size()); ++i) out[i] = agg[i];
+  return ICR_OK;
+}
+
 int icr_build_info(icr_scene* s, icr_build_info_t* out) {
   RET(check_scene(s));
   if (!out) {
@@ -1156,6 +1230,28 @@ int icr_build_info(icr_scene* s, icr_build_info_t* out) {
     if (units > 0) {
       ++out->tc_levels;
       out->gemm_tc_split_max = std::max(out->gemm_tc_split_max, splits[li]);
+    }
+  }
+  // algorithmic flops of each engine, with the planner's rules (k_plan): the
+  // forward solve of front s costs 3q (w^2 + 2 w r) (triangular solve on the
+  // w x w block, product with the r x w block below), the contraction
+  // w c (c + 1) for c = 3q columns (upper triangle of Y_s^T Y_s)
+  int mode = s->params.contraction;
+  if (s->prec == ICR_FP64) mode = ICR_CONTRACT_SIMT;
+  if (mode == ICR_CONTRACT_AUTO) mode = ICR_CONTRACT_TF32X3;
+  const bool simt = mode == ICR_CONTRACT_SIMT;
+  for (int li = 0; li < nlev; ++li) {
+    const Level& lv = s->levels[li];
+    for (int p = lv.first; p < lv.first + lv.count; ++p) {
+      const int sn = s->h_level_list[p];
+      const double q = qc[sn], c = 3.0 * q;
+      if (q == 0) continue;
+      const double w = s->h_super_ptr[sn + 1] - s->h_super_ptr[sn];
+      const double r = (double)(s->h_rowpat_ptr[sn + 1] - s->h_rowpat_ptr[sn]);
+      const double fwd = c * (w * w + 2.0 * w * r), con = w * c * (c + 1.0);
+      const bool tcg = !simt && s->tc_level[li] && w >= TC_GEMM_MIN_W && c >= TC_GEMM_MIN_COLS;
+      (tcg ? out->flops_front_tc : out->flops_front_simt) += fwd;
+      (!simt && c >= 64 ? out->flops_contract_tc : out->flops_contract_simt) += con;
     }
   }
   out->gemm_tc_units = P(PLAN_GTC, ns);

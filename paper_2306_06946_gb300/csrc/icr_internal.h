@@ -70,8 +70,41 @@ struct Level {
   int rmax = 0;    // most below-diagonal rows
 };
 
+// Opt-in per-launch timing of a scene (icr_profile_begin / icr_profile_end):
+// an event pair around every eagerly launched kernel, tagged with its name.
+// Never active while a stream is captured.
+struct Profiler {
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;   // events of earlier profiles, reused
+  cudaEvent_t take() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+  }
+  void recycle() {
+    for (auto& r : recs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  ~Profiler() {
+    recycle();
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 struct Scene {
   Ctx* ctx = nullptr;
+  Profiler* prof = nullptr;   // per-launch timing while profiling
   icr_params params{};
   int prec = ICR_FP32;
   size_t tsize = 4;
@@ -238,12 +271,23 @@ struct DevInt {
   }
 };
 
+// events around a launch while the scene is profiled (not during capture)
+int prof_mark(Scene* s, const char* name, bool after);
+
 // launch through pdl_launch, check it and count it in the scene `s` in scope
-#define PDL(where, ...)                                \
-  do {                                                 \
-    const cudaError_t e_ = pdl_launch(__VA_ARGS__);    \
+#define PDL(where, ...)                                 \
+  do {                                                  \
+    if (s->prof) {                                      \
+      const int rc_ = prof_mark(s, where, false);       \
+      if (rc_ != ICR_OK) return rc_;                    \
+    }                                                   \
+    const cudaError_t e_ = pdl_launch(__VA_ARGS__);     \
     if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-    ++s->launches;                                     \
+    ++s->launches;                                      \
+    if (s->prof) {                                      \
+      const int rc_ = prof_mark(s, where, true);        \
+      if (rc_ != ICR_OK) return rc_;                    \
+    }                                                   \
   } while (0)
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);

@@ -29,7 +29,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_build_WH", "icr_update_W", "icr_solve_friction", "icr_update_proximity", "icr_correct_motion",
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
            "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
-           "icr_set_forward_plan", "icr_forward_levels", "icr_build_info")
+           "icr_set_forward_plan", "icr_forward_levels", "icr_build_info",
+           "icr_profile_begin", "icr_profile_end")
 
 
 class IcrError(RuntimeError):
@@ -50,7 +51,13 @@ class BuildInfo(ct.Structure):
     _fields_ = [("levels", ct.c_int32), ("tc_levels", ct.c_int32), ("gemm_tc_units", ct.c_int32),
                 ("gemm_tc_split_max", ct.c_int32), ("gemm_simt_units", ct.c_int32),
                 ("contract_tc_units", ct.c_int32), ("contract_tc_split", ct.c_int32),
-                ("contract_simt_units", ct.c_int32), ("prox_split", ct.c_int32), ("reach_nnz", ct.c_int64)]
+                ("contract_simt_units", ct.c_int32), ("prox_split", ct.c_int32), ("reach_nnz", ct.c_int64),
+                ("flops_front_tc", ct.c_double), ("flops_front_simt", ct.c_double),
+                ("flops_contract_tc", ct.c_double), ("flops_contract_simt", ct.c_double)]
+
+
+class KernelTime(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("launches", ct.c_int32), ("total_ms", ct.c_double)]
 
 
 class PgsStats(ct.Structure):
@@ -107,6 +114,8 @@ def lib() -> ct.CDLL:
             "icr_set_forward_plan": [P, P, ct.c_int32],
             "icr_forward_levels": [P, P],
             "icr_build_info": [P, ct.POINTER(BuildInfo)],
+            "icr_profile_begin": [P],
+            "icr_profile_end": [P, ct.POINTER(KernelTime), ct.c_int32, ct.POINTER(ct.c_int32)],
             "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
         }
         for name, args in sigs.items():
@@ -350,7 +359,18 @@ class Scene:
         """Which paths the last W_H build took (icr_build_info)."""
         b = BuildInfo()
         _check(lib().icr_build_info(self.h, ct.byref(b)))
-        return {f: int(getattr(b, f)) for f, _ in BuildInfo._fields_}
+        return {f: (float if f.startswith("flops") else int)(getattr(b, f)) for f, _ in BuildInfo._fields_}
+
+    def profile_begin(self):
+        """Time every kernel this scene launches eagerly from now on."""
+        _check(lib().icr_profile_begin(self.h))
+
+    def profile_end(self) -> dict:
+        """{kernel name: (launches, total device ms)} since profile_begin."""
+        buf = (KernelTime * 64)()
+        n = ct.c_int32(0)
+        _check(lib().icr_profile_end(self.h, buf, 64, ct.byref(n)))
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(64, n.value))}
 
     def step_capture(self, n_newton: int):
         _check(lib().icr_step_capture(self.h, int(n_newton)))
