@@ -10,7 +10,9 @@
 // exits.  In host code its name is only a host-side stand-in, not a device
 // address: the device address is looked up with cudaGetSymbolAddress once per
 // device (on the first call made with that device current) and passed to the
-// kernels.
+// kernels.  The cached address belongs to the device's context at that time:
+// after cudaDeviceReset the module is loaded again elsewhere, so the call must
+// not be used across a device reset in one process.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -65,7 +67,11 @@ __global__ void k_na_clear(uint32_t* bitmap, size_t words, int* status) {
 }
 
 // One thread per (contact, node): mark the contact on the etree path from the
-// node's supernode to the root, stopping where another thread already marked it.
+// node's supernode to the root, stopping where another thread already marked
+// it.  Every id is checked before it is used as an index: a node id outside
+// [0, n_nodes), a supernode id outside [0, ns), or a parent that is neither -1
+// nor above its child sets the status word and ends the walk (parents above
+// their children also bound the walk by ns steps).
 __global__ void k_na_mark(const int* __restrict__ nodes, int m, int n_nodes, const int* __restrict__ node_super,
                           const int* __restrict__ parent, int ns, uint32_t* bitmap, int words, int* status) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -77,18 +83,24 @@ __global__ void k_na_mark(const int* __restrict__ nodes, int m, int n_nodes, con
     return;
   }
   int s = node_super[node];
+  if (s < 0 || s >= ns) {
+    *status = 1;
+    return;
+  }
   const uint32_t bit = 1u << (a & 31);
   const int w = a >> 5;
   for (int guard = 0; guard < ns; ++guard) {
-    if (s < 0) return;
-    if (s >= ns) {
+    const uint32_t old = atomicOr(&bitmap[(size_t)s * words + w], bit);
+    if (old & bit) return;
+    const int p = parent[s];
+    if (p == -1) return;
+    if (p <= s || p >= ns) {
       *status = 1;
       return;
     }
-    const uint32_t old = atomicOr(&bitmap[(size_t)s * words + w], bit);
-    if (old & bit) return;
-    s = parent[s];
+    s = p;
   }
+  *status = 1;   // not reached with valid parents (each step climbs)
 }
 
 // One block per supernode: count its contacts and list them in ascending order.
@@ -133,11 +145,19 @@ extern "C" int icr_reach_noalloc(int32_t m, int32_t nsuper, int32_t n_nodes, con
               (int)ICR_NOALLOC_SCRATCH_WORDS);
     return ICR_EINVAL;
   }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // the call reads its status back and synchronises: it cannot be captured
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+  if (ce != cudaSuccess) return cuda_fail(ce, "reach_noalloc: cudaStreamIsCapturing");
+  if (cs != cudaStreamCaptureStatusNone) {
+    set_error("reach_noalloc: the stream is being captured; this call synchronises and cannot be captured");
+    return ICR_ESTATE;
+  }
   uint32_t* bitmap = nullptr;
   int* status = nullptr;
   int rc = scratch_for_current_device(&bitmap, &status);
   if (rc != ICR_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   const int grid_clear = (int)((need + 255) / 256 < 1024 ? (need + 255) / 256 : 1024);
   k_na_clear<<<grid_clear, 256, 0, st>>>(bitmap, need, status);
   cudaError_t e = cudaGetLastError();
@@ -158,7 +178,8 @@ extern "C" int icr_reach_noalloc(int32_t m, int32_t nsuper, int32_t n_nodes, con
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "reach_noalloc: synchronize");
   if (h_status) {
-    set_error("reach_noalloc: a node id or a supernode id was out of range; the outputs are incomplete");
+    set_error("reach_noalloc: a node id, a supernode id or a parent was out of range (a parent must be -1 or "
+              "above its child); the outputs are incomplete");
     return ICR_EINVAL;
   }
   return ICR_OK;
