@@ -142,6 +142,27 @@ int icr_ctx_destroy(icr_ctx* ctx);
 /* Device bytes currently held by the context's scenes. */
 int icr_ctx_bytes_in_use(const icr_ctx* ctx, uint64_t* out);
 
+/* Bound of the tensor-core kernels' pipeline waits (the shared-memory ring
+ * and the TMEM hand-offs between the MMA-issuing thread and the warps that
+ * read the accumulators), in ns of the GPU's global timer; 1 s by default.
+ * A wait that runs out (or sees the other side give up) ends the CTA's work:
+ * bulk copies in flight are allowed to land and every issued MMA to complete
+ * (each of these waits bounded by 1 s) before TMEM is freed, the scene's
+ * device error word is set, and the next synchronising call of that scene
+ * returns ICR_ETIMEOUT (its W_H is then incomplete; the next icr_build_WH
+ * forms it again).  0 makes every pipeline wait a single non-blocking poll:
+ * failure injection for tests of that path.  Kernels read the value when they
+ * are launched (a captured step graph keeps the value of its capture). */
+int icr_ctx_set_wait_limit(icr_ctx* ctx, uint64_t pipeline_wait_ns);
+
+/* Failure injection: the device allocation after the next `after` ones made
+ * for the context's scenes fails with ICR_ENOMEM (once; -1 switches it off).
+ * A set call that fails part way leaves the scene without what it was
+ * replacing (icr_set_system: no system; icr_set_mapping: no mapping; the
+ * obstacle calls: no obstacle), so later calls return ICR_ESTATE until it is
+ * set again. */
+int icr_ctx_inject_alloc_failure(icr_ctx* ctx, int64_t after);
+
 int icr_scene_create(icr_ctx* ctx, icr_scene** out, const icr_params* params);
 int icr_scene_destroy(icr_scene* scene);
 int icr_set_params(icr_scene* scene, const icr_params* params);
@@ -391,11 +412,15 @@ int icr_set_field(icr_scene* scene, int32_t field, const double* src, size_t byt
  * 32-bit words (4 MiB), held by every GPU that loads the library until the
  * process exits; the call allocates nothing.  nsuper * ceil(m / 32) must not
  * exceed that size (ICR_EINVAL otherwise).  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  Every call shares the array and clears the part
- * it uses; calls that overlap on the GPU (for instance on two streams) race and
- * must be serialised by the caller.  An out-of-range node or supernode id gives
- * ICR_EINVAL with incomplete outputs. */
+ * up the array's device address (cudaGetSymbolAddress) and keeps it for the
+ * process, so the call must not be used across a cudaDeviceReset.  Every call
+ * reads a status word back and synchronises the stream, so no call can be
+ * captured into a CUDA graph: on a stream that is being captured it returns
+ * ICR_ESTATE without enqueueing anything.  Every call shares the array and
+ * clears the part it uses; calls that overlap on the GPU (for instance on two
+ * streams) race and must be serialised by the caller.  A node id outside
+ * [0, n_nodes), a supernode id outside [0, nsuper) or a parent that is neither
+ * -1 nor above its child gives ICR_EINVAL with incomplete outputs. */
 #define ICR_NOALLOC_SCRATCH_WORDS (1 << 20)
 int icr_reach_noalloc(int32_t m, int32_t nsuper, int32_t n_nodes, const int32_t* nodes, const int32_t* node_super,
                       const int32_t* parent, int32_t* qcount, int32_t* qidx, void* cuda_stream);

@@ -43,6 +43,10 @@ int dalloc(Scene* s, DBuf& b, size_t bytes) {
   if (b.p && b.bytes >= bytes) return ICR_OK;
   dfree(s, b);
   Ctx* c = s->ctx;
+  if (c->fail_alloc_after >= 0 && c->fail_alloc_after-- == 0) {
+    set_error("allocation of %zu bytes failed (injected by icr_ctx_inject_alloc_failure)", bytes);
+    return ICR_ENOMEM;
+  }
   if (c->budget && c->in_use + bytes > c->budget) {
     set_error("allocation of %zu bytes exceeds the context HBM budget (%llu of %llu in use)", bytes,
               (unsigned long long)c->in_use, (unsigned long long)c->budget);
@@ -67,6 +71,7 @@ void dfree(Scene* s, DBuf& b) {
   if (b.p) {
     cudaFree(b.p);
     s->ctx->in_use -= b.bytes;
+    ++s->alloc_epoch;   // a captured graph that read this buffer is stale
   }
   b.p = nullptr;
   b.bytes = 0;
@@ -308,6 +313,24 @@ int icr_ctx_destroy(icr_ctx* ctx) {
     return ICR_OK;
   }
   delete ctx;
+  return ICR_OK;
+}
+
+int icr_ctx_set_wait_limit(icr_ctx* ctx, uint64_t pipeline_wait_ns) {
+  if (!ctx) {
+    set_error("NULL context");
+    return ICR_EINVAL;
+  }
+  ctx->wait_ns = pipeline_wait_ns;
+  return ICR_OK;
+}
+
+int icr_ctx_inject_alloc_failure(icr_ctx* ctx, int64_t after) {
+  if (!ctx || after < -1) {
+    set_error("inject_alloc_failure: need a context and after >= -1");
+    return ICR_EINVAL;
+  }
+  ctx->fail_alloc_after = after;
   return ICR_OK;
 }
 
@@ -562,6 +585,10 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
 
   RET(set_device(s));
   CK(cudaStreamSynchronize(s->ctx->stream));
+  // from here buffers are replaced: a failure part way leaves no system
+  s->has_system = false;
+  s->has_mapping = s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
+  s->obst_kind = 0;
   RET(dalloc(s, s->super_ptr, (ns + 1) * sizeof(int32_t)));
   RET(dalloc(s, s->rowpat_ptr, (ns + 1) * sizeof(int64_t)));
   RET(dalloc(s, s->rowpat, std::max<int64_t>(1, rp[ns]) * sizeof(int32_t)));
@@ -705,6 +732,9 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   const int64_t ldw = std::max<int64_t>(96, ((3 * (int64_t)m + 95) / 96) * 96);
   const size_t T = s->tsize;
   const size_t mm = std::max(1, m);
+  // from here buffers are replaced: a failure part way leaves no mapping
+  s->has_mapping = s->has_WH = s->has_W = s->has_dirs = s->has_lam = false;
+  s->obst_kind = 0;
   RET(dalloc(s, s->nodes, 4 * mm * sizeof(int32_t)));
   RET(dalloc(s, s->bary, 4 * mm * T));
   RET(dalloc(s, s->bitmap, (size_t)ns * words * sizeof(uint32_t)));
@@ -882,7 +912,13 @@ int icr_set_obstacle_plane(icr_scene* s, int32_t n_iters, const double* normals,
       return ICR_EINVAL;
     }
   }
+  for (int i = 0; i < 3 * m; ++i)
+    if (!std::isfinite(anchors[i])) {
+      set_error("set_obstacle_plane: anchor coordinate %d is not finite", i);
+      return ICR_EINVAL;
+    }
   RET(set_device(s));
+  s->obst_kind = 0;   // until the new obstacle is in place
   RET(dalloc(s, s->obst_normals, std::max<size_t>(1, (size_t)n_iters * m * 3) * sizeof(double)));
   RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)m * 3) * sizeof(double)));
   RET(upload(s, s->obst_normals, normals, (size_t)n_iters * m * 3));
@@ -911,6 +947,11 @@ static int check_spheres(int m, int32_t n_spheres, const double* spheres, const 
       set_error("set_obstacle_spheres: contact %d names sphere %d of %d", a, contact_sphere[a], n_spheres);
       return ICR_EINVAL;
     }
+  for (int i = 0; i < 3 * m; ++i)
+    if (!std::isfinite(anchors[i])) {
+      set_error("set_obstacle_spheres: anchor coordinate %d is not finite", i);
+      return ICR_EINVAL;
+    }
   return ICR_OK;
 }
 
@@ -921,6 +962,7 @@ int icr_set_obstacle_spheres(icr_scene* s, int32_t n_spheres, const double* sphe
   const int m = s->m;
   RET(check_spheres(m, n_spheres, spheres, contact_sphere, anchors));
   RET(set_device(s));
+  s->obst_kind = 0;   // until the new obstacle is in place
   RET(dalloc(s, s->obst_anchors, std::max<size_t>(1, (size_t)m * 3) * sizeof(double)));
   RET(dalloc(s, s->obst_spheres, (size_t)n_spheres * 4 * sizeof(double)));
   RET(dalloc(s, s->obst_of, std::max<size_t>(1, (size_t)m) * sizeof(int32_t)));

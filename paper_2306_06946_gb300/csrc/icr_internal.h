@@ -21,6 +21,8 @@ struct Ctx {
   cudaStream_t stream = nullptr;
   uint64_t budget = 0;
   uint64_t in_use = 0;
+  uint64_t wait_ns = 1000000000ull;   // bound of the tensor-core kernels' pipeline waits
+  int64_t fail_alloc_after = -1;      // failure injection: allocations left before one fails (-1: off)
   int scenes = 0;          // live scenes; the context is freed after the last one
   bool destroyed = false;  // icr_ctx_destroy was called while scenes were alive
 };

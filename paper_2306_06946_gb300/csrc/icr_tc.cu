@@ -38,7 +38,9 @@ namespace {
 
 constexpr int TM = TC_TILE;   // output tile (M = N)
 constexpr int KT = TC_KT;     // K rows per stage
-constexpr long long WAIT_LIMIT = 1LL << 26;
+// bound of the waits that must not be cut short: copies in flight landing and
+// every issued MMA completing before TMEM is freed (microseconds in practice)
+constexpr uint64_t DRAIN_NS = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -71,17 +73,38 @@ __device__ __forceinline__ uint32_t instr_desc(int ab_type) {
          ((uint32_t)(TM >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
-    uint32_t done;
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier: true once the phase has
+// completed; false after limit_ns of global time, at once when `alive` (the
+// CTA's shared ok flag) has been cleared by the other side of the pipeline,
+// or, with limit_ns = 0, after one non-blocking poll (failure injection).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns,
+                                          const volatile int* alive = nullptr) {
+  uint32_t done;
+  if (limit_ns == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+  }
+  const uint64_t t0 = global_ns();
+  for (;;) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if (alive && *alive == 0) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -248,7 +271,7 @@ struct TcBars {
 template <int MODE>
 __device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB, bool same, int nk,
                            unsigned char* smem, TcBars& br, uint32_t tmem, uint32_t& gl, uint32_t& gm,
-                           uint32_t& gc) {
+                           uint32_t& gc, uint64_t wait_ns, const volatile int* alive) {
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   const uint32_t idesc = instr_desc(TR::TYPE);
@@ -261,7 +284,7 @@ __device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB,
     if (kt < nk) {   // load K-block kt
       const uint32_t g = gl + kt;
       const int st = g % STAGES;
-      if (g >= STAGES && !mbar_wait(smem_u32(&br.empty[st]), ((g / STAGES) - 1) & 1)) {
+      if (g >= STAGES && !mbar_wait(smem_u32(&br.empty[st]), ((g / STAGES) - 1) & 1, wait_ns, alive)) {
         ok = false;
         break;
       }
@@ -287,13 +310,13 @@ __device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB,
       const bool last = kc % PROMOTE_KB == PROMOTE_KB - 1 || kc == nk - 1;
       const uint32_t gb = gc + ch;                 // buffer use counter of this chunk
       const uint32_t tb = tmem + (gb & 1) * TM;    // its 128 TMEM columns
-      if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1)) {
+      if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1, wait_ns, alive)) {
         ok = false;
         break;
       }
       const uint32_t g = gm + kc;
       const int st = g % STAGES;
-      if (!mbar_wait(smem_u32(&br.full[st]), (g / STAGES) & 1)) {
+      if (!mbar_wait(smem_u32(&br.full[st]), (g / STAGES) & 1, wait_ns, alive)) {
         ok = false;
         break;
       }
@@ -329,8 +352,8 @@ __device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB,
       ++nm;
     }
   }
-  if (!ok)   // let copies already in flight land
-    for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&br.full[g % STAGES]), (g / STAGES) & 1);
+  if (!ok)   // let copies already in flight land (full bound, no early abort)
+    for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&br.full[g % STAGES]), (g / STAGES) & 1, DRAIN_NS);
   gl += nl;
   gm += nm;
   gc += nchunks;
@@ -338,12 +361,13 @@ __device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB,
 }
 
 // warps 0-3: acc[0..127] <- sum over the unit's chunks of the row's TMEM columns
-__device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, uint32_t& gc, float* acc) {
+__device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, uint32_t& gc, float* acc,
+                         uint64_t wait_ns, const volatile int* alive) {
   const int nchunks = (nk + PROMOTE_KB - 1) / PROMOTE_KB;
   bool ok = true;
   for (int ch = 0; ch < nchunks; ++ch) {
     const uint32_t gb = gc + ch;
-    const int fine = ok && mbar_wait(smem_u32(&br.tfull[gb & 1]), (gb >> 1) & 1);
+    const int fine = ok && mbar_wait(smem_u32(&br.tfull[gb & 1]), (gb >> 1) & 1, wait_ns, alive);
     if (!__all_sync(0xffffffffu, fine)) {
       ok = false;
       break;
@@ -370,7 +394,7 @@ __device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, 
   return ok;
 }
 
-__device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, int* ok_sh) {
+__device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volatile int* ok_sh) {
   const int tid = threadIdx.x;
   if ((tid >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_base)),
@@ -400,7 +424,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
   if (threadIdx.x == 128) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
         smem_u32(&br.fin)));
-    mbar_wait(smem_u32(&br.fin), 0);
+    mbar_wait(smem_u32(&br.fin), 0, DRAIN_NS);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
@@ -417,14 +441,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
                   const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
-                  int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p) {
+                  int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p, uint64_t wait_ns) {
   pdl_entry();
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block), then the list's prefix
   __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
-  __shared__ int ok_sh, unit_sh;
+  __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
+  __shared__ int unit_sh;
   const int total = plan[ns];
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -440,10 +465,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
   for (;;) {
-    if (tid == 0) unit_sh = atomicAdd(counter, 1);
+    // thread 0 decides for the CTA before the barrier (no thread writes ok_sh
+    // between the previous unit's barrier and this one): a CTA whose pipeline
+    // gave up takes no further unit
+    if (tid == 0) unit_sh = ok_sh ? atomicAdd(counter, 1) : total;
     __syncthreads();
     const int ur = unit_sh;
-    if (ur >= total || !ok_sh) break;   // uniform
+    if (ur >= total) break;   // uniform
     const int u = total - 1 - ur;
     const int pos = find_unit(plan_s, 0, ns, u);
     const int s = level_list[pos];
@@ -463,13 +491,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 4) {
       if (lane == 0 && !tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK,
                                          pk + (boff[s] + (int64_t)J * nk + k0) * BLK, I == J, nku, smem, br, tmem,
-                                         gl, gm, gc)) {
+                                         gl, gm, gc, wait_ns, &ok_sh)) {
         ok_sh = 0;
         atomicExch(dev_err, 1);
       }
     } else {
       float acc[TM];
-      if (tc_drain(nku, br, tmem, warp, lane, gc, acc)) {
+      if (tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
         const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
         if (li < ncol) {
           const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
@@ -502,14 +530,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                     const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
                     const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
-                    int* dev_err, const int* __restrict__ gsplit_p) {
+                    int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
   pdl_entry();
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
-  __shared__ int ok_sh, unit_sh;
+  __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
+  __shared__ int unit_sh;
   const int u0 = plan[pa], total = plan[pb] - u0;
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -518,10 +547,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
   for (;;) {
-    if (tid == 0) unit_sh = atomicAdd(counter, 1);
+    // thread 0 decides for the CTA before the barrier (no thread writes ok_sh
+    // between the previous unit's barrier and this one): a CTA whose pipeline
+    // gave up takes no further unit
+    if (tid == 0) unit_sh = ok_sh ? atomicAdd(counter, 1) : total;
     __syncthreads();
     const int ur = unit_sh;
-    if (ur >= total || !ok_sh) break;   // uniform
+    if (ur >= total) break;   // uniform
     const int u = u0 + total - 1 - ur;
     const int pos = find_unit(plan, pa, pb, u);
     const int s = level_list[pos];
@@ -537,13 +569,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 4) {
       if (lane == 0 && !tc_produce<MODE>(gpk + (goff[s] + (int64_t)rt * nk + k0) * BLK,
                                          fpk + (boff[s] + (int64_t)ct * nk + k0) * BLK, false, nku, smem, br, tmem,
-                                         gl, gm, gc)) {
+                                         gl, gm, gc, wait_ns, &ok_sh)) {
         ok_sh = 0;
         atomicExch(dev_err, 1);
       }
     } else {
       float acc[TM];
-      if (tc_drain(nku, br, tmem, warp, lane, gc, acc)) {
+      if (tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
         const int row = rt * TM + 32 * warp + lane;   // front row owned by this thread
         const int cmax = ncol - ct * TM;              // columns of this tile inside the front
         if (row < nrows && nsk > 1) {
@@ -633,7 +665,7 @@ int contract_tc_T(Scene* s) {
       plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_TC, ns, (const int*)s->level_list.p,
       (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
       (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p, cache_plan,
-      plan + PLAN_LISTS * (ns + 1) + 2 + 2 * nlev);
+      plan + PLAN_LISTS * (ns + 1) + 2 + 2 * nlev, s->ctx->wait_ns);
   return ICR_OK;
 }
 
@@ -681,7 +713,7 @@ int launch_front_gemm_tc(Scene* s, int level) {
       (const int*)s->level_list.p, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->gpk_off.p,
       (const unsigned char*)s->Gpk.p, (const int64_t*)s->tc_boff.p, (const unsigned char*)s->Ypk.p, (float*)s->X.p,
-      s->ldx, (int*)s->dev_err.p, plan + PLAN_LISTS * (ns + 1) + 2 + nlev + level);
+      s->ldx, (int*)s->dev_err.p, plan + PLAN_LISTS * (ns + 1) + 2 + nlev + level, s->ctx->wait_ns);
   return ICR_OK;
 }
 

@@ -30,7 +30,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_get", "icr_field_bytes", "icr_set_field", "icr_reach_noalloc", "icr_step", "icr_step_capture",
            "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
            "icr_set_forward_plan", "icr_forward_levels", "icr_build_info",
-           "icr_profile_begin", "icr_profile_end")
+           "icr_profile_begin", "icr_profile_end",
+           "icr_ctx_set_wait_limit", "icr_ctx_inject_alloc_failure")
 
 
 class IcrError(RuntimeError):
@@ -83,6 +84,8 @@ def lib() -> ct.CDLL:
             "icr_ctx_create": [ct.POINTER(P), ct.c_int, P, ct.c_uint64],
             "icr_ctx_destroy": [P],
             "icr_ctx_bytes_in_use": [P, ct.POINTER(ct.c_uint64)],
+            "icr_ctx_set_wait_limit": [P, ct.c_uint64],
+            "icr_ctx_inject_alloc_failure": [P, ct.c_int64],
             "icr_scene_create": [P, ct.POINTER(P), ct.POINTER(Params)],
             "icr_scene_destroy": [P],
             "icr_set_params": [P, ct.POINTER(Params)],
@@ -184,6 +187,14 @@ class Context:
         v = ct.c_uint64()
         _check(lib().icr_ctx_bytes_in_use(self.h, ct.byref(v)))
         return int(v.value)
+
+    def set_wait_limit(self, ns: int):
+        """Bound of the tensor-core pipeline waits in ns (0: one poll, failure injection)."""
+        _check(lib().icr_ctx_set_wait_limit(self.h, int(ns)))
+
+    def inject_alloc_failure(self, after: int):
+        """The allocation after the next ``after`` ones fails once (-1: off)."""
+        _check(lib().icr_ctx_inject_alloc_failure(self.h, int(after)))
 
     def close(self):
         if self.h:
