@@ -759,7 +759,8 @@ def run_serve(args):
     import scenegen
     from paper_2306_06946_gb300 import build, driver, icr
     build.build()
-    pool = [scenegen.NAMED["beam_c0"](), scenegen.NAMED["liver_c1"]()] + scenegen.batch_scenes(14, seed=4)
+    pool = [scenegen.NAMED["beam_c0"](), scenegen.NAMED["liver_c1"](), scenegen.NAMED["tissue_c3"]()] + \
+        scenegen.batch_scenes(14, seed=4)
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     budget = 150 << 30
@@ -786,7 +787,7 @@ def run_serve(args):
     which = rng.integers(0, len(scs), size=nreq)
     icr.serve(scs, which[:64], arrivals[:64] - arrivals[0], n_slots=args.slots)   # warm-up
     with ClockSampler(0) as clk:
-        lat, span = icr.serve(scs, which, arrivals, n_slots=args.slots, timeout_s=120.0)
+        lat, span, adm = icr.serve(scs, which, arrivals, n_slots=args.slots, timeout_s=120.0, stats=True)
     frame = 1.0 / 60.0
     ctx64, scs64, _, _ = admit(icr.FP64)
     n64 = max(1, nreq // 10)
@@ -796,10 +797,11 @@ def run_serve(args):
         "ms_per_step": 1e3 * span / nreq, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"serve_c4: Poisson arrivals, mean {args.rate:g} steps/s for {args.duration:g} s, "
-                               f"over {len(scs)} resident scenes (beam_c0, liver_c1, 14 batched sizes); "
-                               f"HBM budget 150 GB ({rejected} rejected); Newton iteration 1 warm-started from the "
-                               "scene's previous step",
+                               f"over {len(scs)} scenes (beam_c0, liver_c1, tissue_c3, 14 batched sizes), "
+                               f"requests uniform over the scenes; HBM budget 150 GB ({rejected} rejected at load); "
+                               "Newton iteration 1 warm-started from the scene's previous step",
                    "slots": args.slots},
+        "admission": adm,
         "latency_ms": {k: 1e3 * v for k, v in _pcts(lat).items()},
         "within_frame_16.7ms": float(np.mean(lat <= frame)),
         "hbm_resident_gb": ctx.bytes_in_use() / 1e9,

@@ -341,6 +341,25 @@ int icr_sync(icr_scene* scene);
  * starts; 8 by default): streams that share a queue run one after another. */
 int icr_serve(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene, const double* req_arrival_s,
               int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s);
+/* icr_serve with admission under the HBM budget of each scene's context.
+ * Scenes may be evicted (icr_scene_evict) when the call starts.  A request for
+ * an evicted scene readmits it (icr_scene_readmit) before it starts; while the
+ * context's budget is short, the least recently used resident scenes of that
+ * context with no step in flight are evicted first.  A scene that does not fit
+ * even then waits while other steps of its context are in flight and is
+ * rejected (latency_s = -1) when none are.  stats (may be NULL) receives the
+ * evictions, readmissions and rejections and the seconds spent admitting.
+ * Eviction frees device memory (cudaFree), which waits for the device's work in
+ * flight: admissions stall the loop while they run. */
+typedef struct icr_serve_stats {
+  int32_t evictions;
+  int32_t readmissions;
+  int32_t rejected;
+  double admit_s;
+} icr_serve_stats;
+int icr_serve_ex(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_scene, const double* req_arrival_s,
+                 int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s,
+                 icr_serve_stats* stats);
 
 /* Which paths the last icr_build_WH took, read back from the device work
  * lists (synchronises; needs icr_build_WH, ICR_ESTATE otherwise).  Diagnostic:
@@ -379,6 +398,26 @@ typedef struct icr_kernel_time {
 } icr_kernel_time;
 int icr_profile_begin(icr_scene* scene);
 int icr_profile_end(icr_scene* scene, icr_kernel_time* out, int32_t max_out, int32_t* n_out);
+
+/* Eviction (the paper has no counterpart: serving many scenes under an HBM
+ * budget needs it).  icr_scene_evict synchronises, copies what a later time
+ * step needs (the system's operators, the mapping, the obstacle, mu, the
+ * gaps and directions, lambda~ and its warm start, p, p_0, u, dq) to pinned
+ * host memory and frees every device byte of the scene (its buffers, the
+ * input staging buffer and its captured graph), so its bytes return to the
+ * context's budget.  While evicted, every other call on the scene returns
+ * ICR_ESTATE.  icr_scene_readmit allocates the same buffers again
+ * (ICR_ENOMEM over the budget, the scene then stays evicted), restores the
+ * kept contents byte for byte and, when the scene had a captured step, captures
+ * it again without running a step (the warm start is untouched); W_H and W are
+ * formed again by the next step.  Evicting an evicted scene or readmitting a
+ * resident one does nothing.  A device error word that was set (a timed-out
+ * wait) makes icr_scene_evict return ICR_ETIMEOUT and keep the scene resident.
+ * icr_scene_residency: whether the scene is resident, and the device bytes it
+ * holds (or would hold again when readmitted). */
+int icr_scene_evict(icr_scene* scene);
+int icr_scene_readmit(icr_scene* scene);
+int icr_scene_residency(icr_scene* scene, int32_t* resident, uint64_t* device_bytes);
 
 /* Copy a field to host memory as double (float fields) or int32 (index fields).
  * `bytes` must equal the field's size; ICR_EINVAL otherwise. */

@@ -97,6 +97,10 @@ static int check_scene(icr_scene* s) {
     set_error("scene is NULL");
     return ICR_EINVAL;
   }
+  if (s->evicted) {
+    set_error("the scene is evicted: icr_scene_readmit it first");
+    return ICR_ESTATE;
+  }
   return ICR_OK;
 }
 
@@ -391,12 +395,11 @@ int icr_scene_destroy(icr_scene* s) {
   if (!s) return ICR_OK;
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->ctx->stream);
-  DBuf* all[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->G, &s->dinv, &s->dinvsqrt,
-                 &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
-                 &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary, &s->bitmap, &s->wprefix, &s->qcount,
-                 &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop, &s->WH, &s->W, &s->C, &s->delta, &s->mu, &s->lam, &s->p,
-                 &s->p0, &s->u, &s->uk, &s->y, &s->dq, &s->stats, &s->dev_err, &s->Ypk, &s->tc_boff, &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->lam0, &s->plan, &s->Gpk, &s->gpk_off, &s->tc_super, &s->wcoup, &s->level_first};
-  for (DBuf* b : all) dfree(s, *b);
+  std::vector<std::pair<DBuf*, bool>> all;
+  scene_buffers(s, all);
+  for (auto& b : all) dfree(s, *b.first);
+  for (auto& sv : s->saved) cudaFreeHost(sv.host);
+  s->saved.clear();
   if (s->stage_dev.p) {
     cudaFree(s->stage_dev.p);
     s->ctx->in_use -= s->stage_dev.bytes;
@@ -1520,17 +1523,20 @@ int icr_step(icr_scene* s, int32_t n_newton) {
   return step_enqueue(s, n_newton);
 }
 
-int icr_step_capture(icr_scene* s, int32_t n_newton) {
-  RET(check_scene(s));
-  RET(set_device(s));
+// Capture step_enqueue into the scene's graph; with `warm_up` one plain step
+// runs first so that every kernel is set up (per-device attributes) before
+// capture.  A readmitted scene has run its kernels before and is captured
+// without it, which leaves its warm start untouched.
+static int capture_step(Scene* s, int32_t n_newton, bool warm_up) {
   cudaStream_t st = s->ctx->stream;
   if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) {
     set_error("step_capture: the context needs its own CUDA stream to capture a graph");
     return ICR_EINVAL;
   }
-  if (!s->tuned) RET(icr_autotune(s, nullptr, nullptr, 0));
-  RET(step_enqueue(s, n_newton));   // a plain step sets every kernel up before capture
-  CK(cudaStreamSynchronize(st));
+  if (warm_up) {
+    RET(step_enqueue(s, n_newton));
+    CK(cudaStreamSynchronize(st));
+  }
   if (s->step_graph) {
     cudaGraphExecDestroy(s->step_graph);
     s->step_graph = nullptr;
@@ -1557,6 +1563,168 @@ int icr_step_capture(icr_scene* s, int32_t n_newton) {
   if (e2 != cudaSuccess) {
     s->step_graph = nullptr;
     return cuda_fail(e2, "cudaGraphInstantiate");
+  }
+  return ICR_OK;
+}
+
+int icr_step_capture(icr_scene* s, int32_t n_newton) {
+  RET(check_scene(s));
+  RET(set_device(s));
+  if (!s->tuned) RET(icr_autotune(s, nullptr, nullptr, 0));
+  return capture_step(s, n_newton, true);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- eviction
+namespace icr {
+void scene_buffers(Scene* s, std::vector<std::pair<DBuf*, bool>>& out) {
+  DBuf* keep[] = {&s->super_ptr, &s->rowpat_ptr, &s->rowpat, &s->val_ptr, &s->G, &s->dinv, &s->dinvsqrt,
+                  &s->parent, &s->child_ptr, &s->child_list, &s->relidx, &s->level_list, &s->node_super,
+                  &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary,
+                  &s->C, &s->delta, &s->mu, &s->lam, &s->lam0, &s->p, &s->p0, &s->u, &s->dq, &s->tc_boff,
+                  &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->Gpk, &s->gpk_off,
+                  &s->tc_super, &s->level_first};
+  DBuf* scratch[] = {&s->bitmap, &s->wprefix, &s->qcount, &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop,
+                     &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wcoup, &s->stats, &s->dev_err};
+  out.clear();
+  for (DBuf* b : keep) out.push_back({b, true});
+  for (DBuf* b : scratch) out.push_back({b, false});
+}
+
+int scene_evict(Scene* s) {
+  if (s->evicted) return ICR_OK;
+  CK(cudaSetDevice(s->ctx->device));
+  RET(check_device_error(s));   // synchronises; a pending device error is reported, not dropped
+  std::vector<std::pair<DBuf*, bool>> all;
+  scene_buffers(s, all);
+  std::vector<Scene::Saved> saved;
+  auto undo = [&]() {
+    for (auto& sv : saved) cudaFreeHost(sv.host);
+  };
+  for (auto& b : all) {
+    if (!b.second || !b.first->p) continue;
+    void* h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, b.first->bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      undo();
+      return cuda_fail(e, "scene_evict: cudaHostAlloc");
+    }
+    saved.push_back({b.first, h, b.first->bytes});
+    e = cudaMemcpyAsync(h, b.first->p, b.first->bytes, cudaMemcpyDeviceToHost, s->ctx->stream);
+    if (e != cudaSuccess) {
+      undo();
+      return cuda_fail(e, "scene_evict: copy to host");
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(s->ctx->stream);
+  if (e != cudaSuccess) {
+    undo();
+    return cuda_fail(e, "scene_evict: synchronize");
+  }
+  // the scene gives up every device byte: buffers, the input staging buffer, its graph
+  s->evicted_sizes.clear();
+  uint64_t bytes = 0;
+  for (auto& b : all) {
+    s->evicted_sizes.push_back({b.first, b.first->bytes});
+    bytes += b.first->bytes;
+    dfree(s, *b.first);
+  }
+  if (s->stage_dev.p) {
+    for (int k = 0; k < 2; ++k)
+      if (s->stage_used[k]) cudaEventSynchronize(s->stage_ev[k]);
+    cudaFree(s->stage_dev.p);
+    s->ctx->in_use -= s->stage_dev.bytes;
+    s->stage_dev.p = nullptr;
+    s->stage_dev.bytes = 0;
+    for (int k = 0; k < 2; ++k) {
+      if (s->stage_host[k]) cudaFreeHost(s->stage_host[k]);
+      s->stage_host[k] = nullptr;
+      s->stage_used[k] = false;
+    }
+    s->stage_bytes = 0;
+  }
+  s->recapture = s->step_graph != nullptr;
+  if (s->step_graph) {
+    cudaGraphExecDestroy(s->step_graph);
+    s->step_graph = nullptr;
+  }
+  s->saved = std::move(saved);
+  s->resident_bytes = bytes;
+  s->evicted = true;
+  return ICR_OK;
+}
+
+int scene_readmit(Scene* s) {
+  if (!s->evicted) return ICR_OK;
+  CK(cudaSetDevice(s->ctx->device));
+  Ctx* c = s->ctx;
+  if (c->budget && c->in_use + s->resident_bytes > c->budget) {
+    set_error("readmit: %llu bytes exceed the context HBM budget (%llu of %llu in use)",
+              (unsigned long long)s->resident_bytes, (unsigned long long)c->in_use, (unsigned long long)c->budget);
+    return ICR_ENOMEM;
+  }
+  for (auto& b : s->evicted_sizes) {
+    if (b.second == 0) continue;
+    const int rc = dalloc(s, *b.first, b.second);
+    if (rc != ICR_OK) {   // back to the evicted state: nothing is kept on the device
+      for (auto& f : s->evicted_sizes) dfree(s, *f.first);
+      return rc;
+    }
+  }
+  cudaStream_t st = s->ctx->stream;
+  for (auto& sv : s->saved) CK(cudaMemcpyAsync(sv.b->p, sv.host, sv.bytes, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(s->dev_err.p, 0, s->dev_err.bytes, st));
+  // W's padding columns must read zero (icr_update_W writes the 3m x 3m part only)
+  CK(cudaMemsetAsync(s->W.p, 0, s->W.bytes, st));
+  s->W_zeroed = s->W.gen;
+  s->W_zeroed_ld = s->ldw;
+  s->W_zeroed_rows = 3 * (int64_t)std::max(1, s->m);
+  CK(cudaStreamSynchronize(st));
+  for (auto& sv : s->saved) cudaFreeHost(sv.host);
+  s->saved.clear();
+  s->evicted = false;
+  s->has_WH = s->has_W = false;   // rebuilt by the next step
+  if (s->recapture) {
+    s->recapture = false;
+    RET(capture_step(s, s->graph_newton, false));
+  }
+  return ICR_OK;
+}
+}  // namespace icr
+
+extern "C" {
+
+int icr_scene_evict(icr_scene* s) {
+  if (!s) {
+    set_error("scene is NULL");
+    return ICR_EINVAL;
+  }
+  return scene_evict(s);
+}
+
+int icr_scene_readmit(icr_scene* s) {
+  if (!s) {
+    set_error("scene is NULL");
+    return ICR_EINVAL;
+  }
+  return scene_readmit(s);
+}
+
+int icr_scene_residency(icr_scene* s, int32_t* resident, uint64_t* device_bytes) {
+  if (!s || !resident || !device_bytes) {
+    set_error("scene_residency: NULL argument");
+    return ICR_EINVAL;
+  }
+  *resident = s->evicted ? 0 : 1;
+  if (s->evicted) {
+    *device_bytes = s->resident_bytes;
+  } else {
+    std::vector<std::pair<DBuf*, bool>> all;
+    scene_buffers(s, all);
+    uint64_t b = s->stage_dev.bytes;
+    for (auto& x : all) b += x.first->bytes;
+    *device_bytes = b;
   }
   return ICR_OK;
 }

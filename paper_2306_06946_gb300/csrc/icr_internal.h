@@ -164,6 +164,18 @@ struct Scene {
   icr_params graph_params{};
   bool has_WH = false, has_dirs = false, has_W = false, has_lam = false;
 
+  // ---- eviction (icr_scene_evict / icr_scene_readmit)
+  bool evicted = false;
+  struct Saved {
+    DBuf* b;
+    void* host;   // pinned copy of a kept buffer
+    size_t bytes;
+  };
+  std::vector<Saved> saved;                              // kept buffers' contents while evicted
+  std::vector<std::pair<DBuf*, size_t>> evicted_sizes;   // every buffer's size while evicted
+  uint64_t resident_bytes = 0;                           // device bytes the scene held when evicted
+  bool recapture = false;                                // a step graph existed when it was evicted
+
   // ---- obstacle (device linearisation)
   int obst_kind = 0;   // 0 none, 1 plane, 2 sphere
   int obst_iters = 0;
@@ -173,6 +185,11 @@ struct Scene {
 
 int dalloc(Scene* s, DBuf& b, size_t bytes);
 void dfree(Scene* s, DBuf& b);
+// every device buffer of a scene (not the input staging buffer), with
+// whether an eviction keeps its contents (the rest is rebuilt by every step)
+void scene_buffers(Scene* s, std::vector<std::pair<DBuf*, bool>>& out);
+int scene_evict(Scene* s);
+int scene_readmit(Scene* s);
 
 // Device statistics written by the PGS kernels (FP64 residual check).
 struct PgsDevStats {

@@ -517,7 +517,12 @@ static size_t gemm_smem_bytes() {
 
 // ------------------------------------------------------------------ a3 pivot scaling
 // Y = D^-1/2 X in place on the first w rows of every front (one warp per DOF
-// row), with D^-1/2 in the working precision.
+// row), with D^-1/2 kept in FP64.  FP32 scenes split the FP64 value once per
+// row into FP32 parts hi + lo (hi = D^-1/2 rounded, lo = the remainder
+// rounded) and form x hi + (x lo) with one fused rounding: the error of x lo
+// is below 2^-48 of the product, so the result is the FP64 product rounded to
+// FP32 except within 2^-48 (relative) of a rounding midpoint, where the FP64
+// route rounds twice as well.  The FP32 units do it at their full rate.
 template <class T>
 __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                         const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
@@ -528,11 +533,14 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
   if (row >= n) return;
   const int s = dof_super[row];
   const int ncol = 3 * qcount[s];
-  // in the FP32 path D^-1/2 is rounded to FP32 first (one more rounding of
-  // the product, within an FP32 ulp; FP64 arithmetic is a slow path here)
-  const T ds = (T)dinvsqrt[row];
+  const double ds = dinvsqrt[row];
   T* F = X + (fr_ptr[s] + row - super_ptr[s]) * ldx;
-  for (int c = lane; c < ncol; c += 32) F[c] *= ds;
+  if constexpr (sizeof(T) == 8) {
+    for (int c = lane; c < ncol; c += 32) F[c] *= ds;
+  } else {
+    const float hi = (float)ds, lo = (float)(ds - (double)hi);
+    for (int c = lane; c < ncol; c += 32) F[c] = __fmaf_rn(F[c], hi, F[c] * lo);
+  }
 }
 
 // ------------------------------------------------------------------ a4 contraction
@@ -1176,7 +1184,10 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         chg_it[(t + 1) & 1] = 0;   // nothing pending: look ahead from b
       }
       __syncthreads();
-      nsd = tryd = 0;   // again from the end of this sweep
+      // every residual is complete again: the look-ahead from b may start
+      // S-only sweeps over the new S at once (as a sweep's first look-ahead does)
+      nsd = 0;
+      tryd = 1;
       b = pb + 1;
       pb = -1;
       known = false;

@@ -31,7 +31,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_step_launch", "icr_sync", "icr_serve", "icr_autotune",
            "icr_set_forward_plan", "icr_forward_levels", "icr_build_info",
            "icr_profile_begin", "icr_profile_end",
-           "icr_ctx_set_wait_limit", "icr_ctx_inject_alloc_failure")
+           "icr_ctx_set_wait_limit", "icr_ctx_inject_alloc_failure", "icr_scene_evict", "icr_scene_readmit",
+           "icr_scene_residency", "icr_serve_ex")
 
 
 class IcrError(RuntimeError):
@@ -55,6 +56,11 @@ class BuildInfo(ct.Structure):
                 ("contract_simt_units", ct.c_int32), ("prox_split", ct.c_int32), ("reach_nnz", ct.c_int64),
                 ("flops_front_tc", ct.c_double), ("flops_front_simt", ct.c_double),
                 ("flops_contract_tc", ct.c_double), ("flops_contract_simt", ct.c_double)]
+
+
+class ServeStats(ct.Structure):
+    _fields_ = [("evictions", ct.c_int32), ("readmissions", ct.c_int32), ("rejected", ct.c_int32),
+                ("admit_s", ct.c_double)]
 
 
 class KernelTime(ct.Structure):
@@ -120,6 +126,11 @@ def lib() -> ct.CDLL:
             "icr_profile_begin": [P],
             "icr_profile_end": [P, ct.POINTER(KernelTime), ct.c_int32, ct.POINTER(ct.c_int32)],
             "icr_serve": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P],
+            "icr_serve_ex": [ct.POINTER(P), ct.c_int32, P, P, ct.c_int32, ct.c_int32, ct.c_double, P, P,
+                             ct.POINTER(ServeStats)],
+            "icr_scene_evict": [P],
+            "icr_scene_readmit": [P],
+            "icr_scene_residency": [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_uint64)],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -157,15 +168,19 @@ def reach_noalloc(m: int, nsuper: int, n_nodes: int, nodes_ptr: int, node_super_
                                    P(qidx_ptr or None), P(stream or None)))
 
 
-def serve(scenes, req_scene, req_arrival_s, n_slots: int, timeout_s: float = 120.0):
-    """icr_serve: returns (latency_s per request, makespan_s)."""
+def serve(scenes, req_scene, req_arrival_s, n_slots: int, timeout_s: float = 120.0, stats: bool = False):
+    """icr_serve_ex: returns (latency_s per request, makespan_s), and with
+    ``stats`` also a dict of evictions, readmissions, rejections and admit_s."""
     arr = (P * len(scenes))(*[sc.h for sc in scenes])
     rs = _arr(req_scene, np.int32)
     ra = _arr(req_arrival_s, np.float64)
     lat = np.zeros(rs.size)
     mk = ct.c_double()
-    _check(lib().icr_serve(arr, len(scenes), _ptr(rs), _ptr(ra), int(rs.size), int(n_slots), float(timeout_s),
-                           _ptr(lat), ct.byref(mk)))
+    st = ServeStats()
+    _check(lib().icr_serve_ex(arr, len(scenes), _ptr(rs), _ptr(ra), int(rs.size), int(n_slots), float(timeout_s),
+                              _ptr(lat), ct.byref(mk), ct.byref(st)))
+    if stats:
+        return lat, float(mk.value), {f: getattr(st, f) for f, _ in ServeStats._fields_}
     return lat, float(mk.value)
 
 
@@ -365,6 +380,19 @@ class Scene:
     def set_forward_plan(self, tc_levels):
         f = _arr(tc_levels, np.uint8)
         _check(lib().icr_set_forward_plan(self.h, _ptr(f), int(f.size)))
+
+    def evict(self):
+        """icr_scene_evict: keep the scene's state in pinned host memory, free its device memory."""
+        _check(lib().icr_scene_evict(self.h))
+
+    def readmit(self):
+        _check(lib().icr_scene_readmit(self.h))
+
+    def residency(self):
+        """(resident, device bytes held, or held again once readmitted)."""
+        r, b = ct.c_int32(), ct.c_uint64()
+        _check(lib().icr_scene_residency(self.h, ct.byref(r), ct.byref(b)))
+        return bool(r.value), int(b.value)
 
     def build_info(self) -> dict:
         """Which paths the last W_H build took (icr_build_info)."""

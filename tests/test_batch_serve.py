@@ -315,3 +315,125 @@ def test_step_inputs_in_one_call_equal_the_single_calls(batch, torch_mod, prec, 
     sc.step(b.n_newton)
     sc.sync()
     assert np.all(np.isfinite(sc.get("DQ")))
+
+
+# ---------------------------------------------------------------- eviction and admission under a budget
+FIELDS_KEPT = ("LAMBDA0", "LAMBDA", "P", "U", "DQ", "C", "DELTA", "MU")
+
+
+def _warm_scene(icr, driver, ctx, s, prec=None):
+    sc = icr.Scene(ctx, precision=icr.FP32 if prec is None else prec, n_sweeps=s.n_sweeps, warm_start=True)
+    driver.load_system(sc, s.factor)
+    driver.load_contacts(sc, s.nodes, s.bary, s.p0)
+    driver.load_obstacle(sc, s.obstacle)
+    sc.set_field("MU", s.mu)
+    sc.step_capture(s.n_newton)
+    return sc
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
+def test_evict_readmit_restores_the_state_bitwise(batch, torch_mod, prec, tol):
+    """An evicted scene gives its device memory back and refuses calls; once
+    readmitted it holds the same bytes as before, and its next warm-started
+    steps follow those of a twin that was never evicted."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    s = batch[1]
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    twin_ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    sc = _warm_scene(icr, driver, ctx, s, prec)
+    twin = _warm_scene(icr, driver, twin_ctx, s, prec)
+    for x in (sc, twin):
+        for _ in range(2):
+            x.step_launch()
+        x.sync()
+    before = {f: sc.get(f).copy() for f in FIELDS_KEPT}
+    used = ctx.bytes_in_use()
+    assert sc.residency() == (True, used)
+    sc.evict()
+    assert ctx.bytes_in_use() == 0 and sc.residency() == (False, used)
+    for call in (lambda: sc.get("DQ"), sc.step_launch, sc.build_WH):
+        with pytest.raises(icr.IcrError) as e:
+            call()
+        assert e.value.code == icr.ESTATE
+    sc.evict()                               # a second eviction does nothing
+    sc.readmit()
+    assert ctx.bytes_in_use() == used and sc.residency() == (True, used)
+    for f in FIELDS_KEPT:
+        assert np.array_equal(sc.get(f), before[f]), f
+    for x in (sc, twin):
+        x.step_launch()
+        x.sync()
+    assert rel(sc.get("DQ"), twin.get("DQ")) < tol
+    assert rel(sc.get("LAMBDA0"), twin.get("LAMBDA0")) < max(tol, 1e-4 if prec == 0 else tol)
+
+
+def test_serve_evicts_and_readmits_under_a_budget(batch, torch_mod):
+    """Scenes of one context whose budget holds about two of them: the request
+    loop readmits each requested scene, evicting the least recently used idle
+    ones, and every scene ends where the same steps run alone (never evicted)
+    end."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    scenes_ = batch[:4]
+    foot = []
+    for s in scenes_:
+        c = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+        x = _warm_scene(icr, driver, c, s)
+        foot.append(x.residency()[1])
+        x.close()
+        c.close()
+    budget = sorted(foot)[-1] + sorted(foot)[-2] + (1 << 20)
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream, hbm_budget=budget)
+    served = []
+    for s in scenes_:
+        x = _warm_scene(icr, driver, ctx, s)
+        x.evict()
+        served.append(x)
+    rng = np.random.default_rng(31)
+    nreq = 24
+    which = rng.integers(0, len(scenes_), size=nreq)
+    which[:4] = np.arange(4)                 # every scene is requested
+    arrivals = np.cumsum(rng.exponential(1.0 / 2000.0, size=nreq))
+    lat, span, st = icr.serve(served, which, arrivals, n_slots=2, stats=True)
+    assert st["rejected"] == 0 and np.all(lat >= 0)
+    assert st["evictions"] > 0 and st["readmissions"] >= len(scenes_)
+    assert ctx.bytes_in_use() <= budget
+    alone = []
+    for i, s in enumerate(scenes_):
+        c = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+        x = _warm_scene(icr, driver, c, s)
+        for _ in range(int(np.sum(which == i))):
+            x.step_launch()
+        x.sync()
+        alone.append((c, x))
+    for x in served:                         # read the scenes back one at a time
+        x.evict()
+    for x, (_, a) in zip(served, alone):
+        x.readmit()
+        assert rel(x.get("DQ"), a.get("DQ")) < 1e-5
+        l0 = a.get("LAMBDA0")
+        assert rel(x.get("LAMBDA0"), l0) < 1e-4
+        x.evict()
+
+
+def test_serve_rejects_a_scene_that_cannot_fit(batch, torch_mod):
+    """A scene that does not fit next to memory the loop may not evict (a
+    resident scene outside the request loop) is rejected, not waited for."""
+    from paper_2306_06946_gb300 import build, driver, icr
+    build.build()
+    s = batch[0]
+    c = icr.Context(0, torch_mod.cuda.Stream().cuda_stream)
+    probe = _warm_scene(icr, driver, c, s)
+    foot = probe.residency()[1]
+    probe.close()
+    c.close()
+    ctx = icr.Context(0, torch_mod.cuda.Stream().cuda_stream, hbm_budget=int(1.5 * foot))
+    other = _warm_scene(icr, driver, ctx, s)   # stays resident, not served
+    other.evict()                              # room to load y ...
+    y = _warm_scene(icr, driver, ctx, s)
+    y.evict()
+    other.readmit()                            # ... then other takes it back
+    lat, _, st = icr.serve([y], np.zeros(3, np.int32), np.zeros(3), n_slots=1, stats=True)
+    assert st["rejected"] == 3 and np.all(lat == -1.0)
+    assert not y.residency()[0]
