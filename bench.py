@@ -818,7 +818,7 @@ def _oracle_columns(A, nodes, bary, n, cols):
     W_H = H A^-1 H^T through the oracle's sparse LU (run in a spawned process)."""
     from oracle import delassus as dl
     t0 = time.perf_counter()
-    solver = dl.SystemSolver(A)
+    solver = dl.SystemSolver(A, "NATURAL")   # the scene's own nested-dissection order
     t1 = time.perf_counter()
     H = dl.mapping_matrix(nodes, bary, n)
     Z = solver.solve(H.T[:, cols].toarray())
@@ -865,8 +865,8 @@ def run_precision(args):
                 np.add.at(r, 3 * scene.nodes[:, i] + ax, scene.bary[:, i] * U[:, ax])
         return r
 
-    def run(prec, mode):
-        sc = icr.Scene(ctx, precision=prec, n_sweeps=scene.n_sweeps, contraction=mode)
+    def run(prec, mode, w_update="fp32"):
+        sc = icr.Scene(ctx, precision=prec, n_sweeps=scene.n_sweeps, contraction=mode, w_update=w_update)
         driver.load_system(sc, scene.factor)
         driver.load_contacts(sc, scene.nodes, scene.bary, scene.p0)
         driver.load_obstacle(sc, scene.obstacle)
@@ -907,12 +907,15 @@ def run_precision(args):
     with ClockSampler(0) as clk:
         ref = run(icr.FP64, "simt")
         rows = {}
-        for mode in args.modes.split(","):
-            r = run(icr.FP32, mode)
+        jobs = [(mode, mode, "fp32") for mode in args.modes.split(",")]
+        # the W update with TF32 / BF16 operands (FP32 accumulation), 3xTF32 contraction
+        jobs += [(f"tf32x3+W_{w}", "tf32x3", w) for w in ("tf32", "bf16")]
+        for label, mode, wu in jobs:
+            r = run(icr.FP32, mode, wu)
             st_ref, st = _states(ref["lams"][0], scene.mu), _states(r["lams"][0], scene.mu)
             d2 = sum(float(np.linalg.norm(a - b) ** 2) for a, b in zip(r["lams"], ref["lams"]))
             n2 = sum(float(np.linalg.norm(b) ** 2) for b in ref["lams"])
-            rows[mode] = {"W_H_rel_fro": rf(r["WH"], ref["WH"]), "W_rel_fro": rf(r["W"], ref["W"]),
+            rows[label] = {"W_H_rel_fro": rf(r["WH"], ref["WH"]), "W_rel_fro": rf(r["W"], ref["W"]),
                           "lambda_rel_iter1": rf(r["lams"][0], ref["lams"][0]),
                           "lambda_rel_all_iters": (d2 / max(n2, 1e-300)) ** 0.5, "dq_rel": rf(r["dq"], ref["dq"]),
                           "state_mismatches_iter1": int(np.sum(st != st_ref)),

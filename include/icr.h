@@ -86,6 +86,15 @@ enum icr_contraction {
   ICR_CONTRACT_BF16 = 4     /* tensor cores, BF16 operands, FP32 accumulation */
 };
 
+/* Operand precision of W = C W_H C^T (Alg. 3 step 2) in an FP32 scene; the
+ * products are accumulated in FP32 in every mode.  FP64 scenes ignore it. */
+enum icr_w_update {
+  ICR_W_FP32 = 0,   /* C and W_H as stored (FP32) */
+  ICR_W_TF32 = 1,   /* C and W_H rounded to TF32 (10-bit mantissa) before the products */
+  ICR_W_BF16 = 2    /* W_H read from a BF16 copy written when W_H is formed (half the bytes per
+                       update), C rounded to BF16 */
+};
+
 typedef struct icr_params {
   int32_t precision;     /* enum icr_precision */
   int32_t n_sweeps;      /* PGS sweep cap (>= 0) */
@@ -95,6 +104,14 @@ typedef struct icr_params {
                             previous step's iteration-1 lambda~ (zero before the first step),
                             Newton iterations 2..k start from 0 (incremental reading of Alg. 3);
                             0: every PGS starts from 0.  Read by icr_step / icr_step_capture. */
+  int32_t w_update;      /* enum icr_w_update */
+  double newton_tol;     /* >= 0.  0: icr_step runs all n_newton iterations.  > 0: after the proximity
+                            update of iteration k the step linearises for iteration k + 1 and
+                            evaluates, in FP64, the normal complementarity residual of a zero increment
+                            at those gaps, max over contacts of max(0, -delta_n); when it is at most
+                            newton_tol the next solve has nothing to correct and the Newton loop ends
+                            (the remaining iterations' kernels return at once; the corrective motion
+                            runs).  icr_newton_iterations reports the iterations run. */
 } icr_params;
 
 typedef struct icr_pgs_stats {
@@ -287,6 +304,10 @@ int icr_correct_motion(icr_scene* scene, double* dq_out, int reset);
  * Needs a system, a mapping, p_0 and an obstacle; returns once the work is
  * enqueued. */
 int icr_step(icr_scene* scene, int32_t n_newton);
+/* Newton iterations the last device-resident step (icr_step or a launch of
+ * the captured step) ran: n_newton, or fewer when newton_tol ended the loop.
+ * Synchronises. */
+int icr_newton_iterations(icr_scene* scene, int32_t* out);
 /* Capture icr_step(scene, n_newton) into a CUDA graph owned by the scene (one
  * plain step runs first so that every kernel is set up; icr_autotune runs
  * first when the scene is not tuned).  The context's stream must not be the

@@ -45,10 +45,25 @@ def standard_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0
     return {"dq": q, "p": p, "iters": hist}
 
 
-def fast_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0, lam0=None, solver=None, WH=None):
+def zero_increment_residual(delta):
+    """Normal complementarity residual of lambda~ = 0 at the gaps delta
+    (Eq. "signorini's law"): max over contacts of |min(delta_n, 0)|.  When it
+    is zero, lambda~ = 0 solves the next iteration's problem (a zero normal
+    force also forces zero friction in the cone of Eq. "coulomb's law")."""
+    dn = np.asarray(delta, dtype=np.float64)[0::3]
+    return float(np.max(np.maximum(0.0, -dn), initial=0.0))
+
+
+def fast_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0, lam0=None, solver=None, WH=None,
+                newton_tol=0.0):
     """``WH`` (optional): W_H = H A^-1 H^T already formed by the caller, e.g.
     from column blocks of dl.compliance_mapping solved in parallel (W_H is
-    column-separable); formed here otherwise."""
+    column-separable); formed here otherwise.
+
+    ``newton_tol`` > 0 ends the Newton loop early: before iteration k >= 2 the
+    gaps at p_(k-1) are linearised and, when the residual of a zero increment
+    there (zero_increment_residual) is at most newton_tol, the loop stops (the
+    next solve would have nothing to correct); 0 runs all n_newton iterations."""
     n = A.shape[0]
     solver = solver or dl.SystemSolver(A)
     H = dl.mapping_matrix(nodes, bary, n)
@@ -59,6 +74,8 @@ def fast_scheme(A, nodes, bary, mu, p0, linearize, n_newton, sweeps, tol=0.0, la
     hist = []
     for k in range(n_newton):
         C, delta = linearize(p.reshape(-1, 3), k)
+        if k >= 1 and newton_tol > 0 and zero_increment_residual(delta) <= newton_tol:
+            break
         W = dl.delassus_fast(C, WH)
         lam, done, eps = pgs(W, delta, mu, lam0 if k == 0 else None, sweeps, tol)
         uk = np.einsum("aji,aj->ai", C, lam.reshape(-1, 3)).reshape(-1)     # C_k^T lambda~_k

@@ -368,6 +368,14 @@ static int check_params(const icr_params* p) {
     set_error("warm_start must be 0 or 1");
     return ICR_EINVAL;
   }
+  if (p->w_update < ICR_W_FP32 || p->w_update > ICR_W_BF16) {
+    set_error("unknown W update mode %d", p->w_update);
+    return ICR_EINVAL;
+  }
+  if (!(p->newton_tol >= 0) || !std::isfinite(p->newton_tol)) {
+    set_error("newton_tol must be finite and >= 0");
+    return ICR_EINVAL;
+  }
   return ICR_OK;
 }
 
@@ -765,6 +773,8 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
   RET(dalloc(s, s->dev_err, sizeof(int)));
+  RET(dalloc(s, s->newton, 2 * sizeof(int32_t)));
+  RET(dalloc(s, s->WH16, s->prec == ICR_FP32 ? 9 * mm * mm * 2 : 16));
   if (s->prec == ICR_FP32) {
     // tensor-core operand blocks: per supernode ceil(3m/128) column tiles x
     // ceil(w/32) row chunks, 32 KiB each (two TF32 planes)
@@ -1464,8 +1474,20 @@ static int step_enqueue(Scene* s, int n_newton) {
   RET(launch_build_WH(s));
   s->has_WH = true;
   const size_t lam_bytes = 3 * (size_t)s->m * s->tsize;
+  // newton_tol: from iteration 2 on, the kernels of an iteration return at
+  // entry once the FP64 check after the previous linearisation ended the loop
+  const bool nstop = s->params.newton_tol > 0 && n_newton > 1 && s->m;
+  if (nstop) CK(cudaMemsetAsync(s->newton.p, 0, 2 * sizeof(int32_t), st));
+  struct StopGuard {
+    Scene* s;
+    ~StopGuard() { s->step_stop = nullptr; }
+  } guard{s};
+  s->last_newton = n_newton;
+  s->last_newton_tol = nstop;
   for (int k = 0; k < n_newton; ++k) {
+    if (k == 1 && nstop) s->step_stop = (const int*)s->newton.p;
     RET(launch_linearize(s, k));
+    if (k >= 1 && nstop) RET(launch_newton_check(s));
     RET(launch_update_W(s));
     if (k == 0 && s->params.warm_start && s->m) {
       // Newton iteration 1 starts from the previous time step's iteration-1 solution
@@ -1477,6 +1499,7 @@ static int step_enqueue(Scene* s, int n_newton) {
     }
     RET(launch_update_proximity(s));
   }
+  s->step_stop = nullptr;
   RET(launch_correct_motion(s));
   if (s->m) CK(cudaMemsetAsync(s->u.p, 0, 3 * (size_t)s->m * sizeof(double), st));
   s->has_dirs = s->has_W = s->has_lam = true;
@@ -1584,9 +1607,10 @@ void scene_buffers(Scene* s, std::vector<std::pair<DBuf*, bool>>& out) {
                   &s->dof_super, &s->fr_ptr, &s->ctr_ptr, &s->ctr_child, &s->ctr_row, &s->nodes, &s->bary,
                   &s->C, &s->delta, &s->mu, &s->lam, &s->lam0, &s->p, &s->p0, &s->u, &s->dq, &s->tc_boff,
                   &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->Gpk, &s->gpk_off,
-                  &s->tc_super, &s->level_first};
+                  &s->tc_super, &s->level_first, &s->newton};
   DBuf* scratch[] = {&s->bitmap, &s->wprefix, &s->qcount, &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop,
-                     &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wcoup, &s->stats, &s->dev_err};
+                     &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wcoup, &s->stats, &s->dev_err,
+                     &s->WH16};
   out.clear();
   for (DBuf* b : keep) out.push_back({b, true});
   for (DBuf* b : scratch) out.push_back({b, false});
@@ -1735,6 +1759,26 @@ int icr_step_launch(icr_scene* s) {
   RET(set_device(s));
   CK(cudaGraphLaunch(s->step_graph, s->ctx->stream));
   s->launches += s->graph_kernels;
+  s->last_newton = s->graph_newton;
+  s->last_newton_tol = s->graph_params.newton_tol > 0 && s->graph_newton > 1 && s->graph_m > 0;
+  return ICR_OK;
+}
+
+int icr_newton_iterations(icr_scene* s, int32_t* out) {
+  RET(check_scene(s));
+  if (!out) {
+    set_error("newton_iterations: out is NULL");
+    return ICR_EINVAL;
+  }
+  if (!s->last_newton_tol) {
+    *out = s->last_newton;
+    return ICR_OK;
+  }
+  RET(set_device(s));
+  int32_t nw[2] = {0, 0};
+  CK(cudaMemcpyAsync(nw, s->newton.p, sizeof(nw), cudaMemcpyDeviceToHost, s->ctx->stream));
+  CK(cudaStreamSynchronize(s->ctx->stream));
+  *out = 1 + nw[1];
   return ICR_OK;
 }
 

@@ -131,6 +131,11 @@ struct Scene {
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, y, dq, stats;
   DBuf wcoup;   // per contact: max |W[3a, j]| over the other contacts' columns j
+  DBuf WH16;    // BF16 copy of W_H (FP32 scenes with the BF16 W update)
+  DBuf newton;  // device Newton stop: [0] the loop has ended, [1] iterations run after the first
+  const int* step_stop = nullptr;   // while a device-resident step is enqueued with newton_tol: newton.p
+  int last_newton = 0;              // n_newton of the last device-resident step
+  bool last_newton_tol = false;     // ... and whether newton_tol could end it early
   DBuf plan;   // PLAN_LISTS x (ns + 1) prefix sums, 2 + levels counters, levels + 1 K splits (int32)
   DBuf level_first;   // (levels + 1) offsets of the levels in level_list
   // icr_set_step_inputs: device staging buffer, two pinned host slots, their copy events
@@ -211,6 +216,7 @@ int launch_pgs(Scene* s, int warm_start, int want_residuals);
 int launch_update_proximity(Scene* s);
 int launch_correct_motion(Scene* s);
 int launch_linearize(Scene* s, int k);
+int launch_newton_check(Scene* s);
 // tcgen05 contraction for supernodes with at least min_cols front columns (icr_tc.cu)
 int launch_contract_tc(Scene* s, int mode);
 int launch_pack_g(Scene* s, const int32_t* blocks, int nblocks);

@@ -21,6 +21,7 @@
 // End of step:
 //   a9  k_xu, k_bsolve dq = L^-T D^-1 X u, the backward solve as
 //                      dq_s = G_s^T [y_s; -dq_R] per level, top-down
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -55,6 +56,10 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
+
+// The Newton loop of a device-resident step has ended (icr_params.newton_tol):
+// the kernels of the remaining iterations return at entry.  NULL outside it.
+__device__ __forceinline__ bool newton_stopped(const int* stop) { return stop && *(const volatile int*)stop; }
 
 __device__ __forceinline__ int lower_bound_dev(const int* a, int n, int v) {
   int lo = 0, hi = n;
@@ -627,11 +632,18 @@ __global__ void __launch_bounds__(256)
 }
 
 template <class T>
-__global__ void k_symmetrize(int nr, T* A) {
+__global__ void k_symmetrize(int nr, T* A, __nv_bfloat16* A16) {
   pdl_entry();
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y;
-  if (j < i) A[(int64_t)i * nr + j] = A[(int64_t)j * nr + i];
+  if (j >= nr) return;
+  if (j < i) {
+    const T v = A[(int64_t)j * nr + i];
+    A[(int64_t)i * nr + j] = v;
+    if (A16) A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)v);
+  } else if (A16) {   // the BF16 copy the low-precision W update reads
+    A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)A[(int64_t)i * nr + j]);
+  }
 }
 
 // ------------------------------------------------------------------ a6 W = C W_H C^T
@@ -654,9 +666,28 @@ __device__ __forceinline__ T nmax(T a, T b) {
   return a != a ? a : ((b > a || b != b) ? b : a);
 }
 
-template <class T>
-__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH, T* W, int64_t ldw, T* wcoup) {
+// WM: operand precision (enum icr_w_update; FP32 scenes): W_H and C as stored,
+// rounded to TF32, or W_H from its BF16 copy and C rounded to BF16; the
+// products are accumulated in T.
+template <class T, int WM>
+__device__ __forceinline__ T w_operand(T x) {
+  if constexpr (WM == ICR_W_TF32) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)x));
+    return (T)__uint_as_float(r);
+  } else if constexpr (WM == ICR_W_BF16) {
+    return (T)__bfloat162float(__float2bfloat16_rn((float)x));
+  } else {
+    return x;
+  }
+}
+
+template <class T, int WM>
+__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH,
+                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wcoup,
+                           const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;
   if (blockIdx.x < blockIdx.y) return;   // the block pairs of the upper triangle only (uniform)
   __shared__ bits_t<T> mxa[16], mxb[16];
   __shared__ T sC[2][16][9];             // directions of the block's a and b contacts
@@ -668,7 +699,7 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
   for (int e = tid; e < 2 * 16 * 9; e += 256) {
     const int w = e / 144, k = (e % 144) / 9, q = e % 9;
     const int c = (w == 0 ? blockIdx.y : blockIdx.x) * 16 + k;
-    sC[w][k][q] = c < m ? C[9 * c + q] : T(0);
+    sC[w][k][q] = c < m ? w_operand<T, WM>(C[9 * c + q]) : T(0);
   }
   __syncthreads();
   if (a < m && b < m && a <= b) {
@@ -677,7 +708,13 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) M[i][j] = WH[(3 * a + i) * ld + 3 * b + j];
+      for (int j = 0; j < 3; ++j) {
+        const int64_t at = (3 * a + i) * ld + 3 * b + j;
+        if constexpr (WM == ICR_W_BF16)
+          M[i][j] = (T)__bfloat162float(WH16[at]);
+        else
+          M[i][j] = w_operand<T, WM>(WH[at]);
+      }
     const T(*Ca)[3] = reinterpret_cast<const T(*)[3]>(&sC[0][ty][0]);
     const T(*Cb)[3] = reinterpret_cast<const T(*)[3]>(&sC[1][tx][0]);
 #pragma unroll
@@ -1001,8 +1038,10 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
 template <class T, int BC>
 __global__ void __launch_bounds__(PGS_THREADS, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-          const T* __restrict__ mu, const T* __restrict__ wcoup, T* lam_g, int warm, PgsDevStats* st) {
+          const T* __restrict__ mu, const T* __restrict__ wcoup, T* lam_g, int warm, PgsDevStats* st,
+          const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;   // uniform, before any shared memory or barrier
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
   constexpr int RCH = BR / CH;                 // 16-byte copies per block row
@@ -1634,10 +1673,39 @@ __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, cons
   }
 }
 
+// ------------------------------------------------------------------ Newton stop
+// After the linearisation for the next Newton iteration: the FP64
+// complementarity residual of a zero increment at the new gaps,
+// max over contacts of max(0, -delta_n).  At most tol: the next solve has
+// nothing to correct, the loop ends (nw[0] = 1); else one more iteration runs
+// (nw[1] counts the iterations after the first).  One block.
+template <class T>
+__global__ void k_newton_check(int m, const T* __restrict__ delta, double tol, int* nw) {
+  pdl_entry();
+  if (nw[0]) return;
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int a = threadIdx.x; a < m; a += blockDim.x) v = fmax(v, -(double)delta[3 * a]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+    if (mx <= tol)
+      nw[0] = 1;
+    else
+      nw[1] += 1;
+  }
+}
+
 // ------------------------------------------------------------------ a8 proximity update
 template <class T>
-__global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u) {
+__global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u,
+                         const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const T l0 = lam[3 * a], l1 = lam[3 * a + 1], l2 = lam[3 * a + 2];
@@ -1654,8 +1722,9 @@ __global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ l
 // each warp takes one row of W_H.
 template <class T>
 __global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
-                       double* u, double* p, double* dp) {
+                       double* u, double* p, double* dp, const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* uk = (T*)smraw;   // 3m
   for (int a = threadIdx.x; a < m; a += blockDim.x) {
@@ -1689,8 +1758,10 @@ __global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam
 }
 
 template <class T>
-__global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp) {
+__global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp,
+                         const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;
   const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= 3 * m) return;
@@ -1769,8 +1840,10 @@ __global__ void __launch_bounds__(256)
 template <class T>
 __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
                             const double* __restrict__ anchors, const double* __restrict__ spheres,
-                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta) {
+                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta,
+                            const int* __restrict__ stop) {
   pdl_entry();
+  if (newton_stopped(stop)) return;
   int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
@@ -1929,8 +2002,10 @@ static int build_WH_T(Scene* s) {
     const int rc = launch_contract_tc(s, mode);
     if (rc != ICR_OK) return rc;
   }
+  // FP32 scenes with the BF16 W update also get W_H's BF16 copy
+  __nv_bfloat16* wh16 = (sizeof(T) == 4 && s->params.w_update == ICR_W_BF16) ? (__nv_bfloat16*)s->WH16.p : nullptr;
   PDL("k_symmetrize", k_symmetrize<T>, dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st,
-      (int)nr, (T*)s->WH.p);
+      (int)nr, (T*)s->WH.p, wh16);
   return ICR_OK;
 }
 
@@ -1943,8 +2018,17 @@ static int update_W_T(Scene* s) {
   dim3 grid((m + 15) / 16, (m + 15) / 16);
   cudaError_t e = cudaMemsetAsync(s->wcoup.p, 0, (size_t)m * sizeof(T), s->ctx->stream);
   if (e != cudaSuccess) return cuda_fail(e, "memset wcoup");
-  PDL("k_update_W", k_update_W<T>, grid, dim3(16, 16), 0, s->ctx->stream,
-      m, (const T*)s->C.p, (const T*)s->WH.p, (T*)s->W.p, s->ldw, (T*)s->wcoup.p);
+  const int wm = sizeof(T) == 4 ? s->params.w_update : ICR_W_FP32;
+  const __nv_bfloat16* wh16 = (const __nv_bfloat16*)s->WH16.p;
+  if (wm == ICR_W_TF32)
+    PDL("k_update_W", k_update_W<T, ICR_W_TF32>, grid, dim3(16, 16), 0, s->ctx->stream,
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
+  else if (wm == ICR_W_BF16)
+    PDL("k_update_W", k_update_W<T, ICR_W_BF16>, grid, dim3(16, 16), 0, s->ctx->stream,
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
+  else
+    PDL("k_update_W", k_update_W<T, ICR_W_FP32>, grid, dim3(16, 16), 0, s->ctx->stream,
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
   return ICR_OK;
 }
 
@@ -1987,7 +2071,7 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
   PDL("k_pgs", k_pgs<T, BC>, 1, PGS_THREADS, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
-      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wcoup.p, (T*)s->lam.p, warm, ds);
+      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wcoup.p, (T*)s->lam.p, warm, ds, s->step_stop);
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
     PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,
@@ -2010,14 +2094,13 @@ static int prox_T(Scene* s) {
   const size_t smem = 3 * (size_t)m * sizeof(T);
   if (smem <= 48 * 1024) {   // u_k fits the default shared memory: one launch
     PDL("k_prox", k_prox<T>, (3 * m + 15) / 16, 512, smem, st, m, (const T*)s->C.p, (const T*)s->lam.p,
-        (const T*)s->WH.p, u, (double*)s->p.p, u + 3 * (size_t)m);
+        (const T*)s->WH.p, u, (double*)s->p.p, u + 3 * (size_t)m, s->step_stop);
     return ICR_OK;
   }
   PDL("k_prox_u", k_prox_u<T>, (m + 127) / 128, 128, 0, st,
-      m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u);
+      m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u, s->step_stop);
   PDL("k_prox_p", k_prox_p<T>, (3 * m + 7) / 8, 256, 0, st,
-      m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p,
-                                               u + 3 * (size_t)m);
+      m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p, u + 3 * (size_t)m, s->step_stop);
   return ICR_OK;
 }
 
@@ -2159,8 +2242,21 @@ static int linearize_T(Scene* s, int k) {
   const double* nk = s->obst_kind == 1 ? (const double*)s->obst_normals.p + (size_t)k * m * 3 : nullptr;
   PDL("k_linearize", k_linearize<T>, (m + 127) / 128, 128, 0, s->ctx->stream,
       m, s->obst_kind, nk, (const double*)s->obst_anchors.p, (const double*)s->obst_spheres.p,
-      (const int*)s->obst_of.p, (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p);
+      (const int*)s->obst_of.p, (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p, s->step_stop);
   return ICR_OK;
+}
+
+template <class T>
+static int newton_check_T(Scene* s) {
+  const int m = s->m;
+  if (m == 0) return ICR_OK;
+  PDL("k_newton_check", k_newton_check<T>, 1, 1024, 0, s->ctx->stream, m, (const T*)s->delta.p,
+      s->params.newton_tol, (int*)s->newton.p);
+  return ICR_OK;
+}
+
+int launch_newton_check(Scene* s) {
+  return s->prec == ICR_FP64 ? newton_check_T<double>(s) : newton_check_T<float>(s);
 }
 
 int launch_linearize(Scene* s, int k) { return s->prec == ICR_FP64 ? linearize_T<double>(s, k) : linearize_T<float>(s, k); }

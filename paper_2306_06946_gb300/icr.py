@@ -32,7 +32,7 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_set_forward_plan", "icr_forward_levels", "icr_build_info",
            "icr_profile_begin", "icr_profile_end",
            "icr_ctx_set_wait_limit", "icr_ctx_inject_alloc_failure", "icr_scene_evict", "icr_scene_readmit",
-           "icr_scene_residency", "icr_serve_ex")
+           "icr_scene_residency", "icr_serve_ex", "icr_newton_iterations")
 
 
 class IcrError(RuntimeError):
@@ -44,9 +44,13 @@ class IcrError(RuntimeError):
 CONTRACT = {"auto": 0, "simt": 1, "tf32x3": 2, "tf32": 3, "bf16": 4}
 
 
+W_UPDATE = {"fp32": 0, "tf32": 1, "bf16": 2}
+
+
 class Params(ct.Structure):
     _fields_ = [("precision", ct.c_int32), ("n_sweeps", ct.c_int32), ("tol", ct.c_double),
-                ("contraction", ct.c_int32), ("warm_start", ct.c_int32)]
+                ("contraction", ct.c_int32), ("warm_start", ct.c_int32), ("w_update", ct.c_int32),
+                ("newton_tol", ct.c_double)]
 
 
 class BuildInfo(ct.Structure):
@@ -116,6 +120,7 @@ def lib() -> ct.CDLL:
             "icr_set_field": [P, ct.c_int32, P, ct.c_size_t],
             "icr_reach_noalloc": [ct.c_int32, ct.c_int32, ct.c_int32, P, P, P, P, P, P],
             "icr_step": [P, ct.c_int32],
+            "icr_newton_iterations": [P, ct.POINTER(ct.c_int32)],
             "icr_step_capture": [P, ct.c_int32],
             "icr_step_launch": [P],
             "icr_sync": [P],
@@ -227,9 +232,11 @@ class Scene:
     """icr_scene: one deformable body and its contacts."""
 
     def __init__(self, ctx: Context, precision: int = FP32, n_sweeps: int = 50, tol: float = 0.0,
-                 contraction: str = "auto", warm_start: bool = False):
+                 contraction: str = "auto", warm_start: bool = False, w_update: str = "fp32",
+                 newton_tol: float = 0.0):
         self.ctx = ctx
-        self.params = Params(precision, n_sweeps, tol, CONTRACT[contraction], int(bool(warm_start)))
+        self.params = Params(precision, n_sweeps, tol, CONTRACT[contraction], int(bool(warm_start)),
+                             W_UPDATE[w_update], float(newton_tol))
         h = P()
         _check(lib().icr_scene_create(ctx.h, ct.byref(h), ct.byref(self.params)))
         self.h = h
@@ -248,7 +255,11 @@ class Scene:
             pass
 
     def set_params(self, n_sweeps: int | None = None, tol: float | None = None, contraction: str | None = None,
-                   warm_start: bool | None = None):
+                   warm_start: bool | None = None, w_update: str | None = None, newton_tol: float | None = None):
+        if w_update is not None:
+            self.params.w_update = W_UPDATE[w_update]
+        if newton_tol is not None:
+            self.params.newton_tol = float(newton_tol)
         if warm_start is not None:
             self.params.warm_start = int(bool(warm_start))
         if n_sweeps is not None:
@@ -359,6 +370,11 @@ class Scene:
 
     def step(self, n_newton: int):
         _check(lib().icr_step(self.h, int(n_newton)))
+
+    def newton_iterations(self) -> int:
+        v = ct.c_int32()
+        _check(lib().icr_newton_iterations(self.h, ct.byref(v)))
+        return int(v.value)
 
     def autotune(self, level_times: bool = False):
         """Per-level choice of the forward-solve engine; returns the number of

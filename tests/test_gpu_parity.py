@@ -411,3 +411,57 @@ def test_forward_plans_keep_parity(ctx, name, prec, tol):
         with pytest.raises(icr.IcrError) as e:
             sc.set_forward_plan(bad.astype(np.uint8))
         assert e.value.code == icr.EINVAL
+
+
+# ---------------------------------------------------------------- precision of the W update
+@pytest.mark.parametrize("name", ["beam_mid", "liver_c1"])
+@pytest.mark.parametrize("mode,tol", [("fp32", 1e-5), ("tf32", 2e-3), ("bf16", 2e-2)])
+def test_W_update_modes(ctx, name, mode, tol):
+    """W = C W_H C^T with TF32 or BF16 operands and FP32 accumulation against
+    the FP64 oracle's W (the error is reported, the bound is loose)."""
+    from paper_2306_06946_gb300 import icr
+    s = scene(name)
+    sc = make_scene(ctx, name, icr.FP32)
+    sc.set_params(w_update=mode)
+    sc.build_WH()
+    C, delta = s.linearize(s.p0, 0)
+    sc.update_directions(C, delta, s.mu)
+    sc.update_W()
+    W = sc.get("W")
+    err = rel(W, dl.delassus_fast(C, oracle_WH(name)))
+    print(f"{name} W update {mode}: relative Frobenius error of W vs FP64 oracle {err:.3e}")
+    assert err < tol
+    assert np.array_equal(W, W.T)
+    if mode != "fp32":
+        assert err > 1e-6            # the operands were rounded
+    assert rel(sc.get("WH"), oracle_WH(name)) < 1e-5   # W_H itself stays FP32
+
+
+# ---------------------------------------------------------------- Newton stop from the FP64 residual check
+@pytest.mark.parametrize("name,ntol", [("beam_c0", 1e-8), ("liver_c1", 1e-9), ("press_c1", 1e-5)])
+@pytest.mark.parametrize("prec", [1, 0])
+def test_newton_tol_ends_the_loop_like_the_oracle(ctx, name, ntol, prec):
+    torch = pytest.importorskip("torch")
+    from oracle import newton as nw
+    from paper_2306_06946_gb300 import icr
+    from gpu_helpers import oracle_solver
+    s = scene(name)
+    ref = nw.fast_scheme(s.A, s.nodes, s.bary, s.mu, s.p0, s.linearize, s.n_newton, s.n_sweeps,
+                         solver=oracle_solver(name), WH=oracle_WH(name), newton_tol=ntol)
+    assert len(ref["iters"]) < s.n_newton
+    sctx = icr.Context(0, torch.cuda.Stream().cuda_stream)
+    sc = make_scene(sctx, name, prec)
+    sc.set_field("MU", s.mu)
+    sc.set_params(newton_tol=ntol)
+    tol = 1e-9 if prec == 1 else 1e-4
+    sc.step(s.n_newton)                       # eager
+    assert sc.newton_iterations() == len(ref["iters"])
+    assert rel(sc.get("DQ"), ref["dq"]) < tol
+    sc.step_capture(s.n_newton)               # the captured step decides on the device as well
+    for _ in range(2):
+        sc.step_launch()
+        assert sc.newton_iterations() == len(ref["iters"])
+        assert rel(sc.get("DQ"), ref["dq"]) < tol
+    sc.set_params(newton_tol=0.0)
+    sc.step(s.n_newton)
+    assert sc.newton_iterations() == s.n_newton

@@ -452,3 +452,33 @@ def test_column_blocks_form_WH(beam_c0):
     a = nw.fast_scheme(**kw)
     b = nw.fast_scheme(**kw, WH=blocks)
     assert _rel(b["dq"], a["dq"]) < 1e-11
+
+
+# ---------------------------------------------------------------- Newton stop (newton_tol)
+def test_newton_stop_rule(beam_c0, liver_c1):
+    # sphere tool: after iteration 1 every gap is open, so the skipped
+    # iterations would solve to lambda~ = 0 and move nothing: the same dq
+    s = liver_c1
+    kw = dict(A=s.A, nodes=s.nodes, bary=s.bary, mu=s.mu, p0=s.p0, linearize=s.linearize, sweeps=s.n_sweeps)
+    full = nw.fast_scheme(**kw, n_newton=s.n_newton)
+    cut = nw.fast_scheme(**kw, n_newton=s.n_newton, newton_tol=1e-12)
+    assert len(cut["iters"]) == 1 and len(full["iters"]) == s.n_newton
+    assert all(not it["lam"].any() for it in full["iters"][1:])
+    assert _rel(cut["dq"], full["dq"]) < 1e-13
+    # plane with new normals every iteration: the residual of a zero increment
+    # after iteration 1 is above 1e-8, after iteration 2 below: two iterations,
+    # the same as a two-iteration run
+    b = beam_c0
+    kw = dict(A=b.A, nodes=b.nodes, bary=b.bary, mu=b.mu, p0=b.p0, linearize=b.linearize, sweeps=b.n_sweeps)
+    cut = nw.fast_scheme(**kw, n_newton=b.n_newton, newton_tol=1e-8)
+    two = nw.fast_scheme(**kw, n_newton=2)
+    assert len(cut["iters"]) == 2 < b.n_newton
+    assert np.array_equal(cut["dq"], two["dq"])
+    C, d = b.linearize(cut["iters"][-1]["p"].reshape(-1, 3), 2)
+    assert nw.zero_increment_residual(d) <= 1e-8
+    C, d = b.linearize(cut["iters"][0]["p"].reshape(-1, 3), 1)
+    assert nw.zero_increment_residual(d) > 1e-8
+    # the residual is the Signorini residual of lambda~ = 0 (oracle residuals())
+    W = np.eye(3 * b.m)
+    assert nw.zero_increment_residual(d) == pytest.approx(pg.residuals(W, d, np.zeros(3 * b.m), b.mu)["normal"],
+                                                          rel=0, abs=0)
