@@ -129,6 +129,7 @@ typedef struct icr_pgs_stats {
   int32_t sweeps_s_only;  /* sweeps that visited only the blocks of contacts that may change (the
                              others provably keep lambda~ = 0; see icr_solve_friction) */
   int32_t deferred_folds; /* folds of those sweeps' changes into the other contacts' residuals */
+  int32_t rechecks;       /* rechecks of the other contacts' normal residuals when the bound ran out */
 } icr_pgs_stats;
 
 enum icr_field {
@@ -273,8 +274,9 @@ int icr_update_W(icr_scene* scene);
  * A contact with lambda~ = 0 and r_n >= 0 is left unchanged by the local rule,
  * so a sweep passes over it; once every residual is complete, the contacts
  * that may change (S, in blocks of 32, FP64 16) are swept alone while the sum
- * of |changes| since the bound's base stays below min r_n / max_j |W[n, j]|
- * over the others (their r_n then stays non-negative).  When it runs out, the
+ * of |changes| since the bound's base stays below min r_n / max |W[n, j]|
+ * over the others, the maximum over the columns j of S's blocks (their r_n
+ * then stays non-negative).  When it runs out, the
  * others' normal residuals are formed with the deferred changes: all positive,
  * the bound starts again from there; else the changes reach the others'
  * residuals in one deferred fold and full sweeps resume.  The iterate is that

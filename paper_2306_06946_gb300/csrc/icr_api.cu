@@ -541,9 +541,14 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   }
   // front-row contribution lists: for every row of every front, the
   // (child, child update row) pairs the extend-add sums into it, children in
-  // ascending order
+  // ascending order; the child's row is stored as its row in the front
+  // storage (the child's first front row + w_child + its update row)
   std::vector<int64_t> frp0(ns + 1, 0);
   for (int k = 0; k < ns; ++k) frp0[k + 1] = frp0[k] + (sp[k + 1] - sp[k]) + (rp[k + 1] - rp[k]);
+  if (frp0[ns] >= (int64_t)INT32_MAX) {
+    set_error("set_system: %lld front rows exceed the 32-bit row index", (long long)frp0[ns]);
+    return ICR_EINVAL;
+  }
   std::vector<int32_t> cptr_rows(frp0[ns] + 1, 0), crow_child(std::max<int64_t>(1, rp[ns])),
       crow_row(std::max<int64_t>(1, rp[ns]));
   for (int k = 0; k < ns; ++k)
@@ -557,7 +562,7 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
         for (int64_t i = rp[k]; i < rp[k + 1]; ++i) {
           const int64_t slot = fillr[frp0[par[k]] + relidx[i]]++;
           crow_child[slot] = k;
-          crow_row[slot] = (int32_t)(i - rp[k]);
+          crow_row[slot] = (int32_t)(frp0[k] + (sp[k + 1] - sp[k]) + (i - rp[k]));
         }
   }
   int nlev = 0;
@@ -768,7 +773,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->p0, 3 * mm * sizeof(double)));
   RET(dalloc(s, s->u, 6 * mm * sizeof(double)));   // u (3m) then the last increment dp (3m)
   RET(dalloc(s, s->uk, 3 * mm * T));
-  RET(dalloc(s, s->wcoup, mm * T));
+  RET(dalloc(s, s->wblk, mm * ((mm + (s->prec == ICR_FP64 ? 15 : 31)) / (s->prec == ICR_FP64 ? 16 : 32)) * T));
   RET(dalloc(s, s->y, s->n * T));
   RET(dalloc(s, s->dq, s->n * T));
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
@@ -1165,6 +1170,7 @@ int icr_solve_friction(icr_scene* s, int warm_start, icr_pgs_stats* stats) {
   stats->res_slip = r[3];
   stats->sweeps_s_only = d.s_only;
   stats->deferred_folds = d.folds;
+  stats->rechecks = d.rechecks;
   if (s->params.tol > 0 && d.eps > s->params.tol && s->m > 0) {
     set_error("solve_friction: eps %g above tol %g after %d sweeps", d.eps, s->params.tol, d.sweeps);
     return ICR_ENOCONV;
@@ -1609,7 +1615,7 @@ void scene_buffers(Scene* s, std::vector<std::pair<DBuf*, bool>>& out) {
                   &s->obst_normals, &s->obst_anchors, &s->obst_spheres, &s->obst_of, &s->Gpk, &s->gpk_off,
                   &s->tc_super, &s->level_first, &s->newton};
   DBuf* scratch[] = {&s->bitmap, &s->wprefix, &s->qcount, &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop,
-                     &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wcoup, &s->stats, &s->dev_err,
+                     &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wblk, &s->stats, &s->dev_err,
                      &s->WH16};
   out.clear();
   for (DBuf* b : keep) out.push_back({b, true});

@@ -130,7 +130,8 @@ struct Scene {
   int64_t ldw = 0;     // leading dimension of W: 3m rounded up to 96 (16-byte aligned row blocks)
   DBuf nodes, bary, bitmap, wprefix, qcount, qidx, qpos, qinv, X, Ftop;  // Ftop: assembled top rows (n x ldx)
   DBuf WH, W, C, delta, mu, lam, lam0, p, p0, u, uk, y, dq, stats;
-  DBuf wcoup;   // per contact: max |W[3a, j]| over the other contacts' columns j
+  DBuf wblk;    // per contact a and PGS block B (m x ceil(m / block)): max |W[3a, j]| over B's columns
+                //   other than a's own (the coupling bound of the PGS's S-only sweeps)
   DBuf WH16;    // BF16 copy of W_H (FP32 scenes with the BF16 W update)
   DBuf newton;  // device Newton stop: [0] the loop has ended, [1] iterations run after the first
   const int* step_stop = nullptr;   // while a device-resident step is enqueued with newton_tol: newton.p
@@ -201,6 +202,7 @@ struct PgsDevStats {
   int32_t sweeps;
   int32_t n_sep, n_stick, n_slip;
   int32_t s_only, folds;   // sweeps over S only; deferred folds
+  int32_t rechecks;        // rechecks of the passed-over contacts when the coupling bound ran out
   double eps;
   unsigned long long res_bits[4];   // normal, cone, stick, slip as non-negative double bits
 };
@@ -208,7 +210,7 @@ struct PgsDevStats {
 // ---- launchers (icr_kernels.cu); every one enqueues on s->ctx->stream
 int launch_build_WH(Scene* s);
 int launch_update_W(Scene* s);
-int launch_wcoup(Scene* s);   // wcoup of a W given directly
+int launch_wcoup(Scene* s);   // the coupling bounds (wblk) of a W given directly
 // scatter a packed staging buffer into the per-contact inputs and reset the
 // contact state (offsets in bytes: nodes, sphere ids, bary, mu, p0, anchors, spheres)
 int launch_unpack_inputs(Scene* s, int n_spheres, const int64_t* off);

@@ -170,7 +170,8 @@ __global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __
 // one thread per front element: the H^T entry plus the children's update
 // entries listed for that row (extend-add as a gather, children in ascending
 // order).  Rows < w go to Ftop, rows >= w to the front's update rows.
-static constexpr int AR = 4;   // front rows per assembly block
+static constexpr int AR = 4;          // threads per column of an assembly block
+static constexpr int ASM_ROWS = 16;   // front rows per assembly unit (AR threads, 4 rows each)
 
 
 __device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
@@ -222,7 +223,7 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
   const int nt = cdiv(q, TCC);
   const int ncol = 3 * q;
   const bool tcg = tc_gemm && tc_super[s] && q > 0 && w >= TC_GEMM_MIN_W && ncol >= TC_GEMM_MIN_COLS;
-  c[PLAN_ASM] = cdiv(nrows, AR) * nt;
+  c[PLAN_ASM] = cdiv(nrows, ASM_ROWS) * nt;
   c[PLAN_GEMM] = tcg ? 0 : cdiv(nrows, GR) * nt;
   const int nkb = cdiv(w, TC_KT);   // K blocks of a tensor-core unit
   c[PLAN_GTC] = tcg ? cdiv(nrows, TC_TILE) * cdiv(ncol, TC_TILE) * tc_parts(gsplit, nkb) : 0;
@@ -331,10 +332,11 @@ __global__ void __launch_bounds__(1024)
 
 // Entry (row, column 3*kl + d) of supernode s's front: its H^T entry (rows < w)
 // plus the children's update entries listed for that row (extend-add as a
-// gather, children in ascending order).
+// gather, children in ascending order; ctr_row holds each child row's index
+// in the front storage).
 template <class T>
 __device__ __forceinline__ T assemble_entry(int s, int row, int kl, int d, int c0, int w, int m,
-                                           const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+                                           const int64_t* __restrict__ fr_ptr,
                                            const int* __restrict__ ctr_ptr, const int* __restrict__ ctr_child,
                                            const int* __restrict__ ctr_row, const int* __restrict__ nodes,
                                            const T* __restrict__ bary, const int* __restrict__ qidx,
@@ -349,20 +351,20 @@ __device__ __forceinline__ T assemble_entry(int s, int row, int kl, int d, int c
       if (nodes[4 * a + i] == node) v += bary[4 * a + i];
   }
   const int64_t fr = fr_ptr[s] + row;
-  for (int e = ctr_ptr[fr]; e < ctr_ptr[fr + 1]; ++e) {
-    const int c = ctr_child[e];
-    const int jl = qinv[(size_t)c * m + kl];
-    if (jl >= 0) {
-      const int wc = super_ptr[c + 1] - super_ptr[c];
-      v += X[(fr_ptr[c] + wc + ctr_row[e]) * ldx + 3 * jl + d];
-    }
+  const int e1 = ctr_ptr[fr + 1];
+#pragma unroll 2
+  for (int e = ctr_ptr[fr]; e < e1; ++e) {
+    const int jl = qinv[(size_t)ctr_child[e] * m + kl];
+    if (jl >= 0) v += X[(int64_t)ctr_row[e] * ldx + 3 * jl + d];
   }
   return v;
 }
 
 // Assembly of the fronts of one level (positions [pa, pb) of level_list).
-// Work unit (supernode, AR-row tile, TCC-contact tile); one thread per front
-// element: its H^T entry, plus the children's update entries listed for that
+// Work unit (supernode, ASM_ROWS-row tile, TCC-contact tile), found once per
+// unit; a block of TCOLS x AR threads, each thread assembling the front
+// elements of its column in ASM_ROWS / AR rows (independent gathers in
+// flight): the H^T entry, plus the children's update entries listed for that
 // row (extend-add as a gather, children in ascending order).  Rows < w go to
 // Ftop, rows >= w to the front's update rows.
 template <class T>
@@ -385,16 +387,20 @@ __global__ void __launch_bounds__(AR * TCOLS)
     const int k0 = t * TCC;
     const int ncols = 3 * min(TCC, nq - k0);
     const int col = threadIdx.x;
-    const int row = rt * AR + threadIdx.y;
+    if (col >= ncols) continue;
     const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
     const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-    if (row >= nrows || col >= ncols) continue;
-    const T v = assemble_entry<T>(s, row, k0 + col / 3, col % 3, c0, w, m, super_ptr, fr_ptr, ctr_ptr, ctr_child,
-                                  ctr_row, nodes, bary, qidx, qinv, X, ldx);
-    if (row < w)
-      Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
-    else
-      X[(fr_ptr[s] + row) * ldx + 3 * k0 + col] = v;
+#pragma unroll
+    for (int rr = 0; rr < ASM_ROWS / AR; ++rr) {
+      const int row = rt * ASM_ROWS + rr * AR + threadIdx.y;
+      if (row >= nrows) break;
+      const T v = assemble_entry<T>(s, row, k0 + col / 3, col % 3, c0, w, m, fr_ptr, ctr_ptr, ctr_child, ctr_row,
+                                    nodes, bary, qidx, qinv, X, ldx);
+      if (row < w)
+        Ftop[(int64_t)(c0 + row) * ldx + 3 * k0 + col] = v;
+      else
+        X[(fr_ptr[s] + row) * ldx + 3 * k0 + col] = v;
+    }
   }
 }
 
@@ -631,25 +637,49 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Mirrors the upper triangle of the nr x nr matrix A into its lower one, by
+// 32 x 32 tiles (block (32, 8)): a tile at or below the diagonal reads its
+// mirror tile's rows, transposes them in shared memory and writes its own
+// rows, both coalesced.  With A16, also writes the BF16 copy of every entry
+// (tiles above the diagonal copy their own entries).
 template <class T>
 __global__ void k_symmetrize(int nr, T* A, __nv_bfloat16* A16) {
   pdl_entry();
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int i = blockIdx.y;
-  if (j >= nr) return;
-  if (j < i) {
-    const T v = A[(int64_t)j * nr + i];
-    A[(int64_t)i * nr + j] = v;
-    if (A16) A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)v);
-  } else if (A16) {   // the BF16 copy the low-precision W update reads
-    A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)A[(int64_t)i * nr + j]);
+  __shared__ T tile[32][33];
+  const int ti = blockIdx.y, tj = blockIdx.x;   // tile row, tile column
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (tj > ti) {
+    if (!A16) return;
+    for (int r = ty; r < 32; r += 8) {
+      const int i = ti * 32 + r, j = tj * 32 + tx;
+      if (i < nr && j < nr) A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)A[(int64_t)i * nr + j]);
+    }
+    return;
+  }
+  // tile[c][r] = A[tj*32 + r][ti*32 + c] (the mirror tile's rows)
+  for (int r = ty; r < 32; r += 8) {
+    const int i = tj * 32 + r, j = ti * 32 + tx;
+    if (i < nr && j < nr) tile[tx][r] = A[(int64_t)i * nr + j];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = ti * 32 + r, j = tj * 32 + tx;
+    if (i >= nr || j >= nr) continue;
+    if (j < i) {
+      const T v = tile[r][tx];   // A[j][i]
+      A[(int64_t)i * nr + j] = v;
+      if (A16) A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)v);
+    } else if (A16) {   // the diagonal tile's upper part: its own entries
+      A16[(int64_t)i * nr + j] = __float2bfloat16_rn((float)tile[tx][r]);
+    }
   }
 }
 
 // ------------------------------------------------------------------ a6 W = C W_H C^T
-// Also raises wcoup[a] to the largest |W[3a, j]| over the columns j of the
-// other contacts (the normal row's coupling to them; wcoup is zeroed before the
-// launch), the bound PGS uses to pass over separated contacts.
+// Also raises wblk[a][B] to the largest |W[3a, j]| over the columns j of PGS
+// block B other than contact a's own (the normal row's coupling to that block;
+// wblk is zeroed before the launch): the bound PGS uses to pass over separated
+// contacts, taken over the blocks that may change only.
 __device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) { atomicMax(addr, __float_as_uint(v)); }
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));
@@ -684,7 +714,7 @@ __device__ __forceinline__ T w_operand(T x) {
 
 template <class T, int WM>
 __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH,
-                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wcoup,
+                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wblk, int bc,
                            const int* __restrict__ stop) {
   pdl_entry();
   if (newton_stopped(stop)) return;
@@ -745,24 +775,35 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
     const int bg = blockIdx.x * 16 + rr / 3, ag = blockIdx.y * 16 + cc / 3;
     if (bg < m && ag < bg) W[(3 * bg + rr % 3) * ldw + 3 * ag + cc % 3] = tile[rr][cc];
   }
+  // the tile's 16 columns lie in one PGS block of bc contacts (16 divides bc):
+  // per contact, the largest |W[3a, j]| over that block's other columns
+  const int nb = (m + bc - 1) / bc;
   const int ga = blockIdx.y * 16 + tx, gb = blockIdx.x * 16 + tx;
-  if (ty == 0 && ga < m && mxa[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + ga, mxa[tx]);
-  if (ty == 1 && gb < m && mxb[tx] != 0) atomicMax(reinterpret_cast<bits_t<T>*>(wcoup) + gb, mxb[tx]);
+  const int Ba = blockIdx.y * 16 / bc, Bb = blockIdx.x * 16 / bc;
+  if (ty == 0 && ga < m && mxa[tx] != 0)
+    atomicMax(reinterpret_cast<bits_t<T>*>(wblk) + (int64_t)ga * nb + Bb, mxa[tx]);
+  if (ty == 1 && gb < m && mxb[tx] != 0)
+    atomicMax(reinterpret_cast<bits_t<T>*>(wblk) + (int64_t)gb * nb + Ba, mxb[tx]);
 }
 
-// wcoup of a W given directly: one warp per contact's normal row
+// The per-block coupling bounds (wblk) of a W given directly: one warp per
+// contact's normal row
 template <class T>
-__global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wcoup) {
+__global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wblk, int bc) {
   pdl_entry();
   const int a = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (a >= m) return;
   const T* row = W + (int64_t)(3 * a) * ldw;
-  T mx = T(0);
-  for (int j = lane; j < 3 * m; j += 32)
-    if (j / 3 != a) mx = nmax(mx, fabs(row[j]));
+  const int nb = (m + bc - 1) / bc;
+  for (int B = 0; B < nb; ++B) {   // per PGS block: max |W[3a, j]| over its columns (not a's own)
+    T mx = T(0);
+    const int j1 = 3 * min(m, (B + 1) * bc);
+    for (int j = 3 * B * bc + lane; j < j1; j += 32)
+      if (j / 3 != a) mx = nmax(mx, fabs(row[j]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(FULL, mx, o));
-  if (lane == 0) wcoup[a] = mx;
+    for (int o = 16; o > 0; o >>= 1) mx = nmax(mx, __shfl_xor_sync(FULL, mx, o));
+    if (lane == 0) wblk[(int64_t)a * nb + B] = mx;
+  }
 }
 
 // ------------------------------------------------------------------ a7 PGS
@@ -843,21 +884,32 @@ struct PgsDefer {
   T th;                                // the bound sum |D| must stay below
   bits_t<T> thq;                       // theta being formed (bits of a non-negative value)
   int cnt;                             // entries of the compact list of non-zero D
-  int sweeps, folds;                   // statistics: S-only sweeps, deferred folds
+  int sweeps, folds, rechecks;         // statistics: S-only sweeps, deferred folds, rechecks
   int xs[2];                           // sweeps warp 0 ended itself in step t (slot t & 1)
 };
+
+// Largest coupling of contact a's normal row to the columns of the blocks of
+// S: the bound on how far the changes D of S move its normal residual per unit
+// of sum |D| (wblk: per contact and PGS block, from the W update).
+template <class T>
+__device__ __forceinline__ T s_coupling(const T* __restrict__ wblk, int nb, int a, const int* slist, int ns) {
+  T w = T(0);
+  for (int k = 0; k < ns; ++k) w = nmax(w, wblk[(int64_t)a * nb + slist[k]]);
+  return w;
+}
 
 // Entered with every residual complete, at the end of a sweep.  S = the
 // blocks that may change in the next sweep; every other contact has
 // lambda~ = 0 and r_n >= 0 and keeps lambda~ = 0 while r_n stays
-// non-negative.  The changes D of S move its r_n by at most wcoup * sum |D|,
-// so while sum |D| stays below theta = min r_n / wcoup over those contacts,
+// non-negative.  The changes D of S move its r_n by at most ws * sum |D|, ws
+// its largest coupling to the columns of S's blocks (s_coupling), so while
+// sum |D| stays below theta = min r_n / ws over those contacts,
 // sweeps can visit S only and fold S's changes into S's rows; the other rows
 // wait for one fold of D.  Returns |S| when the S-only sweeps start, else 0.
 // Out of line: its temporaries stay out of the solve loop's registers.
 template <class T, int BC>
 __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam, const T* r,
-                                            const T* __restrict__ wcoup, T* dacc, T* dsnap) {
+                                            const T* __restrict__ wblk, T* dacc, T* dsnap) {
   constexpr int BR = 3 * BC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nblk = (m + BC - 1) / BC;
@@ -868,20 +920,10 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
     const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
     const bool a = lane < nbb && (lam[i0 + 3 * lane] != T(0) || lam[i0 + 3 * lane + 1] != T(0) ||
                                   lam[i0 + 3 * lane + 2] != T(0) || r[i0 + 3 * lane] < T(0));
-    if (__ballot_sync(FULL, a) != 0u) {
-      if (lane == 0) atomicOr(&d->sbits[bb >> 5], 1u << (bb & 31));
-    } else {
-      T v = T(INFINITY);
-      if (lane < nbb) {
-        const T rn = r[i0 + 3 * lane], wm = wcoup[bb * BC + lane];
-        v = (wm > T(0) && rn > T(0)) ? rn / wm : (wm == T(0) ? T(INFINITY) : T(0));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
-      if (lane == 0) atomicMin(&d->thq, to_bits(v));
-    }
+    if (__ballot_sync(FULL, a) != 0u && lane == 0) atomicOr(&d->sbits[bb >> 5], 1u << (bb & 31));
   }
   __syncthreads();
+  // S in ascending order (when it is small enough to sweep alone)
   if (wid == 0) {
     const unsigned wd = d->sbits[lane];
     const int c = __popc(wd);
@@ -893,16 +935,37 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
     }
     const int total = __shfl_sync(FULL, off, 31);
     off -= c;
+    if (total <= PGS_MAX_DEFER && total < nblk)
+      for (unsigned w = wd; w != 0u; w &= w - 1u) d->slist[off++] = lane * 32 + __ffs(w) - 1;
+    if (lane == 0) d->ns = total;
+  }
+  __syncthreads();
+  const int total = d->ns;
+  if (total <= PGS_MAX_DEFER && total < nblk) {
+    // theta = min over the other contacts of r_n / (their coupling to the blocks of S)
+    for (int bb = wid; bb < nblk; bb += PGS_WARPS) {
+      if ((d->sbits[bb >> 5] >> (bb & 31)) & 1u) continue;
+      const int i0 = 3 * bb * BC, nbb = min(BC, m - bb * BC);
+      T v = T(INFINITY);
+      if (lane < nbb) {
+        const T rn = r[i0 + 3 * lane], wm = s_coupling(wblk, nblk, bb * BC + lane, d->slist, total);
+        v = (wm > T(0) && rn > T(0)) ? rn / wm : (wm == T(0) ? T(INFINITY) : T(0));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(FULL, v, o));
+      if (lane == 0) atomicMin(&d->thq, to_bits(v));
+    }
+  }
+  __syncthreads();
+  if (wid == 0) {
     const T th = from_bits(d->thq);
     const bool on = total <= PGS_MAX_DEFER && total < nblk && th > T(0);
     if (on) {
-      for (unsigned w = wd; w != 0u; w &= w - 1u) d->slist[off++] = lane * 32 + __ffs(w) - 1;
       for (int i = lane; i < total * BR; i += 32) dacc[i] = dsnap[i] = T(0);
       if (lane < total) d->nb[lane] = T(0);
     }
     if (lane == 0) {
       d->on = on ? 1 : 0;
-      d->ns = total;
       d->th = th * T(1.0 - 1.0 / 1024.0);   // margin for the rounding of the bound
     }
   }
@@ -919,7 +982,7 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
 // of D's non-zero rows is built in drow / dval (stage 0's space).
 template <class T, int BC>
 __device__ __noinline__ int pgs_defer_recheck(PgsDefer<T>* d, int m, int nsd, const T* __restrict__ W, int64_t ldw,
-                                              const T* r, const T* dacc, T* dsnap, const T* __restrict__ wcoup,
+                                              const T* r, const T* dacc, T* dsnap, const T* __restrict__ wblk,
                                               int* drow, T* dval) {
   constexpr int BR = 3 * BC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
@@ -951,7 +1014,7 @@ __device__ __noinline__ int pgs_defer_recheck(PgsDefer<T>* d, int m, int nsd, co
     if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) continue;
     T v = r[3 * a];
     for (int k = 0; k < nd; ++k) v += W[(int64_t)drow[k] * ldw + 3 * a] * dval[k];
-    const T wm = wcoup[a];
+    const T wm = s_coupling(wblk, (m + BC - 1) / BC, a, d->slist, nsd);
     const T q = (wm > T(0) && v > T(0)) ? v / wm : (wm == T(0) && v > T(0) ? T(INFINITY) : T(0));
     atomicMin(&d->thq, to_bits(q));
   }
@@ -1038,7 +1101,7 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
 template <class T, int BC>
 __global__ void __launch_bounds__(PGS_THREADS, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-          const T* __restrict__ mu, const T* __restrict__ wcoup, T* lam_g, int warm, PgsDevStats* st,
+          const T* __restrict__ mu, const T* __restrict__ wblk, T* lam_g, int warm, PgsDevStats* st,
           const int* __restrict__ stop) {
   pdl_entry();
   if (newton_stopped(stop)) return;   // uniform, before any shared memory or barrier
@@ -1094,7 +1157,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
     psuc[0] = 1 % nblk;
     psuc[1] = -1;
     dfs.on = dfs.ns = 0;
-    dfs.sweeps = dfs.folds = 0;
+    dfs.sweeps = dfs.folds = dfs.rechecks = 0;
     dfs.xs[0] = dfs.xs[1] = 0;
     dfs.xf[0] = dfs.xf[1] = 0;
     chg_sweep[0] = chg_sweep[1] = 0;
@@ -1134,6 +1197,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
       st->eps = 0.0;
       st->s_only = 0;
       st->folds = 0;
+      st->rechecks = 0;
     }
     return;
   }
@@ -1194,7 +1258,8 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
       // with the deferred changes: if none would change, the S-only sweeps
       // go on from this new base.  Else fold what was deferred and go on in
       // order after pb.
-      const int ok = since >= nsd ? pgs_defer_recheck<T, BC>(&dfs, m, nsd, W, ldw, r, dacc, dsnap, wcoup, (int*)WD, WR)
+      if (tid == 0 && since >= nsd) ++dfs.rechecks;
+      const int ok = since >= nsd ? pgs_defer_recheck<T, BC>(&dfs, m, nsd, W, ldw, r, dacc, dsnap, wblk, (int*)WD, WR)
                                   : 0;   // the list is built in stage 0
       __syncthreads();   // every thread has read the flag before it is cleared
       if (tid == 0) {
@@ -1259,7 +1324,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         // every residual is complete: the rest of the sweep and the next
         // sweeps may visit S only, starting at b (the first block of S from b)
         tryd = 0;
-        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, dsnap);
+        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, dacc, dsnap);
         kpos = since = 0;
         while (kpos < nsd - 1 && dfs.slist[kpos] != b) ++kpos;
       }
@@ -1298,7 +1363,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         tryd = 1;
         if (!brk && nw_ < nblk && done < sweeps) {
           tryd = 0;
-          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wcoup, dacc, dsnap);
+          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, dacc, dsnap);
           kpos = since = 0;
         }
         b = nw_;
@@ -1620,6 +1685,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
     st->eps = eps;
     st->s_only = dfs.sweeps;
     st->folds = dfs.folds;
+    st->rechecks = dfs.rechecks;
   }
 }
 
@@ -1963,7 +2029,7 @@ static int build_WH_T(Scene* s) {
       e = cudaEventRecord(s->level_events[li], st);
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
     }
-    const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + AR - 1) / AR) * ntiles;
+    const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + ASM_ROWS - 1) / ASM_ROWS) * ntiles;
     PDL("k_assemble", k_assemble<T>, (unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st,
         plan + PLAN_ASM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
@@ -2004,8 +2070,8 @@ static int build_WH_T(Scene* s) {
   }
   // FP32 scenes with the BF16 W update also get W_H's BF16 copy
   __nv_bfloat16* wh16 = (sizeof(T) == 4 && s->params.w_update == ICR_W_BF16) ? (__nv_bfloat16*)s->WH16.p : nullptr;
-  PDL("k_symmetrize", k_symmetrize<T>, dim3((unsigned)((nr + 255) / 256), (unsigned)nr), 256, 0, st,
-      (int)nr, (T*)s->WH.p, wh16);
+  const unsigned nt32 = (unsigned)((nr + 31) / 32);
+  PDL("k_symmetrize", k_symmetrize<T>, dim3(nt32, nt32), dim3(32, 8), 0, st, (int)nr, (T*)s->WH.p, wh16);
   return ICR_OK;
 }
 
@@ -2016,19 +2082,21 @@ static int update_W_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   dim3 grid((m + 15) / 16, (m + 15) / 16);
-  cudaError_t e = cudaMemsetAsync(s->wcoup.p, 0, (size_t)m * sizeof(T), s->ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset wcoup");
+  const int bc = sizeof(T) == 8 ? 16 : 32;   // the PGS block size of the scene's precision
+  const size_t nb = (size_t)(m + bc - 1) / bc;
+  cudaError_t e = cudaMemsetAsync(s->wblk.p, 0, (size_t)m * nb * sizeof(T), s->ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "memset wblk");
   const int wm = sizeof(T) == 4 ? s->params.w_update : ICR_W_FP32;
   const __nv_bfloat16* wh16 = (const __nv_bfloat16*)s->WH16.p;
   if (wm == ICR_W_TF32)
     PDL("k_update_W", k_update_W<T, ICR_W_TF32>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
   else if (wm == ICR_W_BF16)
     PDL("k_update_W", k_update_W<T, ICR_W_BF16>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
   else
     PDL("k_update_W", k_update_W<T, ICR_W_FP32>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wcoup.p, s->step_stop);
+        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
   return ICR_OK;
 }
 
@@ -2039,7 +2107,7 @@ static int wcoup_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   PDL("k_wcoup", k_wcoup<T>, (unsigned)((m + 7) / 8), 256, 0, s->ctx->stream,
-      m, (const T*)s->W.p, s->ldw, (T*)s->wcoup.p);
+      m, (const T*)s->W.p, s->ldw, (T*)s->wblk.p, sizeof(T) == 8 ? 16 : 32);
   return ICR_OK;
 }
 
@@ -2071,7 +2139,7 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
   PDL("k_pgs", k_pgs<T, BC>, 1, PGS_THREADS, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
-      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wcoup.p, (T*)s->lam.p, warm, ds, s->step_stop);
+      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wblk.p, (T*)s->lam.p, warm, ds, s->step_stop);
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
     PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,
