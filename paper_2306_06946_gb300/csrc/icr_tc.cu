@@ -261,11 +261,40 @@ constexpr int PROMOTE_KB = 4;
 constexpr int TC_THREADS = 160;
 constexpr uint32_t TMEM_COLS = 2 * TM;
 
+constexpr int UQ = 4;   // slots of the unit ring from the MMA-issuing thread to the accumulator warps
+
 struct TcBars {
   uint64_t full[STAGES], empty[STAGES];   // shared-memory ring
   uint64_t tfull[2], tfree[2];            // TMEM buffers: MMAs done / drained
   uint64_t fin;                           // teardown: every MMA issued has completed
+  uint64_t qfull[UQ], qfree[UQ];          // unit ring: unit published / taken by the four accumulator warps
+  int uq[UQ];                             // unit ring: the work-list counter value of each unit (>= total: end)
 };
+
+// The MMA-issuing thread takes work units from the list counter and publishes
+// each in the unit ring before it streams the unit's operands and issues its
+// MMAs; the accumulator warps take the units from the ring in the same order.
+// The producer thus runs ahead into the next unit while the accumulator warps
+// still drain the last one (the TMEM buffers and the operand ring bound how
+// far).  Every wait is bounded and gives up when the other side has.
+__device__ __forceinline__ bool uq_push(TcBars& br, uint32_t i, int ur, uint64_t wait_ns, const volatile int* alive) {
+  const int slot = (int)(i % UQ);
+  if (i >= UQ && !mbar_wait(smem_u32(&br.qfree[slot]), ((i / UQ) - 1) & 1, wait_ns, alive)) return false;
+  *(volatile int*)&br.uq[slot] = ur;
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&br.qfull[slot])) : "memory");
+  return true;
+}
+
+// one accumulator warp: the counter value of unit i, or -1 when the wait gave up
+__device__ __forceinline__ int uq_pop(TcBars& br, uint32_t i, int lane, uint64_t wait_ns, const volatile int* alive) {
+  const int slot = (int)(i % UQ);
+  const int fine = mbar_wait(smem_u32(&br.qfull[slot]), (i / UQ) & 1, wait_ns, alive);
+  if (!__all_sync(0xffffffffu, fine)) return -1;
+  const int ur = *(volatile int*)&br.uq[slot];
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&br.qfree[slot])) : "memory");
+  return ur;
+}
 
 // warp 4, lane 0
 template <int MODE>
@@ -411,6 +440,10 @@ __device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volati
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.tfree[i])), "r"(4));
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.fin)), "r"(1));
+    for (int i = 0; i < UQ; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.qfull[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.qfree[i])), "r"(4));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n");
     *ok_sh = 1;
   }
@@ -449,7 +482,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
-  __shared__ int unit_sh;
   const int total = plan[ns];
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -464,57 +496,81 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_setup(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
-  for (;;) {
-    // thread 0 decides for the CTA before the barrier (no thread writes ok_sh
-    // between the previous unit's barrier and this one): a CTA whose pipeline
-    // gave up takes no further unit
-    if (tid == 0) unit_sh = ok_sh ? atomicAdd(counter, 1) : total;
-    __syncthreads();
-    const int ur = unit_sh;
-    if (ur >= total) break;   // uniform
+  // unit ur (counter value): supernode s, tile pair I <= J, K part [k0, k0 + nku)
+  auto decode = [&](int ur, int& s, int& ncol, int& I, int& J, int& nk, int& k0, int& nku) {
     const int u = total - 1 - ur;
     const int pos = find_unit(plan_s, 0, ns, u);
-    const int s = level_list[pos];
-    const int ncol = 3 * qcount[s];
+    s = level_list[pos];
+    ncol = 3 * qcount[s];
     const int nI = (ncol + TM - 1) / TM;
     const int w = super_ptr[s + 1] - super_ptr[s];
-    const int nk = (w + KT - 1) / KT;
+    nk = (w + KT - 1) / KT;
     const int nsk = tc_parts(tsplit, nk);   // unit = (tile pair, K part)
     const int kc = (u - plan_s[pos]) % nsk;
-    int rem = (u - plan_s[pos]) / nsk, I = 0;
+    int rem = (u - plan_s[pos]) / nsk;
+    I = 0;
     while (rem >= nI - I) {
       rem -= nI - I;
       ++I;
     }
-    const int J = I + rem;
-    const int k0 = kc * nk / nsk, nku = (kc + 1) * nk / nsk - k0;
-    if (warp == 4) {
-      if (lane == 0 && !tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK,
-                                         pk + (boff[s] + (int64_t)J * nk + k0) * BLK, I == J, nku, smem, br, tmem,
-                                         gl, gm, gc, wait_ns, &ok_sh)) {
-        ok_sh = 0;
-        atomicExch(dev_err, 1);
-      }
-    } else {
-      float acc[TM];
-      if (tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
-        const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
-        if (li < ncol) {
-          const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
-#pragma unroll
-          for (int j = 0; j < TM; ++j) {
-            const int lj = J * TM + j;
-            if (lj >= ncol || li > lj) continue;
-            const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
-            atomicAdd(&WH[gi * ldw + gj], acc[j]);
-          }
+    J = I + rem;
+    k0 = kc * nk / nsk;
+    nku = (kc + 1) * nk / nsk - k0;
+  };
+  if (warp == 4) {
+    if (lane == 0) {
+      for (uint32_t i = 0;; ++i) {
+        const int ur = ok_sh ? atomicAdd(counter, 1) : total;   // a pipeline that gave up takes no more
+        if (!uq_push(br, i, ur < total ? ur : total, wait_ns, &ok_sh)) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+          break;
         }
-      } else if (lane == 0) {
-        ok_sh = 0;
-        atomicExch(dev_err, 1);
+        if (ur >= total) break;
+        int s, ncol, I, J, nk, k0, nku;
+        decode(ur, s, ncol, I, J, nk, k0, nku);
+        if (!tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK,
+                              pk + (boff[s] + (int64_t)J * nk + k0) * BLK, I == J, nku, smem, br, tmem, gl, gm, gc,
+                              wait_ns, &ok_sh)) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+          break;
+        }
       }
     }
-    __syncthreads();   // unit_sh is read by all before thread 0 takes the next unit
+  } else {
+    for (uint32_t i = 0;; ++i) {
+      const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
+      if (ur < 0) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      if (ur >= total) break;
+      int s, ncol, I, J, nk, k0, nku;
+      decode(ur, s, ncol, I, J, nk, k0, nku);
+      float acc[TM];
+      if (!tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
+      if (li < ncol) {
+        const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
+#pragma unroll
+        for (int j = 0; j < TM; ++j) {
+          const int lj = J * TM + j;
+          if (lj >= ncol || li > lj) continue;
+          const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
+          atomicAdd(&WH[gi * ldw + gj], acc[j]);
+        }
+      }
+    }
   }
   tc_teardown(tmem, br);
 }
@@ -538,7 +594,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ __align__(8) TcBars br;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
-  __shared__ int unit_sh;
   const int u0 = plan[pa], total = plan[pb] - u0;
   if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -546,80 +601,107 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_setup(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
-  for (;;) {
-    // thread 0 decides for the CTA before the barrier (no thread writes ok_sh
-    // between the previous unit's barrier and this one): a CTA whose pipeline
-    // gave up takes no further unit
-    if (tid == 0) unit_sh = ok_sh ? atomicAdd(counter, 1) : total;
-    __syncthreads();
-    const int ur = unit_sh;
-    if (ur >= total) break;   // uniform
+  // unit ur (counter value): supernode s, 128-row tile rt, 128-column tile ct, K part [k0, k0 + nku)
+  struct Unit {
+    int s, ncol, w, nrows, nk, nsk, rt, ct, k0, nku;
+  };
+  auto decode = [&](int ur) {
+    Unit x;
     const int u = u0 + total - 1 - ur;
     const int pos = find_unit(plan, pa, pb, u);
-    const int s = level_list[pos];
-    const int ncol = 3 * qcount[s];
-    const int nJ = (ncol + TM - 1) / TM;
-    const int w = super_ptr[s + 1] - super_ptr[s];
-    const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
-    const int nk = (w + KT - 1) / KT;
-    const int nsk = tc_parts(gsplit, nk);   // unit = (tile, K part)
-    const int local = (u - plan[pos]) / nsk, kc = (u - plan[pos]) % nsk;
-    const int rt = local / nJ, ct = local % nJ;
-    const int k0 = kc * nk / nsk, nku = (kc + 1) * nk / nsk - k0;
-    if (warp == 4) {
-      if (lane == 0 && !tc_produce<MODE>(gpk + (goff[s] + (int64_t)rt * nk + k0) * BLK,
-                                         fpk + (boff[s] + (int64_t)ct * nk + k0) * BLK, false, nku, smem, br, tmem,
-                                         gl, gm, gc, wait_ns, &ok_sh)) {
-        ok_sh = 0;
-        atomicExch(dev_err, 1);
-      }
-    } else {
-      float acc[TM];
-      if (tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
-        const int row = rt * TM + 32 * warp + lane;   // front row owned by this thread
-        const int cmax = ncol - ct * TM;              // columns of this tile inside the front
-        if (row < nrows && nsk > 1) {
-          // K parts add up: X_s (zeroed when F_top was packed) += out, U_s -= out
-          float* F = X + (fr_ptr[s] + row) * ldx + ct * TM;
-          const float sg = row < w ? 1.f : -1.f;
-#pragma unroll
-          for (int c0j = 0; c0j < TM; c0j += 4) {
-            if (c0j >= cmax) break;
-            if (c0j + 4 <= cmax) {
-              atomicAdd((float4*)(F + c0j),
-                        make_float4(sg * acc[c0j], sg * acc[c0j + 1], sg * acc[c0j + 2], sg * acc[c0j + 3]));
-            } else {
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (c0j + j < cmax) atomicAdd(F + c0j + j, sg * acc[c0j + j]);
-            }
-          }
-        } else if (row < nrows) {
-          float* F = X + (fr_ptr[s] + row) * ldx + ct * TM;
-#pragma unroll
-          for (int c0j = 0; c0j < TM; c0j += 4) {
-            if (c0j >= cmax) break;
-            if (c0j + 4 <= cmax) {
-              float4* F4 = (float4*)(F + c0j);
-              float4 o = make_float4(acc[c0j], acc[c0j + 1], acc[c0j + 2], acc[c0j + 3]);
-              if (row >= w) {
-                const float4 x = *F4;
-                o = make_float4(x.x - o.x, x.y - o.y, x.z - o.z, x.w - o.w);
-              }
-              *F4 = o;
-            } else {
-#pragma unroll
-              for (int j = 0; j < 4; ++j)
-                if (c0j + j < cmax) F[c0j + j] = row < w ? acc[c0j + j] : F[c0j + j] - acc[c0j + j];
-            }
-          }
+    x.s = level_list[pos];
+    x.ncol = 3 * qcount[x.s];
+    const int nJ = (x.ncol + TM - 1) / TM;
+    x.w = super_ptr[x.s + 1] - super_ptr[x.s];
+    x.nrows = x.w + (int)(rowpat_ptr[x.s + 1] - rowpat_ptr[x.s]);
+    x.nk = (x.w + KT - 1) / KT;
+    x.nsk = tc_parts(gsplit, x.nk);   // unit = (tile, K part)
+    const int local = (u - plan[pos]) / x.nsk, kc = (u - plan[pos]) % x.nsk;
+    x.rt = local / nJ;
+    x.ct = local % nJ;
+    x.k0 = kc * x.nk / x.nsk;
+    x.nku = (kc + 1) * x.nk / x.nsk - x.k0;
+    return x;
+  };
+  if (warp == 4) {
+    if (lane == 0) {
+      for (uint32_t i = 0;; ++i) {
+        const int ur = ok_sh ? atomicAdd(counter, 1) : total;   // a pipeline that gave up takes no more
+        if (!uq_push(br, i, ur < total ? ur : total, wait_ns, &ok_sh)) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+          break;
         }
-      } else if (lane == 0) {
-        ok_sh = 0;
-        atomicExch(dev_err, 1);
+        if (ur >= total) break;
+        const Unit x = decode(ur);
+        if (!tc_produce<MODE>(gpk + (goff[x.s] + (int64_t)x.rt * x.nk + x.k0) * BLK,
+                              fpk + (boff[x.s] + (int64_t)x.ct * x.nk + x.k0) * BLK, false, x.nku, smem, br, tmem, gl,
+                              gm, gc, wait_ns, &ok_sh)) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+          break;
+        }
       }
     }
-    __syncthreads();
+  } else {
+    for (uint32_t i = 0;; ++i) {
+      const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
+      if (ur < 0) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      if (ur >= total) break;
+      const Unit x = decode(ur);
+      float acc[TM];
+      if (!tc_drain(x.nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      const int row = x.rt * TM + 32 * warp + lane;   // front row owned by this thread
+      const int cmax = x.ncol - x.ct * TM;            // columns of this tile inside the front
+      if (row < x.nrows && x.nsk > 1) {
+        // K parts add up: X_s (zeroed when F_top was packed) += out, U_s -= out
+        float* F = X + (fr_ptr[x.s] + row) * ldx + x.ct * TM;
+        const float sg = row < x.w ? 1.f : -1.f;
+#pragma unroll
+        for (int c0j = 0; c0j < TM; c0j += 4) {
+          if (c0j >= cmax) break;
+          if (c0j + 4 <= cmax) {
+            atomicAdd((float4*)(F + c0j),
+                      make_float4(sg * acc[c0j], sg * acc[c0j + 1], sg * acc[c0j + 2], sg * acc[c0j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (c0j + j < cmax) atomicAdd(F + c0j + j, sg * acc[c0j + j]);
+          }
+        }
+      } else if (row < x.nrows) {
+        float* F = X + (fr_ptr[x.s] + row) * ldx + x.ct * TM;
+#pragma unroll
+        for (int c0j = 0; c0j < TM; c0j += 4) {
+          if (c0j >= cmax) break;
+          if (c0j + 4 <= cmax) {
+            float4* F4 = (float4*)(F + c0j);
+            float4 o = make_float4(acc[c0j], acc[c0j + 1], acc[c0j + 2], acc[c0j + 3]);
+            if (row >= x.w) {
+              const float4 y = *F4;
+              o = make_float4(y.x - o.x, y.y - o.y, y.z - o.z, y.w - o.w);
+            }
+            *F4 = o;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (c0j + j < cmax) F[c0j + j] = row < x.w ? acc[c0j + j] : F[c0j + j] - acc[c0j + j];
+          }
+        }
+      }
+    }
   }
   tc_teardown(tmem, br);
 }
