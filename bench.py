@@ -429,6 +429,7 @@ def rooflines(scene, name, prof, info, phase_ms, pgs_stats, peaks, sm_count):
             "sweeps_per_launch": sweeps, "s_only_sweeps_per_launch": [int(s["sweeps_s_only"]) for s in pgs_stats],
             "deferred_folds_per_launch": [int(s["deferred_folds"]) for s in pgs_stats],
             "rechecks_per_launch": [int(s["rechecks"]) for s in pgs_stats],
+            "joins_per_launch": [int(s["joins"]) for s in pgs_stats],
             "loaded_contacts_per_launch": [int(s["n_stick"] + s["n_slip"]) for s in pgs_stats],
             "ns_per_contact_visit": t * 1e9 / max(visits, 1),
             "note": "one CTA runs the Gauss-Seidel chain; W stays in L2 when it fits (C3: 81 MB of 129 MB) "

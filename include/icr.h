@@ -130,6 +130,7 @@ typedef struct icr_pgs_stats {
                              others provably keep lambda~ = 0; see icr_solve_friction) */
   int32_t deferred_folds; /* folds of those sweeps' changes into the other contacts' residuals */
   int32_t rechecks;       /* rechecks of the other contacts' normal residuals when the bound ran out */
+  int32_t joins;          /* rechecks after which the blocks of contacts that may change joined S */
 } icr_pgs_stats;
 
 enum icr_field {

@@ -779,6 +779,7 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->stats, sizeof(PgsDevStats)));
   RET(dalloc(s, s->dev_err, sizeof(int)));
   RET(dalloc(s, s->newton, 2 * sizeof(int32_t)));
+  RET(dalloc(s, s->pgsb, 2 * mm * T));
   RET(dalloc(s, s->WH16, s->prec == ICR_FP32 ? 9 * mm * mm * 2 : 16));
   if (s->prec == ICR_FP32) {
     // tensor-core operand blocks: per supernode ceil(3m/128) column tiles x
@@ -1171,6 +1172,7 @@ int icr_solve_friction(icr_scene* s, int warm_start, icr_pgs_stats* stats) {
   stats->sweeps_s_only = d.s_only;
   stats->deferred_folds = d.folds;
   stats->rechecks = d.rechecks;
+  stats->joins = d.joins;
   if (s->params.tol > 0 && d.eps > s->params.tol && s->m > 0) {
     set_error("solve_friction: eps %g above tol %g after %d sweeps", d.eps, s->params.tol, d.sweeps);
     return ICR_ENOCONV;
@@ -1616,7 +1618,7 @@ void scene_buffers(Scene* s, std::vector<std::pair<DBuf*, bool>>& out) {
                   &s->tc_super, &s->level_first, &s->newton};
   DBuf* scratch[] = {&s->bitmap, &s->wprefix, &s->qcount, &s->qidx, &s->qpos, &s->qinv, &s->X, &s->Ftop,
                      &s->WH, &s->W, &s->uk, &s->y, &s->plan, &s->Ypk, &s->wblk, &s->stats, &s->dev_err,
-                     &s->WH16};
+                     &s->WH16, &s->pgsb};
   out.clear();
   for (DBuf* b : keep) out.push_back({b, true});
   for (DBuf* b : scratch) out.push_back({b, false});

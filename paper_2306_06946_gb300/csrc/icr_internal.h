@@ -133,6 +133,7 @@ struct Scene {
   DBuf wblk;    // per contact a and PGS block B (m x ceil(m / block)): max |W[3a, j]| over B's columns
                 //   other than a's own (the coupling bound of the PGS's S-only sweeps)
   DBuf WH16;    // BF16 copy of W_H (FP32 scenes with the BF16 W update)
+  DBuf pgsb;    // PGS S-only sweeps (2m): each passed-over contact's residual bound at the base, its coupling to S
   DBuf newton;  // device Newton stop: [0] the loop has ended, [1] iterations run after the first
   const int* step_stop = nullptr;   // while a device-resident step is enqueued with newton_tol: newton.p
   int last_newton = 0;              // n_newton of the last device-resident step
@@ -203,6 +204,7 @@ struct PgsDevStats {
   int32_t n_sep, n_stick, n_slip;
   int32_t s_only, folds;   // sweeps over S only; deferred folds
   int32_t rechecks;        // rechecks of the passed-over contacts when the coupling bound ran out
+  int32_t joins;           // rechecks after which blocks joined S
   double eps;
   unsigned long long res_bits[4];   // normal, cone, stick, slip as non-negative double bits
 };

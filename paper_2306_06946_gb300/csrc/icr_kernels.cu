@@ -884,8 +884,9 @@ struct PgsDefer {
   T th;                                // the bound sum |D| must stay below
   bits_t<T> thq;                       // theta being formed (bits of a non-negative value)
   int cnt;                             // entries of the compact list of non-zero D
-  int sweeps, folds, rechecks;         // statistics: S-only sweeps, deferred folds, rechecks
+  int sweeps, folds, rechecks, joins;  // statistics: S-only sweeps, deferred folds, rechecks, joins
   int xs[2];                           // sweeps warp 0 ended itself in step t (slot t & 1)
+  unsigned jbits[PGS_MAX_BLOCKS / 32]; // blocks a recheck found that may change: they join S
 };
 
 // Largest coupling of contact a's normal row to the columns of the blocks of
@@ -909,7 +910,7 @@ __device__ __forceinline__ T s_coupling(const T* __restrict__ wblk, int nb, int 
 // Out of line: its temporaries stay out of the solve loop's registers.
 template <class T, int BC>
 __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam, const T* r,
-                                            const T* __restrict__ wblk, T* dacc, T* dsnap) {
+                                            const T* __restrict__ wblk, T* beta, T* dacc, T* dsnap) {
   constexpr int BR = 3 * BC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nblk = (m + BC - 1) / BC;
@@ -949,6 +950,8 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
       T v = T(INFINITY);
       if (lane < nbb) {
         const T rn = r[i0 + 3 * lane], wm = s_coupling(wblk, nblk, bb * BC + lane, d->slist, total);
+        beta[bb * BC + lane] = rn;       // the residual at the base (complete here)
+        beta[m + bb * BC + lane] = wm;   // its coupling to S
         v = (wm > T(0) && rn > T(0)) ? rn / wm : (wm == T(0) ? T(INFINITY) : T(0));
       }
 #pragma unroll
@@ -975,17 +978,19 @@ __device__ __noinline__ int pgs_defer_enter(PgsDefer<T>* d, int m, const T* lam,
 
 // The bound on the changes of S since the last base ran out: every contact
 // outside S gets its normal residual with all deferred changes D,
-// r_n + W[n, S] D (W's symmetry: column n of the rows of D).  If all stay
-// positive, no contact outside S changes at its passed-over visit, and the
-// bound starts again from this base (dsnap = D, theta from these residuals):
-// returns 1.  Else returns 0 (the caller leaves the S-only sweeps).  The list
-// of D's non-zero rows is built in drow / dval (stage 0's space).
+// r_n + W[n, S] D (W's symmetry: column n of the rows of D, from the list of
+// D's non-zero rows built in drow / dval, stage 0's space), kept in beta.  If
+// all stay positive, no contact outside S changes at its passed-over visit,
+// and the bound starts again from this base (dsnap = D, theta from these
+// residuals): returns 1.  Else the blocks of the contacts that may change are
+// in jbits, and it returns 2 when S can take them (S-only sweeps with those
+// blocks joined) or 0 (the caller leaves the S-only sweeps).
 template <class T, int BC>
 __device__ __noinline__ int pgs_defer_recheck(PgsDefer<T>* d, int m, int nsd, const T* __restrict__ W, int64_t ldw,
-                                              const T* r, const T* dacc, T* dsnap, const T* __restrict__ wblk,
-                                              int* drow, T* dval) {
+                                              const T* r, const T* dacc, T* dsnap, T* beta, int* drow, T* dval) {
   constexpr int BR = 3 * BC;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
+  if (tid < PGS_MAX_BLOCKS / 32) d->jbits[tid] = 0u;
   if (wid == 0) {
     int cnt = 0;
     for (int k = 0; k < nsd; ++k) {
@@ -1014,30 +1019,109 @@ __device__ __noinline__ int pgs_defer_recheck(PgsDefer<T>* d, int m, int nsd, co
     if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) continue;
     T v = r[3 * a];
     for (int k = 0; k < nd; ++k) v += W[(int64_t)drow[k] * ldw + 3 * a] * dval[k];
-    const T wm = s_coupling(wblk, (m + BC - 1) / BC, a, d->slist, nsd);
-    const T q = (wm > T(0) && v > T(0)) ? v / wm : (wm == T(0) && v > T(0) ? T(INFINITY) : T(0));
-    atomicMin(&d->thq, to_bits(q));
+    beta[a] = v;
+    if (!(v > T(0))) {
+      atomicOr(&d->jbits[blk >> 5], 1u << (blk & 31));
+    } else {
+      const T ws = beta[m + a];
+      atomicMin(&d->thq, to_bits(ws > T(0) ? v / ws : T(INFINITY)));
+    }
   }
   __syncthreads();
-  const T th = from_bits(d->thq);
-  const int ok = th > T(0);
+  int nj = 0;
+#pragma unroll 4
+  for (int w = 0; w < PGS_MAX_BLOCKS / 32; ++w) nj += __popc(d->jbits[w]);
+  const int ok = nj == 0;
   if (ok) {
     for (int i = tid; i < nsd * BR; i += nthr) dsnap[i] = dacc[i];
     if (tid < nsd) d->nb[tid] = T(0);
-    if (tid == 0) d->th = th * T(1.0 - 1.0 / 1024.0);
+    if (tid == 0) d->th = from_bits(d->thq) * T(1.0 - 1.0 / 1024.0);
   }
   __syncthreads();
-  return ok;
+  return ok ? 1 : (nsd + nj <= PGS_MAX_DEFER ? 2 : 0);
+}
+
+// After the deferred changes reached the rows of the blocks in jbits: S takes
+// those blocks.  The new S in ascending order; D moved to its blocks' new
+// positions (a position never moves down, so from the end), the joined blocks'
+// D start at zero; a new base (dsnap = D, nb = 0); each other contact's
+// coupling to S widened by the joined blocks and theta = min beta / ws.
+// Returns the position in the new S of the block after pb (pb is in S).
+template <class T, int BC>
+__device__ __noinline__ int pgs_defer_merge(PgsDefer<T>* d, int m, int pb, T* dacc, T* dsnap,
+                                            const T* __restrict__ wblk, T* beta) {
+  constexpr int BR = 3 * BC;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
+  const int nblk = (m + BC - 1) / BC;
+  if (wid == 0) {
+    const int nold = d->ns;
+    const int oldb = lane < nold ? d->slist[lane] : -1;
+    const unsigned wd = d->sbits[lane] | d->jbits[lane];
+    const int c = __popc(wd);
+    int off = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, off, o);
+      if (lane >= o) off += y;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= c;
+    __syncwarp();
+    for (unsigned w = wd; w != 0u; w &= w - 1u) d->slist[off++] = lane * 32 + __ffs(w) - 1;
+    __syncwarp();
+    for (int kp = total - 1; kp >= 0; --kp) {
+      const int B = d->slist[kp];
+      const unsigned mk = __ballot_sync(FULL, oldb == B);
+      const int k = mk ? __ffs(mk) - 1 : -1;
+      if (k != kp)
+        for (int i = lane; i < BR; i += 32) dacc[kp * BR + i] = k >= 0 ? dacc[k * BR + i] : T(0);
+      __syncwarp();
+    }
+    for (int i = lane; i < total * BR; i += 32) dsnap[i] = dacc[i];
+    if (lane < total) d->nb[lane] = T(0);
+    d->sbits[lane] = wd;
+    if (lane == 0) {
+      d->ns = total;
+      d->thq = to_bits(T(INFINITY));
+    }
+  }
+  __syncthreads();
+  const int ns = d->ns;
+  for (int a = tid; a < m; a += nthr) {
+    const int blk = a / BC;
+    if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) continue;
+    T ws = beta[m + a];
+    for (int k = 0; k < ns; ++k) {
+      const int B = d->slist[k];
+      if ((d->jbits[B >> 5] >> (B & 31)) & 1u) ws = nmax(ws, wblk[(int64_t)a * nblk + B]);
+    }
+    beta[m + a] = ws;
+    const T v = beta[a];
+    const T q = (ws > T(0) && v > T(0)) ? v / ws : (ws == T(0) ? T(INFINITY) : T(0));
+    atomicMin(&d->thq, to_bits(q));
+  }
+  __syncthreads();
+  int kp = 0;
+  while (kp < ns - 1 && d->slist[kp] != pb) ++kp;
+  if (tid < PGS_MAX_BLOCKS / 32) d->jbits[tid] = 0u;
+  if (tid == 0) {
+    d->th = from_bits(d->thq) * T(1.0 - 1.0 / 1024.0);
+    ++d->joins;
+  }
+  __syncthreads();
+  return kp + 1 == ns ? 0 : kp + 1;
 }
 
 // Leaves the S-only sweeps after block pb, whose changes are dlp: they are
 // folded into the rows of S (its successor's pending share included, which
 // warp 0 drops) and the deferred changes D of S into every other row.  Then
 // every residual is complete.  Out of line, like pgs_defer_enter.
+// With `only` (a block bit set) the deferred changes reach the rows of those
+// blocks alone (a join), else every row outside S (a leave).
 template <class T, int BC>
 __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int nsd, const T* dlp,
                                              const T* __restrict__ W, int64_t ldw, T* r, const T* dacc,
-                                             int* nzl, int* drow, T* dval) {
+                                             int* nzl, int* drow, T* dval, const unsigned* only) {
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nthr = blockDim.x;
@@ -1086,8 +1170,10 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
       if ((d->sbits[blk >> 5] >> (blk & 31)) & 1u) {
         const T* Wc = W + (int64_t)pR0 * ldw + j0;
         for (int k = 0; k < cnt; ++k) fma_chunk(acc, Wc + (int64_t)lst[k] * ldw, dlp[lst[k]]);
-      } else {
+      } else if (!only || ((only[blk >> 5] >> (blk & 31)) & 1u)) {
         for (int k = 0; k < nd; ++k) fma_chunk(acc, W + (int64_t)drow[k] * ldw + j0, dval[k]);
+      } else {
+        continue;
       }
 #pragma unroll
       for (int q = 0; q < CH; ++q)
@@ -1101,7 +1187,7 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
 template <class T, int BC>
 __global__ void __launch_bounds__(PGS_THREADS, 1)
     k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-          const T* __restrict__ mu, const T* __restrict__ wblk, T* lam_g, int warm, PgsDevStats* st,
+          const T* __restrict__ mu, const T* __restrict__ wblk, T* pgsb, T* lam_g, int warm, PgsDevStats* st,
           const int* __restrict__ stop) {
   pdl_entry();
   if (newton_stopped(stop)) return;   // uniform, before any shared memory or barrier
@@ -1157,7 +1243,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
     psuc[0] = 1 % nblk;
     psuc[1] = -1;
     dfs.on = dfs.ns = 0;
-    dfs.sweeps = dfs.folds = dfs.rechecks = 0;
+    dfs.sweeps = dfs.folds = dfs.rechecks = dfs.joins = 0;
     dfs.xs[0] = dfs.xs[1] = 0;
     dfs.xf[0] = dfs.xf[1] = 0;
     chg_sweep[0] = chg_sweep[1] = 0;
@@ -1198,6 +1284,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
       st->s_only = 0;
       st->folds = 0;
       st->rechecks = 0;
+      st->joins = 0;
     }
     return;
   }
@@ -1253,14 +1340,15 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
   };
   while (done < sweeps) {
     if (nsd && dfs.xf[(t + 1) & 1]) {   // set in the previous step
-      // The bound on the changes of S ran out after block pb.  When it lasted
-      // a round of S, the passed-over contacts' normal residuals are formed
-      // with the deferred changes: if none would change, the S-only sweeps
-      // go on from this new base.  Else fold what was deferred and go on in
-      // order after pb.
+      // The bound on the changes of S ran out after block pb: the passed-over
+      // contacts' normal residuals are formed with the deferred changes.  If
+      // none would change, the S-only sweeps go on from this new base; if
+      // some would, their blocks join S when it can take them; else fold what
+      // was deferred and go on in order after pb.  (The list of D's non-zero
+      // rows is built in stage 0: its rows are fetched again.)
       if (tid == 0 && since >= nsd) ++dfs.rechecks;
-      const int ok = since >= nsd ? pgs_defer_recheck<T, BC>(&dfs, m, nsd, W, ldw, r, dacc, dsnap, wblk, (int*)WD, WR)
-                                  : 0;   // the list is built in stage 0
+      const int rc = since >= nsd ? pgs_defer_recheck<T, BC>(&dfs, m, nsd, W, ldw, r, dacc, dsnap, pgsb, (int*)WD, WR)
+                                  : 0;
       __syncthreads();   // every thread has read the flag before it is cleared
       if (tid == 0) {
         dfs.xf[0] = dfs.xf[1] = 0;
@@ -1268,7 +1356,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         cst_blk[0] = -1;
       }
       __syncthreads();
-      if (ok) {
+      if (rc == 1) {
         since = 0;
         if (pend) {
           pend = false;
@@ -1276,10 +1364,29 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         }
         continue;
       }
+      if (rc == 2) {
+        // The blocks holding contacts that may change join S: the deferred
+        // changes reach their rows, pb's changes the rows of S (warp 0 drops
+        // its pending share), and the S-only sweeps go on after pb in order,
+        // the joined blocks included (a plain sweep visits them there too).
+        if (wid == 0) p0 = p1 = p2 = T(0);
+        pgs_defer_leave<T, BC>(&dfs, m, pb, nsd, dl + (1 - (int)(t & 1)) * BR, W, ldw, r, dacc, nzl, (int*)WD, WR,
+                               dfs.jbits);
+        kpos = pgs_defer_merge<T, BC>(&dfs, m, pb, dacc, dsnap, wblk, pgsb);
+        nsd = dfs.ns;
+        since = 0;
+        pend = false;
+        const int bnext = dfs.slist[kpos];
+        const bool wrap = bnext <= pb;   // no joined block after pb: the sweep ends here
+        pb = -1;
+        b = bnext;
+        if (wrap && end_sweep()) break;
+        continue;
+      }
       pend = false;
       if (wid == 0) p0 = p1 = p2 = T(0);
       pgs_defer_leave<T, BC>(&dfs, m, pb, nsd, dl + (1 - (int)(t & 1)) * BR, W, ldw, r, dacc, nzl,
-                             (int*)WD, WR);   // scratch in stage 0
+                             (int*)WD, WR, nullptr);   // scratch in stage 0
       if (tid == 0) {
         ++dfs.folds;
         dfs.xf[0] = dfs.xf[1] = 0;
@@ -1324,7 +1431,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         // every residual is complete: the rest of the sweep and the next
         // sweeps may visit S only, starting at b (the first block of S from b)
         tryd = 0;
-        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, dacc, dsnap);
+        nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, pgsb, dacc, dsnap);
         kpos = since = 0;
         while (kpos < nsd - 1 && dfs.slist[kpos] != b) ++kpos;
       }
@@ -1363,7 +1470,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         tryd = 1;
         if (!brk && nw_ < nblk && done < sweeps) {
           tryd = 0;
-          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, dacc, dsnap);
+          nsd = pgs_defer_enter<T, BC>(&dfs, m, lam, r, wblk, pgsb, dacc, dsnap);
           kpos = since = 0;
         }
         b = nw_;
@@ -1580,8 +1687,11 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
         dl[dc * BR + 3 * lane + 2] = e2;
       }
       if (bn == b) p0 = p1 = p2 = T(0);   // single block: the residual already has them
-    } else {
-      const int t2 = tid - 32, n2 = nthr - 32;
+    } else if (wid & 3) {
+      // the streaming warps: the twelve of the three sub-partitions other than
+      // warp 0's (warps are spread over the SM's four schedulers by id mod 4),
+      // so that the serial chain has its scheduler to itself
+      const int t2 = (wid - 1 - (wid >> 2)) * 32 + lane, n2 = (PGS_WARPS - PGS_WARPS / 4) * 32;
       {
         // prefetch the next block's rows when it has a non-zero lambda~ or
         // changed in its last visit (data no streaming warp writes, so every
@@ -1686,6 +1796,7 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
     st->s_only = dfs.sweeps;
     st->folds = dfs.folds;
     st->rechecks = dfs.rechecks;
+    st->joins = dfs.joins;
   }
 }
 
@@ -2139,7 +2250,8 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
   PDL("k_pgs", k_pgs<T, BC>, 1, PGS_THREADS, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
-      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wblk.p, (T*)s->lam.p, warm, ds, s->step_stop);
+      (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wblk.p, (T*)s->pgsb.p, (T*)s->lam.p, warm, ds,
+      s->step_stop);
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
     PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,

@@ -75,7 +75,8 @@ class PgsStats(ct.Structure):
     _fields_ = [("sweeps", ct.c_int32), ("n_separated", ct.c_int32), ("n_stick", ct.c_int32),
                 ("n_slip", ct.c_int32), ("eps", ct.c_double), ("res_normal", ct.c_double),
                 ("res_cone", ct.c_double), ("res_stick", ct.c_double), ("res_slip", ct.c_double),
-                ("sweeps_s_only", ct.c_int32), ("deferred_folds", ct.c_int32), ("rechecks", ct.c_int32)]
+                ("sweeps_s_only", ct.c_int32), ("deferred_folds", ct.c_int32), ("rechecks", ct.c_int32),
+                ("joins", ct.c_int32)]
 
 
 _lib = None

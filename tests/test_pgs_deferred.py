@@ -4,8 +4,9 @@ FP64 oracle's plain sweeps.
 A contact with lambda~ = 0 and a non-negative normal residual keeps
 lambda~ = 0 under the local rule (Eq. "PGS"), so the library sweeps only the
 blocks that may change while the sum of |changes| since the last complete
-residual stays below min r_n / max_j |W[n, j]| over the other contacts, and
-folds those changes into the others' residuals later, in one pass.  The
+residual stays below min r_n / max |W[n, j]| over the other contacts (j over the
+columns of S's blocks), and folds those changes into the others' residuals
+later, in one pass, or lets the blocks of contacts about to change join S.  The
 iterate is that of plain sweeps; these cases drive both the S-only sweeps and
 their ends (the bound running out, |S| above the block limit, the last block
 in S, an exact fixed point) and compare with the oracle on the same W.
@@ -75,10 +76,12 @@ def test_s_only_sweeps_match_the_oracle(ctx, name, prec):
         assert st["sweeps_s_only"] == 0 and st["deferred_folds"] == 0
     elif expect == "fixed":
         assert sw_ref < sweeps and st["sweeps"] < sweeps
+    elif expect == "leave":   # the bound ran out with a 17th block about to change: a fold
+        assert st["deferred_folds"] > 0
     else:
         assert st["sweeps_s_only"] > 0
-        if expect == "leave":
-            assert st["deferred_folds"] > 0
+        if expect == "join":   # a contact outside S started to change: its block joined S
+            assert st["joins"] > 0
     # a warm start from the result continues from it: same lambda~ again after
     # the sweeps a fixed point or the cap allows
     if prec == 1 and expect == "fixed":
@@ -108,5 +111,5 @@ def test_coupling_bound_of_a_given_W(ctx, prec):
     sc2.set_field("MU", s.mu)
     st2 = sc2.solve_friction(stats=True)
     assert np.array_equal(sc2.get("LAMBDA"), a)
-    assert (st2["sweeps"], st2["sweeps_s_only"], st2["deferred_folds"]) == \
-        (st["sweeps"], st["sweeps_s_only"], st["deferred_folds"])
+    assert (st2["sweeps"], st2["sweeps_s_only"], st2["deferred_folds"], st2["joins"]) == \
+        (st["sweeps"], st["sweeps_s_only"], st["deferred_folds"], st["joins"])
