@@ -385,6 +385,79 @@ int icr_serve_ex(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_
                  int32_t n_req, int32_t n_slots, double timeout_s, double* latency_s, double* makespan_s,
                  icr_serve_stats* stats);
 
+/* Batched time steps: many scenes stepped together by one captured CUDA
+ * graph whose every kernel launch covers many of them (each scene runs Alg. 3
+ * exactly as icr_step would; the scenes are independent problems).  At
+ * creation the batch records the launch sequence of icr_step(scene, n_newton)
+ * of every scene (after icr_autotune for scenes not yet tuned) and merges the
+ * sequences into one common supersequence (icr_batch_merge_plan): a merged
+ * launch runs one kernel for the scenes whose launch of that kernel it takes
+ * over, in one grid in which each scene's blocks see the block
+ * indices of that scene's own launch, so a step of N scenes makes about as
+ * many launches as the longest single-scene step instead of N times as many.
+ * Device copies and fills of the step are merged the same way.  All scenes
+ * must share one context, whose stream must not be the legacy default stream
+ * (ICR_EINVAL), and be resident with a system, a mapping and an obstacle
+ * (ICR_ESTATE); a scene may appear once.  Creation runs one batched step
+ * (every scene advances one time step), then captures the graph; the launch
+ * arguments (device addresses, grids) are kept in a device buffer counted
+ * against the context's HBM budget (ICR_ENOMEM).  The scenes must outlive the
+ * batch: icr_scene_destroy refuses a scene held by a batch (ICR_ESTATE).
+ * n_groups (>= 1, at most n_scenes are used) splits the scenes into that
+ * many groups balanced by cost (3 n m + 9 m^2 for n DOF and m contacts; longest
+ * first, each to the least loaded group); each group's sequences are merged
+ * on their own and the groups run as parallel branches of the one graph (a
+ * merged launch lasts as long as its slowest scene's part, so every group
+ * carries about one heavy scene, and groups overlap on the device).  Within a
+ * merged launch the heaviest scene's blocks come first. */
+typedef struct icr_batch icr_batch;
+int icr_batch_create(icr_batch** out, icr_scene* const* scenes, int32_t n_scenes, int32_t n_newton,
+                     int32_t n_groups);
+/* One time step of every scene of the batch, enqueued on the context's stream
+ * (the graph reads each scene's buffers, so new inputs of the same shape are
+ * stepped by launching again, as with icr_step_launch).  ICR_ESTATE when a
+ * scene changed since creation: evicted, a buffer reallocated, another contact
+ * count, obstacle kind or parameters (create the batch again). */
+int icr_batch_launch(icr_batch* batch);
+typedef struct icr_batch_info_t {
+  int32_t n_scenes;
+  int32_t n_groups;
+  int32_t launches_per_step;          /* merged launches of one batched step (kernels and copy/fill groups) */
+  int32_t kernel_launches_per_step;   /* of which kernels */
+  int64_t scene_launches_per_step;    /* kernel launches the scenes' own steps make together */
+  uint64_t argument_bytes;            /* device buffer of the launch arguments */
+  uint64_t steps;                     /* icr_batch_launch calls so far */
+} icr_batch_info_t;
+int icr_batch_info(icr_batch* batch, icr_batch_info_t* out);
+/* One batched step run eagerly (not through the graph) with CUDA events
+ * around every merged launch (diagnostic; the paper has no counterpart).
+ * Synchronises; writes up to max_out entries in launch order (grouped by
+ * group) and the number of merged launches to *n_out.  name: the kernel (or
+ * "copies/fills"), slots: scenes (copies and fills: operations) it covers. */
+typedef struct icr_batch_launch_time {
+  char name[32];
+  int32_t group;
+  int32_t slots;
+  int32_t blocks;
+  double ms;
+} icr_batch_launch_time;
+int icr_batch_profile(icr_batch* batch, icr_batch_launch_time* out, int32_t max_out, int32_t* n_out);
+/* Waits for the context's stream, then frees the batch (not its scenes). */
+int icr_batch_destroy(icr_batch* batch);
+/* The merge rule of icr_batch_create on plain integer sequences (host only,
+ * no GPU).  n_seq sequences of non-negative launch keys, concatenated in keys,
+ * sequence i of lengths[i] keys, are merged into one common supersequence:
+ * taken longest first, each sequence is aligned with the merged sequence so
+ * far through a longest common subsequence of the two (shared launches where
+ * both have the key in compatible order).  Writes the merged launches in
+ * order: out_key[l] the key, out_count[l] how many sequences launch l covers,
+ * and their indices (ascending) concatenated in out_cover, which needs room
+ * for the sum of the lengths.  *n_out receives the number of merged launches
+ * (ICR_EINVAL when it exceeds max_out).  Each sequence's keys are covered in
+ * order, one per merged launch. */
+int icr_batch_merge_plan(const int32_t* keys, const int32_t* lengths, int32_t n_seq, int32_t* out_key,
+                         int32_t* out_count, int32_t* out_cover, int32_t max_out, int32_t* n_out);
+
 /* Which paths the last icr_build_WH took, read back from the device work
  * lists (synchronises; needs icr_build_WH, ICR_ESTATE otherwise).  Diagnostic:
  * the paper has no counterpart; it shows which kernels a workload exercises. */

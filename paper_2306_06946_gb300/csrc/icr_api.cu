@@ -86,11 +86,6 @@ using namespace icr;
     cudaError_t e_ = (call);                       \
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
-#define RET(call)                   \
-  do {                              \
-    int r_ = (call);                \
-    if (r_ != ICR_OK) return r_;    \
-  } while (0)
 
 static int check_scene(icr_scene* s) {
   if (!s) {
@@ -401,6 +396,10 @@ int icr_scene_create(icr_ctx* ctx, icr_scene** out, const icr_params* params) {
 
 int icr_scene_destroy(icr_scene* s) {
   if (!s) return ICR_OK;
+  if (s->batches > 0) {
+    set_error("scene_destroy: the scene is held by %d batch(es); destroy them first", s->batches);
+    return ICR_ESTATE;
+  }
   cudaSetDevice(s->ctx->device);
   cudaStreamSynchronize(s->ctx->stream);
   std::vector<std::pair<DBuf*, bool>> all;
@@ -1461,7 +1460,9 @@ int icr_autotune(icr_scene* s, int32_t* tc_levels, double* level_ms, int32_t max
   return ICR_OK;
 }
 
-static int step_enqueue(Scene* s, int n_newton) {
+}  // extern "C"
+
+int icr::step_enqueue(Scene* s, int n_newton) {
   if (!s->has_mapping || !s->has_system) {
     set_error("step: needs icr_set_system and icr_set_mapping");
     return ICR_ESTATE;
@@ -1474,10 +1475,9 @@ static int step_enqueue(Scene* s, int n_newton) {
     set_error("step: %d Newton iterations not available for this obstacle", n_newton);
     return ICR_EINVAL;
   }
-  cudaStream_t st = s->ctx->stream;
   if (s->m) {
-    CK(cudaMemcpyAsync(s->p.p, s->p0.p, 3 * (size_t)s->m * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemsetAsync(s->u.p, 0, 6 * (size_t)s->m * sizeof(double), st));
+    RET(dcopy(s, s->p.p, s->p0.p, 3 * (size_t)s->m * sizeof(double), "copy p0"));
+    RET(dzero(s, s->u.p, 6 * (size_t)s->m * sizeof(double), "memset u"));
   }
   RET(launch_build_WH(s));
   s->has_WH = true;
@@ -1485,7 +1485,7 @@ static int step_enqueue(Scene* s, int n_newton) {
   // newton_tol: from iteration 2 on, the kernels of an iteration return at
   // entry once the FP64 check after the previous linearisation ended the loop
   const bool nstop = s->params.newton_tol > 0 && n_newton > 1 && s->m;
-  if (nstop) CK(cudaMemsetAsync(s->newton.p, 0, 2 * sizeof(int32_t), st));
+  if (nstop) RET(dzero(s, s->newton.p, 2 * sizeof(int32_t), "memset newton"));
   struct StopGuard {
     Scene* s;
     ~StopGuard() { s->step_stop = nullptr; }
@@ -1499,9 +1499,9 @@ static int step_enqueue(Scene* s, int n_newton) {
     RET(launch_update_W(s));
     if (k == 0 && s->params.warm_start && s->m) {
       // Newton iteration 1 starts from the previous time step's iteration-1 solution
-      CK(cudaMemcpyAsync(s->lam.p, s->lam0.p, lam_bytes, cudaMemcpyDeviceToDevice, st));
+      RET(dcopy(s, s->lam.p, s->lam0.p, lam_bytes, "copy lam0"));
       RET(launch_pgs(s, 1, 0));
-      CK(cudaMemcpyAsync(s->lam0.p, s->lam.p, lam_bytes, cudaMemcpyDeviceToDevice, st));
+      RET(dcopy(s, s->lam0.p, s->lam.p, lam_bytes, "copy lam"));
     } else {
       RET(launch_pgs(s, 0, 0));
     }
@@ -1509,10 +1509,12 @@ static int step_enqueue(Scene* s, int n_newton) {
   }
   s->step_stop = nullptr;
   RET(launch_correct_motion(s));
-  if (s->m) CK(cudaMemsetAsync(s->u.p, 0, 3 * (size_t)s->m * sizeof(double), st));
+  if (s->m) RET(dzero(s, s->u.p, 3 * (size_t)s->m * sizeof(double), "memset u"));
   s->has_dirs = s->has_W = s->has_lam = true;
   return ICR_OK;
 }
+
+extern "C" {
 
 static int field_size(Scene* s, int32_t f, size_t* count, size_t* elem) {
   const size_t m = s->m;

@@ -104,9 +104,13 @@ struct Profiler {
   }
 };
 
+struct BatchRec;
+
 struct Scene {
   Ctx* ctx = nullptr;
   Profiler* prof = nullptr;   // per-launch timing while profiling
+  BatchRec* rec = nullptr;    // while an icr_batch records the scene's step: launches are recorded, not made
+  int batches = 0;            // live icr_batch objects that hold this scene
   icr_params params{};
   int prec = ICR_FP32;
   size_t tsize = 4;
@@ -303,21 +307,181 @@ struct DevInt {
 // events around a launch while the scene is profiled (not during capture)
 int prof_mark(Scene* s, const char* name, bool after);
 
-// launch through pdl_launch, check it and count it in the scene `s` in scope
-#define PDL(where, ...)                                 \
-  do {                                                  \
-    if (s->prof) {                                      \
-      const int rc_ = prof_mark(s, where, false);       \
-      if (rc_ != ICR_OK) return rc_;                    \
-    }                                                   \
-    const cudaError_t e_ = pdl_launch(__VA_ARGS__);     \
-    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-    ++s->launches;                                      \
-    if (s->prof) {                                      \
-      const int rc_ = prof_mark(s, where, true);        \
-      if (rc_ != ICR_OK) return rc_;                    \
-    }                                                   \
+// ---------------------------------------------------------------- batched launches
+// A kernel body reads its block index and grid size from a VB instead of
+// blockIdx / gridDim.  A single-scene launch passes its own (own_block());
+// a batched launch (icr_batch) runs the bodies of many scenes in one flat
+// grid, each scene's blocks numbered as in that scene's own launch.
+struct VB {
+  unsigned bx, by, gx, gy;
+};
+__device__ __forceinline__ VB own_block() { return VB{blockIdx.x, blockIdx.y, gridDim.x, gridDim.y}; }
+
+// The arguments of one launch, stored by value (a small tuple whose layout is
+// the same on the host and the device: it is copied into device memory).
+template <class... A>
+struct Args;
+template <>
+struct Args<> {};
+template <class H, class... R>
+struct Args<H, R...> {
+  H h;
+  Args<R...> r;
+};
+inline Args<> make_args() { return Args<>{}; }
+template <class H, class... R>
+Args<H, R...> make_args(H h, R... r) {
+  return Args<H, R...>{h, make_args(r...)};
+}
+// K::run(d..., the stored arguments in order)
+template <class K, class... D>
+__device__ __forceinline__ void apply_args(const Args<>&, D... d) {
+  K::run(d...);
+}
+template <class K, class H, class... R, class... D>
+__device__ __forceinline__ void apply_args(const Args<H, R...>& a, D... d) {
+  apply_args<K>(a.r, d..., a.h);
+}
+
+// One scene's part of a batched launch: its own grid and its arguments.
+template <class P>
+struct BatchSlot {
+  unsigned gx, gy;
+  P args;
+};
+
+// Batched launch of body K.  Bodies whose work units any grid covers
+// (K::stride: a grid-stride loop or a counter over the scene's device work
+// list) run persistently: every block serves every slot in turn, heaviest
+// scene first, as block bx of a grid of gridDim.x.  Otherwise slot i owns the
+// flat blocks [first[i], first[i+1]) and its blocks run K's body with the
+// block index of the scene's own launch.
+template <class K, class P>
+__global__ void __launch_bounds__(K::threads, K::minb)
+    k_batch(const BatchSlot<P>* __restrict__ slots, const unsigned* __restrict__ first, int nslots) {
+  pdl_entry();
+  if constexpr (K::stride) {
+    for (int i = 0; i < nslots; ++i) {
+      apply_args<K>(slots[i].args, VB{blockIdx.x, 0u, gridDim.x, 1u});
+      __syncthreads();   // the next scene's units reuse the shared memory
+    }
+    return;
+  }
+  __shared__ int slot_sh;
+  const unsigned b = blockIdx.x;
+  const int nt = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid == 0) slot_sh = -1;
+  __syncthreads();
+  for (int i = tid; i < nslots; i += nt)
+    if (first[i] <= b && b < first[i + 1]) slot_sh = i;   // exactly one slot
+  __syncthreads();
+  const int i = slot_sh;
+  if (i < 0) return;   // uniform; cannot happen with the offsets the host checked
+  const BatchSlot<P>& sl = slots[i];
+  const unsigned local = b - first[i];
+  apply_args<K>(sl.args, VB{local % sl.gx, local / sl.gx, sl.gx, sl.gy});
+}
+
+// A device-to-device copy (src != NULL) or a zero fill of `bytes` bytes.
+struct MemOp {
+  void* dst;
+  const void* src;
+  unsigned long long bytes;
+};
+
+using BatchLaunchFn = cudaError_t (*)(const void* slots, const unsigned* first, int nslots, unsigned nblocks,
+                                      dim3 block, size_t smem, cudaStream_t st, int device);
+
+template <class K, class P>
+cudaError_t batch_launch(const void* slots, const unsigned* first, int nslots, unsigned nblocks, dim3 block,
+                         size_t smem, cudaStream_t st, int device) {
+  static SmemLimit lim;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = ensure_smem(k_batch<K, P>, lim, device, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_batch<K, P><<<nblocks, block, smem, st>>>(static_cast<const BatchSlot<P>*>(slots), first, nslots);
+  return cudaGetLastError();
+}
+
+// One recorded launch of a scene's step: a kernel (launch != NULL, one slot)
+// or a group of independent copies and fills (launch == NULL).
+struct BatchEntry {
+  const char* name = nullptr;
+  BatchLaunchFn launch = nullptr;
+  dim3 block;
+  size_t smem = 0;
+  unsigned blocks = 0;                // blocks of the scene's own launch
+  size_t slot_align = 0;
+  bool stride = false;                // K::stride: one persistent grid serves every slot
+  std::vector<unsigned char> slot;    // the BatchSlot<P> bytes
+  std::vector<MemOp> ops;
+};
+struct BatchRec {
+  std::vector<BatchEntry> entries;
+};
+
+template <class K, class... KArgs, class... A>
+int batch_record(BatchRec* rec, const char* where, void (*)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                 A... a) {
+  using P = Args<KArgs...>;
+  if (grid.z != 1) {
+    set_error("%s: a batched launch takes a 1-D or 2-D grid", where);
+    return ICR_EINVAL;
+  }
+  if ((uint64_t)grid.x * grid.y == 0) return ICR_OK;   // nothing to run
+  const BatchSlot<P> sl{grid.x, grid.y, make_args(static_cast<KArgs>(a)...)};
+  BatchEntry e;
+  e.name = where;
+  e.launch = &batch_launch<K, P>;
+  e.block = block;
+  e.smem = smem;
+  e.blocks = grid.x * grid.y;
+  e.slot_align = alignof(BatchSlot<P>);
+  e.stride = K::stride;
+  e.slot.assign(reinterpret_cast<const unsigned char*>(&sl), reinterpret_cast<const unsigned char*>(&sl) + sizeof(sl));
+  rec->entries.push_back(std::move(e));
+  return ICR_OK;
+}
+
+// Zero fill and device-to-device copy on the scene's stream (recorded while a
+// batch records the scene's step).
+int dzero(Scene* s, void* p, size_t bytes, const char* where);
+int dcopy(Scene* s, void* dst, const void* src, size_t bytes, const char* where);
+// the device-resident time step (icr_step), enqueued or recorded
+int step_enqueue(Scene* s, int n_newton);
+
+// Launch body tag K (K::kernel() is its single-scene kernel) through
+// pdl_launch, check it and count it in the scene `s` in scope; while the
+// scene is recorded by a batch, record the launch instead.
+#define PDL(where, K, grid, block, smem, st, ...)                                                          \
+  do {                                                                                                  \
+    if (s->rec) {                                                                                       \
+      const int rc_ = batch_record<K>(s->rec, where, K::kernel(), dim3(grid), dim3(block), (size_t)(smem), \
+                                      __VA_ARGS__);                                                     \
+      if (rc_ != ICR_OK) return rc_;                                                                    \
+      break;                                                                                            \
+    }                                                                                                   \
+    if (s->prof) {                                                                                      \
+      const int rc_ = prof_mark(s, where, false);                                                       \
+      if (rc_ != ICR_OK) return rc_;                                                                    \
+    }                                                                                                   \
+    const cudaError_t e_ = pdl_launch(K::kernel(), grid, block, smem, st, __VA_ARGS__);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where);                                                 \
+    ++s->launches;                                                                                      \
+    if (s->prof) {                                                                                      \
+      const int rc_ = prof_mark(s, where, true);                                                        \
+      if (rc_ != ICR_OK) return rc_;                                                                    \
+    }                                                                                                   \
   } while (0)
+// return a non-OK status of a call
+#define RET(call)                \
+  do {                           \
+    int r_ = (call);             \
+    if (r_ != ICR_OK) return r_; \
+  } while (0)
+
 // ICR_ETIMEOUT when a kernel reported a bounded wait that ran out (synchronises)
 int check_device_error(Scene* s);
 

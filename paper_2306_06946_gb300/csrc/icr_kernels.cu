@@ -80,10 +80,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // One thread per (contact, node): mark the contact in every supernode on the
 // etree path from the node's supernode to the root.  A thread stops at the
 // first supernode already marked for its contact: whoever marked it walks on.
-__global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
+__device__ __forceinline__ void d_reach_mark(const VB& vb, const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
                              const int* __restrict__ parent, int ns, uint32_t* bitmap, int words) {
-  pdl_entry();
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int t = vb.bx * blockDim.x + threadIdx.x;
   if (t >= 4 * m) return;
   int a = t >> 2;
   int s = node_super[nodes[t]];
@@ -96,13 +95,28 @@ __global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __
   }
 }
 
+__global__ void k_reach_mark(const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
+                             const int* __restrict__ parent, int ns, uint32_t* bitmap, int words) {
+  pdl_entry();
+  d_reach_mark(own_block(), nodes, m, node_super, parent, ns, bitmap, words);
+}
+
+struct reach_mark_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_reach_mark; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_reach_mark(vb, a...);
+  }
+};
+
 // One block per supernode: count its contacts, prefix the per-word counts and
 // list the contacts in ascending order.
-__global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
+__device__ __forceinline__ void d_reach_rows(const VB& vb, const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
                              int* qidx) {
-  pdl_entry();
   extern __shared__ int sh[];
-  int s = blockIdx.x;
+  int s = vb.bx;
   int w = threadIdx.x;
   uint32_t bits = (w < words) ? bitmap[(size_t)s * words + w] : 0u;
   int c = __popc(bits);
@@ -125,13 +139,28 @@ __global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int
   }
 }
 
+__global__ void k_reach_rows(const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
+                             int* qidx) {
+  pdl_entry();
+  d_reach_rows(own_block(), bitmap, words, m, wprefix, qcount, qidx);
+}
+
+struct reach_rows_body {
+  static constexpr int threads = 1024, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_reach_rows; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_reach_rows(vb, a...);
+  }
+};
+
 // Position of each of a supernode's contacts in its parent's contact list.
-__global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
+__device__ __forceinline__ void d_reach_parentpos(const VB& vb, const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
                                   int m, const int* __restrict__ parent, const int* __restrict__ qcount,
                                   const int* __restrict__ qidx, int* qpos) {
-  pdl_entry();
-  int s = blockIdx.y;
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = vb.by;
+  int j = vb.bx * blockDim.x + threadIdx.x;
   if (j >= qcount[s]) return;
   int p = parent[s];
   int a = qidx[(size_t)s * m + j];
@@ -143,12 +172,28 @@ __global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int
   qpos[(size_t)s * m + j] = pos;
 }
 
+__global__ void k_reach_parentpos(const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
+                                  int m, const int* __restrict__ parent, const int* __restrict__ qcount,
+                                  const int* __restrict__ qidx, int* qpos) {
+  pdl_entry();
+  d_reach_parentpos(own_block(), bitmap, wprefix, words, m, parent, qcount, qidx, qpos);
+}
+
+struct reach_parentpos_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_reach_parentpos; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_reach_parentpos(vb, a...);
+  }
+};
+
 // For every supernode c: the local position in c's contact list of each
 // contact of its parent's list (-1 when the contact does not reach c).
-__global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __restrict__ qcount,
+__device__ __forceinline__ void d_reach_inv(const VB& vb, int m, const int* __restrict__ parent, const int* __restrict__ qcount,
                             const int* __restrict__ qpos, int* qinv) {
-  pdl_entry();
-  const int c = blockIdx.x;
+  const int c = vb.bx;
   const int p = parent[c];
   if (p < 0) return;
   const int np = qcount[p], nc = qcount[c];
@@ -157,6 +202,22 @@ __global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __
   __syncthreads();
   for (int j = threadIdx.x; j < nc; j += blockDim.x) inv[qpos[(size_t)c * m + j]] = j;
 }
+
+__global__ void k_reach_inv(int m, const int* __restrict__ parent, const int* __restrict__ qcount,
+                            const int* __restrict__ qpos, int* qinv) {
+  pdl_entry();
+  d_reach_inv(own_block(), m, parent, qcount, qpos, qinv);
+}
+
+struct reach_inv_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_reach_inv; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_reach_inv(vb, a...);
+  }
+};
 
 // ------------------------------------------------------------------ a2 forward solve
 // The front of supernode s has w + r rows (its DOF columns, then R_s) and
@@ -242,12 +303,10 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
 // tensor-core contraction, with fewer tiles than target (one per SM) split
 // their units over K into about target / tiles parts (plan counters area,
 // after the 2 + nlev counters: nlev level factors, then the contraction's).
-__global__ void __launch_bounds__(1024)
-    k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+__device__ __forceinline__ void d_plan(const VB& vb, int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
            const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
            int tc_gemm, const unsigned char* __restrict__ tc_super, const int* __restrict__ level_first, int nlev,
            int target, int* plan) {
-  pdl_entry();
   __shared__ int wsum[PLAN_LISTS][32];
   __shared__ int tiles[PLAN_MAX_LEV + 1];   // unsplit tensor-core tiles per level; [PLAN_MAX_LEV]: contraction
   __shared__ int split[PLAN_MAX_LEV + 1];
@@ -330,6 +389,25 @@ __global__ void __launch_bounds__(1024)
   for (int i = tid; i < 2 + nlev; i += blockDim.x) plan[PLAN_LISTS * (ns + 1) + i] = 0;
 }
 
+__global__ void __launch_bounds__(1024)
+    k_plan(int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+           const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
+           int tc_gemm, const unsigned char* __restrict__ tc_super, const int* __restrict__ level_first, int nlev,
+           int target, int* plan) {
+  pdl_entry();
+  d_plan(own_block(), ns, level_list, super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, level_first, nlev, target, plan);
+}
+
+struct plan_body {
+  static constexpr int threads = 1024, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_plan; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_plan(vb, a...);
+  }
+};
+
 // Entry (row, column 3*kl + d) of supernode s's front: its H^T entry (rows < w)
 // plus the children's update entries listed for that row (extend-add as a
 // gather, children in ascending order; ctr_row holds each child row's index
@@ -368,16 +446,14 @@ __device__ __forceinline__ T assemble_entry(int s, int row, int kl, int d, int c
 // row (extend-add as a gather, children in ascending order).  Rows < w go to
 // Ftop, rows >= w to the front's update rows.
 template <class T>
-__global__ void __launch_bounds__(AR * TCOLS)
-    k_assemble(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_assemble(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
                const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                const int64_t* __restrict__ fr_ptr, const int* __restrict__ ctr_ptr,
                const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
                const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
                const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
-  pdl_entry();
   const int u1 = plan[pb];
-  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {
+  for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {
     const int pos = find_pos(plan, pa, pb, u);
     const int s = level_list[pos];
     const int nq = qcount[s];
@@ -403,6 +479,29 @@ __global__ void __launch_bounds__(AR * TCOLS)
     }
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(AR * TCOLS)
+    k_assemble(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+               const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+               const int64_t* __restrict__ fr_ptr, const int* __restrict__ ctr_ptr,
+               const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
+               const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
+               const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
+  pdl_entry();
+  d_assemble<T>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, fr_ptr, ctr_ptr, ctr_child, ctr_row, nodes, bary, qcount, qidx, qinv, m, X, Ftop, ldx);
+}
+
+template <class T>
+struct assemble_body {
+  static constexpr int threads = AR * TCOLS, minb = 1;
+  static constexpr bool stride = true;
+  static auto kernel() { return &k_assemble<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_assemble<T>(vb, a...);
+  }
+};
 
 // Block (supernode, 64-row tile of the w + r front rows, 32-contact tile):
 // out = G_s[rows, :] F_top; top rows store X_s = out, bottom rows U_s -= out.
@@ -499,18 +598,16 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
 }
 
 template <class T>
-__global__ void __launch_bounds__(256)
-    k_front_gemm(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_front_gemm(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
                  const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                  const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
                  const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
-  pdl_entry();
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sG = (T*)smraw;                 // 2 x KB x GLD
   T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
   __shared__ int pos_sh;
   const int u1 = plan[pb];
-  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {   // block-uniform
+  for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {   // block-uniform
     const int pos = block_find_pos(plan, pa, pb, u, &pos_sh);
     const int s = level_list[pos];
     const int nq = qcount[s];
@@ -520,6 +617,27 @@ __global__ void __launch_bounds__(256)
     front_gemm_tile<T>(s, rt, t, nq, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, X, Ftop, ldx, sG, sF);
   }
 }
+
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_front_gemm(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+                 const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
+                 const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
+  pdl_entry();
+  d_front_gemm<T>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, qcount, X, Ftop, ldx);
+}
+
+template <class T>
+struct front_gemm_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = true;
+  static auto kernel() { return &k_front_gemm<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_front_gemm<T>(vb, a...);
+  }
+};
 
 template <class T>
 static size_t gemm_smem_bytes() {
@@ -535,11 +653,10 @@ static size_t gemm_smem_bytes() {
 // FP32 except within 2^-48 (relative) of a rounding midpoint, where the FP64
 // route rounds twice as well.  The FP32 units do it at their full rate.
 template <class T>
-__global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+__device__ __forceinline__ void d_scale(const VB& vb, int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                         const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                         const double* __restrict__ dinvsqrt, T* X, int64_t ldx) {
-  pdl_entry();
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int row = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const int s = dof_super[row];
@@ -554,6 +671,25 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
   }
 }
 
+template <class T>
+__global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+                        const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                        const double* __restrict__ dinvsqrt, T* X, int64_t ldx) {
+  pdl_entry();
+  d_scale<T>(own_block(), n, dof_super, super_ptr, fr_ptr, qcount, dinvsqrt, X, ldx);
+}
+
+template <class T>
+struct scale_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_scale<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_scale<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ a4 contraction
 // Work unit (supernode s, tile pair I <= J of its local columns), for the
 // fronts narrower than the tensor-core threshold (all fronts in SIMT mode):
@@ -562,12 +698,10 @@ __global__ void k_scale(int n, const int* __restrict__ dof_super, const int* __r
 // it.  Blocks take units from a counter, largest supernodes (the end of
 // level_list) first.
 template <class T>
-__global__ void __launch_bounds__(256)
-    k_contract(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_contract(const VB& vb, const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
                const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
                const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
                const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
-  pdl_entry();
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
   __shared__ int unit_sh, pos_sh;
@@ -637,16 +771,36 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_contract(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+               const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
+               const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
+  pdl_entry();
+  d_contract<T>(own_block(), plan, counter, ns, level_list, super_ptr, fr_ptr, qcount, qidx, m, X, ldx, WH, ldw);
+}
+
+template <class T>
+struct contract_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = true;
+  static auto kernel() { return &k_contract<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_contract<T>(vb, a...);
+  }
+};
+
 // Mirrors the upper triangle of the nr x nr matrix A into its lower one, by
 // 32 x 32 tiles (block (32, 8)): a tile at or below the diagonal reads its
 // mirror tile's rows, transposes them in shared memory and writes its own
 // rows, both coalesced.  With A16, also writes the BF16 copy of every entry
 // (tiles above the diagonal copy their own entries).
 template <class T>
-__global__ void k_symmetrize(int nr, T* A, __nv_bfloat16* A16) {
-  pdl_entry();
+__device__ __forceinline__ void d_symmetrize(const VB& vb, int nr, T* A, __nv_bfloat16* A16) {
   __shared__ T tile[32][33];
-  const int ti = blockIdx.y, tj = blockIdx.x;   // tile row, tile column
+  const int ti = vb.by, tj = vb.bx;   // tile row, tile column
   const int tx = threadIdx.x, ty = threadIdx.y;
   if (tj > ti) {
     if (!A16) return;
@@ -674,6 +828,23 @@ __global__ void k_symmetrize(int nr, T* A, __nv_bfloat16* A16) {
     }
   }
 }
+
+template <class T>
+__global__ void k_symmetrize(int nr, T* A, __nv_bfloat16* A16) {
+  pdl_entry();
+  d_symmetrize<T>(own_block(), nr, A, A16);
+}
+
+template <class T>
+struct symmetrize_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_symmetrize<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_symmetrize<T>(vb, a...);
+  }
+};
 
 // ------------------------------------------------------------------ a6 W = C W_H C^T
 // Also raises wblk[a][B] to the largest |W[3a, j]| over the columns j of PGS
@@ -713,22 +884,21 @@ __device__ __forceinline__ T w_operand(T x) {
 }
 
 template <class T, int WM>
-__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH,
+__device__ __forceinline__ void d_update_W(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ WH,
                            const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wblk, int bc,
                            const int* __restrict__ stop) {
-  pdl_entry();
   if (newton_stopped(stop)) return;
-  if (blockIdx.x < blockIdx.y) return;   // the block pairs of the upper triangle only (uniform)
+  if (vb.bx < vb.by) return;   // the block pairs of the upper triangle only (uniform)
   __shared__ bits_t<T> mxa[16], mxb[16];
   __shared__ T sC[2][16][9];             // directions of the block's a and b contacts
   __shared__ T tile[48][49];             // W[3b + j, 3a + i] of the block, for coalesced mirror rows
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
-  const int b = blockIdx.x * 16 + tx, a = blockIdx.y * 16 + ty;
+  const int b = vb.bx * 16 + tx, a = vb.by * 16 + ty;
   if (ty == 0) mxb[tx] = 0;
   if (tx == 0) mxa[ty] = 0;
   for (int e = tid; e < 2 * 16 * 9; e += 256) {
     const int w = e / 144, k = (e % 144) / 9, q = e % 9;
-    const int c = (w == 0 ? blockIdx.y : blockIdx.x) * 16 + k;
+    const int c = (w == 0 ? vb.by : vb.bx) * 16 + k;
     sC[w][k][q] = c < m ? w_operand<T, WM>(C[9 * c + q]) : T(0);
   }
   __syncthreads();
@@ -772,26 +942,44 @@ __global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__
   // the mirror W[3b + j, 3a + i] (a < b), 48 consecutive columns per row
   for (int e = tid; e < 48 * 48; e += 256) {
     const int rr = e / 48, cc = e % 48;
-    const int bg = blockIdx.x * 16 + rr / 3, ag = blockIdx.y * 16 + cc / 3;
+    const int bg = vb.bx * 16 + rr / 3, ag = vb.by * 16 + cc / 3;
     if (bg < m && ag < bg) W[(3 * bg + rr % 3) * ldw + 3 * ag + cc % 3] = tile[rr][cc];
   }
   // the tile's 16 columns lie in one PGS block of bc contacts (16 divides bc):
   // per contact, the largest |W[3a, j]| over that block's other columns
   const int nb = (m + bc - 1) / bc;
-  const int ga = blockIdx.y * 16 + tx, gb = blockIdx.x * 16 + tx;
-  const int Ba = blockIdx.y * 16 / bc, Bb = blockIdx.x * 16 / bc;
+  const int ga = vb.by * 16 + tx, gb = vb.bx * 16 + tx;
+  const int Ba = vb.by * 16 / bc, Bb = vb.bx * 16 / bc;
   if (ty == 0 && ga < m && mxa[tx] != 0)
     atomicMax(reinterpret_cast<bits_t<T>*>(wblk) + (int64_t)ga * nb + Bb, mxa[tx]);
   if (ty == 1 && gb < m && mxb[tx] != 0)
     atomicMax(reinterpret_cast<bits_t<T>*>(wblk) + (int64_t)gb * nb + Ba, mxb[tx]);
 }
 
+template <class T, int WM>
+__global__ void k_update_W(int m, const T* __restrict__ C, const T* __restrict__ WH,
+                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wblk, int bc,
+                           const int* __restrict__ stop) {
+  pdl_entry();
+  d_update_W<T, WM>(own_block(), m, C, WH, WH16, W, ldw, wblk, bc, stop);
+}
+
+template <class T, int WM>
+struct update_W_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_update_W<T, WM>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_update_W<T, WM>(vb, a...);
+  }
+};
+
 // The per-block coupling bounds (wblk) of a W given directly: one warp per
 // contact's normal row
 template <class T>
-__global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wblk, int bc) {
-  pdl_entry();
-  const int a = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+__device__ __forceinline__ void d_wcoup(const VB& vb, int m, const T* __restrict__ W, int64_t ldw, T* wblk, int bc) {
+  const int a = (int)((vb.bx * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   if (a >= m) return;
   const T* row = W + (int64_t)(3 * a) * ldw;
   const int nb = (m + bc - 1) / bc;
@@ -805,6 +993,23 @@ __global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wblk, in
     if (lane == 0) wblk[(int64_t)a * nb + B] = mx;
   }
 }
+
+template <class T>
+__global__ void k_wcoup(int m, const T* __restrict__ W, int64_t ldw, T* wblk, int bc) {
+  pdl_entry();
+  d_wcoup<T>(own_block(), m, W, ldw, wblk, bc);
+}
+
+template <class T>
+struct wcoup_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_wcoup<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_wcoup<T>(vb, a...);
+  }
+};
 
 // ------------------------------------------------------------------ a7 PGS
 // One CTA of PGS_THREADS threads.  The residual r = delta + W lambda~ of every
@@ -1185,11 +1390,9 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
 
 
 template <class T, int BC>
-__global__ void __launch_bounds__(PGS_THREADS, 1)
-    k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
+__device__ __forceinline__ void d_pgs(const VB& vb, int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
           const T* __restrict__ mu, const T* __restrict__ wblk, T* pgsb, T* lam_g, int warm, PgsDevStats* st,
           const int* __restrict__ stop) {
-  pdl_entry();
   if (newton_stopped(stop)) return;   // uniform, before any shared memory or barrier
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
@@ -1801,6 +2004,26 @@ __global__ void __launch_bounds__(PGS_THREADS, 1)
 }
 
 template <class T, int BC>
+__global__ void __launch_bounds__(PGS_THREADS, 1)
+    k_pgs(int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
+          const T* __restrict__ mu, const T* __restrict__ wblk, T* pgsb, T* lam_g, int warm, PgsDevStats* st,
+          const int* __restrict__ stop) {
+  pdl_entry();
+  d_pgs<T, BC>(own_block(), m, sweeps, tol, W, ldw, delta, mu, wblk, pgsb, lam_g, warm, st, stop);
+}
+
+template <class T, int BC>
+struct pgs_body {
+  static constexpr int threads = PGS_THREADS, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_pgs<T, BC>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_pgs<T, BC>(vb, a...);
+  }
+};
+
+template <class T, int BC>
 static size_t pgs_smem_bytes(int m) {
   const size_t BR = 3 * BC;
   return (4 * BR * BR + 6 * (size_t)m + 2 * BR + 2 * PGS_MAX_DEFER * BR) * sizeof(T) +
@@ -1809,10 +2032,9 @@ static size_t pgs_smem_bytes(int m) {
 
 // FP64 residuals of the final iterate: one warp per contact.
 template <class T>
-__global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
+__device__ __forceinline__ void d_pgs_residual(const VB& vb, int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
                                const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
-  pdl_entry();
-  const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int a = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= m) return;
   double d[3];
@@ -1850,6 +2072,24 @@ __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, cons
   }
 }
 
+template <class T>
+__global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
+                               const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
+  pdl_entry();
+  d_pgs_residual<T>(own_block(), m, W, ldw, delta, mu, lam, rel, st);
+}
+
+template <class T>
+struct pgs_residual_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_pgs_residual<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_pgs_residual<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ Newton stop
 // After the linearisation for the next Newton iteration: the FP64
 // complementarity residual of a zero increment at the new gaps,
@@ -1857,8 +2097,7 @@ __global__ void k_pgs_residual(int m, const T* __restrict__ W, int64_t ldw, cons
 // nothing to correct, the loop ends (nw[0] = 1); else one more iteration runs
 // (nw[1] counts the iterations after the first).  One block.
 template <class T>
-__global__ void k_newton_check(int m, const T* __restrict__ delta, double tol, int* nw) {
-  pdl_entry();
+__device__ __forceinline__ void d_newton_check(const VB& vb, int m, const T* __restrict__ delta, double tol, int* nw) {
   if (nw[0]) return;
   __shared__ double red[32];
   double v = 0.0;
@@ -1877,13 +2116,29 @@ __global__ void k_newton_check(int m, const T* __restrict__ delta, double tol, i
   }
 }
 
+template <class T>
+__global__ void k_newton_check(int m, const T* __restrict__ delta, double tol, int* nw) {
+  pdl_entry();
+  d_newton_check<T>(own_block(), m, delta, tol, nw);
+}
+
+template <class T>
+struct newton_check_body {
+  static constexpr int threads = 1024, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_newton_check<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_newton_check<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ a8 proximity update
 template <class T>
-__global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u,
+__device__ __forceinline__ void d_prox_u(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u,
                          const int* __restrict__ stop) {
-  pdl_entry();
   if (newton_stopped(stop)) return;
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = vb.bx * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const T l0 = lam[3 * a], l1 = lam[3 * a + 1], l2 = lam[3 * a + 2];
 #pragma unroll
@@ -1894,13 +2149,30 @@ __global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ l
   }
 }
 
+template <class T>
+__global__ void k_prox_u(int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u,
+                         const int* __restrict__ stop) {
+  pdl_entry();
+  d_prox_u<T>(own_block(), m, C, lam, uk, u, stop);
+}
+
+template <class T>
+struct prox_u_body {
+  static constexpr int threads = 128, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_prox_u<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_prox_u<T>(vb, a...);
+  }
+};
+
 // u_k = C_k^T lambda~_k and p += W_H u_k in one launch: every CTA forms u_k in
 // shared memory (12 flops per contact), CTA 0 also adds it to u (FP64), and
 // each warp takes one row of W_H.
 template <class T>
-__global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
+__device__ __forceinline__ void d_prox(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
                        double* u, double* p, double* dp, const int* __restrict__ stop) {
-  pdl_entry();
   if (newton_stopped(stop)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* uk = (T*)smraw;   // 3m
@@ -1910,14 +2182,14 @@ __global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam
     for (int j = 0; j < 3; ++j) {
       const T v = C[9 * a + j] * l0 + C[9 * a + 3 + j] * l1 + C[9 * a + 6 + j] * l2;
       uk[3 * a + j] = v;
-      if (blockIdx.x == 0) u[3 * a + j] += (double)v;
+      if (vb.bx == 0) u[3 * a + j] += (double)v;
     }
   }
   __syncthreads();
   bool nz = false;
   for (int a = threadIdx.x; a < 3 * m; a += blockDim.x) nz |= uk[a] != T(0);
   nz = __syncthreads_or(nz);
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int i = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= 3 * m) return;
   if (!nz) {   // C^T lambda~ = 0: p stays, dp = 0 (no row of W_H is read)
@@ -1935,11 +2207,28 @@ __global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam
 }
 
 template <class T>
-__global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp,
-                         const int* __restrict__ stop) {
+__global__ void k_prox(int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
+                       double* u, double* p, double* dp, const int* __restrict__ stop) {
   pdl_entry();
+  d_prox<T>(own_block(), m, C, lam, WH, u, p, dp, stop);
+}
+
+template <class T>
+struct prox_body {
+  static constexpr int threads = 512, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_prox<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_prox<T>(vb, a...);
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void d_prox_p(const VB& vb, int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp,
+                         const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
-  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int i = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= 3 * m) return;
   const T* Wr = WH + (int64_t)i * 3 * m;
@@ -1952,16 +2241,33 @@ __global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ 
   }
 }
 
+template <class T>
+__global__ void k_prox_p(int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp,
+                         const int* __restrict__ stop) {
+  pdl_entry();
+  d_prox_p<T>(own_block(), m, WH, uk, p, dp, stop);
+}
+
+template <class T>
+struct prox_p_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_prox_p<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_prox_p<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ a9 corrective motion
 // y = D^-1 X u = D^-1/2 (Y u), one warp per DOF row (Y holds the scaled front
 // rows, restricted to the contacts reaching them); u in the working precision
 template <class T>
-__global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+__device__ __forceinline__ void d_xu(const VB& vb, int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
                      const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                      const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
                      const T* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
-  pdl_entry();
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int row = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const int s = dof_super[row];
@@ -1977,24 +2283,58 @@ __global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __rest
   if (lane == 0) y[row] = (T)(dinvsqrt[row] * (double)acc);
 }
 
+template <class T>
+__global__ void k_xu(int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
+                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                     const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
+                     const T* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
+  pdl_entry();
+  d_xu<T>(own_block(), n, dof_super, super_ptr, fr_ptr, qcount, qidx, m, X, ldx, u, dinvsqrt, y);
+}
+
+template <class T>
+struct xu_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_xu<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_xu<T>(vb, a...);
+  }
+};
+
 // u in the working precision for k_xu
+template <class T>
+__device__ __forceinline__ void d_u_round(const VB& vb, int n3, const double* __restrict__ u, T* ut) {
+  const int i = vb.bx * blockDim.x + threadIdx.x;
+  if (i < n3) ut[i] = (T)u[i];
+}
+
 template <class T>
 __global__ void k_u_round(int n3, const double* __restrict__ u, T* ut) {
   pdl_entry();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n3) ut[i] = (T)u[i];
+  d_u_round<T>(own_block(), n3, u, ut);
 }
+
+template <class T>
+struct u_round_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_u_round<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_u_round<T>(vb, a...);
+  }
+};
 
 // Backward solve L^T dq = y for the supernodes of one level (top-down):
 // dq_s = G_s^T [y_s ; -dq_R], one warp per DOF column of the supernode.
 template <class T>
-__global__ void __launch_bounds__(256)
-    k_bsolve(const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
+__device__ __forceinline__ void d_bsolve(const VB& vb, const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
              const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
              const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const T* __restrict__ y, T* dq) {
-  pdl_entry();
-  const int s = level_list[lvl_first + blockIdx.x / nchunk];
-  const int k = (blockIdx.x % nchunk) * 8 + (threadIdx.x >> 5);
+  const int s = level_list[lvl_first + vb.bx / nchunk];
+  const int k = (vb.bx % nchunk) * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
   if (k >= w) return;
@@ -2008,6 +2348,26 @@ __global__ void __launch_bounds__(256)
   if (lane == 0) dq[c0 + k] = acc;
 }
 
+template <class T>
+__global__ void __launch_bounds__(256)
+    k_bsolve(const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
+             const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
+             const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const T* __restrict__ y, T* dq) {
+  pdl_entry();
+  d_bsolve<T>(own_block(), level_list, lvl_first, nchunk, super_ptr, rowpat_ptr, rowpat, val_ptr, G, y, dq);
+}
+
+template <class T>
+struct bsolve_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_bsolve<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_bsolve<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ linearisation
 // C rows n, t1, t2 and the gaps from the current proximity positions.  The
 // normal, the choice of the tangent axis and the normal gap are formed in
@@ -2015,13 +2375,12 @@ __global__ void __launch_bounds__(256)
 // the tangent frame and the tangential gaps are formed in FP32, the precision
 // C and delta are stored in (FP64 arithmetic is a slow path on this part).
 template <class T>
-__global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
+__device__ __forceinline__ void d_linearize(const VB& vb, int m, int kind, const double* __restrict__ normals_k,
                             const double* __restrict__ anchors, const double* __restrict__ spheres,
                             const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta,
                             const int* __restrict__ stop) {
-  pdl_entry();
   if (newton_stopped(stop)) return;
-  int a = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = vb.bx * blockDim.x + threadIdx.x;
   if (a >= m) return;
   const double px = p[3 * a], py = p[3 * a + 1], pz = p[3 * a + 2];
   const double rx = px - anchors[3 * a], ry = py - anchors[3 * a + 1], rz = pz - anchors[3 * a + 2];
@@ -2079,6 +2438,26 @@ __global__ void k_linearize(int m, int kind, const double* __restrict__ normals_
   delta[3 * a + 2] = t20 * qx + t21 * qy + t22 * qz;
 }
 
+template <class T>
+__global__ void k_linearize(int m, int kind, const double* __restrict__ normals_k,
+                            const double* __restrict__ anchors, const double* __restrict__ spheres,
+                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta,
+                            const int* __restrict__ stop) {
+  pdl_entry();
+  d_linearize<T>(own_block(), m, kind, normals_k, anchors, spheres, sphere_of, p, C, delta, stop);
+}
+
+template <class T>
+struct linearize_body {
+  static constexpr int threads = 128, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_linearize<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_linearize<T>(vb, a...);
+  }
+};
+
 // ------------------------------------------------------------------ launchers
 template <class T>
 static int build_WH_T(Scene* s) {
@@ -2087,19 +2466,19 @@ static int build_WH_T(Scene* s) {
   const int64_t ldx = s->ldx;
   T* X = (T*)s->X.p;
   if (m == 0) return ICR_OK;
-  cudaError_t e = cudaMemsetAsync(s->bitmap.p, 0, (size_t)ns * words * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset bitmap");
-  PDL("k_reach_mark", k_reach_mark, (4 * m + 255) / 256, 256, 0, st,
+  RET(dzero(s, s->bitmap.p, (size_t)ns * words * sizeof(uint32_t), "memset bitmap"));
+  cudaError_t e = cudaSuccess;
+  PDL("k_reach_mark", reach_mark_body, (4 * m + 255) / 256, 256, 0, st,
       (const int*)s->nodes.p, m, (const int*)s->node_super.p,
                                                      (const int*)s->parent.p, ns, (uint32_t*)s->bitmap.p, words);
   const int bt = ((words + 31) / 32) * 32;
-  PDL("k_reach_rows", k_reach_rows, ns, bt, bt * sizeof(int), st,
+  PDL("k_reach_rows", reach_rows_body, ns, bt, bt * sizeof(int), st,
       (const uint32_t*)s->bitmap.p, words, m, (int*)s->wprefix.p,
                                                   (int*)s->qcount.p, (int*)s->qidx.p);
-  PDL("k_reach_parentpos", k_reach_parentpos, dim3((m + 255) / 256, ns), 256, 0, st,
+  PDL("k_reach_parentpos", reach_parentpos_body, dim3((m + 255) / 256, ns), 256, 0, st,
       (const uint32_t*)s->bitmap.p, (const int*)s->wprefix.p, words, m, (const int*)s->parent.p,
       (const int*)s->qcount.p, (const int*)s->qidx.p, (int*)s->qpos.p);
-  PDL("k_reach_inv", k_reach_inv, ns, 256, 0, st,
+  PDL("k_reach_inv", reach_inv_body, ns, 256, 0, st,
       m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
                                   (int*)s->qinv.p);
   static SmemLimit gemm_lim;
@@ -2126,7 +2505,7 @@ static int build_WH_T(Scene* s) {
   const int tc_gemm = mode != ICR_CONTRACT_SIMT ? 1 : 0;
   int* plan = (int*)s->plan.p;
   const int nlev = (int)s->levels.size();
-  PDL("k_plan", k_plan, 1, 1024, 0, st,
+  PDL("k_plan", plan_body, 1, 1024, 0, st,
       ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
                              (const int64_t*)s->rowpat_ptr.p, (const int*)s->qcount.p, simt_max, tc_min, tc_gemm,
                              (const unsigned char*)s->tc_super.p, (const int*)s->level_first.p, nlev,
@@ -2141,13 +2520,13 @@ static int build_WH_T(Scene* s) {
       if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
     }
     const int64_t ub_a = (int64_t)lv.count * ((lv.wmax + lv.rmax + ASM_ROWS - 1) / ASM_ROWS) * ntiles;
-    PDL("k_assemble", k_assemble<T>, (unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st,
+    PDL("k_assemble", assemble_body<T>, (unsigned)std::min<int64_t>(ub_a, 4 * nsm), dim3(TCOLS, AR), 0, st,
         plan + PLAN_ASM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
         (const int*)s->ctr_child.p, (const int*)s->ctr_row.p, (const int*)s->nodes.p, (const T*)s->bary.p,
         (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qinv.p, m, X, (T*)s->Ftop.p, ldx);
     const int64_t ub_g = (int64_t)lv.count * ((lv.wmax + lv.rmax + GR - 1) / GR) * ntiles;
-    PDL("k_front_gemm", k_front_gemm<T>, (unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st,
+    PDL("k_front_gemm", front_gemm_body<T>, (unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st,
         plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
         (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
@@ -2160,17 +2539,16 @@ static int build_WH_T(Scene* s) {
     e = cudaEventRecord(s->level_events[nlev], st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord(level)");
   }
-  PDL("k_scale", k_scale<T>, (s->n + 7) / 8, 256, 0, st,
+  PDL("k_scale", scale_body<T>, (s->n + 7) / 8, 256, 0, st,
       s->n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                              (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p,
                                              (const double*)s->dinvsqrt.p, X, ldx);
   const int64_t nr = 3 * (int64_t)m;
-  e = cudaMemsetAsync(s->WH.p, 0, (size_t)nr * nr * sizeof(T), st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset WH");
+  RET(dzero(s, s->WH.p, (size_t)nr * nr * sizeof(T), "memset WH"));
   {
     const int64_t ntc = (nr + CT - 1) / CT;
     const int64_t ub = (int64_t)ns * (ntc * (ntc + 1) / 2);
-    PDL("k_contract", k_contract<T>, (unsigned)std::min<int64_t>(ub, 4 * nsm), 256, 0, st,
+    PDL("k_contract", contract_body<T>, (unsigned)std::min<int64_t>(ub, 4 * nsm), 256, 0, st,
         plan + PLAN_SIMT * (ns + 1), plan + PLAN_LISTS * (ns + 1), ns, (const int*)s->level_list.p,
         (const int*)s->super_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, m,
         X, ldx, (T*)s->WH.p, nr);
@@ -2182,11 +2560,19 @@ static int build_WH_T(Scene* s) {
   // FP32 scenes with the BF16 W update also get W_H's BF16 copy
   __nv_bfloat16* wh16 = (sizeof(T) == 4 && s->params.w_update == ICR_W_BF16) ? (__nv_bfloat16*)s->WH16.p : nullptr;
   const unsigned nt32 = (unsigned)((nr + 31) / 32);
-  PDL("k_symmetrize", k_symmetrize<T>, dim3(nt32, nt32), dim3(32, 8), 0, st, (int)nr, (T*)s->WH.p, wh16);
+  PDL("k_symmetrize", symmetrize_body<T>, dim3(nt32, nt32), dim3(32, 8), 0, st, (int)nr, (T*)s->WH.p, wh16);
   return ICR_OK;
 }
 
 int launch_build_WH(Scene* s) { return s->prec == ICR_FP64 ? build_WH_T<double>(s) : build_WH_T<float>(s); }
+
+template <class T, int WM>
+static int update_W_mode(Scene* s, dim3 grid, int bc) {
+  using K = update_W_body<T, WM>;
+  PDL("k_update_W", K, grid, dim3(16, 16), 0, s->ctx->stream, s->m, (const T*)s->C.p, (const T*)s->WH.p,
+      (const __nv_bfloat16*)s->WH16.p, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
+  return ICR_OK;
+}
 
 template <class T>
 static int update_W_T(Scene* s) {
@@ -2195,20 +2581,11 @@ static int update_W_T(Scene* s) {
   dim3 grid((m + 15) / 16, (m + 15) / 16);
   const int bc = sizeof(T) == 8 ? 16 : 32;   // the PGS block size of the scene's precision
   const size_t nb = (size_t)(m + bc - 1) / bc;
-  cudaError_t e = cudaMemsetAsync(s->wblk.p, 0, (size_t)m * nb * sizeof(T), s->ctx->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "memset wblk");
+  RET(dzero(s, s->wblk.p, (size_t)m * nb * sizeof(T), "memset wblk"));
   const int wm = sizeof(T) == 4 ? s->params.w_update : ICR_W_FP32;
-  const __nv_bfloat16* wh16 = (const __nv_bfloat16*)s->WH16.p;
-  if (wm == ICR_W_TF32)
-    PDL("k_update_W", k_update_W<T, ICR_W_TF32>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
-  else if (wm == ICR_W_BF16)
-    PDL("k_update_W", k_update_W<T, ICR_W_BF16>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
-  else
-    PDL("k_update_W", k_update_W<T, ICR_W_FP32>, grid, dim3(16, 16), 0, s->ctx->stream,
-        m, (const T*)s->C.p, (const T*)s->WH.p, wh16, (T*)s->W.p, s->ldw, (T*)s->wblk.p, bc, s->step_stop);
-  return ICR_OK;
+  if (wm == ICR_W_TF32) return update_W_mode<T, ICR_W_TF32>(s, grid, bc);
+  if (wm == ICR_W_BF16) return update_W_mode<T, ICR_W_BF16>(s, grid, bc);
+  return update_W_mode<T, ICR_W_FP32>(s, grid, bc);
 }
 
 int launch_update_W(Scene* s) { return s->prec == ICR_FP64 ? update_W_T<double>(s) : update_W_T<float>(s); }
@@ -2217,7 +2594,7 @@ template <class T>
 static int wcoup_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
-  PDL("k_wcoup", k_wcoup<T>, (unsigned)((m + 7) / 8), 256, 0, s->ctx->stream,
+  PDL("k_wcoup", wcoup_body<T>, (unsigned)((m + 7) / 8), 256, 0, s->ctx->stream,
       m, (const T*)s->W.p, s->ldw, (T*)s->wblk.p, sizeof(T) == 8 ? 16 : 32);
   return ICR_OK;
 }
@@ -2229,8 +2606,8 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   cudaStream_t st = s->ctx->stream;
   const int m = s->m;
   PgsDevStats* ds = (PgsDevStats*)s->stats.p;
-  cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(PgsDevStats), st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset stats");
+  RET(dzero(s, ds, sizeof(PgsDevStats), "memset stats"));
+  cudaError_t e = cudaSuccess;
   if (m == 0) return ICR_OK;
   const size_t smem = pgs_smem_bytes<T, BC>(m);
   // the opt-in limit covers static plus dynamic shared memory
@@ -2248,13 +2625,14 @@ static int pgs_T(Scene* s, int warm, int want_res) {
   }
   e = ensure_smem(k_pgs<T, BC>, pgs_lim, s->ctx->device, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_pgs)");
-  PDL("k_pgs", k_pgs<T, BC>, 1, PGS_THREADS, smem, st,
+  using KP = pgs_body<T, BC>;
+  PDL("k_pgs", KP, 1, PGS_THREADS, smem, st,
       m, s->params.n_sweeps, s->params.tol, (const T*)s->W.p, s->ldw,
       (const T*)s->delta.p, (const T*)s->mu.p, (const T*)s->wblk.p, (T*)s->pgsb.p, (T*)s->lam.p, warm, ds,
       s->step_stop);
   if (want_res) {
     const double rel = sizeof(T) == 8 ? 1e-9 : 1e-5;
-    PDL("k_pgs_residual", k_pgs_residual<T>, (m + 7) / 8, 256, 0, st,
+    PDL("k_pgs_residual", pgs_residual_body<T>, (m + 7) / 8, 256, 0, st,
         m, (const T*)s->W.p, s->ldw, (const T*)s->delta.p, (const T*)s->mu.p,
                                                    (const T*)s->lam.p, rel, ds);
   }
@@ -2273,23 +2651,22 @@ static int prox_T(Scene* s) {
   double* u = (double*)s->u.p;
   const size_t smem = 3 * (size_t)m * sizeof(T);
   if (smem <= 48 * 1024) {   // u_k fits the default shared memory: one launch
-    PDL("k_prox", k_prox<T>, (3 * m + 15) / 16, 512, smem, st, m, (const T*)s->C.p, (const T*)s->lam.p,
+    PDL("k_prox", prox_body<T>, (3 * m + 15) / 16, 512, smem, st, m, (const T*)s->C.p, (const T*)s->lam.p,
         (const T*)s->WH.p, u, (double*)s->p.p, u + 3 * (size_t)m, s->step_stop);
     return ICR_OK;
   }
-  PDL("k_prox_u", k_prox_u<T>, (m + 127) / 128, 128, 0, st,
+  PDL("k_prox_u", prox_u_body<T>, (m + 127) / 128, 128, 0, st,
       m, (const T*)s->C.p, (const T*)s->lam.p, (T*)s->uk.p, u, s->step_stop);
-  PDL("k_prox_p", k_prox_p<T>, (3 * m + 7) / 8, 256, 0, st,
+  PDL("k_prox_p", prox_p_body<T>, (3 * m + 7) / 8, 256, 0, st,
       m, (const T*)s->WH.p, (const T*)s->uk.p, (double*)s->p.p, u + 3 * (size_t)m, s->step_stop);
   return ICR_OK;
 }
 
 // one thread per contact: its entries of every per-contact buffer
 template <class T>
-__global__ void k_reset_contacts(int mm, T* lam, T* lam0, T* mu, T* delta, T* C, double* p, double* p0, double* u,
+__device__ __forceinline__ void d_reset_contacts(const VB& vb, int mm, T* lam, T* lam0, T* mu, T* delta, T* C, double* p, double* p0, double* u,
                                  int* stats, int nstats, int* dev_err) {
-  pdl_entry();
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = vb.bx * blockDim.x + threadIdx.x;
   if (a < mm) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -2309,16 +2686,33 @@ __global__ void k_reset_contacts(int mm, T* lam, T* lam0, T* mu, T* delta, T* C,
   if (a == 0) *dev_err = 0;
 }
 
+template <class T>
+__global__ void k_reset_contacts(int mm, T* lam, T* lam0, T* mu, T* delta, T* C, double* p, double* p0, double* u,
+                                 int* stats, int nstats, int* dev_err) {
+  pdl_entry();
+  d_reset_contacts<T>(own_block(), mm, lam, lam0, mu, delta, C, p, p0, u, stats, nstats, dev_err);
+}
+
+template <class T>
+struct reset_contacts_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_reset_contacts<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_reset_contacts<T>(vb, a...);
+  }
+};
+
 // one thread per contact: the inputs of icr_set_step_inputs from the staging
 // buffer, and the contact state reset as in k_reset_contacts
 template <class T>
-__global__ void k_unpack_inputs(int m, int nsph, const unsigned char* __restrict__ stg, int64_t o_nodes,
+__device__ __forceinline__ void d_unpack_inputs(const VB& vb, int m, int nsph, const unsigned char* __restrict__ stg, int64_t o_nodes,
                                 int64_t o_of, int64_t o_bary, int64_t o_mu, int64_t o_p0, int64_t o_anch,
                                 int64_t o_sph, int* nodes, int* sphere_of, T* bary, T* mu, double* p, double* p0,
                                 double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C, double* u,
                                 int* stats, int nstats, int* dev_err) {
-  pdl_entry();
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = vb.bx * blockDim.x + threadIdx.x;
   if (a < m) {
     const int* sn = (const int*)(stg + o_nodes);
     const T* sb = (const T*)(stg + o_bary);
@@ -2351,11 +2745,32 @@ __global__ void k_unpack_inputs(int m, int nsph, const unsigned char* __restrict
 }
 
 template <class T>
+__global__ void k_unpack_inputs(int m, int nsph, const unsigned char* __restrict__ stg, int64_t o_nodes,
+                                int64_t o_of, int64_t o_bary, int64_t o_mu, int64_t o_p0, int64_t o_anch,
+                                int64_t o_sph, int* nodes, int* sphere_of, T* bary, T* mu, double* p, double* p0,
+                                double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C, double* u,
+                                int* stats, int nstats, int* dev_err) {
+  pdl_entry();
+  d_unpack_inputs<T>(own_block(), m, nsph, stg, o_nodes, o_of, o_bary, o_mu, o_p0, o_anch, o_sph, nodes, sphere_of, bary, mu, p, p0, anchors, spheres, lam, lam0, delta, C, u, stats, nstats, dev_err);
+}
+
+template <class T>
+struct unpack_inputs_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_unpack_inputs<T>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_unpack_inputs<T>(vb, a...);
+  }
+};
+
+template <class T>
 static int unpack_T(Scene* s, int nsph, const int64_t* o) {
   const int m = s->m;
   const int nstats = (int)(sizeof(PgsDevStats) / sizeof(int));
   const int n = std::max(std::max(m, 4 * nsph), nstats);
-  PDL("k_unpack_inputs", k_unpack_inputs<T>, (n + 255) / 256, 256, 0, s->ctx->stream, m, nsph,
+  PDL("k_unpack_inputs", unpack_inputs_body<T>, (n + 255) / 256, 256, 0, s->ctx->stream, m, nsph,
       (const unsigned char*)s->stage_dev.p, o[0], o[1], o[2], o[3], o[4], o[5], o[6], (int*)s->nodes.p,
       (int*)s->obst_of.p, (T*)s->bary.p, (T*)s->mu.p, (double*)s->p.p, (double*)s->p0.p,
       (double*)s->obst_anchors.p, (double*)s->obst_spheres.p, (T*)s->lam.p, (T*)s->lam0.p, (T*)s->delta.p,
@@ -2370,7 +2785,7 @@ int launch_unpack_inputs(Scene* s, int n_spheres, const int64_t* off) {
 template <class T>
 static int reset_T(Scene* s, int mm) {
   const int nstats = (int)(sizeof(PgsDevStats) / sizeof(int));
-  PDL("k_reset_contacts", k_reset_contacts<T>, (std::max(mm, nstats) + 255) / 256, 256, 0, s->ctx->stream, mm,
+  PDL("k_reset_contacts", reset_contacts_body<T>, (std::max(mm, nstats) + 255) / 256, 256, 0, s->ctx->stream, mm,
       (T*)s->lam.p, (T*)s->lam0.p, (T*)s->mu.p, (T*)s->delta.p, (T*)s->C.p, (double*)s->p.p, (double*)s->p0.p,
       (double*)s->u.p, (int*)s->stats.p, nstats, (int*)s->dev_err.p);
   return ICR_OK;
@@ -2387,16 +2802,14 @@ static int correct_T(Scene* s) {
   cudaStream_t st = s->ctx->stream;
   const int m = s->m, n = s->n;
   if (m == 0) {
-    cudaError_t e = cudaMemsetAsync(s->dq.p, 0, (size_t)n * sizeof(T), st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset dq");
-    return ICR_OK;
+    return dzero(s, s->dq.p, (size_t)n * sizeof(T), "memset dq");
   }
   const T* uw = (const T*)s->u.p;   // FP64: u as it is
   if (sizeof(T) == 4) {
-    PDL("k_u_round", k_u_round<T>, (3 * m + 255) / 256, 256, 0, st, 3 * m, (const double*)s->u.p, (T*)s->uk.p);
+    PDL("k_u_round", u_round_body<T>, (3 * m + 255) / 256, 256, 0, st, 3 * m, (const double*)s->u.p, (T*)s->uk.p);
     uw = (const T*)s->uk.p;
   }
-  PDL("k_xu", k_xu<T>, (n + 7) / 8, 256, 0, st,
+  PDL("k_xu", xu_body<T>, (n + 7) / 8, 256, 0, st,
       n, (const int*)s->dof_super.p, (const int*)s->super_ptr.p,
                                        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p,
                                        m, (const T*)s->X.p, s->ldx, uw, (const double*)s->dinvsqrt.p,
@@ -2404,7 +2817,7 @@ static int correct_T(Scene* s) {
   for (int l = (int)s->levels.size() - 1; l >= 0; --l) {
     const Level& lv = s->levels[l];
     const int nchunk = (lv.wmax + 7) / 8;
-    PDL("k_bsolve", k_bsolve<T>, lv.count * nchunk, 256, 0, st,
+    PDL("k_bsolve", bsolve_body<T>, lv.count * nchunk, 256, 0, st,
         (const int*)s->level_list.p, lv.first, nchunk,
                                                    (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
                                                    (const int*)s->rowpat.p, (const int64_t*)s->val_ptr.p,
@@ -2420,7 +2833,7 @@ static int linearize_T(Scene* s, int k) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
   const double* nk = s->obst_kind == 1 ? (const double*)s->obst_normals.p + (size_t)k * m * 3 : nullptr;
-  PDL("k_linearize", k_linearize<T>, (m + 127) / 128, 128, 0, s->ctx->stream,
+  PDL("k_linearize", linearize_body<T>, (m + 127) / 128, 128, 0, s->ctx->stream,
       m, s->obst_kind, nk, (const double*)s->obst_anchors.p, (const double*)s->obst_spheres.p,
       (const int*)s->obst_of.p, (const double*)s->p.p, (T*)s->C.p, (T*)s->delta.p, s->step_stop);
   return ICR_OK;
@@ -2430,7 +2843,7 @@ template <class T>
 static int newton_check_T(Scene* s) {
   const int m = s->m;
   if (m == 0) return ICR_OK;
-  PDL("k_newton_check", k_newton_check<T>, 1, 1024, 0, s->ctx->stream, m, (const T*)s->delta.p,
+  PDL("k_newton_check", newton_check_body<T>, 1, 1024, 0, s->ctx->stream, m, (const T*)s->delta.p,
       s->params.newton_tol, (int*)s->newton.p);
   return ICR_OK;
 }

@@ -186,16 +186,14 @@ __device__ __forceinline__ void pack_tile(const float (*sy)[TM + 1], unsigned ch
 // rows F_top (rows from super_ptr[s]).  Staged through shared memory so that
 // global reads and writes are coalesced.
 template <int MODE>
-__global__ void __launch_bounds__(256)
-    k_pack_tc(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_pack_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
               const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
               int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
-  pdl_entry();
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
   const int u1 = plan[pb];
-  for (int u = plan[pa] + blockIdx.x; u < u1; u += gridDim.x) {   // block-uniform
+  for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {   // block-uniform
     const int pos = find_unit(plan, pa, pb, u);
     const int s = level_list[pos];
     const int ncol = 3 * qcount[s];
@@ -219,6 +217,27 @@ __global__ void __launch_bounds__(256)
     __syncthreads();   // sy is refilled by the next unit
   }
 }
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+    k_pack_tc(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
+              const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+              const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
+              int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
+  pdl_entry();
+  d_pack_tc<MODE>(own_block(), plan, pa, pb, level_list, super_ptr, fr_ptr, qcount, boff, src, from_ftop, ldx, pk, X);
+}
+
+template <int MODE>
+struct pack_tc_body {
+  static constexpr int threads = 256, minb = 1;
+  static constexpr bool stride = true;
+  static auto kernel() { return &k_pack_tc<MODE>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_pack_tc<MODE>(vb, a...);
+  }
+};
 
 // Packs the solve operators G_s of the supernodes at least TC_GEMM_MIN_W wide
 // (column-major (w + r) x w panels, ld = w + r) into 128-row x 32-K blocks with
@@ -470,12 +489,10 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
 // of supernode s) from a counter, largest fronts first; the row warps add the
 // tile's upper-triangle entries into W_H.
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
                   const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
                   int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p, uint64_t wait_ns) {
-  pdl_entry();
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block), then the list's prefix
@@ -483,7 +500,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
   const int total = plan[ns];
-  if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
+  if ((int)vb.bx >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tsplit = *tsplit_p;
   // the unit search reads the list's prefix sums from shared memory when they fit
@@ -575,19 +592,38 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_teardown(tmem, br);
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_contract_tc(const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
+                  const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
+                  const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
+                  int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p, uint64_t wait_ns) {
+  pdl_entry();
+  d_contract_tc<MODE>(own_block(), plan, counter, ns, level_list, super_ptr, qcount, qidx, boff, m, pk, WH, ldw, dev_err, cache_plan, tsplit_p, wait_ns);
+}
+
+template <int MODE>
+struct contract_tc_body {
+  static constexpr int threads = TC_THREADS, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_contract_tc<MODE>; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_contract_tc<MODE>(vb, a...);
+  }
+};
+
 // Forward-solve product of the wide fronts of one level (3xTF32): persistent
 // CTAs take units (supernode s, 128-row tile rt of its w + r front rows,
 // 128-column tile ct of its 3|Q_s| columns) from the level's counter, largest
 // fronts first, and form out = G_s[rt rows, :] F_top[:, ct columns]; rows < w
 // store X_s = out, the update rows take U_s -= out.
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    k_front_gemm_tc(const int* __restrict__ plan, int pa, int pb, int* counter, const int* __restrict__ level_list,
+__device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb, int* counter, const int* __restrict__ level_list,
                     const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                     const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
                     const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
                     int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
-  pdl_entry();
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -595,7 +631,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ uint32_t tmem_base;
   __shared__ volatile int ok_sh;   // cleared by the side of the pipeline whose wait ran out
   const int u0 = plan[pa], total = plan[pb] - u0;
-  if ((int)blockIdx.x >= total) return;   // uniform: before any allocation
+  if ((int)vb.bx >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gsplit = *gsplit_p;
   tc_setup(&tmem_base, br, &ok_sh);
@@ -706,6 +742,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_teardown(tmem, br);
 }
 
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_front_gemm_tc(const int* __restrict__ plan, int pa, int pb, int* counter, const int* __restrict__ level_list,
+                    const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                    const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                    const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
+                    const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
+                    int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
+  pdl_entry();
+  d_front_gemm_tc(own_block(), plan, pa, pb, counter, level_list, super_ptr, rowpat_ptr, fr_ptr, qcount, goff, gpk, boff, fpk, X, ldx, dev_err, gsplit_p, wait_ns);
+}
+
+struct front_gemm_tc_body {
+  static constexpr int threads = TC_THREADS, minb = 1;
+  static constexpr bool stride = false;
+  static auto kernel() { return &k_front_gemm_tc; }
+  template <class... A>
+  __device__ __forceinline__ static void run(const VB& vb, A... a) {
+    d_front_gemm_tc(vb, a...);
+  }
+};
+
 // dynamic shared memory of a tensor-core CTA: the ring, padded so that at most
 // two CTAs share an SM (2 x 256 TMEM columns fill its 512)
 template <int MODE>
@@ -737,13 +794,13 @@ int contract_tc_T(Scene* s) {
   const int nsm = s->ctx->sm_count;
   const int tmax = s->tc_tmax;
   const int64_t ub_pack = (int64_t)ns * tmax * ((s->wmax + KT - 1) / KT);
-  PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
+  PDL("k_pack_tc", pack_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_PACK * (ns + 1), 0, ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p, 0,
       s->ldx, (unsigned char*)s->Ypk.p, (float*)nullptr);
   const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2 * TC_MAX_SPLIT;
   const int nlev = (int)s->levels.size();
-  PDL("k_contract_tc", k_contract_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem, s->ctx->stream,
+  PDL("k_contract_tc", contract_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_TC * (ns + 1), (int*)plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_TC, ns, (const int*)s->level_list.p,
       (const int*)s->super_ptr.p, (const int*)s->qcount.p, (const int*)s->qidx.p, (const int64_t*)s->tc_boff.p, m,
       (const unsigned char*)s->Ypk.p, (float*)s->WH.p, nr, (int*)s->dev_err.p, cache_plan,
@@ -784,13 +841,13 @@ int launch_front_gemm_tc(Scene* s, int level) {
   const int nsm = s->ctx->sm_count;
   const int tmax = s->tc_tmax;
   const int64_t ub_pack = (int64_t)lv.count * tmax * ((lv.wmax + KT - 1) / KT);
-  PDL("k_pack_tc", k_pack_tc<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
+  PDL("k_pack_tc", pack_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_FPACK * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->Ftop.p, 1,
       s->ldx, (unsigned char*)s->Ypk.p, (float*)s->X.p);
   const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax * TC_MAX_SPLIT;
   const int nlev = (int)s->levels.size();
-  PDL("k_front_gemm_tc", k_front_gemm_tc, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream,
+  PDL("k_front_gemm_tc", front_gemm_tc_body, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream,
       plan + PLAN_GTC * (ns + 1), pa, pb, plan + PLAN_LISTS * (ns + 1) + PLAN_CNT_GTC + level,
       (const int*)s->level_list.p, (const int*)s->super_ptr.p, (const int64_t*)s->rowpat_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->gpk_off.p,

@@ -32,7 +32,8 @@ EXPORTS = ("icr_last_error", "icr_ctx_create", "icr_ctx_destroy", "icr_ctx_bytes
            "icr_set_forward_plan", "icr_forward_levels", "icr_build_info",
            "icr_profile_begin", "icr_profile_end",
            "icr_ctx_set_wait_limit", "icr_ctx_inject_alloc_failure", "icr_scene_evict", "icr_scene_readmit",
-           "icr_scene_residency", "icr_serve_ex", "icr_newton_iterations")
+           "icr_scene_residency", "icr_serve_ex", "icr_newton_iterations", "icr_batch_create", "icr_batch_launch",
+           "icr_batch_info", "icr_batch_destroy", "icr_batch_merge_plan", "icr_batch_profile")
 
 
 class IcrError(RuntimeError):
@@ -65,6 +66,17 @@ class BuildInfo(ct.Structure):
 class ServeStats(ct.Structure):
     _fields_ = [("evictions", ct.c_int32), ("readmissions", ct.c_int32), ("rejected", ct.c_int32),
                 ("admit_s", ct.c_double)]
+
+
+class BatchInfo(ct.Structure):
+    _fields_ = [("n_scenes", ct.c_int32), ("n_groups", ct.c_int32), ("launches_per_step", ct.c_int32),
+                ("kernel_launches_per_step", ct.c_int32), ("scene_launches_per_step", ct.c_int64),
+                ("argument_bytes", ct.c_uint64), ("steps", ct.c_uint64)]
+
+
+class BatchLaunchTime(ct.Structure):
+    _fields_ = [("name", ct.c_char * 32), ("group", ct.c_int32), ("slots", ct.c_int32), ("blocks", ct.c_int32),
+                ("ms", ct.c_double)]
 
 
 class KernelTime(ct.Structure):
@@ -137,6 +149,12 @@ def lib() -> ct.CDLL:
             "icr_scene_evict": [P],
             "icr_scene_readmit": [P],
             "icr_scene_residency": [P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_uint64)],
+            "icr_batch_create": [ct.POINTER(P), ct.POINTER(P), ct.c_int32, ct.c_int32, ct.c_int32],
+            "icr_batch_launch": [P],
+            "icr_batch_info": [P, ct.POINTER(BatchInfo)],
+            "icr_batch_destroy": [P],
+            "icr_batch_profile": [P, ct.POINTER(BatchLaunchTime), ct.c_int32, ct.POINTER(ct.c_int32)],
+            "icr_batch_merge_plan": [P, P, ct.c_int32, P, P, P, ct.c_int32, P],
         }
         for name, args in sigs.items():
             fn = getattr(L, name)
@@ -229,6 +247,66 @@ class Context:
             pass
 
 
+def batch_merge_plan(sequences):
+    """icr_batch_merge_plan (host only): the merged launches of integer key
+    sequences, as a list of (key, [indices of the sequences it covers])."""
+    lens = _arr([len(q) for q in sequences], np.int32)
+    keys = _arr([k for q in sequences for k in q] or [0], np.int32)
+    total = int(lens.sum())
+    out_key = np.zeros(max(total, 1), np.int32)
+    out_count = np.zeros(max(total, 1), np.int32)
+    out_cover = np.zeros(max(total, 1), np.int32)
+    n = ct.c_int32()
+    _check(lib().icr_batch_merge_plan(_ptr(keys), _ptr(lens), len(sequences), _ptr(out_key),
+                                      _ptr(out_count), _ptr(out_cover), int(out_key.size), ct.byref(n)))
+    res, c = [], 0
+    for i in range(n.value):
+        res.append((int(out_key[i]), out_cover[c:c + out_count[i]].tolist()))
+        c += int(out_count[i])
+    return res
+
+
+class Batch:
+    """icr_batch: many scenes of one context stepped together by one captured
+    graph whose every kernel launch covers all of them.  Creating it runs one
+    batched step; every launch() runs one more time step of every scene."""
+
+    def __init__(self, scenes, n_newton: int, n_groups: int = 1):
+        self.scenes = list(scenes)   # kept alive while the batch holds them
+        arr = (P * len(self.scenes))(*[sc.h for sc in self.scenes])
+        h = P()
+        _check(lib().icr_batch_create(ct.byref(h), arr, len(self.scenes), int(n_newton), int(n_groups)))
+        self.h = h
+
+    def launch(self):
+        _check(lib().icr_batch_launch(self.h))
+
+    def info(self) -> dict:
+        bi = BatchInfo()
+        _check(lib().icr_batch_info(self.h, ct.byref(bi)))
+        return {f: getattr(bi, f) for f, _ in BatchInfo._fields_}
+
+    def profile(self) -> list[dict]:
+        """One eager batched step with CUDA events around every merged launch."""
+        n = ct.c_int32()
+        _check(lib().icr_batch_profile(self.h, None, 0, ct.byref(n)))
+        arr = (BatchLaunchTime * max(1, n.value))()
+        _check(lib().icr_batch_profile(self.h, arr, n.value, ct.byref(n)))
+        return [{"name": a.name.decode(), "group": a.group, "slots": a.slots, "blocks": a.blocks, "ms": a.ms}
+                for a in arr[:n.value]]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().icr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Scene:
     """icr_scene: one deformable body and its contacts."""
 
@@ -246,7 +324,7 @@ class Scene:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().icr_scene_destroy(self.h)
+            _check(lib().icr_scene_destroy(self.h))   # refused (ICR_ESTATE) while a batch holds the scene
             self.h = None
 
     def __del__(self):
