@@ -97,8 +97,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="leave out the liver_c1 and press_c1 keys")
     ap.add_argument("--no-parity", action="store_true", help="leave out the parity figures of the timed run")
     ap.add_argument("--tc-levels", default=None,
-                    help="comma list, per etree level (leaves first) 1 = forward solve on tcgen05; fixes the "
-                         "plan instead of autotuning (a profiler distorts the autotuner's timings)")
+                    help="comma list, per etree level (leaves first) the forward-solve tile: 0 = 64-row "
+                         "CUDA-core tiles, 1 = tcgen05, 2 = 32-row CUDA-core tiles; fixes the plan instead of "
+                         "autotuning (a profiler distorts the autotuner's timings)")
     ap.add_argument("--nvtx-step", action="store_true",
                     help="after the timed steps, replay one more step inside an NVTX range named 'step' "
                          "(for a per-step kernel list: ncu --nvtx --nvtx-include step/)")
@@ -454,7 +455,7 @@ def run_workload(torch, icr, driver, scene, name, ctx, stream, flush, args, tc_l
     if tc_levels_arg:
         plan = [int(x) for x in tc_levels_arg.split(",")]
         sc.set_forward_plan(plan)
-        tc_levels = int(sum(plan))
+        tc_levels = sum(1 for x in plan if x == 1)
     else:
         tc_levels = sc.autotune()
     sc.step_capture(scene.n_newton)
@@ -504,7 +505,7 @@ def run_icr(args):
     if args.tc_levels:
         plan = [int(x) for x in args.tc_levels.split(",")]
         sc.set_forward_plan(plan)
-        tc_levels = int(sum(plan))
+        tc_levels = sum(1 for x in plan if x == 1)
     else:
         tc_levels = sc.autotune()
     sc.step_capture(scene.n_newton)
@@ -648,8 +649,9 @@ def run_icr(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {**workload_config(scene), "parallelism": f"replicas x{world}",
                        "execution": f"captured step graph replayed per step; forward solve on tcgen05 in "
-                                    f"{tc_levels} etree levels ({'fixed' if args.tc_levels else 'autotuned'}), "
-                                    f"CUDA cores elsewhere; 3xTF32 contraction"},
+                                    f"{tc_levels} etree levels, 32-row CUDA-core tiles in "
+                                    f"{info['short_tile_levels']}, 64-row tiles elsewhere "
+                                    f"({'fixed' if args.tc_levels else 'autotuned'}); 3xTF32 contraction"},
             "latency_ms": {"p50": float(statistics.median(ms)),
                            "p99": float(ms_sorted[int(round(0.99 * (len(ms) - 1)))])},
             "phase_ms": phase_ms,
@@ -775,8 +777,8 @@ def run_batch(args):
         "config": {"workload": f"batch_c2: {len(scenes)} independent scenes, nodes log-uniform 500-8000 (ellipsoids "
                                f"and beams), 20-600 contacts, mu U(0.1, 0.6), {sum(x.n for x in scenes)} DOF and "
                                f"{sum(x.m for x in scenes)} contacts in total, 5 Newton x <=50 PGS sweeps",
-                   "execution": f"batched step: one captured CUDA graph of {n_groups} parallel branches (groups of "
-                                f"scenes of similar cost), every kernel launch covering all scenes of its group "
+                   "execution": f"batched step: one captured CUDA graph of {n_groups} parallel branches (cost-balanced groups of "
+                                f"scenes), every kernel launch covering all scenes of its group "
                                 f"({info['kernel_launches_per_step']} kernel launches per step for the "
                                 f"{info['scene_launches_per_step']} of the scenes' own steps)",
                    "l2": f"not flushed: the scenes hold {resident / 2**20:.0f} MiB on the device, above the 129 MB L2",

@@ -321,26 +321,29 @@ int icr_newton_iterations(icr_scene* scene, int32_t* out);
 int icr_step_capture(icr_scene* scene, int32_t n_newton);
 /* Autotuner of the forward solve X = L^-1 H^T (the multi-RHS supernodal solve
  * of Eq. "schur complemnt reformulated").  For every elimination-tree level it
- * times the level's front products with 64 x 96 CUDA-core tiles and with
- * 128 x 128 tcgen05 tiles (3xTF32, for fronts at least 64 wide with 64
- * columns) on the scene's current mapping and keeps the faster (the tensor
- * cores must win by 3 %).  Synchronises; runs several W_H builds (W_H is left
- * formed).  Needs a system and a mapping (ICR_ESTATE); not while the stream is
- * being captured (ICR_ESTATE).  FP64 scenes and the SIMT contraction mode keep
- * CUDA cores.  tc_levels (may be NULL) receives the number of levels on the
- * tensor cores.  Until it runs, every level with a front at least 64 wide uses
- * the tensor cores; icr_set_mapping and a change of contraction mode mark the
- * scene untuned.  Each level's time is the median of 5 builds per engine, the
- * engines alternating; level_ms (may be NULL when max_levels = 0) receives,
- * for the first max_levels levels (leaves first), the CUDA-core and the
- * tensor-core time in ms (the same value twice for levels too narrow for the
- * tensor cores). */
+ * times the level's front products with three tile shapes: CUDA-core tiles of
+ * 64 front rows x 96 columns, CUDA-core tiles of 32 rows x 96 columns (short
+ * fronts), and 128 x 128 tcgen05 tiles (3xTF32, for fronts at least 64 wide
+ * with 64 columns; FP32 scenes outside the SIMT contraction mode), on the
+ * scene's current mapping, and keeps the fastest (the tensor cores must win by
+ * 3 % over the faster CUDA-core tile).  Synchronises; runs several W_H builds
+ * (W_H is left formed).  Needs a system and a mapping (ICR_ESTATE); not while
+ * the stream is being captured (ICR_ESTATE).  tc_levels (may be NULL) receives
+ * the number of levels on the tensor cores.  Until it runs, every level with
+ * a front at least 64 wide uses the tensor cores and the others 64-row tiles;
+ * icr_set_mapping and a change of contraction mode mark the scene untuned.
+ * Each level's time is the median of 5 builds per tile shape, the shapes
+ * alternating; level_ms (may be NULL when max_levels = 0) receives, for the
+ * first max_levels levels (leaves first), the 64-row, the 32-row and the
+ * tensor-core time in ms (the 64-row time again where the tensor cores do not
+ * apply). */
 int icr_autotune(icr_scene* scene, int32_t* tc_levels, double* level_ms, int32_t max_levels);
 /* Fix the forward-solve plan instead of tuning it: for every etree level
- * (n_levels = icr_forward_levels, leaves first) 1 puts the level's wide fronts
- * on the tensor cores (where they qualify, FP32 scenes outside the SIMT
- * contraction mode), 0 keeps CUDA cores.  Marks the scene tuned.  Needs a
- * system (ICR_ESTATE); ICR_EINVAL on a wrong count or a flag other than 0/1. */
+ * (n_levels = icr_forward_levels, leaves first) 0 puts the level's fronts on
+ * 64-row CUDA-core tiles, 1 its wide fronts on the tensor cores (where they
+ * qualify, FP32 scenes outside the SIMT contraction mode; the others on 64-row
+ * tiles), 2 on 32-row CUDA-core tiles.  Marks the scene tuned.  Needs a
+ * system (ICR_ESTATE); ICR_EINVAL on a wrong count or a value above 2. */
 int icr_set_forward_plan(icr_scene* scene, const uint8_t* tc_levels, int32_t n_levels);
 int icr_forward_levels(icr_scene* scene, int32_t* n_levels);
 /* Launch the captured step on the context's stream.  ICR_ESTATE without a
@@ -477,6 +480,7 @@ typedef struct icr_build_info_t {
      3q (w^2 + 2 w r) (w columns, r rows below, q reaching contacts), contraction
      w c (c + 1) with c = 3q (the upper triangle of Y_s^T Y_s) */
   double flops_front_tc, flops_front_simt, flops_contract_tc, flops_contract_simt;
+  int32_t short_tile_levels;   /* levels whose CUDA-core front products use 32-row tiles */
 } icr_build_info_t;
 int icr_build_info(icr_scene* scene, icr_build_info_t* out);
 

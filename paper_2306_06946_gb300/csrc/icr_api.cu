@@ -1311,7 +1311,7 @@ int icr_build_info(icr_scene* s, icr_build_info_t* out) {
       const double w = s->h_super_ptr[sn + 1] - s->h_super_ptr[sn];
       const double r = (double)(s->h_rowpat_ptr[sn + 1] - s->h_rowpat_ptr[sn]);
       const double fwd = c * (w * w + 2.0 * w * r), con = w * c * (c + 1.0);
-      const bool tcg = !simt && s->tc_level[li] && w >= TC_GEMM_MIN_W && c >= TC_GEMM_MIN_COLS;
+      const bool tcg = !simt && s->tc_level[li] == FWD_TC && w >= TC_GEMM_MIN_W && c >= TC_GEMM_MIN_COLS;
       (tcg ? out->flops_front_tc : out->flops_front_simt) += fwd;
       (!simt && c >= 64 ? out->flops_contract_tc : out->flops_contract_simt) += con;
     }
@@ -1322,6 +1322,7 @@ int icr_build_info(icr_scene* s, icr_build_info_t* out) {
   out->contract_tc_split = out->contract_tc_units > 0 ? splits[nlev] : 1;
   out->contract_simt_units = P(PLAN_SIMT, ns);
   for (int i = 0; i < ns; ++i) out->reach_nnz += qc[i];
+  for (uint8_t f : s->tc_level) out->short_tile_levels += f == FWD_SIMT_SHORT ? 1 : 0;
   return ICR_OK;
 }
 
@@ -1357,18 +1358,25 @@ static int autotune(Scene* s, double* level_ms, int max_levels) {
     for (auto& x : ev) cudaEventDestroy(x);
     return rc;
   };
+  // every level on one tile shape (the tensor cores only where a level has a
+  // front wide enough; its narrower fronts then take 64-row CUDA-core tiles)
   auto configure = [&](int cfg) {
-    for (int l = 0; l < nlev; ++l) s->tc_level[l] = cfg && s->levels[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
+    for (int l = 0; l < nlev; ++l)
+      s->tc_level[l] = cfg == FWD_TC ? (s->levels[l].wmax >= TC_GEMM_MIN_W ? FWD_TC : FWD_SIMT) : cfg;
     return upload_tc_super(s);
   };
-  // per level and engine, the median of REPS timed builds; the two engines
-  // alternate so that clock and cache drift affect both alike
+  const int mode = s->params.contraction;
+  const bool tc_ok = s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT;
+  const int ncfg = tc_ok ? FWD_TILES : FWD_TILES - 1;
+  const int cfgs[FWD_TILES] = {FWD_SIMT, FWD_SIMT_SHORT, FWD_TC};
+  // per level and tile shape, the median of REPS timed builds; the shapes
+  // alternate so that clock and cache drift affect them alike
   constexpr int REPS = 5;
-  std::vector<double> samp[2];
-  samp[0].assign((size_t)nlev * REPS, 0.0);
-  samp[1].assign((size_t)nlev * REPS, 0.0);
+  std::vector<double> samp[FWD_TILES];
+  for (auto& v : samp) v.assign((size_t)nlev * REPS, 0.0);
   for (int rep = -1; rep < REPS; ++rep) {
-    for (int cfg = 0; cfg < 2; ++cfg) {
+    for (int ci = 0; ci < ncfg; ++ci) {
+      const int cfg = cfgs[ci];
       int rc = configure(cfg);
       if (rc != ICR_OK) return done(rc);
       s->level_events = rep >= 0 ? ev.data() : nullptr;   // rep -1 warms up
@@ -1385,17 +1393,27 @@ static int autotune(Scene* s, double* level_ms, int max_levels) {
       }
     }
   }
+  // per level: the faster CUDA-core tile, replaced by the tensor cores when
+  // they win by 3 %
   for (int l = 0; l < nlev; ++l) {
-    double med[2];
-    for (int cfg = 0; cfg < 2; ++cfg) {
+    double med[FWD_TILES];
+    for (int ci = 0; ci < FWD_TILES; ++ci) {
+      const int cfg = cfgs[ci];
+      if (ci >= ncfg) {
+        med[cfg] = med[FWD_SIMT];
+        continue;
+      }
       std::vector<double> v(samp[cfg].begin() + (size_t)l * REPS, samp[cfg].begin() + (size_t)(l + 1) * REPS);
       std::nth_element(v.begin(), v.begin() + REPS / 2, v.end());
       med[cfg] = v[REPS / 2];
     }
-    s->tc_level[l] = s->levels[l].wmax >= TC_GEMM_MIN_W && med[1] < 0.97 * med[0] ? 1 : 0;
+    const int simt = med[FWD_SIMT_SHORT] < med[FWD_SIMT] ? FWD_SIMT_SHORT : FWD_SIMT;
+    const bool wide = tc_ok && s->levels[l].wmax >= TC_GEMM_MIN_W;
+    s->tc_level[l] = wide && med[FWD_TC] < 0.97 * med[simt] ? FWD_TC : simt;
     if (level_ms && l < max_levels) {
-      level_ms[2 * l] = med[0];
-      level_ms[2 * l + 1] = s->levels[l].wmax >= TC_GEMM_MIN_W ? med[1] : med[0];
+      level_ms[3 * l] = med[FWD_SIMT];
+      level_ms[3 * l + 1] = med[FWD_SIMT_SHORT];
+      level_ms[3 * l + 2] = wide ? med[FWD_TC] : med[FWD_SIMT];
     }
   }
   const int rc = upload_tc_super(s);
@@ -1419,12 +1437,13 @@ int icr_set_forward_plan(icr_scene* s, const uint8_t* tc_levels, int32_t n_level
     return ICR_EINVAL;
   }
   for (int l = 0; l < nlev; ++l)
-    if (tc_levels[l] > 1) {
-      set_error("set_forward_plan: flag %d of level %d is not 0 or 1", tc_levels[l], l);
+    if (tc_levels[l] >= FWD_TILES) {
+      set_error("set_forward_plan: tile %d of level %d is not 0, 1 or 2", tc_levels[l], l);
       return ICR_EINVAL;
     }
   RET(set_device(s));
-  for (int l = 0; l < nlev; ++l) s->tc_level[l] = tc_levels[l] && s->levels[l].wmax >= TC_GEMM_MIN_W ? 1 : 0;
+  for (int l = 0; l < nlev; ++l)
+    s->tc_level[l] = tc_levels[l] == FWD_TC ? (s->levels[l].wmax >= TC_GEMM_MIN_W ? FWD_TC : FWD_SIMT) : tc_levels[l];
   RET(upload_tc_super(s));
   s->tuned = true;
   return ICR_OK;
@@ -1445,16 +1464,16 @@ int icr_autotune(icr_scene* s, int32_t* tc_levels, double* level_ms, int32_t max
   RET(need_mapping(s, "autotune"));
   RET(set_device(s));
   if (max_levels < 0 || (max_levels > 0 && !level_ms)) {
-    set_error("autotune: level_ms needs room for 2 x max_levels doubles");
+    set_error("autotune: level_ms needs room for 3 x max_levels doubles");
     return ICR_EINVAL;
   }
   const int mode = s->params.contraction;
-  const bool tunable = s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT && s->m > 0;
-  if (tunable) RET(autotune(s, level_ms, max_levels));
+  const bool tc_ok = s->prec == ICR_FP32 && mode != ICR_CONTRACT_SIMT;
+  if (s->m > 0) RET(autotune(s, level_ms, max_levels));
   s->tuned = true;
   if (tc_levels) {
     int n = 0;
-    for (uint8_t f : s->tc_level) n += tunable ? f : 0;
+    for (uint8_t f : s->tc_level) n += tc_ok && f == FWD_TC ? 1 : 0;
     *tc_levels = n;
   }
   return ICR_OK;

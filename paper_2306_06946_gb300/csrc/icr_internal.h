@@ -49,6 +49,12 @@ enum PlanList {
   PLAN_LISTS = 7
 };
 enum PlanCounter { PLAN_CNT_SIMT = 0, PLAN_CNT_TC = 1, PLAN_CNT_GTC = 2 };
+// Forward-solve tile shape of an etree level (icr_autotune / icr_set_forward_plan):
+// CUDA-core tiles of 64 front rows x 96 columns, tcgen05 tiles of 128 x 128 for
+// the level's fronts at least TC_GEMM_MIN_W wide (the others on 64-row tiles),
+// or CUDA-core tiles of 32 front rows x 96 columns.
+enum FwdTile { FWD_SIMT = 0, FWD_TC = 1, FWD_SIMT_SHORT = 2, FWD_TILES = 3 };
+constexpr int GR_LONG = 64, GR_SHORT = 32;   // front rows of the two CUDA-core tiles
 constexpr int TC_TILE = 128;         // tensor-core output tile (M = N)
 constexpr int TC_KT = 32;            // front rows per packed operand block
 constexpr int TC_GEMM_MIN_W = 64;    // fronts at least this wide ...

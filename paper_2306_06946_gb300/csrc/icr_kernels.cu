@@ -48,7 +48,7 @@ static constexpr int SOLVE_THREADS = 192; // 2 x 96 columns
 static constexpr int CT = 64;             // contraction output tile
 static constexpr int CK_ = 16;            // contraction k-chunk
 static constexpr int TC_MIN_COLS = 64;    // fronts this wide use the tensor-core contraction
-static constexpr int GR = 64;             // front rows per front-GEMM tile
+
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -283,9 +283,9 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
   const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
   const int nt = cdiv(q, TCC);
   const int ncol = 3 * q;
-  const bool tcg = tc_gemm && tc_super[s] && q > 0 && w >= TC_GEMM_MIN_W && ncol >= TC_GEMM_MIN_COLS;
+  const bool tcg = tc_gemm && tc_super[s] == FWD_TC && q > 0 && w >= TC_GEMM_MIN_W && ncol >= TC_GEMM_MIN_COLS;
   c[PLAN_ASM] = cdiv(nrows, ASM_ROWS) * nt;
-  c[PLAN_GEMM] = tcg ? 0 : cdiv(nrows, GR) * nt;
+  c[PLAN_GEMM] = tcg ? 0 : cdiv(nrows, tc_super[s] == FWD_SIMT_SHORT ? GR_SHORT : GR_LONG) * nt;
   const int nkb = cdiv(w, TC_KT);   // K blocks of a tensor-core unit
   c[PLAN_GTC] = tcg ? cdiv(nrows, TC_TILE) * cdiv(ncol, TC_TILE) * tc_parts(gsplit, nkb) : 0;
   c[PLAN_FPACK] = tcg ? cdiv(ncol, TC_TILE) * cdiv(w, TC_KT) : 0;
@@ -503,10 +503,16 @@ struct assemble_body {
   }
 };
 
-// Block (supernode, 64-row tile of the w + r front rows, 32-contact tile):
+// Block (supernode, GR-row tile of the w + r front rows, 32-contact tile):
 // out = G_s[rows, :] F_top; top rows store X_s = out, bottom rows U_s -= out.
 // K is streamed in 32-wide chunks through a double-buffered cp.async pipeline.
-static constexpr int GLD = GR + 4, FLD = TCOLS + 4;
+// 256 threads as 16 x 16, each RPT rows x 6 columns: GR = 16 RPT front rows
+// (RPT = 4: 64-row tiles; RPT = 2: 32-row tiles for short fronts).
+static constexpr int FLD = TCOLS + 4;
+template <int RPT>
+struct GemmTile {
+  static constexpr int GR = 16 * RPT, GLD = GR + 4;
+};
 template <class T>
 __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool ok) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -517,7 +523,7 @@ __device__ __forceinline__ void cp_async_zfill(T* smem, const T* gmem, bool ok) 
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
 }
 
-template <class T>
+template <class T, int RPT>
 __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, const int* __restrict__ super_ptr,
                                                 const int64_t* __restrict__ rowpat_ptr,
                                                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G,
@@ -527,6 +533,7 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
   const int ncols = 3 * min(TCC, nq - k0);
   const int c0 = super_ptr[s], w = super_ptr[s + 1] - c0;
   const int nrows = w + (int)(rowpat_ptr[s + 1] - rowpat_ptr[s]);
+  constexpr int GR = GemmTile<RPT>::GR, GLD = GemmTile<RPT>::GLD;
   const int row0 = rt * GR;
   const int64_t ldG = nrows;
   const T* Gs = G + val_ptr[s];
@@ -548,9 +555,9 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
     }
     cp_async_commit();
   };
-  T acc[4][6];
+  T acc[RPT][6];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < RPT; ++q)
 #pragma unroll
     for (int c = 0; c < 6; ++c) acc[q][c] = T(0);
   load(0, 0);
@@ -567,13 +574,13 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
     const T* cF = sF + buf * KB * FLD;
 #pragma unroll 8
     for (int k = 0; k < KB; ++k) {
-      T a[4], bv[6];
+      T a[RPT], bv[6];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) a[q] = cG[k * GLD + 4 * ty + q];
+      for (int q = 0; q < RPT; ++q) a[q] = cG[k * GLD + RPT * ty + q];
 #pragma unroll
       for (int c = 0; c < 6; ++c) bv[c] = cF[k * FLD + 6 * tx + c];
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int q = 0; q < RPT; ++q)
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[q][c] += a[q] * bv[c];
     }
@@ -582,8 +589,8 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
   }
   T* F = X + fr_ptr[s] * ldx + 3 * k0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int row = row0 + 4 * ty + q;
+  for (int q = 0; q < RPT; ++q) {
+    const int row = row0 + RPT * ty + q;
     if (row >= nrows) continue;
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -597,14 +604,16 @@ __device__ __forceinline__ void front_gemm_tile(int s, int rt, int t, int nq, co
   }
 }
 
-template <class T>
-__device__ __forceinline__ void d_front_gemm(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
-                 const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
-                 const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
-                 const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
+template <class T, int RPT>
+__device__ __forceinline__ void d_front_gemm(const VB& vb, const int* __restrict__ plan, int pa, int pb,
+                                             const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+                                             const int64_t* __restrict__ rowpat_ptr,
+                                             const int64_t* __restrict__ val_ptr, const T* __restrict__ G,
+                                             const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                                             T* X, const T* __restrict__ Ftop, int64_t ldx) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sG = (T*)smraw;                 // 2 x KB x GLD
-  T* sF = sG + 2 * KB * GLD;         // 2 x KB x FLD
+  T* sG = (T*)smraw;                                  // 2 x KB x GLD
+  T* sF = sG + 2 * KB * GemmTile<RPT>::GLD;           // 2 x KB x FLD
   __shared__ int pos_sh;
   const int u1 = plan[pb];
   for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {   // block-uniform
@@ -614,34 +623,35 @@ __device__ __forceinline__ void d_front_gemm(const VB& vb, const int* __restrict
     const int local = u - plan[pos];
     const int nt = cdiv(nq, TCC);
     const int rt = local / nt, t = local % nt;
-    front_gemm_tile<T>(s, rt, t, nq, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, X, Ftop, ldx, sG, sF);
+    front_gemm_tile<T, RPT>(s, rt, t, nq, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, X, Ftop, ldx, sG, sF);
   }
 }
 
-template <class T>
+template <class T, int RPT>
 __global__ void __launch_bounds__(256)
     k_front_gemm(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
                  const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
                  const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const int64_t* __restrict__ fr_ptr,
                  const int* __restrict__ qcount, T* X, const T* __restrict__ Ftop, int64_t ldx) {
   pdl_entry();
-  d_front_gemm<T>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, qcount, X, Ftop, ldx);
+  d_front_gemm<T, RPT>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, val_ptr, G, fr_ptr, qcount, X,
+                       Ftop, ldx);
 }
 
-template <class T>
+template <class T, int RPT>
 struct front_gemm_body {
   static constexpr int threads = 256, minb = 1;
   static constexpr bool stride = true;
-  static auto kernel() { return &k_front_gemm<T>; }
+  static auto kernel() { return &k_front_gemm<T, RPT>; }
   template <class... A>
   __device__ __forceinline__ static void run(const VB& vb, A... a) {
-    d_front_gemm<T>(vb, a...);
+    d_front_gemm<T, RPT>(vb, a...);
   }
 };
 
-template <class T>
+template <class T, int RPT>
 static size_t gemm_smem_bytes() {
-  return 2 * (size_t)KB * (GLD + FLD) * sizeof(T);
+  return 2 * (size_t)KB * (GemmTile<RPT>::GLD + FLD) * sizeof(T);
 }
 
 // ------------------------------------------------------------------ a3 pivot scaling
@@ -2459,6 +2469,25 @@ struct linearize_body {
 };
 
 // ------------------------------------------------------------------ launchers
+// the front GEMM's dynamic shared memory set up on the device, and its
+// resident blocks per SM (cached per device)
+template <class T, int RPT>
+static int gemm_occupancy(int dev, int* occ) {
+  static SmemLimit lim;
+  static DevInt occ_dev;
+  cudaError_t e = ensure_smem(k_front_gemm<T, RPT>, lim, dev, (int)gemm_smem_bytes<T, RPT>());
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
+  int o = occ_dev.get(dev);
+  if (o == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_front_gemm<T, RPT>, 256, gemm_smem_bytes<T, RPT>());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_front_gemm)");
+    o = std::max(1, o);
+    occ_dev.put(dev, o);
+  }
+  *occ = o;
+  return ICR_OK;
+}
+
 template <class T>
 static int build_WH_T(Scene* s) {
   cudaStream_t st = s->ctx->stream;
@@ -2481,18 +2510,12 @@ static int build_WH_T(Scene* s) {
   PDL("k_reach_inv", reach_inv_body, ns, 256, 0, st,
       m, (const int*)s->parent.p, (const int*)s->qcount.p, (const int*)s->qpos.p,
                                   (int*)s->qinv.p);
-  static SmemLimit gemm_lim;
-  static DevInt gemm_occ_dev;
   const int dev = s->ctx->device;
-  e = ensure_smem(k_front_gemm<T>, gemm_lim, dev, (int)gemm_smem_bytes<T>());
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_front_gemm)");
-  int gemm_occ = gemm_occ_dev.get(dev);
-  if (gemm_occ == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gemm_occ, k_front_gemm<T>, 256, gemm_smem_bytes<T>());
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor(k_front_gemm)");
-    gemm_occ = std::max(1, gemm_occ);
-    gemm_occ_dev.put(dev, gemm_occ);
-  }
+  int gemm_occ[2] = {0, 0};   // resident blocks per SM of the 64-row and the 32-row front GEMM
+  RET((gemm_occupancy<T, 4>(dev, &gemm_occ[0])));
+  RET((gemm_occupancy<T, 2>(dev, &gemm_occ[1])));
+  using KGemmLong = front_gemm_body<T, 4>;
+  using KGemmShort = front_gemm_body<T, 2>;
   // contraction: FP32 scenes put fronts of TC_MIN_COLS or more columns on the
   // tensor cores (unless SIMT is asked for), the rest on CUDA cores
   int mode = s->params.contraction;
@@ -2525,12 +2548,21 @@ static int build_WH_T(Scene* s) {
         (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->fr_ptr.p, (const int*)s->ctr_ptr.p,
         (const int*)s->ctr_child.p, (const int*)s->ctr_row.p, (const int*)s->nodes.p, (const T*)s->bary.p,
         (const int*)s->qcount.p, (const int*)s->qidx.p, (const int*)s->qinv.p, m, X, (T*)s->Ftop.p, ldx);
-    const int64_t ub_g = (int64_t)lv.count * ((lv.wmax + lv.rmax + GR - 1) / GR) * ntiles;
-    PDL("k_front_gemm", front_gemm_body<T>, (unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ * nsm), 256, gemm_smem_bytes<T>(), st,
-        plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
-        (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
-        (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
-    if (tc_gemm && s->tc_level[li] && lv.wmax >= TC_GEMM_MIN_W) {
+    const bool short_rows = s->tc_level[li] == FWD_SIMT_SHORT;
+    const int gr = short_rows ? GR_SHORT : GR_LONG;
+    const int64_t ub_g = (int64_t)lv.count * ((lv.wmax + lv.rmax + gr - 1) / gr) * ntiles;
+    const unsigned grid_g = (unsigned)std::min<int64_t>(ub_g, (int64_t)gemm_occ[short_rows ? 1 : 0] * nsm);
+    if (short_rows)
+      PDL("k_front_gemm", KGemmShort, grid_g, 256, (gemm_smem_bytes<T, 2>()), st,
+          plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+          (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
+          (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
+    else
+      PDL("k_front_gemm", KGemmLong, grid_g, 256, (gemm_smem_bytes<T, 4>()), st,
+          plan + PLAN_GEMM * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
+          (const int64_t*)s->rowpat_ptr.p, (const int64_t*)s->val_ptr.p, (const T*)s->G.p,
+          (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, X, (const T*)s->Ftop.p, ldx);
+    if (tc_gemm && s->tc_level[li] == FWD_TC && lv.wmax >= TC_GEMM_MIN_W) {
       const int rc = launch_front_gemm_tc(s, li);
       if (rc != ICR_OK) return rc;
     }

@@ -60,7 +60,8 @@ class BuildInfo(ct.Structure):
                 ("contract_tc_units", ct.c_int32), ("contract_tc_split", ct.c_int32),
                 ("contract_simt_units", ct.c_int32), ("prox_split", ct.c_int32), ("reach_nnz", ct.c_int64),
                 ("flops_front_tc", ct.c_double), ("flops_front_simt", ct.c_double),
-                ("flops_contract_tc", ct.c_double), ("flops_contract_simt", ct.c_double)]
+                ("flops_contract_tc", ct.c_double), ("flops_contract_simt", ct.c_double),
+                ("short_tile_levels", ct.c_int32)]
 
 
 class ServeStats(ct.Structure):
@@ -456,16 +457,17 @@ class Scene:
         return int(v.value)
 
     def autotune(self, level_times: bool = False):
-        """Per-level choice of the forward-solve engine; returns the number of
-        levels on the tensor cores (and, with ``level_times``, an array of
-        [CUDA-core ms, tensor-core ms] per etree level)."""
+        """Per-level choice of the forward-solve tile shape; returns the number
+        of levels on the tensor cores (and, with ``level_times``, an array of
+        [64-row CUDA-core ms, 32-row CUDA-core ms, tensor-core ms] per etree
+        level)."""
         n = ct.c_int32(0)
         nlev = self.forward_levels()
-        lv = np.zeros(2 * nlev) if level_times else None
+        lv = np.zeros(3 * nlev) if level_times else None
         _check(lib().icr_autotune(self.h, ct.byref(n), _ptr(lv), nlev if level_times else 0))
         if not level_times:
             return int(n.value)
-        return int(n.value), lv.reshape(nlev, 2)
+        return int(n.value), lv.reshape(nlev, 3)
 
     def forward_levels(self) -> int:
         n = ct.c_int32(0)

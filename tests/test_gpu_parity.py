@@ -390,24 +390,34 @@ def test_autotune_keeps_parity(ctx):
     sc.build_WH()
     assert rel(sc.get("WH"), oracle_WH("liver_c1")) < 1e-5
     sc64 = make_scene(ctx, "liver_c1", icr.FP64)
-    assert sc64.autotune() == 0
+    assert sc64.autotune() == 0          # FP64: CUDA-core tiles only (64 or 32 rows per level)
+    sc64.build_WH()
+    assert rel(sc64.get("WH"), oracle_WH("liver_c1")) < 1e-12
+    n, ms = sc.autotune(level_times=True)
+    assert ms.shape == (sc.forward_levels(), 3) and np.all(ms > 0)
+    sc.build_WH()   # the tuning builds ran every shape; build_info reads the last build's work lists
+    info = sc.build_info()
+    assert info["tc_levels"] == n and 0 <= info["short_tile_levels"] <= sc.forward_levels() - n
 
 
 # ---------------------------------------------------------------- forward-solve plans
 @pytest.mark.parametrize("name", ["beam_mid", "liver_c1"])
 @pytest.mark.parametrize("prec,tol", [(1, 1e-12), (0, 1e-5)])
 def test_forward_plans_keep_parity(ctx, name, prec, tol):
-    """Every plan of the forward solve (tensor cores or CUDA cores per level,
-    alternating) forms the same W_H."""
+    """Every plan of the forward solve (tile shape per level: 64-row or 32-row
+    CUDA-core tiles, tensor cores; uniform and mixed) forms the same W_H."""
     from paper_2306_06946_gb300 import icr
     sc = make_scene(ctx, name, prec)
     nlev = sc.forward_levels()
     assert nlev >= 2
-    for plan in [np.zeros(nlev), np.ones(nlev), np.arange(nlev) % 2, 1 - np.arange(nlev) % 2]:
+    plans = [np.zeros(nlev), np.ones(nlev), np.full(nlev, 2), np.arange(nlev) % 2, 1 - np.arange(nlev) % 2,
+             np.arange(nlev) % 3, 2 - np.arange(nlev) % 3]
+    for plan in plans:
         sc.set_forward_plan(plan.astype(np.uint8))
         sc.build_WH()
         assert rel(sc.get("WH"), oracle_WH(name)) < tol, plan
-    for bad in [np.zeros(nlev + 1), np.full(nlev, 2)]:
+        assert sc.build_info()["short_tile_levels"] == int(np.sum(plan == 2))
+    for bad in [np.zeros(nlev + 1), np.full(nlev, 3)]:
         with pytest.raises(icr.IcrError) as e:
             sc.set_forward_plan(bad.astype(np.uint8))
         assert e.value.code == icr.EINVAL
