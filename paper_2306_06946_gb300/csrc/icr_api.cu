@@ -642,7 +642,7 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
   RET(upload(s, s->ctr_row, crow_row.data(), crow_row.size()));
   if (s->prec == ICR_FP32) {
     // G_s of the supernodes wide enough for the tensor-core forward solve, as
-    // 3xTF32 operand blocks of 128 rows x 32 columns (32 KiB each)
+    // 3xTF32 operand blocks of 128 rows x TC_KT columns (TC_BLOCK_BYTES each)
     std::vector<int64_t> goff(ns + 1, -1);
     std::vector<int32_t> blocks;
     int64_t nb = 0;
@@ -662,7 +662,7 @@ int icr_set_system(icr_scene* s, int32_t n, int32_t ns, const int32_t* super_ptr
     }
     RET(dalloc(s, s->gpk_off, (ns + 1) * sizeof(int64_t)));
     RET(upload(s, s->gpk_off, goff.data(), ns + 1));
-    RET(dalloc(s, s->Gpk, std::max<int64_t>(1, nb) * 32768));
+    RET(dalloc(s, s->Gpk, std::max<int64_t>(1, nb) * TC_BLOCK_BYTES));
     if (nb) {
       DBuf list;
       RET(dalloc(s, list, blocks.size() * sizeof(int32_t)));
@@ -782,16 +782,16 @@ int icr_set_mapping(icr_scene* s, int32_t m, const int32_t* nodes, const double*
   RET(dalloc(s, s->WH16, s->prec == ICR_FP32 ? 9 * mm * mm * 2 : 16));
   if (s->prec == ICR_FP32) {
     // tensor-core operand blocks: per supernode ceil(3m/128) column tiles x
-    // ceil(w/32) row chunks, 32 KiB each (two TF32 planes)
+    // ceil(w/TC_KT) row chunks of TC_BLOCK_BYTES (two TF32 planes)
     const int tmax = std::max(1, (int)((3 * (int64_t)m + 127) / 128));
     if (tmax != s->tc_tmax || !s->tc_boff.p) {   // the block offsets depend on the tile count only
       std::vector<int64_t> boff(ns + 1, 0);
       for (int k = 0; k < ns; ++k)
-        boff[k + 1] = boff[k] + (int64_t)tmax * ((s->h_super_ptr[k + 1] - s->h_super_ptr[k] + 31) / 32);
+        boff[k + 1] = boff[k] + (int64_t)tmax * ((s->h_super_ptr[k + 1] - s->h_super_ptr[k] + TC_KT - 1) / TC_KT);
       RET(dalloc(s, s->tc_boff, (ns + 1) * sizeof(int64_t)));
       RET(upload(s, s->tc_boff, boff.data(), ns + 1));
       CK(cudaStreamSynchronize(s->ctx->stream));   // boff is a local vector
-      RET(dalloc(s, s->Ypk, (size_t)boff[ns] * 32768));
+      RET(dalloc(s, s->Ypk, (size_t)boff[ns] * TC_BLOCK_BYTES));
       s->tc_tmax = tmax;
     }
   }

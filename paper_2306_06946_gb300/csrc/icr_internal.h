@@ -56,10 +56,12 @@ enum PlanCounter { PLAN_CNT_SIMT = 0, PLAN_CNT_TC = 1, PLAN_CNT_GTC = 2 };
 enum FwdTile { FWD_SIMT = 0, FWD_TC = 1, FWD_SIMT_SHORT = 2, FWD_TILES = 3 };
 constexpr int GR_LONG = 64, GR_SHORT = 32;   // front rows of the two CUDA-core tiles
 constexpr int TC_TILE = 128;         // tensor-core output tile (M = N)
-constexpr int TC_KT = 32;            // front rows per packed operand block
+constexpr int TC_KT = 32;            // front rows (K) per packed operand block
+// bytes of one packed operand block in the widest mode (3xTF32: two TF32 planes)
+constexpr size_t TC_BLOCK_BYTES = (size_t)TC_TILE * TC_KT * 4 * 2;
 constexpr int TC_GEMM_MIN_W = 64;    // fronts at least this wide ...
 constexpr int TC_GEMM_MIN_COLS = 64; // ... and with this many columns take the tensor-core forward solve
-constexpr int TC_PART_KB = 2;        // fewest K blocks in a part of a split tensor-core unit
+constexpr int TC_PART_KB = 2;        // fewest K blocks (64 K) in a part of a split tensor-core unit
 constexpr int TC_MAX_SPLIT = 8;      // most K parts of a tensor-core unit
 constexpr int PLAN_MAX_LEV = 128;    // levels with their own K split (deeper ones are not split)
 // K parts of a tensor-core unit over nk K blocks, given the split factor of

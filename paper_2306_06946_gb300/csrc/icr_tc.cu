@@ -10,12 +10,13 @@
 // layout: 8 rows x 16 bytes per core matrix, no swizzle), converted to the MMA
 // operand type: k_pack_tc packs Y_s (contraction, B = A) or F_top (forward
 // solve, B operand) once per build, k_pack_g packs G_s once per system.
-// k_contract_tc, persistent blocks of 4 warps taking work units (128 x 128
+// k_contract_tc, persistent blocks of 6 warps taking work units (128 x 128
 // output tile pair I <= J of supernode s) from a counter, largest fronts first:
-//   * one thread streams the blocks of tiles I and J through three
-//     shared-memory stages with cp.async.bulk (mbarrier transaction counts)
-//     and issues tcgen05.mma (M = N = 128) into a 128-column TMEM
-//     accumulator, committing to the stage's release barrier;
+//   * a loader thread streams the blocks of tiles I and J through a ring of
+//     STAGES shared-memory stages with cp.async.bulk (mbarrier transaction
+//     counts), an MMA thread issues tcgen05.mma (M = N = 128) into a
+//     128-column TMEM accumulator as stages land, committing each stage to
+//     its release barrier;
 //   * the epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w..32w+31, i.e. the tile's rows) and adds the upper-triangle
 //     entries into W_H.
@@ -179,7 +180,7 @@ __device__ __forceinline__ void pack_tile(const float (*sy)[TM + 1], unsigned ch
 }
 
 // Packs, for the work units [plan[pa], plan[pb]) of a list over level_list
-// positions, 128-column x 32-row blocks of a front: unit (s, I, kt) holds rows
+// positions, 128-column x KT-row blocks of a front: unit (s, I, kt) holds rows
 // kt*KT.. of the source restricted to columns I*TM.., as PARTS planes of a
 // K-major TM x KT tile (tile row r = column I*TM + r, tile k = row kt*KT + k).
 // The source is the scaled front Y_s (rows from fr_ptr[s]) or the assembled top
@@ -267,17 +268,19 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- pipeline
-// CTA of 5 warps.  Warp 4 (lane 0) streams the nk K-blocks of A and B (B = A
-// when same) through the STAGES-deep shared-memory ring with cp.async.bulk and
-// issues the MMAs (M = N = 128); warps 0-3 own the tile's rows (warp w reads
-// TMEM lanes 32w..32w+31).  The tensor cores accumulate at most PROMOTE_KB
+// CTA of 6 warps.  Warp 5 (lane 0) streams the nk K-blocks of A and B (B = A
+// when same) through the STAGES-deep shared-memory ring with cp.async.bulk,
+// refilling a stage as soon as the MMAs that read it have completed; warp 4
+// (lane 0) issues the MMAs (M = N = 128) as soon as a stage has landed, so the
+// tensor pipe holds the MMAs of every landed stage while copies run ahead;
+// warps 0-3 own the tile's rows (warp w reads TMEM lanes 32w..32w+31).  The tensor cores accumulate at most PROMOTE_KB
 // K-blocks (128 K) into one of two 128-column TMEM buffers; the row warps then
 // add that partial tile into FP32 registers (IEEE adds) and free the buffer, so
 // the MMA's own accumulation never runs over more than 128 products.  Load,
 // MMA-chunk and buffer counters run over the CTA's whole life: stage or buffer
 // = count % depth, phase parity = (count / depth) & 1.  Every wait is bounded.
-constexpr int PROMOTE_KB = 4;
-constexpr int TC_THREADS = 160;
+constexpr int PROMOTE_KB = 128 / KT;   // K-blocks per TMEM chunk: 128 K
+constexpr int TC_THREADS = 192;
 constexpr uint32_t TMEM_COLS = 2 * TM;
 
 constexpr int UQ = 4;   // slots of the unit ring from the MMA-issuing thread to the accumulator warps
@@ -291,8 +294,8 @@ struct TcBars {
 };
 
 // The MMA-issuing thread takes work units from the list counter and publishes
-// each in the unit ring before it streams the unit's operands and issues its
-// MMAs; the accumulator warps take the units from the ring in the same order.
+// each in the unit ring before it issues the unit's MMAs; the loader warp and
+// the accumulator warps take the units from the ring in the same order.
 // The producer thus runs ahead into the next unit while the accumulator warps
 // still drain the last one (the TMEM buffers and the operand ring bound how
 // far).  Every wait is bounded and gives up when the other side has.
@@ -315,97 +318,101 @@ __device__ __forceinline__ int uq_pop(TcBars& br, uint32_t i, int lane, uint64_t
   return ur;
 }
 
-// warp 4, lane 0
+// warp 5, lane 0: the copies of one unit's nk K-blocks into the ring, each
+// into the next stage once the MMAs of its last use have completed (gl: the
+// CTA's running count of copies)
 template <int MODE>
-__device__ bool tc_produce(const unsigned char* blkA, const unsigned char* blkB, bool same, int nk,
-                           unsigned char* smem, TcBars& br, uint32_t tmem, uint32_t& gl, uint32_t& gm,
-                           uint32_t& gc, uint64_t wait_ns, const volatile int* alive) {
+__device__ bool tc_load(const unsigned char* blkA, const unsigned char* blkB, bool same, int nk,
+                        unsigned char* smem, TcBars& br, uint32_t& gl, uint64_t wait_ns, const volatile int* alive) {
+  using TR = TcTraits<MODE>;
+  constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
+  const uint32_t bytes = same ? BLK : 2 * BLK;
+  for (int kt = 0; kt < nk; ++kt) {
+    const uint32_t g = gl;
+    const int st = g % STAGES;
+    if (g >= STAGES && !mbar_wait(smem_u32(&br.empty[st]), ((g / STAGES) - 1) & 1, wait_ns, alive)) return false;
+    unsigned char* dA = smem + st * 2 * BLK;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&br.full[st])),
+                 "r"(bytes));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dA)),
+        "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
+        : "memory");
+    if (!same)
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+              smem_u32(dA + BLK)),
+          "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
+          : "memory");
+    ++gl;
+  }
+  return true;
+}
+
+// warp 5, lane 0, before the CTA exits: the last copy into every stage has
+// landed (bounded; no later copy reuses those stages, so each wait names one
+// phase), so no copy writes shared memory after the CTA is gone
+__device__ __forceinline__ void tc_load_drain(TcBars& br, uint32_t gl) {
+  for (uint32_t g = gl > (uint32_t)STAGES ? gl - STAGES : 0u; g < gl; ++g)
+    mbar_wait(smem_u32(&br.full[g % STAGES]), (g / STAGES) & 1, DRAIN_NS);
+}
+
+// warp 4, lane 0: the MMAs of one unit's nk K-blocks (gm: running count of
+// K-blocks multiplied, gc: of TMEM chunks); each stage is released to the
+// loader by a commit when its MMAs complete, each chunk's TMEM buffer handed
+// to the accumulator warps by a commit after its last K-block
+template <int MODE>
+__device__ bool tc_mma(bool same, int nk, unsigned char* smem, TcBars& br, uint32_t tmem, uint32_t& gm, uint32_t& gc,
+                       uint64_t wait_ns, const volatile int* alive) {
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   const uint32_t idesc = instr_desc(TR::TYPE);
   constexpr int SBO = (KT / (16 / TR::EB)) * 128;
-  const uint32_t bytes = same ? BLK : 2 * BLK;
   const int nchunks = (nk + PROMOTE_KB - 1) / PROMOTE_KB;
-  bool ok = true;
-  int nl = 0, nm = 0;
-  for (int kt = 0; kt < nk + STAGES - 1 && ok; ++kt) {
-    if (kt < nk) {   // load K-block kt
-      const uint32_t g = gl + kt;
-      const int st = g % STAGES;
-      if (g >= STAGES && !mbar_wait(smem_u32(&br.empty[st]), ((g / STAGES) - 1) & 1, wait_ns, alive)) {
-        ok = false;
-        break;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int ch = kc / PROMOTE_KB, first = kc % PROMOTE_KB == 0;
+    const bool last = kc % PROMOTE_KB == PROMOTE_KB - 1 || kc == nk - 1;
+    const uint32_t gb = gc + ch;                 // buffer use counter of this chunk
+    const uint32_t tb = tmem + (gb & 1) * TM;    // its 128 TMEM columns
+    if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1, wait_ns, alive))
+      return false;
+    const uint32_t g = gm + kc;
+    const int st = g % STAGES;
+    if (!mbar_wait(smem_u32(&br.full[st]), (g / STAGES) & 1, wait_ns, alive)) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const unsigned char* sA = smem + st * 2 * BLK;
+    const unsigned char* sB = same ? sA : sA + BLK;
+#pragma unroll
+    for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
+      const uint32_t off = kk * 256;   // two core matrices along K per MMA
+#pragma unroll
+      for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
+        const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
+        const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
+        const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
+        const uint32_t acc = (!first || kk > 0 || term > 0) ? 1u : 0u;
+        if constexpr (MODE == ICR_CONTRACT_BF16)
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                  tb),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        else
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                  tb),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
       }
-      unsigned char* dA = smem + st * 2 * BLK;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&br.full[st])),
-                   "r"(bytes));
-      asm volatile(
-          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-              smem_u32(dA)),
-          "l"(blkA + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
-          : "memory");
-      if (!same)
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                smem_u32(dA + BLK)),
-            "l"(blkB + (int64_t)kt * BLK), "r"((uint32_t)BLK), "r"(smem_u32(&br.full[st]))
-            : "memory");
-      ++nl;
     }
-    const int kc = kt - (STAGES - 1);
-    if (kc >= 0) {   // multiply K-block kc
-      const int ch = kc / PROMOTE_KB, first = kc % PROMOTE_KB == 0;
-      const bool last = kc % PROMOTE_KB == PROMOTE_KB - 1 || kc == nk - 1;
-      const uint32_t gb = gc + ch;                 // buffer use counter of this chunk
-      const uint32_t tb = tmem + (gb & 1) * TM;    // its 128 TMEM columns
-      if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1, wait_ns, alive)) {
-        ok = false;
-        break;
-      }
-      const uint32_t g = gm + kc;
-      const int st = g % STAGES;
-      if (!mbar_wait(smem_u32(&br.full[st]), (g / STAGES) & 1, wait_ns, alive)) {
-        ok = false;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const unsigned char* sA = smem + st * 2 * BLK;
-      const unsigned char* sB = same ? sA : sA + BLK;
-#pragma unroll
-      for (int kk = 0; kk < KT / TR::KMMA; ++kk) {
-        const uint32_t off = kk * 256;   // two core matrices along K per MMA
-#pragma unroll
-        for (int term = 0; term < (TR::PARTS == 2 ? 3 : 1); ++term) {
-          const int ai = term == 2 ? 1 : 0, bi = term == 1 ? 1 : 0;
-          const uint64_t ad = smem_desc(smem_u32(sA + ai * tile_bytes<MODE>()) + off, 128, SBO);
-          const uint64_t bd = smem_desc(smem_u32(sB + bi * tile_bytes<MODE>()) + off, 128, SBO);
-          const uint32_t acc = (!first || kk > 0 || term > 0) ? 1u : 0u;
-          if constexpr (MODE == ICR_CONTRACT_BF16)
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tb),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-          else
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                    tb),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-      }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+        smem_u32(&br.empty[st])));
+    if (last)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&br.empty[st])));
-      if (last)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&br.tfull[gb & 1])));
-      ++nm;
-    }
+          smem_u32(&br.tfull[gb & 1])));
   }
-  if (!ok)   // let copies already in flight land (full bound, no early abort)
-    for (uint32_t g = gm + nm; g < gl + nl; ++g) mbar_wait(smem_u32(&br.full[g % STAGES]), (g / STAGES) & 1, DRAIN_NS);
-  gl += nl;
-  gm += nm;
+  gm += nk;
   gc += nchunks;
-  return ok;
+  return true;
 }
 
 // warps 0-3: acc[0..127] <- sum over the unit's chunks of the row's TMEM columns
@@ -461,7 +468,7 @@ __device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volati
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.fin)), "r"(1));
     for (int i = 0; i < UQ; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.qfull[i])), "r"(1));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.qfree[i])), "r"(4));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.qfree[i])), "r"(5));
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n");
     *ok_sh = 1;
@@ -546,15 +553,38 @@ __device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restric
         if (ur >= total) break;
         int s, ncol, I, J, nk, k0, nku;
         decode(ur, s, ncol, I, J, nk, k0, nku);
-        if (!tc_produce<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK,
-                              pk + (boff[s] + (int64_t)J * nk + k0) * BLK, I == J, nku, smem, br, tmem, gl, gm, gc,
-                              wait_ns, &ok_sh)) {
+        if (!tc_mma<MODE>(I == J, nku, smem, br, tmem, gm, gc, wait_ns, &ok_sh)) {
           ok_sh = 0;
           atomicExch(dev_err, 1);
           break;
         }
       }
     }
+  } else if (warp == 5) {   // the loader
+    for (uint32_t i = 0;; ++i) {
+      const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
+      if (ur < 0) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      if (ur >= total) break;
+      int fine = 1;
+      if (lane == 0) {
+        int s, ncol, I, J, nk, k0, nku;
+        decode(ur, s, ncol, I, J, nk, k0, nku);
+        fine = tc_load<MODE>(pk + (boff[s] + (int64_t)I * nk + k0) * BLK, pk + (boff[s] + (int64_t)J * nk + k0) * BLK,
+                             I == J, nku, smem, br, gl, wait_ns, &ok_sh);
+        if (!fine) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, fine, 0)) break;
+    }
+    if (lane == 0) tc_load_drain(br, gl);
   } else {
     for (uint32_t i = 0;; ++i) {
       const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
@@ -670,15 +700,38 @@ __device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restr
         }
         if (ur >= total) break;
         const Unit x = decode(ur);
-        if (!tc_produce<MODE>(gpk + (goff[x.s] + (int64_t)x.rt * x.nk + x.k0) * BLK,
-                              fpk + (boff[x.s] + (int64_t)x.ct * x.nk + x.k0) * BLK, false, x.nku, smem, br, tmem, gl,
-                              gm, gc, wait_ns, &ok_sh)) {
+        if (!tc_mma<MODE>(false, x.nku, smem, br, tmem, gm, gc, wait_ns, &ok_sh)) {
           ok_sh = 0;
           atomicExch(dev_err, 1);
           break;
         }
       }
     }
+  } else if (warp == 5) {   // the loader
+    for (uint32_t i = 0;; ++i) {
+      const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
+      if (ur < 0) {
+        if (lane == 0) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+        break;
+      }
+      if (ur >= total) break;
+      int fine = 1;
+      if (lane == 0) {
+        const Unit x = decode(ur);
+        fine = tc_load<MODE>(gpk + (goff[x.s] + (int64_t)x.rt * x.nk + x.k0) * BLK,
+                             fpk + (boff[x.s] + (int64_t)x.ct * x.nk + x.k0) * BLK, false, x.nku, smem, br, gl,
+                             wait_ns, &ok_sh);
+        if (!fine) {
+          ok_sh = 0;
+          atomicExch(dev_err, 1);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, fine, 0)) break;
+    }
+    if (lane == 0) tc_load_drain(br, gl);
   } else {
     for (uint32_t i = 0;; ++i) {
       const int ur = uq_pop(br, i, lane, wait_ns, &ok_sh);
