@@ -80,8 +80,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // One thread per (contact, node): mark the contact in every supernode on the
 // etree path from the node's supernode to the root.  A thread stops at the
 // first supernode already marked for its contact: whoever marked it walks on.
-__device__ __forceinline__ void d_reach_mark(const VB& vb, const int* __restrict__ nodes, int m, const int* __restrict__ node_super,
-                             const int* __restrict__ parent, int ns, uint32_t* bitmap, int words) {
+__device__ __forceinline__ void d_reach_mark(const VB& vb, const int* __restrict__ nodes, int m,
+                                             const int* __restrict__ node_super, const int* __restrict__ parent,
+                                             int ns, uint32_t* bitmap, int words) {
   int t = vb.bx * blockDim.x + threadIdx.x;
   if (t >= 4 * m) return;
   int a = t >> 2;
@@ -113,8 +114,8 @@ struct reach_mark_body {
 
 // One block per supernode: count its contacts, prefix the per-word counts and
 // list the contacts in ascending order.
-__device__ __forceinline__ void d_reach_rows(const VB& vb, const uint32_t* __restrict__ bitmap, int words, int m, int* wprefix, int* qcount,
-                             int* qidx) {
+__device__ __forceinline__ void d_reach_rows(const VB& vb, const uint32_t* __restrict__ bitmap, int words, int m,
+                                             int* wprefix, int* qcount, int* qidx) {
   extern __shared__ int sh[];
   int s = vb.bx;
   int w = threadIdx.x;
@@ -156,9 +157,10 @@ struct reach_rows_body {
 };
 
 // Position of each of a supernode's contacts in its parent's contact list.
-__device__ __forceinline__ void d_reach_parentpos(const VB& vb, const uint32_t* __restrict__ bitmap, const int* __restrict__ wprefix, int words,
-                                  int m, const int* __restrict__ parent, const int* __restrict__ qcount,
-                                  const int* __restrict__ qidx, int* qpos) {
+__device__ __forceinline__ void d_reach_parentpos(const VB& vb, const uint32_t* __restrict__ bitmap,
+                                                  const int* __restrict__ wprefix, int words, int m,
+                                                  const int* __restrict__ parent, const int* __restrict__ qcount,
+                                                  const int* __restrict__ qidx, int* qpos) {
   int s = vb.by;
   int j = vb.bx * blockDim.x + threadIdx.x;
   if (j >= qcount[s]) return;
@@ -191,8 +193,8 @@ struct reach_parentpos_body {
 
 // For every supernode c: the local position in c's contact list of each
 // contact of its parent's list (-1 when the contact does not reach c).
-__device__ __forceinline__ void d_reach_inv(const VB& vb, int m, const int* __restrict__ parent, const int* __restrict__ qcount,
-                            const int* __restrict__ qpos, int* qinv) {
+__device__ __forceinline__ void d_reach_inv(const VB& vb, int m, const int* __restrict__ parent,
+                                            const int* __restrict__ qcount, const int* __restrict__ qpos, int* qinv) {
   const int c = vb.bx;
   const int p = parent[c];
   if (p < 0) return;
@@ -303,10 +305,11 @@ __device__ __forceinline__ void plan_counts(int s, const int* __restrict__ super
 // tensor-core contraction, with fewer tiles than target (one per SM) split
 // their units over K into about target / tiles parts (plan counters area,
 // after the 2 + nlev counters: nlev level factors, then the contraction's).
-__device__ __forceinline__ void d_plan(const VB& vb, int ns, const int* __restrict__ level_list, const int* __restrict__ super_ptr,
-           const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ qcount, int simt_max, int tc_min,
-           int tc_gemm, const unsigned char* __restrict__ tc_super, const int* __restrict__ level_first, int nlev,
-           int target, int* plan) {
+__device__ __forceinline__ void d_plan(const VB& vb, int ns, const int* __restrict__ level_list,
+                                       const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                                       const int* __restrict__ qcount, int simt_max, int tc_min, int tc_gemm,
+                                       const unsigned char* __restrict__ tc_super,
+                                       const int* __restrict__ level_first, int nlev, int target, int* plan) {
   __shared__ int wsum[PLAN_LISTS][32];
   __shared__ int tiles[PLAN_MAX_LEV + 1];   // unsplit tensor-core tiles per level; [PLAN_MAX_LEV]: contraction
   __shared__ int split[PLAN_MAX_LEV + 1];
@@ -395,7 +398,8 @@ __global__ void __launch_bounds__(1024)
            int tc_gemm, const unsigned char* __restrict__ tc_super, const int* __restrict__ level_first, int nlev,
            int target, int* plan) {
   pdl_entry();
-  d_plan(own_block(), ns, level_list, super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, level_first, nlev, target, plan);
+  d_plan(own_block(), ns, level_list, super_ptr, rowpat_ptr, qcount, simt_max, tc_min, tc_gemm, tc_super, level_first,
+         nlev, target, plan);
 }
 
 struct plan_body {
@@ -446,12 +450,14 @@ __device__ __forceinline__ T assemble_entry(int s, int row, int kl, int d, int c
 // row (extend-add as a gather, children in ascending order).  Rows < w go to
 // Ftop, rows >= w to the front's update rows.
 template <class T>
-__device__ __forceinline__ void d_assemble(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
-               const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
-               const int64_t* __restrict__ fr_ptr, const int* __restrict__ ctr_ptr,
-               const int* __restrict__ ctr_child, const int* __restrict__ ctr_row, const int* __restrict__ nodes,
-               const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
-               const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
+__device__ __forceinline__ void d_assemble(const VB& vb, const int* __restrict__ plan, int pa, int pb,
+                                           const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+                                           const int64_t* __restrict__ rowpat_ptr, const int64_t* __restrict__ fr_ptr,
+                                           const int* __restrict__ ctr_ptr, const int* __restrict__ ctr_child,
+                                           const int* __restrict__ ctr_row, const int* __restrict__ nodes,
+                                           const T* __restrict__ bary, const int* __restrict__ qcount,
+                                           const int* __restrict__ qidx, const int* __restrict__ qinv, int m, T* X,
+                                           T* Ftop, int64_t ldx) {
   const int u1 = plan[pb];
   for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {
     const int pos = find_pos(plan, pa, pb, u);
@@ -489,7 +495,8 @@ __global__ void __launch_bounds__(AR * TCOLS)
                const T* __restrict__ bary, const int* __restrict__ qcount, const int* __restrict__ qidx,
                const int* __restrict__ qinv, int m, T* X, T* Ftop, int64_t ldx) {
   pdl_entry();
-  d_assemble<T>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, fr_ptr, ctr_ptr, ctr_child, ctr_row, nodes, bary, qcount, qidx, qinv, m, X, Ftop, ldx);
+  d_assemble<T>(own_block(), plan, pa, pb, level_list, super_ptr, rowpat_ptr, fr_ptr, ctr_ptr, ctr_child, ctr_row,
+                nodes, bary, qcount, qidx, qinv, m, X, Ftop, ldx);
 }
 
 template <class T>
@@ -609,8 +616,8 @@ __device__ __forceinline__ void d_front_gemm(const VB& vb, const int* __restrict
                                              const int* __restrict__ level_list, const int* __restrict__ super_ptr,
                                              const int64_t* __restrict__ rowpat_ptr,
                                              const int64_t* __restrict__ val_ptr, const T* __restrict__ G,
-                                             const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
-                                             T* X, const T* __restrict__ Ftop, int64_t ldx) {
+                                             const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount, T* X,
+                                             const T* __restrict__ Ftop, int64_t ldx) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sG = (T*)smraw;                                  // 2 x KB x GLD
   T* sF = sG + 2 * KB * GemmTile<RPT>::GLD;           // 2 x KB x FLD
@@ -663,9 +670,10 @@ static size_t gemm_smem_bytes() {
 // FP32 except within 2^-48 (relative) of a rounding midpoint, where the FP64
 // route rounds twice as well.  The FP32 units do it at their full rate.
 template <class T>
-__device__ __forceinline__ void d_scale(const VB& vb, int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
-                        const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
-                        const double* __restrict__ dinvsqrt, T* X, int64_t ldx) {
+__device__ __forceinline__ void d_scale(const VB& vb, int n, const int* __restrict__ dof_super,
+                                        const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+                                        const int* __restrict__ qcount, const double* __restrict__ dinvsqrt, T* X,
+                                        int64_t ldx) {
   const int row = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -708,10 +716,11 @@ struct scale_body {
 // it.  Blocks take units from a counter, largest supernodes (the end of
 // level_list) first.
 template <class T>
-__device__ __forceinline__ void d_contract(const VB& vb, const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
-               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
-               const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
-               const T* __restrict__ X, int64_t ldx, T* WH, int64_t ldw) {
+__device__ __forceinline__ void d_contract(const VB& vb, const int* __restrict__ plan, int* counter, int ns,
+                                           const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+                                           const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                                           const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
+                                           T* WH, int64_t ldw) {
   __shared__ T sA[CK_][CT + 1];
   __shared__ T sB[CK_][CT + 1];
   __shared__ int unit_sh, pos_sh;
@@ -895,8 +904,8 @@ __device__ __forceinline__ T w_operand(T x) {
 
 template <class T, int WM>
 __device__ __forceinline__ void d_update_W(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ WH,
-                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wblk, int bc,
-                           const int* __restrict__ stop) {
+                                           const __nv_bfloat16* __restrict__ WH16, T* W, int64_t ldw, T* wblk, int bc,
+                                           const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
   if (vb.bx < vb.by) return;   // the block pairs of the upper triangle only (uniform)
   __shared__ bits_t<T> mxa[16], mxb[16];
@@ -1400,9 +1409,10 @@ __device__ __noinline__ void pgs_defer_leave(PgsDefer<T>* d, int m, int pb, int 
 
 
 template <class T, int BC>
-__device__ __forceinline__ void d_pgs(const VB& vb, int m, int sweeps, double tol, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-          const T* __restrict__ mu, const T* __restrict__ wblk, T* pgsb, T* lam_g, int warm, PgsDevStats* st,
-          const int* __restrict__ stop) {
+__device__ __forceinline__ void d_pgs(const VB& vb, int m, int sweeps, double tol, const T* __restrict__ W,
+                                      int64_t ldw, const T* __restrict__ delta, const T* __restrict__ mu,
+                                      const T* __restrict__ wblk, T* pgsb, T* lam_g, int warm, PgsDevStats* st,
+                                      const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;   // uniform, before any shared memory or barrier
   constexpr int BR = 3 * BC;
   constexpr int CH = 16 / (int)sizeof(T);      // elements per 16-byte copy
@@ -2042,8 +2052,9 @@ static size_t pgs_smem_bytes(int m) {
 
 // FP64 residuals of the final iterate: one warp per contact.
 template <class T>
-__device__ __forceinline__ void d_pgs_residual(const VB& vb, int m, const T* __restrict__ W, int64_t ldw, const T* __restrict__ delta,
-                               const T* __restrict__ mu, const T* __restrict__ lam, double rel, PgsDevStats* st) {
+__device__ __forceinline__ void d_pgs_residual(const VB& vb, int m, const T* __restrict__ W, int64_t ldw,
+                                               const T* __restrict__ delta, const T* __restrict__ mu,
+                                               const T* __restrict__ lam, double rel, PgsDevStats* st) {
   const int a = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= m) return;
@@ -2145,8 +2156,8 @@ struct newton_check_body {
 
 // ------------------------------------------------------------------ a8 proximity update
 template <class T>
-__device__ __forceinline__ void d_prox_u(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam, T* uk, double* u,
-                         const int* __restrict__ stop) {
+__device__ __forceinline__ void d_prox_u(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam,
+                                         T* uk, double* u, const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
   int a = vb.bx * blockDim.x + threadIdx.x;
   if (a >= m) return;
@@ -2181,8 +2192,9 @@ struct prox_u_body {
 // shared memory (12 flops per contact), CTA 0 also adds it to u (FP64), and
 // each warp takes one row of W_H.
 template <class T>
-__device__ __forceinline__ void d_prox(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam, const T* __restrict__ WH,
-                       double* u, double* p, double* dp, const int* __restrict__ stop) {
+__device__ __forceinline__ void d_prox(const VB& vb, int m, const T* __restrict__ C, const T* __restrict__ lam,
+                                       const T* __restrict__ WH, double* u, double* p, double* dp,
+                                       const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* uk = (T*)smraw;   // 3m
@@ -2235,8 +2247,8 @@ struct prox_body {
 };
 
 template <class T>
-__device__ __forceinline__ void d_prox_p(const VB& vb, int m, const T* __restrict__ WH, const T* __restrict__ uk, double* p, double* dp,
-                         const int* __restrict__ stop) {
+__device__ __forceinline__ void d_prox_p(const VB& vb, int m, const T* __restrict__ WH, const T* __restrict__ uk,
+                                         double* p, double* dp, const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
   const int i = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -2273,10 +2285,11 @@ struct prox_p_body {
 // y = D^-1 X u = D^-1/2 (Y u), one warp per DOF row (Y holds the scaled front
 // rows, restricted to the contacts reaching them); u in the working precision
 template <class T>
-__device__ __forceinline__ void d_xu(const VB& vb, int n, const int* __restrict__ dof_super, const int* __restrict__ super_ptr,
-                     const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
-                     const int* __restrict__ qidx, int m, const T* __restrict__ X, int64_t ldx,
-                     const T* __restrict__ u, const double* __restrict__ dinvsqrt, T* y) {
+__device__ __forceinline__ void d_xu(const VB& vb, int n, const int* __restrict__ dof_super,
+                                     const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
+                                     const int* __restrict__ qcount, const int* __restrict__ qidx, int m,
+                                     const T* __restrict__ X, int64_t ldx, const T* __restrict__ u,
+                                     const double* __restrict__ dinvsqrt, T* y) {
   const int row = vb.bx * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
@@ -2340,9 +2353,10 @@ struct u_round_body {
 // Backward solve L^T dq = y for the supernodes of one level (top-down):
 // dq_s = G_s^T [y_s ; -dq_R], one warp per DOF column of the supernode.
 template <class T>
-__device__ __forceinline__ void d_bsolve(const VB& vb, const int* __restrict__ level_list, int lvl_first, int nchunk, const int* __restrict__ super_ptr,
-             const int64_t* __restrict__ rowpat_ptr, const int* __restrict__ rowpat,
-             const int64_t* __restrict__ val_ptr, const T* __restrict__ G, const T* __restrict__ y, T* dq) {
+__device__ __forceinline__ void d_bsolve(const VB& vb, const int* __restrict__ level_list, int lvl_first, int nchunk,
+                                         const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
+                                         const int* __restrict__ rowpat, const int64_t* __restrict__ val_ptr,
+                                         const T* __restrict__ G, const T* __restrict__ y, T* dq) {
   const int s = level_list[lvl_first + vb.bx / nchunk];
   const int k = (vb.bx % nchunk) * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -2386,9 +2400,9 @@ struct bsolve_body {
 // C and delta are stored in (FP64 arithmetic is a slow path on this part).
 template <class T>
 __device__ __forceinline__ void d_linearize(const VB& vb, int m, int kind, const double* __restrict__ normals_k,
-                            const double* __restrict__ anchors, const double* __restrict__ spheres,
-                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C, T* delta,
-                            const int* __restrict__ stop) {
+                                            const double* __restrict__ anchors, const double* __restrict__ spheres,
+                                            const int* __restrict__ sphere_of, const double* __restrict__ p, T* C,
+                                            T* delta, const int* __restrict__ stop) {
   if (newton_stopped(stop)) return;
   int a = vb.bx * blockDim.x + threadIdx.x;
   if (a >= m) return;
@@ -2696,8 +2710,9 @@ static int prox_T(Scene* s) {
 
 // one thread per contact: its entries of every per-contact buffer
 template <class T>
-__device__ __forceinline__ void d_reset_contacts(const VB& vb, int mm, T* lam, T* lam0, T* mu, T* delta, T* C, double* p, double* p0, double* u,
-                                 int* stats, int nstats, int* dev_err) {
+__device__ __forceinline__ void d_reset_contacts(const VB& vb, int mm, T* lam, T* lam0, T* mu, T* delta, T* C,
+                                                 double* p, double* p0, double* u, int* stats, int nstats,
+                                                 int* dev_err) {
   const int a = vb.bx * blockDim.x + threadIdx.x;
   if (a < mm) {
 #pragma unroll
@@ -2739,11 +2754,12 @@ struct reset_contacts_body {
 // one thread per contact: the inputs of icr_set_step_inputs from the staging
 // buffer, and the contact state reset as in k_reset_contacts
 template <class T>
-__device__ __forceinline__ void d_unpack_inputs(const VB& vb, int m, int nsph, const unsigned char* __restrict__ stg, int64_t o_nodes,
-                                int64_t o_of, int64_t o_bary, int64_t o_mu, int64_t o_p0, int64_t o_anch,
-                                int64_t o_sph, int* nodes, int* sphere_of, T* bary, T* mu, double* p, double* p0,
-                                double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C, double* u,
-                                int* stats, int nstats, int* dev_err) {
+__device__ __forceinline__ void d_unpack_inputs(const VB& vb, int m, int nsph, const unsigned char* __restrict__ stg,
+                                                int64_t o_nodes, int64_t o_of, int64_t o_bary, int64_t o_mu,
+                                                int64_t o_p0, int64_t o_anch, int64_t o_sph, int* nodes,
+                                                int* sphere_of, T* bary, T* mu, double* p, double* p0,
+                                                double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C,
+                                                double* u, int* stats, int nstats, int* dev_err) {
   const int a = vb.bx * blockDim.x + threadIdx.x;
   if (a < m) {
     const int* sn = (const int*)(stg + o_nodes);
@@ -2783,7 +2799,8 @@ __global__ void k_unpack_inputs(int m, int nsph, const unsigned char* __restrict
                                 double* anchors, double* spheres, T* lam, T* lam0, T* delta, T* C, double* u,
                                 int* stats, int nstats, int* dev_err) {
   pdl_entry();
-  d_unpack_inputs<T>(own_block(), m, nsph, stg, o_nodes, o_of, o_bary, o_mu, o_p0, o_anch, o_sph, nodes, sphere_of, bary, mu, p, p0, anchors, spheres, lam, lam0, delta, C, u, stats, nstats, dev_err);
+  d_unpack_inputs<T>(own_block(), m, nsph, stg, o_nodes, o_of, o_bary, o_mu, o_p0, o_anch, o_sph, nodes, sphere_of,
+                     bary, mu, p, p0, anchors, spheres, lam, lam0, delta, C, u, stats, nstats, dev_err);
 }
 
 template <class T>

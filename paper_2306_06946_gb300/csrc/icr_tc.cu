@@ -187,10 +187,11 @@ __device__ __forceinline__ void pack_tile(const float (*sy)[TM + 1], unsigned ch
 // rows F_top (rows from super_ptr[s]).  Staged through shared memory so that
 // global reads and writes are coalesced.
 template <int MODE>
-__device__ __forceinline__ void d_pack_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
-              const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
-              const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
-              int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
+__device__ __forceinline__ void d_pack_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb,
+                                          const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+                                          const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                                          const int64_t* __restrict__ boff, const float* __restrict__ src,
+                                          int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
   const int u1 = plan[pb];
@@ -496,10 +497,13 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
 // of supernode s) from a counter, largest fronts first; the row warps add the
 // tile's upper-triangle entries into W_H.
 template <int MODE>
-__device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restrict__ plan, int* counter, int ns, const int* __restrict__ level_list,
-                  const int* __restrict__ super_ptr, const int* __restrict__ qcount, const int* __restrict__ qidx,
-                  const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
-                  int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p, uint64_t wait_ns) {
+__device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restrict__ plan, int* counter, int ns,
+                                              const int* __restrict__ level_list, const int* __restrict__ super_ptr,
+                                              const int* __restrict__ qcount, const int* __restrict__ qidx,
+                                              const int64_t* __restrict__ boff, int m,
+                                              const unsigned char* __restrict__ pk, float* WH, int64_t ldw,
+                                              int* dev_err, int cache_plan, const int* __restrict__ tsplit_p,
+                                              uint64_t wait_ns) {
   using TR = TcTraits<MODE>;
   constexpr int BLK = TR::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];   // STAGES x (A block, B block), then the list's prefix
@@ -629,7 +633,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                   const int64_t* __restrict__ boff, int m, const unsigned char* __restrict__ pk, float* WH,
                   int64_t ldw, int* dev_err, int cache_plan, const int* __restrict__ tsplit_p, uint64_t wait_ns) {
   pdl_entry();
-  d_contract_tc<MODE>(own_block(), plan, counter, ns, level_list, super_ptr, qcount, qidx, boff, m, pk, WH, ldw, dev_err, cache_plan, tsplit_p, wait_ns);
+  d_contract_tc<MODE>(own_block(), plan, counter, ns, level_list, super_ptr, qcount, qidx, boff, m, pk, WH, ldw,
+                      dev_err, cache_plan, tsplit_p, wait_ns);
 }
 
 template <int MODE>
@@ -648,12 +653,16 @@ struct contract_tc_body {
 // 128-column tile ct of its 3|Q_s| columns) from the level's counter, largest
 // fronts first, and form out = G_s[rt rows, :] F_top[:, ct columns]; rows < w
 // store X_s = out, the update rows take U_s -= out.
-__device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb, int* counter, const int* __restrict__ level_list,
-                    const int* __restrict__ super_ptr, const int64_t* __restrict__ rowpat_ptr,
-                    const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
-                    const int64_t* __restrict__ goff, const unsigned char* __restrict__ gpk,
-                    const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
-                    int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
+__device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restrict__ plan, int pa, int pb,
+                                                int* counter, const int* __restrict__ level_list,
+                                                const int* __restrict__ super_ptr,
+                                                const int64_t* __restrict__ rowpat_ptr,
+                                                const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
+                                                const int64_t* __restrict__ goff,
+                                                const unsigned char* __restrict__ gpk,
+                                                const int64_t* __restrict__ boff,
+                                                const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
+                                                int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
   constexpr int MODE = ICR_CONTRACT_TF32X3;
   constexpr int BLK = TcTraits<MODE>::PARTS * tile_bytes<MODE>();
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -803,7 +812,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const int64_t* __restrict__ boff, const unsigned char* __restrict__ fpk, float* X, int64_t ldx,
                     int* dev_err, const int* __restrict__ gsplit_p, uint64_t wait_ns) {
   pdl_entry();
-  d_front_gemm_tc(own_block(), plan, pa, pb, counter, level_list, super_ptr, rowpat_ptr, fr_ptr, qcount, goff, gpk, boff, fpk, X, ldx, dev_err, gsplit_p, wait_ns);
+  d_front_gemm_tc(own_block(), plan, pa, pb, counter, level_list, super_ptr, rowpat_ptr, fr_ptr, qcount, goff, gpk,
+                  boff, fpk, X, ldx, dev_err, gsplit_p, wait_ns);
 }
 
 struct front_gemm_tc_body {
