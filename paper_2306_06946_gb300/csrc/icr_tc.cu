@@ -282,13 +282,21 @@ __global__ void __launch_bounds__(256)
 // = count % depth, phase parity = (count / depth) & 1.  Every wait is bounded.
 constexpr int PROMOTE_KB = 128 / KT;   // K-blocks per TMEM chunk: 128 K
 constexpr int TC_THREADS = 192;
-constexpr uint32_t TMEM_COLS = 2 * TM;
+// TMEM accumulator buffers of 128 columns: four (all 512 columns of the SM)
+// in 3xTF32 mode, where the shared-memory ring keeps one CTA per SM, so that
+// the MMA thread can run up to four chunks ahead of a unit's epilogue; two
+// in the TF32 and BF16 modes, which fit two CTAs per SM
+template <int MODE>
+__host__ __device__ constexpr int tmem_bufs() {
+  return TcTraits<MODE>::PARTS == 2 ? 4 : 2;
+}
+constexpr int TMEM_MAX_BUFS = 4;
 
 constexpr int UQ = 4;   // slots of the unit ring from the MMA-issuing thread to the accumulator warps
 
 struct TcBars {
   uint64_t full[STAGES], empty[STAGES];   // shared-memory ring
-  uint64_t tfull[2], tfree[2];            // TMEM buffers: MMAs done / drained
+  uint64_t tfull[TMEM_MAX_BUFS], tfree[TMEM_MAX_BUFS];   // TMEM buffers: MMAs done / drained
   uint64_t fin;                           // teardown: every MMA issued has completed
   uint64_t qfull[UQ], qfree[UQ];          // unit ring: unit published / taken by the four accumulator warps
   int uq[UQ];                             // unit ring: the work-list counter value of each unit (>= total: end)
@@ -375,8 +383,9 @@ __device__ bool tc_mma(bool same, int nk, unsigned char* smem, TcBars& br, uint3
     const int ch = kc / PROMOTE_KB, first = kc % PROMOTE_KB == 0;
     const bool last = kc % PROMOTE_KB == PROMOTE_KB - 1 || kc == nk - 1;
     const uint32_t gb = gc + ch;                 // buffer use counter of this chunk
-    const uint32_t tb = tmem + (gb & 1) * TM;    // its 128 TMEM columns
-    if (first && gb >= 2 && !mbar_wait(smem_u32(&br.tfree[gb & 1]), ((gb >> 1) - 1) & 1, wait_ns, alive))
+    constexpr int NB = tmem_bufs<MODE>();
+    const uint32_t tb = tmem + (gb % NB) * TM;   // its 128 TMEM columns
+    if (first && gb >= NB && !mbar_wait(smem_u32(&br.tfree[gb % NB]), ((gb / NB) - 1) & 1, wait_ns, alive))
       return false;
     const uint32_t g = gm + kc;
     const int st = g % STAGES;
@@ -409,7 +418,7 @@ __device__ bool tc_mma(bool same, int nk, unsigned char* smem, TcBars& br, uint3
         smem_u32(&br.empty[st])));
     if (last)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&br.tfull[gb & 1])));
+          smem_u32(&br.tfull[gb % NB])));
   }
   gm += nk;
   gc += nchunks;
@@ -417,19 +426,20 @@ __device__ bool tc_mma(bool same, int nk, unsigned char* smem, TcBars& br, uint3
 }
 
 // warps 0-3: acc[0..127] <- sum over the unit's chunks of the row's TMEM columns
+template <int NB>
 __device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, uint32_t& gc, float* acc,
                          uint64_t wait_ns, const volatile int* alive) {
   const int nchunks = (nk + PROMOTE_KB - 1) / PROMOTE_KB;
   bool ok = true;
   for (int ch = 0; ch < nchunks; ++ch) {
     const uint32_t gb = gc + ch;
-    const int fine = ok && mbar_wait(smem_u32(&br.tfull[gb & 1]), (gb >> 1) & 1, wait_ns, alive);
+    const int fine = ok && mbar_wait(smem_u32(&br.tfull[gb % NB]), (gb / NB) & 1, wait_ns, alive);
     if (!__all_sync(0xffffffffu, fine)) {
       ok = false;
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    const uint32_t base = tmem + (gb & 1) * TM + ((uint32_t)(32 * warp) << 16);
+    const uint32_t base = tmem + (gb % NB) * TM + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
     for (int c0j = 0; c0j < TM; c0j += 16) {
       uint32_t v[16];
@@ -444,17 +454,18 @@ __device__ bool tc_drain(int nk, TcBars& br, uint32_t tmem, int warp, int lane, 
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncwarp();
-    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&br.tfree[gb & 1])));
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&br.tfree[gb % NB])));
   }
   gc += nchunks;
   return ok;
 }
 
+template <int NB>
 __device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volatile int* ok_sh) {
   const int tid = threadIdx.x;
   if ((tid >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_base)),
-                 "r"(TMEM_COLS));
+                 "r"((uint32_t)(NB * TM)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
@@ -462,7 +473,7 @@ __device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volati
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.full[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.empty[i])), "r"(1));
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NB; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.tfull[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&br.tfree[i])), "r"(4));
     }
@@ -480,6 +491,7 @@ __device__ __forceinline__ void tc_setup(uint32_t* tmem_base, TcBars& br, volati
 }
 
 // every MMA the CTA issued has completed (bounded) before TMEM is freed
+template <int NB>
 __device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
   if (threadIdx.x == 128) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
@@ -490,7 +502,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, TcBars& br) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)(NB * TM)));
 }
 
 // Contraction: persistent CTAs take units (128 x 128 output tile pair I <= J
@@ -521,7 +533,7 @@ __device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restric
     for (int i = tid; i <= ns; i += TC_THREADS) ps[i] = plan[i];
     plan_s = ps;
   }
-  tc_setup(&tmem_base, br, &ok_sh);
+  tc_setup<tmem_bufs<MODE>()>(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
   // unit ur (counter value): supernode s, tile pair I <= J, K part [k0, k0 + nku)
@@ -603,7 +615,7 @@ __device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restric
       int s, ncol, I, J, nk, k0, nku;
       decode(ur, s, ncol, I, J, nk, k0, nku);
       float acc[TM];
-      if (!tc_drain(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
+      if (!tc_drain<tmem_bufs<MODE>()>(nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
         if (lane == 0) {
           ok_sh = 0;
           atomicExch(dev_err, 1);
@@ -623,7 +635,7 @@ __device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restric
       }
     }
   }
-  tc_teardown(tmem, br);
+  tc_teardown<tmem_bufs<MODE>()>(tmem, br);
 }
 
 template <int MODE>
@@ -673,7 +685,7 @@ __device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restr
   if ((int)vb.bx >= total) return;   // uniform: before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gsplit = *gsplit_p;
-  tc_setup(&tmem_base, br, &ok_sh);
+  tc_setup<tmem_bufs<MODE>()>(&tmem_base, br, &ok_sh);
   const uint32_t tmem = tmem_base;
   uint32_t gl = 0, gm = 0, gc = 0;
   // unit ur (counter value): supernode s, 128-row tile rt, 128-column tile ct, K part [k0, k0 + nku)
@@ -754,7 +766,7 @@ __device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restr
       if (ur >= total) break;
       const Unit x = decode(ur);
       float acc[TM];
-      if (!tc_drain(x.nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
+      if (!tc_drain<tmem_bufs<MODE>()>(x.nku, br, tmem, warp, lane, gc, acc, wait_ns, &ok_sh)) {
         if (lane == 0) {
           ok_sh = 0;
           atomicExch(dev_err, 1);
@@ -801,7 +813,7 @@ __device__ __forceinline__ void d_front_gemm_tc(const VB& vb, const int* __restr
       }
     }
   }
-  tc_teardown(tmem, br);
+  tc_teardown<tmem_bufs<MODE>()>(tmem, br);
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
