@@ -435,7 +435,8 @@ int icr_batch_info(icr_batch* batch, icr_batch_info_t* out);
 /* One batched step run eagerly (not through the graph) with CUDA events
  * around every merged launch (diagnostic; the paper has no counterpart).
  * Synchronises; writes up to max_out entries in launch order (grouped by
- * group) and the number of merged launches to *n_out.  name: the kernel (or
+ * group) and the number of merged launches to *n_out.  ICR_ESTATE when a scene
+ * changed since creation, as icr_batch_launch.  name: the kernel (or
  * "copies/fills"), slots: scenes (copies and fills: operations) it covers. */
 typedef struct icr_batch_launch_time {
   char name[32];

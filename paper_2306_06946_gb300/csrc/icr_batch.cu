@@ -526,22 +526,36 @@ int icr_batch_create(icr_batch** out, icr_scene* const* scenes, int32_t n_scenes
   return ICR_OK;
 }
 
-int icr_batch_launch(icr_batch* b) {
-  if (!b) {
-    set_error("batch_launch: NULL batch");
-    return ICR_EINVAL;
-  }
+}  // extern "C"
+
+namespace {
+// the recorded launches hold the scenes' device addresses and launch shapes:
+// ICR_ESTATE once a scene was evicted, reallocated a buffer, or changed its
+// contact count, obstacle kind or parameters
+int check_batch(const icr_batch* b, const char* where) {
   for (size_t i = 0; i < b->scenes.size(); ++i) {
     const Scene* s = b->scenes[i];
     const icr_batch::Snap& sn = b->snaps[i];
     if (s->evicted || s->alloc_epoch != sn.epoch || s->m != sn.m || s->obst_kind != sn.obst ||
         std::memcmp(&s->params, &sn.params, sizeof(icr_params)) != 0) {
-      set_error("batch_launch: scene %zu changed since the batch was created (evicted, buffers, contact count, "
-                "obstacle or parameters); create the batch again",
-                i);
+      set_error("%s: scene %zu changed since the batch was created (evicted, buffers, contact count, obstacle or "
+                "parameters); create the batch again",
+                where, i);
       return ICR_ESTATE;
     }
   }
+  return ICR_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int icr_batch_launch(icr_batch* b) {
+  if (!b) {
+    set_error("batch_launch: NULL batch");
+    return ICR_EINVAL;
+  }
+  RET(check_batch(b, "batch_launch"));
   CKB(cudaSetDevice(b->ctx->device));
   CKB(cudaGraphLaunch(b->graph, b->ctx->stream));
   ++b->steps;
@@ -575,6 +589,7 @@ int icr_batch_profile(icr_batch* b, icr_batch_launch_time* out, int32_t max_out,
     set_error("batch_profile: invalid arguments");
     return ICR_EINVAL;
   }
+  RET(check_batch(b, "batch_profile"));
   CKB(cudaSetDevice(b->ctx->device));
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev(b->launches.size(), {nullptr, nullptr});
   auto release = [&](int rc) {

@@ -290,9 +290,9 @@ class Batch:
     def profile(self) -> list[dict]:
         """One eager batched step with CUDA events around every merged launch."""
         n = ct.c_int32()
-        _check(lib().icr_batch_profile(self.h, None, 0, ct.byref(n)))
-        arr = (BatchLaunchTime * max(1, n.value))()
-        _check(lib().icr_batch_profile(self.h, arr, n.value, ct.byref(n)))
+        size = max(1, self.info()["launches_per_step"])
+        arr = (BatchLaunchTime * size)()
+        _check(lib().icr_batch_profile(self.h, arr, size, ct.byref(n)))
         return [{"name": a.name.decode(), "group": a.group, "slots": a.slots, "blocks": a.blocks, "ms": a.ms}
                 for a in arr[:n.value]]
 

@@ -57,3 +57,18 @@ def test_null_arguments_are_rejected_without_gpu(libicr):
 def test_kernels_are_built_for_sm103a():
     from paper_2306_06946_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_batch_calls_reject_null_arguments_without_gpu(libicr):
+    # every batch entry point checks its arguments before any CUDA call
+    for name in ("icr_batch_create", "icr_batch_launch", "icr_batch_info", "icr_batch_profile"):
+        getattr(libicr, name).restype = ctypes.c_int
+    assert libicr.icr_batch_create(None, None, 0, 1, 1) == 1            # ICR_EINVAL
+    out = ctypes.c_void_p()
+    assert libicr.icr_batch_create(ctypes.byref(out), None, 1, 1, 1) == 1
+    assert libicr.icr_batch_launch(None) == 1
+    assert libicr.icr_batch_info(None, None) == 1
+    n = ctypes.c_int32()
+    assert libicr.icr_batch_profile(None, None, 0, ctypes.byref(n)) == 1
+    libicr.icr_batch_destroy.restype = ctypes.c_int
+    assert libicr.icr_batch_destroy(None) == 0                          # ICR_OK: nothing to free

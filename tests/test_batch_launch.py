@@ -82,8 +82,15 @@ def test_batch_equals_alone_and_oracle(members, oracle_refs, torch_mod, prec, gr
             ref = oracle_refs[i]
             assert rel(dq, ref["dq"]) < tol_oracle, (i, s.n, s.m)
             assert rel(lam, ref["iters"][-1]["lam"]) < tol_oracle, (i, s.n, s.m)
+    prof = b.profile()                # one more step, eager, with events around each merged launch
+    assert len(prof) == b.info()["launches_per_step"]
+    assert all(p["ms"] >= 0 and 0 <= p["group"] < groups and p["slots"] >= 1 for p in prof)
+    assert sum(1 for p in prof if p["name"] != "copies/fills") == b.info()["kernel_launches_per_step"]
+    stream.synchronize()
+    for i, sc in enumerate(scenes):
+        assert rel(sc.get("DQ"), alone[i][0]) < tol_alone
     info = b.info()
-    assert info["n_scenes"] == len(members) and info["steps"] == 2 and info["n_groups"] == groups
+    assert info["n_scenes"] == len(members) and info["steps"] == 3 and info["n_groups"] == groups
     # the scenes' launches share kernels: far fewer launches than one by one
     assert info["kernel_launches_per_step"] * (4 if groups == 1 else 2) < info["scene_launches_per_step"]
     b.close()
@@ -149,6 +156,9 @@ def test_batch_argument_and_state_errors(members, torch_mod):
     a.set_mapping(s.nodes[:keep], s.bary[:keep])
     with pytest.raises(icr.IcrError) as e:
         b.launch()
+    assert e.value.code == icr.ESTATE
+    with pytest.raises(icr.IcrError) as e:
+        b.profile()                                  # the eager path refuses a stale batch too
     assert e.value.code == icr.ESTATE
     b.close()
     for x in (a, c, other, bare):
