@@ -191,10 +191,12 @@ __device__ __forceinline__ void d_pack_tc(const VB& vb, const int* __restrict__ 
                                           const int* __restrict__ level_list, const int* __restrict__ super_ptr,
                                           const int64_t* __restrict__ fr_ptr, const int* __restrict__ qcount,
                                           const int64_t* __restrict__ boff, const float* __restrict__ src,
-                                          int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
+                                          int from_ftop, int64_t ldx, unsigned char* pk, float* X,
+                                          const int* __restrict__ gsplit_p) {
   using TR = TcTraits<MODE>;
   __shared__ float sy[KT][TM + 1];
   const int u1 = plan[pb];
+  const int gsplit = from_ftop ? *gsplit_p : 1;   // read once: the unit loop has no other dependent load on it
   for (int u = plan[pa] + vb.bx; u < u1; u += vb.gx) {   // block-uniform
     const int pos = find_unit(plan, pa, pb, u);
     const int s = level_list[pos];
@@ -204,8 +206,10 @@ __device__ __forceinline__ void d_pack_tc(const VB& vb, const int* __restrict__ 
     const int local = u - plan[pos];
     const int I = local / nk, kt = local % nk;
     const float* Ys = src + (from_ftop ? (int64_t)super_ptr[s] : fr_ptr[s]) * ldx;
-    // F_top: the product's rows < w (X_s) are accumulated over K parts
-    float* Xz = from_ftop ? X + fr_ptr[s] * ldx : nullptr;
+    // F_top of a level whose units are split over K (gsplit_p: the level's
+    // split factor): the K parts add the product's rows < w (X_s) into X, so
+    // those rows start at zero; unsplit units store them
+    float* Xz = from_ftop && tc_parts(gsplit, nk) > 1 ? X + fr_ptr[s] * ldx : nullptr;
     for (int e = threadIdx.x; e < KT * TM; e += blockDim.x) {
       const int k = e / TM, r = e % TM;
       const int row = kt * KT + k, col = I * TM + r;
@@ -225,9 +229,10 @@ __global__ void __launch_bounds__(256)
     k_pack_tc(const int* __restrict__ plan, int pa, int pb, const int* __restrict__ level_list,
               const int* __restrict__ super_ptr, const int64_t* __restrict__ fr_ptr,
               const int* __restrict__ qcount, const int64_t* __restrict__ boff, const float* __restrict__ src,
-              int from_ftop, int64_t ldx, unsigned char* pk, float* X) {
+              int from_ftop, int64_t ldx, unsigned char* pk, float* X, const int* __restrict__ gsplit_p) {
   pdl_entry();
-  d_pack_tc<MODE>(own_block(), plan, pa, pb, level_list, super_ptr, fr_ptr, qcount, boff, src, from_ftop, ldx, pk, X);
+  d_pack_tc<MODE>(own_block(), plan, pa, pb, level_list, super_ptr, fr_ptr, qcount, boff, src, from_ftop, ldx, pk, X,
+                  gsplit_p);
 }
 
 template <int MODE>
@@ -625,12 +630,29 @@ __device__ __forceinline__ void d_contract_tc(const VB& vb, const int* __restric
       const int li = I * TM + 32 * warp + lane;   // tile row owned by this thread
       if (li < ncol) {
         const int64_t gi = 3 * (int64_t)qidx[(size_t)s * m + li / 3] + li % 3;
+        float* Wrow = WH + gi * ldw;
+        // four columns at a time: one 16-byte atomic add when they are four
+        // consecutive, aligned entries of W_H's row (consecutive contacts, e.g.
+        // a front every contact reaches), else one add per entry
 #pragma unroll
-        for (int j = 0; j < TM; ++j) {
-          const int lj = J * TM + j;
-          if (lj >= ncol || li > lj) continue;
-          const int64_t gj = 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3;
-          atomicAdd(&WH[gi * ldw + gj], acc[j]);
+        for (int j0 = 0; j0 < TM; j0 += 4) {
+          int64_t g[4];
+          bool ok[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int lj = J * TM + j0 + k;
+            ok[k] = lj < ncol && li <= lj;
+            g[k] = ok[k] ? 3 * (int64_t)qidx[(size_t)s * m + lj / 3] + lj % 3 : 0;
+          }
+          const bool vec = ok[0] && ok[1] && ok[2] && ok[3] && g[1] == g[0] + 1 && g[2] == g[0] + 2 &&
+                           g[3] == g[0] + 3 && (((uintptr_t)(Wrow + g[0])) & 15) == 0;
+          if (vec) {
+            atomicAdd((float4*)(Wrow + g[0]), make_float4(acc[j0], acc[j0 + 1], acc[j0 + 2], acc[j0 + 3]));
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              if (ok[k]) atomicAdd(Wrow + g[k], acc[j0 + k]);
+          }
         }
       }
     }
@@ -872,7 +894,7 @@ int contract_tc_T(Scene* s) {
   PDL("k_pack_tc", pack_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_PACK * (ns + 1), 0, ns, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->X.p, 0,
-      s->ldx, (unsigned char*)s->Ypk.p, (float*)nullptr);
+      s->ldx, (unsigned char*)s->Ypk.p, (float*)nullptr, (const int*)nullptr);
   const int64_t ub_tc = (int64_t)ns * tmax * (tmax + 1) / 2 * TC_MAX_SPLIT;
   const int nlev = (int)s->levels.size();
   PDL("k_contract_tc", contract_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_tc, (int64_t)occ * nsm)), TC_THREADS, smem, s->ctx->stream,
@@ -919,7 +941,8 @@ int launch_front_gemm_tc(Scene* s, int level) {
   PDL("k_pack_tc", pack_tc_body<MODE>, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub_pack, 4 * nsm)), 256, 0, s->ctx->stream,
       plan + PLAN_FPACK * (ns + 1), pa, pb, (const int*)s->level_list.p, (const int*)s->super_ptr.p,
       (const int64_t*)s->fr_ptr.p, (const int*)s->qcount.p, (const int64_t*)s->tc_boff.p, (const float*)s->Ftop.p, 1,
-      s->ldx, (unsigned char*)s->Ypk.p, (float*)s->X.p);
+      s->ldx, (unsigned char*)s->Ypk.p, (float*)s->X.p,
+      (const int*)plan + PLAN_LISTS * (ns + 1) + 2 + (int)s->levels.size() + level);
   const int64_t ub = (int64_t)lv.count * ((lv.wmax + lv.rmax + TM - 1) / TM) * tmax * TC_MAX_SPLIT;
   const int nlev = (int)s->levels.size();
   PDL("k_front_gemm_tc", front_gemm_tc_body, (unsigned)std::max<int64_t>(1, std::min<int64_t>(ub, nsm)), TC_THREADS, smem, s->ctx->stream,
