@@ -1,16 +1,19 @@
 // Batched time steps: many scenes stepped by one captured CUDA graph in which
-// every kernel launch covers all of them (Alg. 3 per scene; the scenes are
+// every kernel launch covers many of them (Alg. 3 per scene; the scenes are
 // independent problems).
 //
 // A batch records the device-resident step of each of its scenes (the launch
 // sequence icr_step would make: kernels with their grids and arguments, plus
-// device copies and fills) instead of launching it.  The per-scene sequences
-// are then merged into one: a launch of the merged sequence runs one kernel
-// body for every scene whose next recorded launch is that kernel, in one flat
-// grid (k_batch: each scene's blocks see the block index of the scene's own
-// launch), so each scene runs exactly its own step and the kernels of
-// different scenes share launches, waves and SMs.  Each scene's launches stay
-// in its own order; scenes never wait on one another inside a launch.
+// device copies and fills) instead of launching it.  The scenes are split into
+// cost-balanced groups; within a group the per-scene sequences are merged into
+// one, and a launch of the merged sequence runs one kernel body for every
+// scene whose recorded launch it takes over (k_batch): either one flat grid in
+// which each scene's blocks see the block index of the scene's own launch, or,
+// for bodies whose work units any grid covers, one persistent grid that serves
+// every scene in turn.  So each scene runs exactly its own step, and the
+// kernels of different scenes share launches, waves and SMs.  Each scene's
+// launches stay in its own order; scenes never wait on one another inside a
+// launch.  The groups run as parallel branches of the graph.
 //
 // The merge (merge_sequences) builds a common supersequence of the scenes'
 // sequences by pairwise longest-common-subsequence alignment.  The merged
@@ -273,6 +276,24 @@ void free_batch(icr_batch* b) {
   delete b;
 }
 
+// the recorded launches hold the scenes' device addresses and launch shapes:
+// ICR_ESTATE once a scene was evicted, reallocated a buffer, or changed its
+// contact count, obstacle kind or parameters
+int check_batch(const icr_batch* b, const char* where) {
+  for (size_t i = 0; i < b->scenes.size(); ++i) {
+    const Scene* s = b->scenes[i];
+    const icr_batch::Snap& sn = b->snaps[i];
+    if (s->evicted || s->alloc_epoch != sn.epoch || s->m != sn.m || s->obst_kind != sn.obst ||
+        std::memcmp(&s->params, &sn.params, sizeof(icr_params)) != 0) {
+      set_error("%s: scene %zu changed since the batch was created (evicted, buffers, contact count, obstacle or "
+                "parameters); create the batch again",
+                where, i);
+      return ICR_ESTATE;
+    }
+  }
+  return ICR_OK;
+}
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 int build_batch(icr_batch* b) {
@@ -525,30 +546,6 @@ int icr_batch_create(icr_batch** out, icr_scene* const* scenes, int32_t n_scenes
   *out = b;
   return ICR_OK;
 }
-
-}  // extern "C"
-
-namespace {
-// the recorded launches hold the scenes' device addresses and launch shapes:
-// ICR_ESTATE once a scene was evicted, reallocated a buffer, or changed its
-// contact count, obstacle kind or parameters
-int check_batch(const icr_batch* b, const char* where) {
-  for (size_t i = 0; i < b->scenes.size(); ++i) {
-    const Scene* s = b->scenes[i];
-    const icr_batch::Snap& sn = b->snaps[i];
-    if (s->evicted || s->alloc_epoch != sn.epoch || s->m != sn.m || s->obst_kind != sn.obst ||
-        std::memcmp(&s->params, &sn.params, sizeof(icr_params)) != 0) {
-      set_error("%s: scene %zu changed since the batch was created (evicted, buffers, contact count, obstacle or "
-                "parameters); create the batch again",
-                where, i);
-      return ICR_ESTATE;
-    }
-  }
-  return ICR_OK;
-}
-}  // namespace
-
-extern "C" {
 
 int icr_batch_launch(icr_batch* b) {
   if (!b) {
