@@ -395,10 +395,13 @@ int icr_serve_ex(icr_scene* const* scenes, int32_t n_scenes, const int32_t* req_
  * of every scene (after icr_autotune for scenes not yet tuned) and merges the
  * sequences into one common supersequence (icr_batch_merge_plan): a merged
  * launch runs one kernel for the scenes whose launch of that kernel it takes
- * over, in one grid in which each scene's blocks see the block
- * indices of that scene's own launch, so a step of N scenes makes about as
- * many launches as the longest single-scene step instead of N times as many.
- * Device copies and fills of the step are merged the same way.  All scenes
+ * over, either in one grid in which each scene's blocks see the block indices
+ * of that scene's own launch, or, for kernels whose work units any grid
+ * covers (assembly, CUDA-core forward-solve product, operand packing, CUDA-core
+ * contraction), in one persistent grid that serves every scene's units in
+ * turn.  A step of N scenes in one group makes about as many launches as the
+ * longest single-scene step instead of N times as many.  Device copies and
+ * fills of the step are merged the same way.  All scenes
  * must share one context, whose stream must not be the legacy default stream
  * (ICR_EINVAL), and be resident with a system, a mapping and an obstacle
  * (ICR_ESTATE); a scene may appear once.  Creation runs one batched step
