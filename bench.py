@@ -82,8 +82,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["icr", "reference"], default="icr")
-    ap.add_argument("--workload", choices=["tissue_c3", "batch_c2", "precision_c3", "serve_c4"],
-                    default="tissue_c3", help="tissue_c3 is the bench line; the others print their own line")
+    ap.add_argument("--workload", choices=["tissue_c3", "batch_c2", "precision_c3", "serve_c4", "liver_c1", "press_c1"],
+                    default="tissue_c3", help="tissue_c3 is the bench line; the others print their own line "
+                                              "(liver_c1 and press_c1: the bench line's measurements on that scene)")
     ap.add_argument("--scenes", type=int, default=64, help="batch_c2: number of scenes")
     ap.add_argument("--batch-groups", default="1,2,4,8,16",
                     help="batch_c2: group counts to try (the fastest of a short timing is used)")
@@ -596,6 +597,8 @@ def run_icr(args):
     extras = {}
     if rank == 0 and not args.no_extras:
         for name in EXTRA_WORKLOADS:
+            if name == WORKLOAD:
+                continue
             s2 = scenegen.NAMED[name]()
             sc2, r = run_workload(torch, icr, driver, s2, name, ctx, stream, flush, args)
             ro = rooflines(s2, name, r["kernels"], r["build_info"], r["phase_ms"], r["pgs_stats"], peaks, sm_count)
@@ -1004,7 +1007,10 @@ def run_precision(args):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    if args.workload in ("tissue_c3", "liver_c1", "press_c1"):
+        WORKLOAD = args.workload
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch_c2":
