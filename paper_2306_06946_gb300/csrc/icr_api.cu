@@ -229,7 +229,7 @@ int check_step_graph(Scene* s, const char* where) {
     return ICR_ESTATE;
   }
   if (s->graph_epoch != s->alloc_epoch || s->graph_m != s->m || s->graph_obst != s->obst_kind ||
-      std::memcmp(&s->graph_params, &s->params, sizeof(icr_params)) != 0) {
+      !same_params(s->graph_params, s->params)) {
     set_error("%s: the captured step is stale (buffers, contact count, obstacle or parameters changed); "
               "capture it again", where);
     return ICR_ESTATE;

@@ -284,7 +284,7 @@ int check_batch(const icr_batch* b, const char* where) {
     const Scene* s = b->scenes[i];
     const icr_batch::Snap& sn = b->snaps[i];
     if (s->evicted || s->alloc_epoch != sn.epoch || s->m != sn.m || s->obst_kind != sn.obst ||
-        std::memcmp(&s->params, &sn.params, sizeof(icr_params)) != 0) {
+        !same_params(s->params, sn.params)) {
       set_error("%s: scene %zu changed since the batch was created (evicted, buffers, contact count, obstacle or "
                 "parameters); create the batch again",
                 where, i);

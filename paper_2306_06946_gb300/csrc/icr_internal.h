@@ -114,6 +114,14 @@ struct Profiler {
 
 struct BatchRec;
 
+// parameters compared field by field: the struct has padding, whose bytes a
+// copy need not keep
+static_assert(sizeof(icr_params) == 40, "a new icr_params field must be compared in same_params");
+inline bool same_params(const icr_params& a, const icr_params& b) {
+  return a.precision == b.precision && a.n_sweeps == b.n_sweeps && a.tol == b.tol && a.contraction == b.contraction &&
+         a.warm_start == b.warm_start && a.w_update == b.w_update && a.newton_tol == b.newton_tol;
+}
+
 struct Scene {
   Ctx* ctx = nullptr;
   Profiler* prof = nullptr;   // per-launch timing while profiling
