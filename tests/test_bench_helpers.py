@@ -3,7 +3,9 @@
 achieved = algorithmic work per launch / the launch's measured time; frac =
 achieved / peak, the peak from the measured file (3xTF32: the TF32 rate, the
 measured BF16 rate times the nominal TF32/BF16 ratio, over three products);
-a profiled DRAM traffic counts only while the kernel's source is unchanged."""
+a profiled DRAM traffic counts only while the kernel's source is unchanged.
+The reference arm (the FP64 oracle on the host cores) prints its own line on
+rank 0 only."""
 import os
 import types
 
@@ -76,3 +78,30 @@ def test_profiled_traffic_follows_the_source_hash():
         assert got is None
     assert bench.profiled_traffic("k_contract_tc", "no_such_workload") is None
     assert bench.profiled_traffic("k_unknown", "tissue_c3") is None
+
+
+def test_reference_arm_prints_its_line(monkeypatch, capsys):
+    # the oracle arm on the 9k-DOF liver scene: one JSON line with the arm's
+    # keys, copies declared as none, and the host cores the solves kept busy
+    import json
+    monkeypatch.setattr(bench, "WORKLOAD", "liver_c1")
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    bench.run_reference(types.SimpleNamespace(steps=3, warmup=1, gpus=1))
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 3 and line["warmup"] == 1 and line["n_gpus"] == 1
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["ms_per_step"] == pytest.approx(1e3 / line["value"])
+    assert line["config"]["contacts"] == 300 and line["config"]["workload"].startswith("liver_c1")
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == line["value"] and 1 <= cb["cores"] <= (os.cpu_count() or 1)
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["gpu_launches"] == 0
+
+
+def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.run_reference(types.SimpleNamespace(steps=3, warmup=1, gpus=2))
+    assert capsys.readouterr().out == ""
